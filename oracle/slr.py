@@ -1,0 +1,110 @@
+"""Square-root statistical linear regression (Sec. 4).  Oracle: test
+infrastructure only.
+
+Cubature rule (Sec. 4.3 cites the cubature Kalman filter without printing the
+rule; reading): the third-degree spherical-radial rule with 2 n_x points
+X_i = m +- sqrt(n_x) N e_i and equal weights w^m = w^c = 1/(2 n_x).
+
+The transition noise is additive, so the conditional square root
+S_x[x_k | x_{k-1}](X_i) is the constant S_Q for every point.
+
+Bearings are angles (model.branch): every transformed point and the
+measurement are taken on the branch nearest h(m); the 2 pi multiple that
+this moves y by is added to d, so that y - H x - d uses the wrapped residual.
+"""
+import numpy as np
+
+from .linalg import tria, downdate, solve_lower, solve_upper
+
+
+def cubature_points(m, N):
+    """Sigma points and weights of the third-degree spherical-radial rule."""
+    nx = m.shape[0]
+    s = np.sqrt(nx)
+    X = [m + s * N[:, i] for i in range(nx)] + [m - s * N[:, i] for i in range(nx)]
+    w = np.full(2 * nx, 1.0 / (2 * nx))
+    return np.array(X), w
+
+
+def _gslr_sigma(m, N, Zs, w, S_cond):
+    """Sec. 4.3: z_bar (eq. z-bar), the regression matrix
+    sum_i w_i (Z_i - z_bar)(X_i - m)^T (N N^T)^{-1}, the offset
+    z_bar - G m, and the noise factor
+    DownDate(Tria(sqrt(w_1) S_1, ..., sqrt(w_s) S_s, Z), G N)
+    (eqs. lambda-prime and sqr-lambda-sigma-point)."""
+    X, _ = cubature_points(m, N)
+    zbar = np.sum(w[:, None] * Zs, axis=0)
+    Cross = sum(w[i] * np.outer(Zs[i] - zbar, X[i] - m) for i in range(len(w)))
+    # G = Cross (N N^T)^{-1} = ((N N^T)^{-1} Cross^T)^T via two triangular solves
+    G = solve_upper(N.T, solve_lower(N, Cross.T)).T
+    off = zbar - G @ m
+    Zdev = np.array([np.sqrt(w[i]) * (Zs[i] - zbar) for i in range(len(w))]).T
+    blocks = [np.sqrt(w[i]) * S_cond for i in range(len(w))] + [Zdev]
+    S_prime = tria(np.hstack(blocks))
+    S = downdate(S_prime, G @ N)
+    return G, off, S
+
+
+def residual_noise_factor(m, N, Zs, w, S_cond, G):
+    """Cross-check of the DownDate result: Tria of
+    [sqrt(w_i) S_i, sqrt(w_i) (Z_i - z_bar - G (X_i - m))]_i has the same
+    product S S^T, because sum_i w_i (X_i - m)(X_i - m)^T = N N^T for this
+    rule and G is the regression matrix."""
+    X, _ = cubature_points(m, N)
+    zbar = np.sum(w[:, None] * Zs, axis=0)
+    cols = [np.sqrt(w[i]) * S_cond for i in range(len(w))]
+    cols += [np.sqrt(w[i]) * (Zs[i] - zbar - G @ (X[i] - m))[:, None]
+             for i in range(len(w))]
+    return tria(np.hstack(cols))
+
+
+def transition_cubature(model, m, N):
+    """(F_{k-1}, c_{k-1}, S_Lambda_{k-1}) from (m^s_{k-1}, N^s_{k-1})."""
+    X, w = cubature_points(m, N)
+    Zs = np.array([model.f(x) for x in X])
+    return _gslr_sigma(m, N, Zs, w, model.SQ())
+
+
+def observation_cubature(model, m, N, y):
+    """(H_k, d_k, S_Omega_k) from (m^s_k, N^s_k); bearings on the branch
+    nearest h(m), d absorbing the 2 pi shift of y."""
+    X, w = cubature_points(m, N)
+    ref = model.h(m)
+    Zs = np.array([model.branch(model.h(x), ref) for x in X])
+    H, d, S = _gslr_sigma(m, N, Zs, w, model.SR())
+    d = d + (y - model.branch(y, ref))
+    return H, d, S
+
+
+def transition_taylor(model, m):
+    """Sec. 4.2: F = grad f(m^s_{k-1}), c = f(m) - F m, S_Lambda = S_Q."""
+    F = model.jac_f(m)
+    return F, model.f(m) - F @ m, model.SQ()
+
+
+def observation_taylor(model, m, y):
+    """Sec. 4.2: H = grad h(m^s_k), d = h(m) - H m (+ branch shift of y),
+    S_Omega = S_R."""
+    H = model.jac_h(m)
+    ref = model.h(m)
+    d = ref - H @ m + (y - model.branch(y, ref))
+    return H, d, model.SR()
+
+
+def linearize(model, ms, Ns, y, method):
+    """Gamma^sqrt (eq. Gamma-s) for all steps: transition t from
+    (ms[t], Ns[t]), observation of x_{t+1} from (ms[t+1], Ns[t+1])."""
+    n = y.shape[0]
+    nx, ny = model.nx, model.ny
+    F = np.zeros((n, nx, nx)); c = np.zeros((n, nx)); SQ = np.zeros((n, nx, nx))
+    H = np.zeros((n, ny, nx)); d = np.zeros((n, ny)); SR = np.zeros((n, ny, ny))
+    for t in range(n):
+        if method == "cubature":
+            F[t], c[t], SQ[t] = transition_cubature(model, ms[t], Ns[t])
+            H[t], d[t], SR[t] = observation_cubature(model, ms[t + 1], Ns[t + 1], y[t])
+        elif method == "extended":
+            F[t], c[t], SQ[t] = transition_taylor(model, ms[t])
+            H[t], d[t], SR[t] = observation_taylor(model, ms[t + 1], y[t])
+        else:
+            raise ValueError(method)
+    return F, c, SQ, H, d, SR

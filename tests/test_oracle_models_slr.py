@@ -1,0 +1,162 @@
+"""Pins of the CT model (Jacobians vs central differences, series vs
+high-precision closed forms, noise factor vs Cholesky) and of the SLR
+(exact on linear functions; cubature exact for quadratics; DownDate form
+equal to the residual form; bearing branches)."""
+import mpmath
+import numpy as np
+import pytest
+
+from oracle import models, slr
+from oracle.linalg import tria
+
+THETA = np.log([0.05, 0.01, 0.1])
+
+
+def _fd_jac(fun, x, h=1e-6):
+    J = np.zeros((len(fun(x)), len(x)))
+    for i in range(len(x)):
+        e = np.zeros_like(x); e[i] = h
+        J[:, i] = (fun(x + e) - fun(x - e)) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("w", [0.0, 0.05, -0.09, 0.5, 5.0, 12.0, -20.0])
+@pytest.mark.parametrize("dt", [0.01, 0.3])
+def test_ct_jacobian_matches_central_differences(w, dt):
+    m = models.CTBearings(THETA, dt=dt)
+    x = np.array([0.3, -1.2, 1.1, -0.4, w])
+    np.testing.assert_allclose(m.jac_f(x), _fd_jac(m.f, x), atol=1e-8)
+    np.testing.assert_allclose(m.jac_h(x), _fd_jac(m.h, x), atol=1e-8)
+
+
+@pytest.mark.parametrize("a", [1e-5, 9.99e-4, 1.001e-3, 0.02, 0.0999, 0.1001, 0.7])
+def test_turn_coefficients_match_high_precision(a):
+    mpmath.mp.dps = 40
+    dt = 0.01
+    w = a / dt
+    S, C = models._turn_coeffs(w, dt)
+    dS, dC = models._turn_coeff_derivs(w, dt)
+    A = mpmath.mpf(a)
+    S_ref = dt * mpmath.sin(A) / A
+    C_ref = dt * (1 - mpmath.cos(A)) / A
+    dS_ref = dt * dt * (A * mpmath.cos(A) - mpmath.sin(A)) / A ** 2
+    dC_ref = dt * dt * (A * mpmath.sin(A) - (1 - mpmath.cos(A))) / A ** 2
+    assert abs(S - float(S_ref)) <= 1e-15 * abs(float(S_ref))
+    assert abs(C - float(C_ref)) <= 1e-13 * abs(float(C_ref))
+    assert abs(dS - float(dS_ref)) <= 1e-12 * abs(float(dS_ref))
+    assert abs(dC - float(dC_ref)) <= 1e-12 * abs(float(dC_ref))
+
+
+def test_ct_constant_velocity_limit_and_speed():
+    m = models.CTBearings(THETA, dt=0.01)
+    x = np.array([1.0, 2.0, 0.5, -0.7, 0.0])
+    np.testing.assert_allclose(m.f(x)[:2], x[:2] + 0.01 * x[2:4], atol=1e-16)
+    x[4] = 3.0
+    fx = m.f(x)
+    assert abs(np.hypot(*fx[2:4]) - np.hypot(*x[2:4])) < 1e-15
+
+
+def test_ct_noise_factor_is_cholesky_of_Q():
+    m = models.CTBearings(THETA, dt=0.01)
+    np.testing.assert_allclose(m.SQ() @ m.SQ().T, m.Q(), rtol=1e-13, atol=1e-20)
+    np.testing.assert_allclose(m.SQ(), np.linalg.cholesky(m.Q()), rtol=1e-9, atol=1e-15)
+
+
+class _Linear:
+    nx, ny = 3, 2
+
+    def __init__(self, seed=0):
+        rng = np.random.default_rng(seed)
+        self.A = rng.standard_normal((3, 3))
+        self.u = rng.standard_normal(3)
+        self.Hm = rng.standard_normal((2, 3))
+        self.dv = rng.standard_normal(2)
+        self.S = np.tril(rng.standard_normal((3, 3))) + 2 * np.eye(3)
+        self.R = np.tril(rng.standard_normal((2, 2))) + 2 * np.eye(2)
+
+    def f(self, x): return self.A @ x + self.u
+    def jac_f(self, x): return self.A
+    def SQ(self): return self.S
+    def h(self, x): return self.Hm @ x + self.dv
+    def jac_h(self, x): return self.Hm
+    def SR(self): return self.R
+    def branch(self, z, ref): return z
+
+
+def test_slr_exact_on_linear_functions():
+    lm = _Linear()
+    rng = np.random.default_rng(1)
+    m = rng.standard_normal(3)
+    N = np.tril(rng.standard_normal((3, 3))) + 1.5 * np.eye(3)
+    for F, c, S in (slr.transition_cubature(lm, m, N), slr.transition_taylor(lm, m)):
+        np.testing.assert_allclose(F, lm.A, atol=1e-12)
+        np.testing.assert_allclose(c, lm.u, atol=1e-12)
+        np.testing.assert_allclose(S @ S.T, lm.S @ lm.S.T, atol=1e-12)
+    y = rng.standard_normal(2)
+    for H, d, S in (slr.observation_cubature(lm, m, N, y), slr.observation_taylor(lm, m, y)):
+        np.testing.assert_allclose(H, lm.Hm, atol=1e-12)
+        np.testing.assert_allclose(d, lm.dv, atol=1e-12)
+        np.testing.assert_allclose(S @ S.T, lm.R @ lm.R.T, atol=1e-12)
+
+
+class _Quadratic(_Linear):
+    def __init__(self):
+        super().__init__(3)
+        rng = np.random.default_rng(4)
+        B = rng.standard_normal((3, 3, 3))
+        self.B = B + np.transpose(B, (0, 2, 1))
+
+    def f(self, x): return np.einsum("ijk,j,k->i", self.B, x, x)
+
+
+def test_cubature_exact_for_quadratics():
+    """E[x^T B x] = tr(B P) + m^T B m and Cov(x^T B x, x) = 2 P B m for
+    Gaussian x; the degree-3 rule reproduces both."""
+    q = _Quadratic()
+    rng = np.random.default_rng(2)
+    m = rng.standard_normal(3)
+    N = np.tril(rng.standard_normal((3, 3))) + 1.5 * np.eye(3)
+    Pm = N @ N.T
+    F, c, _ = slr.transition_cubature(q, m, N)
+    mean = np.array([np.trace(q.B[i] @ Pm) + m @ q.B[i] @ m for i in range(3)])
+    Fref = np.array([2 * q.B[i] @ m for i in range(3)])      # Cov(f_i, x) P^{-1}
+    np.testing.assert_allclose(F, Fref, atol=1e-11)
+    np.testing.assert_allclose(c + F @ m, mean, atol=1e-11)
+
+
+def test_downdate_form_equals_residual_form():
+    ct = models.CTBearings(THETA, dt=0.01)
+    m = np.array([0.4, -0.8, 1.0, 0.5, 2.0])
+    N = np.diag([0.1, 0.12, 0.2, 0.15, 0.5])
+    N[3, 1] = 0.03; N[4, 2] = -0.1
+    X, w = slr.cubature_points(m, N)
+    Zs = np.array([ct.f(x) for x in X])
+    F, c, S = slr.transition_cubature(ct, m, N)
+    S2 = slr.residual_noise_factor(m, N, Zs, w, ct.SQ(), F)
+    np.testing.assert_allclose(S @ S.T, S2 @ S2.T, rtol=1e-9, atol=1e-15)
+    Xs = np.array([ct.branch(ct.h(x), ct.h(m)) for x in X])
+    H, d, So = slr.observation_cubature(ct, m, N, ct.h(m))
+    So2 = slr.residual_noise_factor(m, N, Xs, w, ct.SR(), H)
+    np.testing.assert_allclose(So @ So.T, So2 @ So2.T, rtol=1e-9, atol=1e-15)
+
+
+def test_cubature_tends_to_taylor_for_small_covariance():
+    ct = models.CTBearings(THETA, dt=0.01)
+    m = np.array([0.4, -0.8, 1.0, 0.5, 2.0])
+    N = 1e-5 * np.eye(5)
+    F, c, _ = slr.transition_cubature(ct, m, N)
+    np.testing.assert_allclose(F, ct.jac_f(m), atol=1e-8)
+    H, d, _ = slr.observation_cubature(ct, m, N, ct.h(m))
+    np.testing.assert_allclose(H, ct.jac_h(m), atol=1e-6)
+
+
+def test_bearing_branch_across_the_cut():
+    """Target left of sensor 1 at its height: bearings straddle +-pi."""
+    ct = models.CTBearings(THETA, dt=0.01)
+    m = np.array([-3.0, 0.5 + 1e-3, 0.0, 0.0, 0.0])
+    N = 0.05 * np.eye(5)
+    y = np.array([-np.pi + 0.01, ct.h(m)[1]])          # measured across the cut
+    for H, d, _ in (slr.observation_cubature(ct, m, N, y), slr.observation_taylor(ct, m, y)):
+        r = y - H @ m - d
+        np.testing.assert_allclose(r, models.wrap_angle(y - ct.h(m)), atol=5e-3)
+        assert np.all(np.abs(r) < 0.1)
