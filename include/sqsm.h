@@ -1,0 +1,192 @@
+/*
+ * sqsm.h -- C ABI of the GB300 parallel square-root smoothers.
+ *
+ * Implements the data-parallel hot path of "Parallel square-root statistical
+ * linear regression for inference in nonlinear state space models"
+ * (Yaghoobi, Corenflos, Hassan, Saerkkae; arXiv 2207.00426):
+ *   - the square-root parallel Kalman filter (Sec. 3.1, Lemmas 1-2,
+ *     Tables 1-3, Alg. 1) and RTS smoother (Sec. 3.2, Lemmas 3-4,
+ *     Tables 4-5, Alg. 2) as associative scans whose operator uses Tria;
+ *   - Taylor (Sec. 4.2) and cubature sigma-point (Sec. 4.3) statistical
+ *     linear regression inside iterated posterior linearisation (Alg. 3);
+ *   - the pseudo log-likelihood (Sec. 5.1) and its gradient through the
+ *     fixed point of Alg. 3 (Sec. 5.2, eq. implicity_function_theorem,
+ *     Alg. 4) by a reverse-mode adjoint.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - All array arguments are DEVICE pointers unless stated otherwise, in
+ *   row-major order; matrices of one time step are contiguous.
+ * - dtype selects the element type of every floating-point array argument:
+ *   SQSM_F32 (float) or SQSM_F64 (double).  Log-likelihoods, gradients and
+ *   model parameters are always double.
+ * - "Lower factor" arguments are full nx x nx (or ny x ny) matrices whose
+ *   strictly upper part is ignored on input and written as zero on output.
+ * - Time indexing follows eq. linear-model: for t = 0..n-1, row t of the
+ *   transition arrays holds (F_t, c_t, S_Lambda_t) of
+ *   x_{t+1} = F_t x_t + c_t + q_t, and row t of the observation arrays holds
+ *   (H_{t+1}, d_{t+1}, S_Omega_{t+1}, y_{t+1}).  State outputs have n+1 rows,
+ *   k = 0..n (row 0 is the prior).
+ * - Ownership: the caller owns every argument buffer.  The library never
+ *   frees or retains caller memory beyond the call, and never synchronises
+ *   the stream except where stated.  Work is enqueued on `stream`
+ *   (a cudaStream_t passed as void*; NULL = legacy default stream).
+ * - Errors: every call returns an sqsm_status.  Argument errors are detected
+ *   on the host before anything is enqueued.  Numerical failures detected
+ *   on the device (a non-finite output) are OR-ed into a device status word
+ *   that sqsm_get_status() reads.  sqsm_last_error() gives the text of the
+ *   last host-side error of a context.
+ * - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SQSM_H
+#define SQSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SQSM_OK = 0,
+  SQSM_ERR_INVALID_ARG = 1,      /* null pointer, bad size/stride/enum      */
+  SQSM_ERR_UNSUPPORTED = 2,      /* (nx, ny) pair not compiled in            */
+  SQSM_ERR_NOT_PD = 4,           /* device: zero pivot in a triangular solve */
+  SQSM_ERR_NONFINITE = 8,        /* device: NaN/Inf in an output             */
+  SQSM_ERR_CUDA = 16,            /* a CUDA runtime call failed               */
+  SQSM_ERR_NO_MEMORY = 32        /* workspace allocation failed              */
+} sqsm_status;
+
+typedef enum { SQSM_F32 = 0, SQSM_F64 = 1 } sqsm_dtype;
+
+/* Linearisation rule of the SLR step (Sec. 4.2 / 4.3). */
+typedef enum {
+  SQSM_CUBATURE = 0,   /* third-degree spherical-radial rule, 2 nx points */
+  SQSM_EXTENDED = 1    /* first-order Taylor expansion at the mean         */
+} sqsm_linearization;
+
+/* Compiled-in model families (a C ABI cannot carry device functions). */
+typedef enum {
+  SQSM_MODEL_CT_BEARINGS = 1   /* coordinated turn, two bearing sensors */
+} sqsm_model_kind;
+
+/* Coordinated-turn bearings-only model (Sec. 6.2): state
+ * (p_x, p_y, v_x, v_y, omega), nx = 5; two bearings atan2(p_y - s_y,
+ * p_x - s_x), ny = 2; additive process noise with covariance
+ * q_c [[dt^3/3 I, dt^2/2 I], [dt^2/2 I, dt I]] on (p, v) and q_omega dt on
+ * omega; bearing noise sigma^2 I.  theta = (log sigma, log q_c,
+ * log q_omega) is passed separately (host double[3]). */
+typedef struct {
+  int kind;             /* sqsm_model_kind                          */
+  double dt;            /* time step                                */
+  double sensors[4];    /* s_x^1, s_y^1, s_x^2, s_y^2               */
+} sqsm_model;
+
+/* Scan shape.  Zero fields take defaults. */
+typedef struct {
+  int leaf_chunk;       /* time steps folded by one thread at the leaf  */
+  int radix;            /* items folded by one thread at upper levels   */
+  int use_graph;        /* 1: replay the IPLS iterations as a CUDA graph */
+} sqsm_options;
+
+typedef struct sqsm_ctx sqsm_ctx;
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * The context owns scan workspaces, cached plans and captured graphs; they
+ * are freed by sqsm_destroy.  Returns SQSM_ERR_CUDA if the device cannot be
+ * used. */
+int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt);
+
+/* Free a context and everything it owns (synchronises the device first).
+ * NULL is accepted. */
+int sqsm_destroy(sqsm_ctx* ctx);
+
+/* Text of the last host-side error of ctx ("" if none).  The pointer stays
+ * valid until the next call on ctx. */
+const char* sqsm_last_error(const sqsm_ctx* ctx);
+
+/* Synchronise ctx's device, read and clear the device status word: 0 or an
+ * OR of SQSM_ERR_NONFINITE / SQSM_ERR_NOT_PD raised by kernels since the
+ * last read.  *status is host memory. */
+int sqsm_get_status(sqsm_ctx* ctx, int* status);
+
+/* Parallel square-root Kalman filter and RTS smoother on one linear-Gaussian
+ * model (Alg. 1 then Alg. 2) plus its log-likelihood (Sec. 5.1).
+ *
+ *   nx, ny   state / observation dimensions (1 <= nx, ny <= 8; the
+ *            compiled-in pairs are listed by sqsm_supported_shape).
+ *   n        number of observations (n >= 1).
+ *   F  [n][nx][nx], c [n][nx], SQ [n][nx][nx] lower: transition model;
+ *   H  [n][ny][nx], d [n][ny], SR [n][ny][ny] lower: observation model;
+ *            each with a per-step stride in elements (sF, sc, ...); a
+ *            stride of 0 means the same matrix for every step.
+ *   m0 [nx], N0 [nx][nx] lower: prior x_0 ~ N(m0, N0 N0^T).
+ *   y  [n][ny] observations.
+ *   mf, Nf   [n+1][nx], [n+1][nx][nx]: filtering means / lower factors
+ *            (either may be NULL if not wanted).
+ *   ms, Ns   [n+1][nx], [n+1][nx][nx]: smoothing means / lower factors.
+ *   loglik   device double[1]: sum_k log N(y_k; H m^-_k + d, S_k), or NULL.
+ * Arrays must not overlap outputs.  Uses ctx workspace (allocated on first
+ * use of a shape). */
+int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n,
+                      const void* F, int64_t sF, const void* c, int64_t sc,
+                      const void* SQ, int64_t sSQ, const void* H, int64_t sH,
+                      const void* d, int64_t sd, const void* SR, int64_t sSR,
+                      const void* m0, const void* N0, const void* y,
+                      void* mf, void* Nf, void* ms, void* Ns, double* loglik,
+                      void* stream);
+
+/* Iterated posterior linearisation smoother (Alg. 3) on `batch`
+ * independent sequences of a compiled-in model, in one set of launches.
+ *
+ *   model, theta   model description and host double[3] parameters.
+ *   linearization  sqsm_linearization.
+ *   M              number of iterations (>= 1).
+ *   batch          number of sequences (>= 1).
+ *   offsets        HOST int64[batch+1], offsets[0] = 0, increasing:
+ *                  sequence b has n_b = offsets[b+1]-offsets[b] >= 1
+ *                  observations, rows offsets[b].. of y.  Its states are
+ *                  rows offsets[b]+b .. offsets[b+1]+b of the state arrays
+ *                  (n_b + 1 rows).
+ *   y              [offsets[batch]][ny].
+ *   m0, N0         [batch][nx], [batch][nx][nx] lower: priors.
+ *   init_ms, init_Ns  initial nominal trajectory in state layout, or both
+ *                  NULL for the prior broadcast to every step.
+ *   ms, Ns         outputs, state layout: smoothing means / lower factors
+ *                  after iteration M.
+ *   loglik         device double[batch]: pseudo log-likelihood of each
+ *                  sequence (filter of iteration M, Sec. 5.1), or NULL.
+ * The plan and graph for an (offsets, pointers, M) combination are cached in
+ * ctx; the first call for a combination builds them. */
+int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
+                     const double* theta, int linearization, int M,
+                     int64_t batch, const int64_t* offsets, const void* y,
+                     const void* m0, const void* N0, const void* init_ms,
+                     const void* init_Ns, void* ms, void* Ns, double* loglik,
+                     void* stream);
+
+/* Statistical linear regression of a compiled-in model about a nominal
+ * trajectory (one application of Sec. 4.2 / 4.3 to every step, the first
+ * half of one iteration of Alg. 3).  Same batch layout as
+ * sqsm_ipls_smooth; ms, Ns (state layout) are the nominal means / lower
+ * factors.  Writes, for every observation row t of sequence b, the
+ * linearised model of eq. Gamma-s: F[t] (nx x nx), c[t], SQ[t] (lower)
+ * about state row t + b (k - 1), and H[t] (ny x nx), d[t], SR[t] (lower)
+ * about state row t + b + 1 (k); d includes the 2 pi multiple that puts
+ * y[t] on the branch of the bearings nearest h(m).  The outputs can be
+ * passed to sqsm_lgssm_smooth with strides nx*nx, nx, nx*nx, ny*nx, ny,
+ * ny*ny. */
+int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
+                      const double* theta, int linearization, int64_t batch,
+                      const int64_t* offsets, const void* y, const void* ms,
+                      const void* Ns, void* F, void* c, void* SQ, void* H,
+                      void* d, void* SR, void* stream);
+
+/* 1 if the (nx, ny) pair is compiled into sqsm_lgssm_smooth, else 0. */
+int sqsm_supported_shape(int nx, int ny);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQSM_H */

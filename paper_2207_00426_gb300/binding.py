@@ -1,0 +1,239 @@
+"""Thin ctypes binding of include/sqsm.h.
+
+Argument marshalling only: tensors are checked for device, dtype and
+contiguity and passed as raw pointers together with the current CUDA stream.
+Every computation happens in libsqsm.so; there is no CPU fallback, and
+importing this module fails if the library has not been built.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsqsm.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_UNSUPPORTED = 2
+ERR_NOT_PD = 4
+ERR_NONFINITE = 8
+ERR_CUDA = 16
+ERR_NO_MEMORY = 32
+F32, F64 = 0, 1
+CUBATURE, EXTENDED = 0, 1
+MODEL_CT_BEARINGS = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2207_00426_gb300.build` (needs nvcc)")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("kind", _int), ("dt", ctypes.c_double), ("sensors", ctypes.c_double * 4)]
+
+
+lib.sqsm_create.argtypes = [ctypes.POINTER(_p), _int, ctypes.POINTER(Options)]
+lib.sqsm_create.restype = _int
+lib.sqsm_destroy.argtypes = [_p]
+lib.sqsm_destroy.restype = _int
+lib.sqsm_last_error.argtypes = [_p]
+lib.sqsm_last_error.restype = ctypes.c_char_p
+lib.sqsm_get_status.argtypes = [_p, ctypes.POINTER(_int)]
+lib.sqsm_get_status.restype = _int
+lib.sqsm_supported_shape.argtypes = [_int, _int]
+lib.sqsm_supported_shape.restype = _int
+lib.sqsm_lgssm_smooth.argtypes = ([_p, _int, _int, _int, _i64] + [_p, _i64] * 6
+                                  + [_p] * 3 + [_p] * 4 + [_p, _p])
+lib.sqsm_lgssm_smooth.restype = _int
+lib.sqsm_ipls_smooth.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
+                                 _int, _int, _i64, ctypes.POINTER(_i64)] + [_p] * 8 + [_p]
+lib.sqsm_ipls_smooth.restype = _int
+lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
+                                  _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
+lib.sqsm_ct_linearize.restype = _int
+
+EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
+            "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
+            "sqsm_ct_linearize"]
+
+
+class SqsmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sqsm error {code}: {msg}")
+        self.code = code
+
+
+def _dtype_code(t):
+    if t == torch.float32:
+        return F32
+    if t == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    return t.data_ptr()
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """Owns an sqsm_ctx (workspaces, plans, graphs) on one device."""
+
+    def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = _p()
+        opt = Options(leaf_chunk, radix, 1 if use_graph else 0)
+        rc = lib.sqsm_create(ctypes.byref(h), self.device, ctypes.byref(opt))
+        if rc != OK:
+            raise SqsmError(rc, "sqsm_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sqsm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != OK:
+            raise SqsmError(rc, lib.sqsm_last_error(self.h).decode())
+
+    def status(self):
+        v = _int(0)
+        self.check(lib.sqsm_get_status(self.h, ctypes.byref(v)))
+        return v.value
+
+
+def supported_shape(nx, ny):
+    return bool(lib.sqsm_supported_shape(nx, ny))
+
+
+def sqsm_lgssm_smooth(ctx, F, c, SQ, H, d, SR, m0, N0, y, mf=None, Nf=None, ms=None, Ns=None,
+                      loglik=None, strides=None):
+    """Call sqsm_lgssm_smooth.  Per-step arrays have a leading time axis of
+    length n, or none (time-invariant, stride 0).  Outputs are allocated if
+    not given; returns (mf, Nf, ms, Ns, loglik)."""
+    dt = y.dtype
+    code = _dtype_code(dt)
+    n, ny = y.shape
+    nx = m0.shape[0]
+    dev = y.device
+
+    def stride(a, per):
+        return 0 if a.dim() == per else a[0].numel()
+
+    if strides is None:
+        strides = (stride(F, 2), stride(c, 1), stride(SQ, 2), stride(H, 2), stride(d, 1), stride(SR, 2))
+    if mf is None:
+        mf = torch.empty((n + 1, nx), dtype=dt, device=dev)
+    if Nf is None:
+        Nf = torch.empty((n + 1, nx, nx), dtype=dt, device=dev)
+    if ms is None:
+        ms = torch.empty((n + 1, nx), dtype=dt, device=dev)
+    if Ns is None:
+        Ns = torch.empty((n + 1, nx, nx), dtype=dt, device=dev)
+    if loglik is None:
+        loglik = torch.empty(1, dtype=torch.float64, device=dev)
+    args = []
+    for name, a, s in zip("F c SQ H d SR".split(), (F, c, SQ, H, d, SR), strides):
+        args += [_ptr(a, dt, name), s]
+    rc = lib.sqsm_lgssm_smooth(ctx.h, code, nx, ny, n, *args, _ptr(m0, dt, "m0"), _ptr(N0, dt, "N0"),
+                               _ptr(y, dt, "y"), _ptr(mf, dt, "mf"), _ptr(Nf, dt, "Nf"),
+                               _ptr(ms, dt, "ms"), _ptr(Ns, dt, "Ns"),
+                               _ptr(loglik, torch.float64, "loglik"), _stream())
+    ctx.check(rc)
+    return mf, Nf, ms, Ns, loglik
+
+
+def _model(dt, sensors):
+    s = (ctypes.c_double * 4)(*[float(v) for v in sensors.reshape(-1)])
+    return Model(MODEL_CT_BEARINGS, float(dt), s)
+
+
+def _offsets(offsets):
+    off = [int(v) for v in offsets]
+    return (_i64 * len(off))(*off), len(off) - 1
+
+
+def sqsm_ipls_smooth(ctx, theta, y, offsets, m0, N0, M, linearization=CUBATURE, dt=0.01,
+                     sensors=None, init_ms=None, init_Ns=None, ms=None, Ns=None, loglik=None):
+    """Call sqsm_ipls_smooth for the CT bearings model.  offsets is a host
+    sequence of batch+1 ints; m0 [batch, 5], N0 [batch, 5, 5]."""
+    import numpy as np
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    if sensors is None:
+        sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    off, batch = _offsets(offsets)
+    rows = int(off[batch]) + batch
+    dev = y.device
+    if ms is None:
+        ms = torch.empty((rows, 5), dtype=dtp, device=dev)
+    if Ns is None:
+        Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
+    if loglik is None:
+        loglik = torch.empty(batch, dtype=torch.float64, device=dev)
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = _model(dt, np.asarray(sensors))
+    rc = lib.sqsm_ipls_smooth(ctx.h, code, ctypes.byref(mdl), th, int(linearization), int(M),
+                              batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
+                              _ptr(N0, dtp, "N0"), _ptr(init_ms, dtp, "init_ms"),
+                              _ptr(init_Ns, dtp, "init_Ns"), _ptr(ms, dtp, "ms"),
+                              _ptr(Ns, dtp, "Ns"), _ptr(loglik, torch.float64, "loglik"),
+                              _stream())
+    ctx.check(rc)
+    return ms, Ns, loglik
+
+
+def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt=0.01,
+                      sensors=None):
+    """Call sqsm_ct_linearize; returns (F, c, SQ, H, d, SR) with a leading
+    axis over observation rows."""
+    import numpy as np
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    if sensors is None:
+        sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    off, batch = _offsets(offsets)
+    n = int(off[batch])
+    dev = y.device
+    out = [torch.empty(s, dtype=dtp, device=dev) for s in
+           ((n, 5, 5), (n, 5), (n, 5, 5), (n, 2, 5), (n, 2), (n, 2, 2))]
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = _model(dt, np.asarray(sensors))
+    rc = lib.sqsm_ct_linearize(ctx.h, code, ctypes.byref(mdl), th, int(linearization), batch, off,
+                               _ptr(y, dtp, "y"), _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"),
+                               *[_ptr(o, dtp) for o in out], _stream())
+    ctx.check(rc)
+    return tuple(out)

@@ -1,0 +1,510 @@
+// C ABI of include/sqsm.h: argument validation, plans (per batch layout),
+// workspaces (per plan, dtype and nx) and captured graphs, all owned by the
+// context.  Host code only builds index tables and enqueues kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sqsm.h"
+#include "dispatch.h"
+
+using namespace sqsm;
+
+namespace {
+
+struct Alloc {
+  std::vector<void*> ptrs;
+  ~Alloc() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  void* get(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return p;
+  }
+};
+
+struct Workspace {
+  Alloc mem;
+  ScanBuffers filt, smth;
+  double* partial = nullptr;
+  void* mf = nullptr;        // filter outputs when the caller wants none / IPLS
+  void* Nf = nullptr;
+  void* gamma[6] = {};       // IPLS linearised model F, c, SQ, H, d, SR
+  void* params = nullptr;    // IPLS model constants
+  bool ipls_ready = false;
+};
+
+struct Plan {
+  Alloc mem;
+  int B = 0;
+  int L0 = 0, R = 0;
+  std::vector<int64_t> offsets;
+  int64_t* d_offsets = nullptr;
+  LevelSet filt, smth;
+  std::map<std::pair<int, int>, std::unique_ptr<Workspace>> ws;   // (dtype, nx)
+};
+
+struct GraphKey {
+  const Plan* plan;
+  int dtype, lin, M;
+  const void *y, *m0, *N0, *ims, *iNs, *ms, *Ns, *ll;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(plan, dtype, lin, M, y, m0, N0, ims, iNs, ms, Ns, ll) <
+           std::tie(o.plan, o.dtype, o.lin, o.M, o.y, o.m0, o.N0, o.ims, o.iNs, o.ms, o.Ns, o.ll);
+  }
+};
+
+}  // namespace
+
+struct sqsm_ctx {
+  int device = 0;
+  sqsm_options opt{};
+  std::string err;
+  int* d_status = nullptr;
+  cudaStream_t capture_stream = nullptr;   // graphs are recorded here
+  std::vector<std::unique_ptr<Plan>> plans;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int fail(sqsm_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(sqsm_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, SQSM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Levels of a segmented scan whose level-0 items are `counts[b]` per
+// sequence: chunks of L0 items at the leaf, R items above, until each
+// sequence has one item.
+bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
+  std::vector<int64_t> counts = counts0;
+  int level = 0;
+  int64_t total = 0;
+  for (int64_t v : counts) total += v;
+  L.n_items.push_back(total);
+  for (;;) {
+    const int64_t size = level == 0 ? p.L0 : p.R;
+    std::vector<int64_t> first;
+    std::vector<int32_t> count, seq;
+    std::vector<int64_t> next(counts.size());
+    int64_t item_off = 0;
+    bool all_one = true;
+    for (size_t b = 0; b < counts.size(); ++b) {
+      const int64_t nch = (counts[b] + size - 1) / size;
+      for (int64_t j = 0; j < nch; ++j) {
+        first.push_back(item_off + j * size);
+        count.push_back((int32_t)std::min<int64_t>(size, counts[b] - j * size));
+        seq.push_back((int32_t)b);
+      }
+      next[b] = nch;
+      if (nch != 1) all_one = false;
+      item_off += counts[b];
+    }
+    DevLevel d;
+    d.n_chunks = (int64_t)first.size();
+    int64_t* df = (int64_t*)p.mem.get(sizeof(int64_t) * first.size());
+    int32_t* dc = (int32_t*)p.mem.get(sizeof(int32_t) * count.size());
+    int32_t* ds = (int32_t*)p.mem.get(sizeof(int32_t) * seq.size());
+    if (!df || !dc || !ds) return false;
+    cudaMemcpy(df, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(dc, count.data(), sizeof(int32_t) * count.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(ds, seq.data(), sizeof(int32_t) * seq.size(), cudaMemcpyHostToDevice);
+    d.first = df;
+    d.count = dc;
+    d.seq = ds;
+    L.lv.push_back(d);
+    L.n_items.push_back(d.n_chunks);
+    if (level == 0) {
+      std::vector<int64_t> lco(counts.size() + 1, 0);
+      for (size_t b = 0; b < counts.size(); ++b) lco[b + 1] = lco[b] + next[b];
+      L.leaf_chunk_off = (int64_t*)p.mem.get(sizeof(int64_t) * lco.size());
+      if (!L.leaf_chunk_off) return false;
+      cudaMemcpy(L.leaf_chunk_off, lco.data(), sizeof(int64_t) * lco.size(),
+                 cudaMemcpyHostToDevice);
+    }
+    counts = next;
+    ++level;
+    if (all_one) break;
+  }
+  return true;
+}
+
+Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
+  const int L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk : 4;
+  const int R = ctx->opt.radix > 1 ? ctx->opt.radix : 4;
+  for (auto& p : ctx->plans)
+    if (p->B == batch && p->L0 == L0 && p->R == R &&
+        std::memcmp(p->offsets.data(), offsets, sizeof(int64_t) * (batch + 1)) == 0)
+      return p.get();
+  auto p = std::make_unique<Plan>();
+  p->B = (int)batch;
+  p->L0 = L0;
+  p->R = R;
+  p->offsets.assign(offsets, offsets + batch + 1);
+  p->d_offsets = (int64_t*)p->mem.get(sizeof(int64_t) * (batch + 1));
+  if (!p->d_offsets) return nullptr;
+  cudaMemcpy(p->d_offsets, offsets, sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice);
+  std::vector<int64_t> nf(batch), ns(batch);
+  for (int64_t b = 0; b < batch; ++b) {
+    nf[b] = offsets[b + 1] - offsets[b];
+    ns[b] = nf[b] + 1;
+  }
+  if (!build_levels(*p, nf, p->filt) || !build_levels(*p, ns, p->smth)) return nullptr;
+  if (ctx->plans.size() >= 8) {
+    // graphs replaying the evicted plan's buffers go with it
+    const Plan* victim = ctx->plans.front().get();
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+      if (it->first.plan == victim) {
+        cudaGraphExecDestroy(it->second);
+        it = ctx->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    cudaDeviceSynchronize();
+    ctx->plans.erase(ctx->plans.begin());
+  }
+  ctx->plans.push_back(std::move(p));
+  return ctx->plans.back().get();
+}
+
+bool alloc_scan(Alloc& mem, const LevelSet& L, ScanBuffers& W, size_t item_bytes,
+                size_t carry_bytes) {
+  const size_t Lc = L.lv.size();
+  W.items.assign(Lc + 1, nullptr);
+  W.carry.assign(Lc + 1, nullptr);
+  W.flag.assign(Lc + 1, nullptr);
+  for (size_t l = 1; l <= Lc; ++l) {
+    const int64_t n = L.n_items[l];
+    W.items[l] = mem.get(item_bytes * n);
+    W.carry[l] = mem.get(carry_bytes * n);
+    W.flag[l] = (int*)mem.get(sizeof(int) * n);
+    if (!W.items[l] || !W.carry[l] || !W.flag[l]) return false;
+    cudaMemset(W.carry[l], 0, carry_bytes * n);
+  }
+  return true;
+}
+
+Workspace* get_ws(Plan* p, int dtype, int nx) {
+  auto key = std::make_pair(dtype, nx);
+  auto it = p->ws.find(key);
+  if (it != p->ws.end()) return it->second.get();
+  auto w = std::make_unique<Workspace>();
+  const size_t es = dtype == SQSM_F64 ? 8 : 4;
+  const size_t frec = 3 * nx * nx + 2 * nx, srec = 2 * nx * nx + nx, crec = nx + nx * nx;
+  if (!alloc_scan(w->mem, p->filt, w->filt, es * frec, es * crec)) return nullptr;
+  if (!alloc_scan(w->mem, p->smth, w->smth, es * srec, es * crec)) return nullptr;
+  w->partial = (double*)w->mem.get(sizeof(double) * p->filt.lv[0].n_chunks);
+  const int64_t rows = p->smth.n_items[0];
+  w->mf = w->mem.get(es * nx * rows);
+  w->Nf = w->mem.get(es * nx * nx * rows);
+  if (!w->partial || !w->mf || !w->Nf) return nullptr;
+  Workspace* r = w.get();
+  p->ws[key] = std::move(w);
+  return r;
+}
+
+bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
+  if (w->ipls_ready) return true;
+  const size_t es = dtype == SQSM_F64 ? 8 : 4;
+  const int64_t n = p->filt.n_items[0];
+  const int nx = 5, ny = 2;
+  const size_t sizes[6] = {(size_t)nx * nx, (size_t)nx, (size_t)nx * nx,
+                           (size_t)ny * nx, (size_t)ny, (size_t)ny * ny};
+  for (int i = 0; i < 6; ++i) {
+    w->gamma[i] = w->mem.get(es * sizes[i] * n);
+    if (!w->gamma[i]) return false;
+  }
+  w->params = w->mem.get(512);
+  if (!w->params) return false;
+  w->ipls_ready = true;
+  return true;
+}
+
+DevSeqs seqs_of(const Plan* p) {
+  DevSeqs s;
+  s.B = p->B;
+  s.offsets = p->d_offsets;
+  s.leaf_chunk_off = p->filt.leaf_chunk_off;
+  return s;
+}
+
+bool valid_offsets(const int64_t* off, int64_t batch) {
+  if (!off || off[0] != 0) return false;
+  for (int64_t b = 0; b < batch; ++b)
+    if (off[b + 1] <= off[b]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
+  if (!out) return SQSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return SQSM_ERR_CUDA;
+  auto* ctx = new sqsm_ctx();
+  ctx->device = device;
+  if (opt) ctx->opt = *opt;
+  DeviceGuard g(device);
+  if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess) {
+    delete ctx;
+    return SQSM_ERR_CUDA;
+  }
+  cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return SQSM_ERR_CUDA;
+  }
+  *out = ctx;
+  return SQSM_OK;
+}
+
+int sqsm_destroy(sqsm_ctx* ctx) {
+  if (!ctx) return SQSM_OK;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    ctx->plans.clear();
+    cudaFree(ctx->d_status);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  }
+  delete ctx;
+  return SQSM_OK;
+}
+
+const char* sqsm_last_error(const sqsm_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int sqsm_get_status(sqsm_ctx* ctx, int* status) {
+  if (!ctx || !status) return SQSM_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_get_status");
+  int v = 0;
+  e = cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_get_status");
+  cudaMemset(ctx->d_status, 0, sizeof(int));
+  *status = v;
+  return SQSM_OK;
+}
+
+int sqsm_supported_shape(int nx, int ny) { return lgssm_shape_supported(nx, ny) ? 1 : 0; }
+
+int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const void* F,
+                      int64_t sF, const void* c, int64_t sc, const void* SQ, int64_t sSQ,
+                      const void* H, int64_t sH, const void* d, int64_t sd, const void* SR,
+                      int64_t sSR, const void* m0, const void* N0, const void* y, void* mf,
+                      void* Nf, void* ms, void* Ns, double* loglik, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (n < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "n must be >= 1");
+  if (nx < 1 || ny < 1 || nx > 8 || ny > 8)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "nx, ny must be in 1..8");
+  if (!lgssm_shape_supported(nx, ny))
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "(nx, ny) pair not compiled in");
+  if (!F || !c || !SQ || !H || !d || !SR || !m0 || !N0 || !y || !ms || !Ns)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or smoother output pointer");
+  if (sF < 0 || sc < 0 || sSQ < 0 || sH < 0 || sd < 0 || sSR < 0)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "negative stride");
+  DeviceGuard g(ctx->device);
+  const int64_t offsets[2] = {0, n};
+  Plan* p = get_plan(ctx, offsets, 1);
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, nx);
+  if (!w) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace allocation failed");
+  LgssmArgs a{nx, ny, F, c, SQ, H, d, SR, sF, sc, sSQ, sH, sd, sSR, m0, N0, y,
+              mf ? mf : w->mf, Nf ? Nf : w->Nf, ms, Ns};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  const DevSeqs sq = seqs_of(p);
+  int rc = dtype == SQSM_F32
+               ? lgssm_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial,
+                                   ctx->d_status, s)
+               : lgssm_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial,
+                                   ctx->d_status, s);
+  if (rc) return fail(ctx, rc, "(nx, ny) pair not compiled in");
+  if (loglik) enqueue_loglik_reduce(sq, w->partial, loglik, ctx->d_status, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_lgssm_smooth launch");
+  return SQSM_OK;
+}
+
+int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                     int linearization, int M, int64_t batch, const int64_t* offsets,
+                     const void* y, const void* m0, const void* N0, const void* init_ms,
+                     const void* init_Ns, void* ms, void* Ns, double* loglik, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
+  if (M < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "M must be >= 1");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !m0 || !N0 || !ms || !Ns)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
+  if ((init_ms == nullptr) != (init_Ns == nullptr))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  DeviceGuard g(ctx->device);
+  Plan* p = get_plan(ctx, offsets, batch);
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, 5);
+  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  IplsArgs a{};
+  a.linearization = linearization;
+  a.M = M;
+  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  a.dt = model->dt;
+  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
+  a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
+  a.ms = ms; a.Ns = Ns; a.loglik = loglik;
+  a.mf = w->mf; a.Nf = w->Nf;
+  a.F = w->gamma[0]; a.c = w->gamma[1]; a.SQ = w->gamma[2];
+  a.H = w->gamma[3]; a.d = w->gamma[4]; a.SR = w->gamma[5];
+  a.params = w->params;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
+  auto enqueue = [&](cudaStream_t st) {
+    if (dtype == SQSM_F32)
+      ipls_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
+    else
+      ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
+  };
+  if (!ctx->opt.use_graph) {
+    enqueue(s);
+  } else {
+    GraphKey key{p, dtype, linearization, M, y, m0, N0, init_ms, init_Ns, ms, Ns, loglik};
+    auto it = ctx->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != ctx->graphs.end()) {
+      exec = it->second;
+    } else {
+      // Recording executes nothing, so it happens on the context's own
+      // stream (the legacy default stream cannot be captured); the graph is
+      // then launched on the caller's stream.
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cs = ctx->capture_stream;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+      enqueue(cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      if (ctx->graphs.size() >= 16) {
+        cudaGraphExecDestroy(ctx->graphs.begin()->second);
+        ctx->graphs.erase(ctx->graphs.begin());
+      }
+      ctx->graphs[key] = exec;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth launch");
+  return SQSM_OK;
+}
+
+int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                      int linearization, int64_t batch, const int64_t* offsets, const void* y,
+                      const void* ms, const void* Ns, void* F, void* c, void* SQ, void* H,
+                      void* d, void* SR, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !ms || !Ns || !F || !c || !SQ || !H || !d || !SR)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null pointer");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  DeviceGuard g(ctx->device);
+  Plan* p = get_plan(ctx, offsets, batch);
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, 5);
+  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  IplsArgs a{};
+  a.linearization = linearization;
+  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  a.dt = model->dt;
+  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
+  a.y = y;
+  a.ms = const_cast<void*>(ms);
+  a.Ns = const_cast<void*>(Ns);
+  a.F = F; a.c = c; a.SQ = SQ; a.H = H; a.d = d; a.SR = SR;
+  a.params = w->params;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32) {
+    ipls_params_f32(a, s);
+    ct_linearize_f32(a, p->filt, sq, s);
+  } else {
+    ipls_params_f64(a, s);
+    ct_linearize_f64(a, p->filt, sq, s);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ct_linearize launch");
+  return SQSM_OK;
+}
+
+}  // extern "C"
+
+namespace sqsm {
+bool lgssm_shape_supported(int nx, int ny) {
+#define SQSM_CASE(X, Y) \
+  if (nx == X && ny == Y) return true;
+  SQSM_LGSSM_SHAPES(SQSM_CASE)
+#undef SQSM_CASE
+  return false;
+}
+}  // namespace sqsm

@@ -1,0 +1,339 @@
+// Coordinated-turn bearings-only model (Sec. 6.2) and its square-root
+// statistical linear regression (Sec. 4.2 Taylor, Sec. 4.3 cubature), one
+// thread per time step, plus the IPLS loop of Alg. 3.
+//
+// Model: x = (p_x, p_y, v_x, v_y, w), a = w dt,
+//   p' = p + [[S, -C], [C, S]] v,  v' = [[cos a, -sin a], [sin a, cos a]] v,
+//   w' = w,  S = sin(a)/w,  C = (1 - cos a)/w = 2 sin^2(a/2)/w
+//   (series S = dt(1 - a^2/6 + a^4/120), C = dt(a/2 - a^3/24 + a^5/720) for
+//   |a| < 1e-3); process noise factor in closed form; bearings
+//   atan2(p_y - s_y, p_x - s_x) with noise sigma.
+//
+// Cubature (third-degree spherical-radial rule, points m +- sqrt(nx) N e_i,
+// weights 1/(2 nx)).  Two exact rewritings of Sec. 4.3 are used:
+//  * because X_i - m = +-sqrt(nx) N e_i, the regression matrix
+//    sum_i w (Z_i - z)(X_i - m)^T (N N^T)^{-1} equals D N^{-1} with
+//    D e_i = (Z_i^+ - Z_i^-)/(2 sqrt(nx));
+//  * the noise factor DownDate(Tria([sqrt(w) S, ..., Z_x]), F N) of eqs.
+//    lambda-prime / sqr-lambda-sigma-point has the same product as
+//    Tria([S, s_1/sqrt(nx), ..., s_nx/sqrt(nx)]) with
+//    s_i = (Z_i^+ + Z_i^-)/2 - z_bar (the residual Z_i - z_bar - F(X_i - m)
+//    of both points of pair i); this needs no downdate and cannot fail.
+// Transformed points are evaluated as differences f(m + delta) - f(m) in a
+// form without cancellation against large positions, and bearings of the
+// points as the signed angle from the mean's line of sight, which also takes
+// them on the branch nearest h(m).  d absorbs the 2 pi multiple that moves y
+// onto that branch.
+#pragma once
+
+#include "engine.cuh"
+
+namespace sqsm {
+
+template <typename T>
+struct CTParams {
+  T dt;
+  T sx[2], sy[2];
+  T sigma;
+  T SQ[25];      // lower Cholesky factor of the process noise
+};
+
+SQSM_DEV void sq_sincos(float a, float* s, float* c) { sincosf(a, s, c); }
+SQSM_DEV void sq_sincos(double a, double* s, double* c) { sincos(a, s, c); }
+SQSM_DEV float sq_atan2(float y, float x) { return atan2f(y, x); }
+SQSM_DEV double sq_atan2(double y, double x) { return atan2(y, x); }
+SQSM_DEV float sq_floor(float x) { return floorf(x); }
+SQSM_DEV double sq_floor(double x) { return floor(x); }
+
+// Parameters from theta = (log sigma, log q_c, log q_w) (closed-form factor
+// of q_c [[dt^3/3, dt^2/2], [dt^2/2, dt]] per axis and q_w dt).
+template <typename T>
+__global__ void ct_params_kernel(double th0, double th1, double th2, double dt, double s1x,
+                                 double s1y, double s2x, double s2y, CTParams<T>* P) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double sigma = exp(th0), qc = exp(th1), qw = exp(th2);
+  CTParams<T> p;
+  p.dt = (T)dt;
+  p.sx[0] = (T)s1x; p.sy[0] = (T)s1y; p.sx[1] = (T)s2x; p.sy[1] = (T)s2y;
+  p.sigma = (T)sigma;
+  for (int i = 0; i < 25; ++i) p.SQ[i] = T(0);
+  const double a = sqrt(qc * dt * dt * dt / 3.0);
+  const double b = sqrt(qc) * sqrt(3.0 * dt) / 2.0;
+  const double c = sqrt(qc) * sqrt(dt) / 2.0;
+  for (int i = 0; i < 2; ++i) {
+    p.SQ[i * 5 + i] = (T)a;
+    p.SQ[(i + 2) * 5 + i] = (T)b;
+    p.SQ[(i + 2) * 5 + i + 2] = (T)c;
+  }
+  p.SQ[24] = (T)sqrt(qw * dt);
+  *P = p;
+}
+
+template <typename T>
+SQSM_DEV void turn_coeffs(T w, T dt, T& S, T& C, T& ca, T& sa) {
+  const T a = w * dt;
+  sq_sincos(a, &sa, &ca);
+  if (fabs(a) < T(1e-3)) {
+    const T a2 = a * a;
+    S = dt * (T(1) - a2 / T(6) + a2 * a2 / T(120));
+    C = dt * a * (T(0.5) - a2 / T(24) + a2 * a2 / T(720));
+  } else {
+    T sh, ch;
+    sq_sincos(T(0.5) * a, &sh, &ch);
+    S = sa / w;
+    C = T(2) * sh * sh / w;
+  }
+}
+
+// dS/dw and dC/dw: series in a for |a| < 0.1, closed forms otherwise.
+template <typename T>
+SQSM_DEV void turn_coeff_derivs(T w, T dt, T& dS, T& dC) {
+  const T a = w * dt;
+  T dsa, dca;
+  if (fabs(a) < T(0.1)) {
+    const T a2 = a * a;
+    dsa = a * (T(-1) / T(3) + a2 * (T(1) / T(30) + a2 * (T(-1) / T(840) + a2 / T(45360))));
+    dca = T(0.5) + a2 * (T(-1) / T(8) + a2 * (T(1) / T(144) + a2 * (T(-1) / T(5760) + a2 / T(403200))));
+  } else {
+    T sa, ca, sh, ch;
+    sq_sincos(a, &sa, &ca);
+    sq_sincos(T(0.5) * a, &sh, &ch);
+    dsa = (a * ca - sa) / (a * a);
+    dca = (a * sa - T(2) * sh * sh) / (a * a);
+  }
+  dS = dt * dt * dsa;
+  dC = dt * dt * dca;
+}
+
+template <typename T>
+SQSM_DEV void ct_f(const CTParams<T>& P, const T* x, T* o) {
+  T S, C, ca, sa;
+  turn_coeffs(x[4], P.dt, S, C, ca, sa);
+  o[0] = x[0] + S * x[2] - C * x[3];
+  o[1] = x[1] + C * x[2] + S * x[3];
+  o[2] = ca * x[2] - sa * x[3];
+  o[3] = sa * x[2] + ca * x[3];
+  o[4] = x[4];
+}
+
+// f(m + dl) - f(m) without forming the large position terms twice.
+template <typename T>
+SQSM_DEV void ct_f_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
+  T Sm, Cm, cam, sam, Sx, Cx, cax, sax;
+  turn_coeffs(m[4], P.dt, Sm, Cm, cam, sam);
+  turn_coeffs(m[4] + dl[4], P.dt, Sx, Cx, cax, sax);
+  const T vx = m[2] + dl[2], vy = m[3] + dl[3];
+  o[0] = dl[0] + (Sx * vx - Cx * vy) - (Sm * m[2] - Cm * m[3]);
+  o[1] = dl[1] + (Cx * vx + Sx * vy) - (Cm * m[2] + Sm * m[3]);
+  o[2] = (cax * vx - sax * vy) - (cam * m[2] - sam * m[3]);
+  o[3] = (sax * vx + cax * vy) - (sam * m[2] + cam * m[3]);
+  o[4] = dl[4];
+}
+
+template <typename T>
+SQSM_DEV void ct_jac_f(const CTParams<T>& P, const T* x, T* J) {
+  T S, C, ca, sa, dS, dC;
+  const T dt = P.dt;
+  turn_coeffs(x[4], dt, S, C, ca, sa);
+  turn_coeff_derivs(x[4], dt, dS, dC);
+  const T vx = x[2], vy = x[3];
+  const T r[25] = {T(1), T(0), S, -C, vx * dS - vy * dC,
+                   T(0), T(1), C, S, vx * dC + vy * dS,
+                   T(0), T(0), ca, -sa, -dt * sa * vx - dt * ca * vy,
+                   T(0), T(0), sa, ca, dt * ca * vx - dt * sa * vy,
+                   T(0), T(0), T(0), T(0), T(1)};
+#pragma unroll
+  for (int i = 0; i < 25; ++i) J[i] = r[i];
+}
+
+template <typename T>
+SQSM_DEV void ct_h(const CTParams<T>& P, const T* x, T* o) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) o[j] = sq_atan2(x[1] - P.sy[j], x[0] - P.sx[j]);
+}
+
+// Signed angle from the line of sight of m to that of m + dl (= the bearing
+// of m + dl on the branch nearest h(m), minus h(m)).
+template <typename T>
+SQSM_DEV void ct_h_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T ux = m[0] - P.sx[j], uy = m[1] - P.sy[j];
+    const T cross = ux * dl[1] - uy * dl[0];
+    const T dot = ux * ux + uy * uy + ux * dl[0] + uy * dl[1];
+    o[j] = sq_atan2(cross, dot);
+  }
+}
+
+template <typename T>
+SQSM_DEV void ct_jac_h(const CTParams<T>& P, const T* x, T* J) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T dx = x[0] - P.sx[j], dy = x[1] - P.sy[j];
+    const T r2 = dx * dx + dy * dy;
+    J[j * 5 + 0] = -dy / r2;
+    J[j * 5 + 1] = dx / r2;
+    J[j * 5 + 2] = T(0);
+    J[j * 5 + 3] = T(0);
+    J[j * 5 + 4] = T(0);
+  }
+}
+
+// 2 pi multiple that moves y onto the branch nearest the reference bearing.
+template <typename T>
+SQSM_DEV T branch_shift(T y, T ref) {
+  const T twopi = T(6.283185307179586476925286766559);
+  return twopi * sq_floor((y - ref) / twopi + T(0.5));
+}
+
+// Cubature regression of g(x) = ref + delta_g(m, x - m) about (m, N):
+// G = D N^{-1}, off = z_bar - G m, noise factor Tria([Sc, s_i / sqrt(5)]).
+// DG(m, dl, out) returns g(m + dl) - g(m); gm is g(m).
+template <typename T, int NO, typename DG>
+SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, const T* Sc, DG dg, T* G,
+                               T* off, T* Sout) {
+  constexpr int NX = 5;
+  const T sq = sq_sqrt(T(NX));
+  T D[NO * NX], Hs[NO * NX], dsum[NO];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) dsum[r] = T(0);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T dp[NX], dn[NX], zp[NO], zn[NO];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      dp[r] = sq * N[r * NX + i];
+      dn[r] = -dp[r];
+    }
+    dg(m, dp, zp);
+    dg(m, dn, zn);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      D[r * NX + i] = (zp[r] - zn[r]) / (T(2) * sq);
+      Hs[r * NX + i] = T(0.5) * (zp[r] + zn[r]);
+      dsum[r] += zp[r] + zn[r];
+    }
+  }
+  T dbar[NO];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) dbar[r] = dsum[r] / T(2 * NX);
+  rsolve<T, NO, NX>(D, N);           // G = D N^{-1}
+#pragma unroll
+  for (int r = 0; r < NO; ++r) {
+    T s = gm[r] + dbar[r];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s -= D[r * NX + k] * m[k];
+    off[r] = s;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) G[r * NX + k] = D[r * NX + k];
+  }
+  constexpr int C = NO + NX;
+  T B[NO * C];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) {
+#pragma unroll
+    for (int j = 0; j < NO; ++j) B[r * C + j] = Sc[r * NO + j];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) B[r * C + NO + i] = (Hs[r * NX + i] - dbar[r]) / sq;
+  }
+  tria<T, NO, C>(B);
+  take_lower<T, NO, C>(B, Sout);
+}
+
+// One thread per leaf chunk of the filter plan: for every step s of the
+// chunk, the transition is linearised at state row s + b (k - 1) and the
+// observation at row s + b + 1 (k) of the nominal trajectory (ms, Ns).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int linearization,
+              const T* __restrict__ ms, const T* __restrict__ Ns, const T* __restrict__ y,
+              T* __restrict__ F, T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H,
+              T* __restrict__ d, T* __restrict__ SRo) {
+  const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ch >= lv.n_chunks) return;
+  constexpr int NX = 5, NY = 2;
+  const CTParams<T> P = *Pp;
+  const int b = lv.seq[ch];
+  const int64_t s0 = lv.first[ch];
+  const int cnt = lv.count[ch];
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t s = s0 + j;
+    const int64_t rp = s + b, rk = s + b + 1;
+    T m[NX], N[NX * NX];
+    // transition at k - 1
+    load<T, NX>(ms + rp * NX, m);
+    load_lower<T, NX>(Ns + rp * NX * NX, N);
+    T Fm[NX * NX], cm[NX], Sl[NX * NX];
+    if (linearization == 0) {
+      T fm[NX];
+      ct_f(P, m, fm);
+      cubature_regress<T, NX>(m, N, fm, P.SQ,
+                              [&](const T* mm_, const T* dl, T* o) { ct_f_delta(P, mm_, dl, o); },
+                              Fm, cm, Sl);
+    } else {
+      T fm[NX];
+      ct_f(P, m, fm);
+      ct_jac_f(P, m, Fm);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        T sacc = fm[r];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) sacc -= Fm[r * NX + k] * m[k];
+        cm[r] = sacc;
+      }
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) Sl[i] = P.SQ[i];
+    }
+    store<T, NX * NX>(F + s * NX * NX, Fm);
+    store<T, NX>(c + s * NX, cm);
+    store_lower<T, NX>(SQo + s * NX * NX, Sl);
+    // observation at k
+    load<T, NX>(ms + rk * NX, m);
+    load_lower<T, NX>(Ns + rk * NX * NX, N);
+    T hm[NY], Hm[NY * NX], dm[NY], So[NY * NY], ys[NY];
+    load<T, NY>(y + s * NY, ys);
+    ct_h(P, m, hm);
+    if (linearization == 0) {
+      const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
+      cubature_regress<T, NY>(m, N, hm, Sr,
+                              [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
+                              Hm, dm, So);
+    } else {
+      ct_jac_h(P, m, Hm);
+#pragma unroll
+      for (int r = 0; r < NY; ++r) {
+        T sacc = hm[r];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) sacc -= Hm[r * NX + k] * m[k];
+        dm[r] = sacc;
+      }
+      So[0] = P.sigma; So[1] = T(0); So[2] = T(0); So[3] = P.sigma;
+    }
+#pragma unroll
+    for (int r = 0; r < NY; ++r) dm[r] += branch_shift(ys[r], hm[r]);
+    store<T, NY * NX>(H + s * NY * NX, Hm);
+    store<T, NY>(d + s * NY, dm);
+    store_lower<T, NY>(SRo + s * NY * NY, So);
+  }
+}
+
+// Initial nominal trajectory (Alg. 3 input): the prior of each sequence
+// broadcast to all of its state rows.  One thread per smoother leaf chunk.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+broadcast_prior_kernel(DevLevel lv, const T* __restrict__ m0, const T* __restrict__ N0,
+                       T* __restrict__ ms, T* __restrict__ Ns) {
+  const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ch >= lv.n_chunks) return;
+  const int b = lv.seq[ch];
+  T m[NX], N[NX * NX];
+  load<T, NX>(m0 + (int64_t)b * NX, m);
+  load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N);
+  for (int j = 0; j < lv.count[ch]; ++j) {
+    const int64_t e = lv.first[ch] + j;
+    store<T, NX>(ms + e * NX, m);
+    store_lower<T, NX>(Ns + e * NX * NX, N);
+  }
+}
+
+}  // namespace sqsm

@@ -1,0 +1,62 @@
+// Interface between the host API (api.cu) and the kernel translation units
+// (one per dtype and path, compiled in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace sqsm {
+
+struct LgssmArgs {
+  int nx, ny;
+  const void *F, *c, *SQ, *H, *d, *SR;
+  int64_t sF, sc, sSQ, sH, sd, sSR;
+  const void *m0, *N0, *y;
+  void *mf, *Nf, *ms, *Ns;
+};
+
+// Returns 0 if (nx, ny) is compiled in and the launches were enqueued,
+// SQSM_ERR_UNSUPPORTED otherwise.  mf/Nf must be valid device buffers
+// (the caller substitutes workspace for NULL outputs).
+int lgssm_enqueue_f32(const LgssmArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s);
+int lgssm_enqueue_f64(const LgssmArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s);
+bool lgssm_shape_supported(int nx, int ny);
+
+struct IplsArgs {
+  int linearization, M;
+  double theta[3], dt, sensors[4];
+  const void *y, *m0, *N0, *init_ms, *init_Ns;
+  void *ms, *Ns;
+  double* loglik;
+  // workspace
+  void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params;
+};
+
+// Everything of Alg. 3 after the parameter kernel; capturable.
+void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s);
+void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s);
+// The parameter kernel (theta -> model constants), launched before each
+// replay so that theta is not baked into a captured graph.
+void ipls_params_f32(const IplsArgs& a, cudaStream_t s);
+void ipls_params_f64(const IplsArgs& a, cudaStream_t s);
+
+// One SLR pass (Sec. 4.2 / 4.3) of the CT model into caller arrays.
+void ct_linearize_f32(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s);
+void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s);
+
+void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, int* status,
+                           cudaStream_t s);
+
+}  // namespace sqsm
+
+// (nx, ny) pairs compiled into the linear smoother.
+#define SQSM_LGSSM_SHAPES(X) X(1, 1) X(1, 2) X(2, 2) X(3, 2) X(2, 3) X(4, 2) X(5, 2) X(6, 3)

@@ -1,0 +1,549 @@
+// Scan elements and associative operators of the square-root parallel
+// Kalman filter and RTS smoother (Sec. 3: Lemmas 1-4, Tables 1-5), one thread
+// per element or combine, operands in registers.
+//
+// Filter element record (Pi^f_k of eq. pi-f), NX x NX matrices row-major:
+//   A | b | U (lower) | eta | Z (lower, square)    -> FREC = 3 NX^2 + 2 NX
+// Smoother element record (Pi^s_k = {E, g, D}):
+//   E | g | D (lower)                               -> SREC = 2 NX^2 + NX
+#pragma once
+
+#include "linalg.cuh"
+
+namespace sqsm {
+
+// Per-step view of a linear(ised) model.  Row t holds the transition
+// (F_t, c_t, S_Lambda_t) of x_{t+1} = F_t x_t + c_t + q_t and the
+// observation (H_{t+1}, d_{t+1}, S_Omega_{t+1}) of y_{t+1}
+// (eq. linear-model); strides are in elements, 0 = time-invariant.
+template <typename T>
+struct GammaView {
+  const T *F, *c, *SQ, *H, *d, *SR;
+  int64_t sF, sc, sSQ, sH, sd, sSR;
+};
+
+template <typename T, int NX, int NY>
+struct Gamma {
+  T F[NX * NX], c[NX], SQ[NX * NX], H[NY * NX], d[NY], SR[NY * NY];
+
+  SQSM_DEV void load_transition(const GammaView<T>& g, int64_t t) {
+    load<T, NX * NX>(g.F + t * g.sF, F);
+    load<T, NX>(g.c + t * g.sc, c);
+    load_lower<T, NX>(g.SQ + t * g.sSQ, SQ);
+  }
+  SQSM_DEV void load_observation(const GammaView<T>& g, int64_t t) {
+    load<T, NY * NX>(g.H + t * g.sH, H);
+    load<T, NY>(g.d + t * g.sd, d);
+    load_lower<T, NY>(g.SR + t * g.sSR, SR);
+  }
+  SQSM_DEV void load_all(const GammaView<T>& g, int64_t t) {
+    load_transition(g, t);
+    load_observation(g, t);
+  }
+};
+
+template <int NX> struct FRec {
+  static constexpr int A = 0, b = NX * NX, U = NX * NX + NX, eta = 2 * NX * NX + NX,
+                       Z = 2 * NX * NX + 2 * NX, size = 3 * NX * NX + 2 * NX;
+};
+template <int NX> struct SRec {
+  static constexpr int E = 0, g = NX * NX, D = NX * NX + NX, size = 2 * NX * NX + NX;
+};
+
+constexpr double kLog2Pi = 1.8378770664093454835606594728112;
+
+// Square-root Kalman predict + update from (m, N) at step k-1 to step k.
+// This is the k = 1 construction of Lemma 1 / Table 1 with (m_0, N_0)
+// replaced by (m, N): it is also the filter operator of Table 3 applied to a
+// left operand that is a filtering distribution (A = 0), which is how the
+// scan's carry is applied to the elements of a chunk.
+//   m^- = F m + c, N^- = Tria([F N, S_Lambda]),
+//   Psi = Tria([[H N^-, S_Omega], [N^-, 0]]),
+//   m <- m^- + Psi_21 Psi_11^{-1} (y - H m^- - d),  N <- Psi_22,
+// and returns l_k = log N(y; H m^- + d, Psi_11 Psi_11^T) (Sec. 5.1).
+template <typename T, int NX, int NY>
+SQSM_DEV T kf_step(const Gamma<T, NX, NY>& g, const T* y, T* m, T* N) {
+  T mp[NX];
+  mv<T, NX, NX>(g.F, m, mp);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
+  T P[NX * 2 * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += g.F[i * NX + k] * N[k * NX + j];
+      P[i * 2 * NX + j] = s;                       // F N  (N lower)
+      P[i * 2 * NX + NX + j] = g.SQ[i * NX + j];   // S_Lambda
+    }
+  }
+  tria<T, NX, 2 * NX>(P);
+  constexpr int W = NX + NY;
+  T Psi[W * W];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += g.H[i * NX + k] * P[k * 2 * NX + j];
+      Psi[i * W + j] = s;                          // H N^-
+    }
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Psi[i * W + NX + j] = g.SR[i * NY + j];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Psi[(NY + i) * W + j] = j <= i ? P[i * 2 * NX + j] : T(0);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Psi[(NY + i) * W + NX + j] = T(0);
+  }
+  tria<T, W, W>(Psi);
+  T e[NY], Y[NY * NY];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    T s = y[i] - g.d[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s -= g.H[i * NX + k] * mp[k];
+    e[i] = s;
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Y[i * NY + j] = j <= i ? Psi[i * W + j] : T(0);
+  }
+  lsolve<T, NY>(Y, e);                             // e = Y^{-1} v
+  T ll = T(0);
+#pragma unroll
+  for (int i = 0; i < NY; ++i) ll += T(2) * sq_log(Y[i * NY + i]) + e[i] * e[i];
+  ll = T(-0.5) * (T(NY) * T(kLog2Pi) + ll);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T s = mp[i];
+#pragma unroll
+    for (int k = 0; k < NY; ++k) s += Psi[(NY + i) * W + k] * e[k];  // K v = Psi21 e
+    m[i] = s;
+#pragma unroll
+    for (int j = 0; j < NX; ++j) N[i * NX + j] = j <= i ? Psi[(NY + i) * W + NY + j] : T(0);
+  }
+  return ll;
+}
+
+// Z_k made square as in the proof of Lemma 1: zero columns when NX > NY,
+// Tria(Z_k) when NX < NY.  Zr is NX x NY.
+template <typename T, int NX, int NY>
+SQSM_DEV void square_Z(T* Zr, T* Z) {
+  if constexpr (NX >= NY) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) Z[i * NX + j] = j < NY ? Zr[i * NY + j] : T(0);
+  } else {
+    tria<T, NX, NY>(Zr);
+    take_lower<T, NX, NY>(Zr, Z);
+  }
+}
+
+// Filter element of Lemma 1.  first = true: Table 1 (k = 1, uses m0, N0);
+// otherwise Table 2 (1 < k <= n) with Psi of eq. sqrt-filter-init-2.
+// b_k uses d_k (the printed d_{k-1} is read as d_k).
+template <typename T, int NX, int NY>
+SQSM_DEV void filter_element(const Gamma<T, NX, NY>& g, const T* y, bool first, const T* m0,
+                             const T* N0, T* e) {
+  using R = FRec<NX>;
+  constexpr int W = NX + NY;
+  T Psi[W * W];
+  T Bm[NX * NX];       // S_Lambda (k > 1) or N^- (k = 1)
+  T mp[NX];            // c (k > 1) or m^- (k = 1)
+  if (first) {
+    mv<T, NX, NX>(g.F, m0, mp);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
+    T P[NX * 2 * NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int k = j; k < NX; ++k) s += g.F[i * NX + k] * N0[k * NX + j];
+        P[i * 2 * NX + j] = s;
+        P[i * 2 * NX + NX + j] = g.SQ[i * NX + j];
+      }
+    tria<T, NX, 2 * NX>(P);
+    take_lower<T, NX, 2 * NX>(P, Bm);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mp[i] = g.c[i];
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) Bm[i] = g.SQ[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += g.H[i * NX + k] * Bm[k * NX + j];
+      Psi[i * W + j] = s;
+    }
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Psi[i * W + NX + j] = g.SR[i * NY + j];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Psi[(NY + i) * W + j] = Bm[i * NX + j];
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Psi[(NY + i) * W + NX + j] = T(0);
+  }
+  tria<T, W, W>(Psi);
+  T Y[NY * NY];
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Y[i * NY + j] = j <= i ? Psi[i * W + j] : T(0);
+  // residual for b: y - H m^- - d (k = 1) or y - H c - d (k > 1)
+  T v[NY], r[NY];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    T s = y[i] - g.d[i], s2 = y[i] - g.d[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      s -= g.H[i * NX + k] * mp[k];
+      s2 -= g.H[i * NX + k] * g.c[k];
+    }
+    v[i] = s;
+    r[i] = s2;
+  }
+  lsolve<T, NY>(Y, v);
+  lsolve<T, NY>(Y, r);
+  // b = m^- (or c) + Psi21 Y^{-1} v
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T s = mp[i];
+#pragma unroll
+    for (int k = 0; k < NY; ++k) s += Psi[(NY + i) * W + k] * v[k];
+    e[R::b + i] = s;
+  }
+  // Wm = Y^{-1} H F (NY x NX); Z = Wm^T; eta = Wm^T Y^{-1} (y - H c - d)
+  T Wm[NY * NX];
+  mm<T, NY, NX, NX>(g.H, g.F, Wm);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T col[NY];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) col[i] = Wm[i * NX + j];
+    lsolve<T, NY>(Y, col);
+#pragma unroll
+    for (int i = 0; i < NY; ++i) Wm[i * NX + j] = col[i];
+  }
+  // A = (I - K H) F = F - Psi21 Wm  (k > 1);  A = 0 (k = 1)
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = g.F[i * NX + j];
+#pragma unroll
+      for (int k = 0; k < NY; ++k) s -= Psi[(NY + i) * W + k] * Wm[k * NX + j];
+      e[R::A + i * NX + j] = first ? T(0) : s;
+    }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+      e[R::U + i * NX + j] = j <= i ? Psi[(NY + i) * W + NY + j] : T(0);
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < NY; ++k) s += Wm[k * NX + i] * r[k];
+    e[R::eta + i] = s;
+  }
+  T Zr[NX * NY];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Zr[i * NY + j] = Wm[j * NX + i];
+  square_Z<T, NX, NY>(Zr, e + R::Z);
+}
+
+// Xi of eq. sqrt-filter-com-2 from U_i and Z_j: the 2NX x 2NX matrix
+// [[U_i^T Z_j, I], [Z_j, 0]] triangularised (NREF reflections).
+template <typename T, int NX, int NREF>
+SQSM_DEV void make_xi(const T* Ui, const T* Zj, T* X) {
+  constexpr int C2 = 2 * NX;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = i; k < NX; ++k) s += Ui[k * NX + i] * Zj[k * NX + j];   // U_i^T Z_j
+      X[i * C2 + j] = s;
+      X[i * C2 + NX + j] = i == j ? T(1) : T(0);
+      X[(NX + i) * C2 + j] = Zj[i * NX + j];
+      X[(NX + i) * C2 + NX + j] = T(0);
+    }
+  }
+  tria<T, C2, C2, NREF>(X);
+}
+
+// Filter operator of Lemma 2 / Table 3 (right column) on full elements:
+// out = e_i (x) e_j.  out must not alias the inputs.
+//   G = Xi_21 Xi_11^{-1} (so that Xi_11^{-T} Xi_21^T = G^T),
+//   (I + C_i J_j)^{-1} = I - U_i G^T                   (eq. sqrt-filter-com-3),
+//   A_ij = A_j (I - U_i G^T) A_i,
+//   b_ij = A_j (I - U_i G^T)(b_i + U_i U_i^T eta_j) + b_j,
+//   U_ij = Tria([A_j U_i Xi_11^{-T}, U_j]),
+//   eta_ij = A_i^T (I - G U_i^T)(eta_j - Z_j Z_j^T b_i) + eta_i,
+//   Z_ij = Tria([A_i^T Xi_22, Z_i]).
+template <typename T, int NX>
+SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
+  using R = FRec<NX>;
+  constexpr int C2 = 2 * NX;
+  T X[C2 * C2];
+  make_xi<T, NX, C2>(ei + R::U, ej + R::Z, X);
+  T G[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
+  T X11[NX * NX];
+  take_lower<T, NX, C2>(X, X11);
+  rsolve<T, NX, NX>(G, X11);
+  const T* Ui = ei + R::U;
+  // Minv = I - U_i G^T
+  T Mi[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = i == j ? T(1) : T(0);
+#pragma unroll
+      for (int k = 0; k <= i; ++k) s -= Ui[i * NX + k] * G[j * NX + k];
+      Mi[i * NX + j] = s;
+    }
+  T AjM[NX * NX];
+  mm<T, NX, NX, NX>(ej + R::A, Mi, AjM);
+  mm<T, NX, NX, NX>(AjM, ei + R::A, out + R::A);
+  // b_ij
+  {
+    T t[NX], u[NX];
+    mtv<T, NX, NX>(Ui, ej + R::eta, t);
+    mv<T, NX, NX>(Ui, t, u);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) u[i] += ei[R::b + i];
+    mv<T, NX, NX>(AjM, u, t);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) out[R::b + i] = t[i] + ej[R::b + i];
+  }
+  // U_ij = Tria([A_j U_i Xi11^{-T}, U_j])
+  {
+    T V[NX * NX];
+    mm<T, NX, NX, NX>(ej + R::A, Ui, V);
+    rsolve_t<T, NX, NX>(V, X11);
+    T B[NX * C2];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        B[i * C2 + j] = V[i * NX + j];
+        B[i * C2 + NX + j] = ej[R::U + i * NX + j];
+      }
+    tria<T, NX, C2>(B);
+    take_lower<T, NX, C2>(B, out + R::U);
+  }
+  // eta_ij
+  {
+    const T* Zj = ej + R::Z;
+    T s[NX], r[NX], t[NX];
+    mtv<T, NX, NX>(Zj, ei + R::b, s);
+    mv<T, NX, NX>(Zj, s, r);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[i] = ej[R::eta + i] - r[i];
+    mtv<T, NX, NX>(Ui, r, t);
+    mv<T, NX, NX>(G, t, s);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[i] -= s[i];
+    mtv<T, NX, NX>(ei + R::A, r, t);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) out[R::eta + i] = t[i] + ei[R::eta + i];
+  }
+  // Z_ij = Tria([A_i^T Xi22, Z_i])
+  {
+    T B[NX * C2];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int k = j; k < NX; ++k) s += ei[R::A + k * NX + i] * X[(NX + k) * C2 + NX + j];
+        B[i * C2 + j] = s;
+        B[i * C2 + NX + j] = ei[R::Z + i * NX + j];
+      }
+    tria<T, NX, C2>(B);
+    take_lower<T, NX, C2>(B, out + R::Z);
+  }
+}
+
+// Table 3 with a left operand that is a filtering distribution (A_i = 0):
+// only b_ij and U_ij are needed, so Xi_22 (the last NX reflections) and
+// eta_ij, Z_ij are skipped.  (bi, Ui) -> (bo, Uo).
+template <typename T, int NX>
+SQSM_DEV void filter_apply(const T* bi, const T* Ui, const T* ej, T* bo, T* Uo) {
+  using R = FRec<NX>;
+  constexpr int C2 = 2 * NX;
+  T X[C2 * C2];
+  make_xi<T, NX, NX>(Ui, ej + R::Z, X);
+  T G[NX * NX], X11[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
+  take_lower<T, NX, C2>(X, X11);
+  rsolve<T, NX, NX>(G, X11);
+  T t[NX], u[NX], w[NX];
+  mtv<T, NX, NX>(Ui, ej + R::eta, t);
+  mv<T, NX, NX>(Ui, t, u);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) u[i] += bi[i];
+  // (I - U_i G^T) u
+  // t = G^T u
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s += G[k * NX + i] * u[k];
+    t[i] = s;
+  }
+  mv<T, NX, NX>(Ui, t, w);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) w[i] = u[i] - w[i];
+  mv<T, NX, NX>(ej + R::A, w, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) bo[i] = t[i] + ej[R::b + i];
+  T V[NX * NX];
+  mm<T, NX, NX, NX>(ej + R::A, Ui, V);
+  rsolve_t<T, NX, NX>(V, X11);
+  T B[NX * C2];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      B[i * C2 + j] = V[i * NX + j];
+      B[i * C2 + NX + j] = ej[R::U + i * NX + j];
+    }
+  tria<T, NX, C2>(B);
+  take_lower<T, NX, C2>(B, Uo);
+}
+
+// Smoother element of Lemma 3 / Table 4 (right column), 0 <= k < n, with Phi
+// of eq. smooth-init-2:  E = Phi_21 Phi_11^{-1}, g = m^f - E (F m^f + c),
+// D = Phi_22.  Uses only the transition part of g.
+template <typename T, int NX, int NY>
+SQSM_DEV void smoother_element(const Gamma<T, NX, NY>& g, const T* mf, const T* Nf, T* e) {
+  using R = SRec<NX>;
+  constexpr int C2 = 2 * NX;
+  T Phi[C2 * C2];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += g.F[i * NX + k] * Nf[k * NX + j];
+      Phi[i * C2 + j] = s;
+      Phi[i * C2 + NX + j] = g.SQ[i * NX + j];
+      Phi[(NX + i) * C2 + j] = Nf[i * NX + j];
+      Phi[(NX + i) * C2 + NX + j] = T(0);
+    }
+  tria<T, C2, C2>(Phi);
+  T P11[NX * NX];
+  take_lower<T, NX, C2>(Phi, P11);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) e[R::E + i * NX + j] = Phi[(NX + i) * C2 + j];
+  rsolve<T, NX, NX>(e + R::E, P11);
+  T fm[NX];
+  mv<T, NX, NX>(g.F, mf, fm);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) fm[i] += g.c[i];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T s = mf[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s -= e[R::E + i * NX + k] * fm[k];
+    e[R::g + i] = s;
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+      e[R::D + i * NX + j] = j <= i ? Phi[(NX + i) * C2 + NX + j] : T(0);
+  }
+}
+
+// Caption of Table 4: E_n = 0, g_n = m^f_n, D_n = N^f_n.
+template <typename T, int NX>
+SQSM_DEV void smoother_element_last(const T* mf, const T* Nf, T* e) {
+  using R = SRec<NX>;
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) {
+    e[R::E + i] = T(0);
+    e[R::D + i] = Nf[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) e[R::g + i] = mf[i];
+}
+
+// Smoother operator of Lemma 4 / Table 5 (right column): out = e_i (x) e_j,
+//   E_ij = E_i E_j, g_ij = E_i g_j + g_i, D_ij = Tria([E_i D_j, D_i]).
+template <typename T, int NX>
+SQSM_DEV void smoother_combine(const T* ei, const T* ej, T* out) {
+  using R = SRec<NX>;
+  constexpr int C2 = 2 * NX;
+  mm<T, NX, NX, NX>(ei + R::E, ej + R::E, out + R::E);
+  T t[NX];
+  mv<T, NX, NX>(ei + R::E, ej + R::g, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) out[R::g + i] = t[i] + ei[R::g + i];
+  T B[NX * C2];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += ei[R::E + i * NX + k] * ej[R::D + k * NX + j];
+      B[i * C2 + j] = s;
+      B[i * C2 + NX + j] = ei[R::D + i * NX + j];
+    }
+  tria<T, NX, C2>(B);
+  take_lower<T, NX, C2>(B, out + R::D);
+}
+
+// Table 5 with a right operand whose E is 0 (a smoothing distribution
+// (g, D) = (m^s_{k+1}, N^s_{k+1})): this is the RTS step
+//   m <- E_i m + g_i,  N <- Tria([E_i N, D_i]).   (gm, Dm) updated in place.
+template <typename T, int NX>
+SQSM_DEV void smoother_apply(const T* ei, T* gm, T* Dm) {
+  using R = SRec<NX>;
+  constexpr int C2 = 2 * NX;
+  T t[NX];
+  mv<T, NX, NX>(ei + R::E, gm, t);
+  T B[NX * C2];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += ei[R::E + i * NX + k] * Dm[k * NX + j];
+      B[i * C2 + j] = s;
+      B[i * C2 + NX + j] = ei[R::D + i * NX + j];
+    }
+  tria<T, NX, C2>(B);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) gm[i] = t[i] + ei[R::g + i];
+  take_lower<T, NX, C2>(B, Dm);
+}
+
+}  // namespace sqsm

@@ -1,0 +1,76 @@
+// Host-side enqueueing of the two scans over a plan (shared by the linear
+// smoother and the IPLS loop).  Only launches kernels; no host compute on the
+// data path.
+#pragma once
+
+#include <vector>
+
+#include "scan.cuh"
+
+namespace sqsm {
+
+// Levels of one scan (filter or smoother) for one batch layout.
+// lv[l] (l = 0..Lc-1) folds the items of level l into items[l+1];
+// n_items[l] is the number of items at level l (n_items[Lc] = B).
+struct LevelSet {
+  std::vector<DevLevel> lv;
+  std::vector<int64_t> n_items;
+  int64_t* leaf_chunk_off = nullptr;   // device, B+1
+};
+
+// Device buffers of one scan for one (dtype, nx): items[l], carry[l],
+// flag[l] for item levels l = 1..Lc (index 0 unused).
+struct ScanBuffers {
+  std::vector<void*> items, carry;
+  std::vector<int*> flag;
+};
+
+inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <typename T, int NX, int NY>
+void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
+                    const T* y, const T* m0, const T* N0, T* mf, T* Nf, double* partial,
+                    int* status, cudaStream_t s) {
+  const int Lc = (int)L.lv.size();
+  if (Lc > 1) {
+    filter_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+        L.lv[0], sq, gv, y, m0, N0, (T*)W.items[1]);
+    for (int l = 1; l < Lc; ++l)
+      filter_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+  }
+  cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
+  for (int l = Lc - 1; l >= 1; --l)
+    filter_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+        L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
+        W.flag[l]);
+  filter_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      L.lv[0], sq, gv, y, m0, N0, (const T*)W.carry[1], W.flag[1], mf, Nf, partial, status);
+}
+
+template <typename T, int NX, int NY>
+void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
+                      const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s) {
+  const int Lc = (int)L.lv.size();
+  if (Lc > 1) {
+    smoother_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+        L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
+    for (int l = 1; l < Lc; ++l)
+      smoother_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+  }
+  cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
+  for (int l = Lc - 1; l >= 1; --l)
+    smoother_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+        L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
+        W.flag[l]);
+  smoother_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status);
+}
+
+// Record sizes (elements) of the scan buffers.
+template <int NX> constexpr int filter_item_size() { return FRec<NX>::size; }
+template <int NX> constexpr int smoother_item_size() { return SRec<NX>::size; }
+template <int NX> constexpr int carry_size() { return NX + NX * NX; }
+
+}  // namespace sqsm

@@ -1,0 +1,49 @@
+// Iterated posterior linearisation smoother (Alg. 3) for the CT model, double.
+#include "ct_model.cuh"
+#include "dispatch.h"
+
+namespace sqsm {
+
+void ipls_params_f64(const IplsArgs& a, cudaStream_t s) {
+  ct_params_kernel<double><<<1, 1, 0, s>>>(a.theta[0], a.theta[1], a.theta[2], a.dt,
+                                       a.sensors[0], a.sensors[1], a.sensors[2], a.sensors[3],
+                                       (CTParams<double>*)a.params);
+}
+
+void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
+  using T = double;
+  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+      Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, (const T*)a.ms,
+      (const T*)a.Ns, (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+}
+
+void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s) {
+  using T = double;
+  constexpr int NX = 5, NY = 2;
+  T* ms = (T*)a.ms;
+  T* Ns = (T*)a.Ns;
+  const int64_t rows = Ls.n_items[0];
+  if (a.init_ms) {
+    cudaMemcpyAsync(ms, a.init_ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(Ns, a.init_Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
+  } else {
+    broadcast_prior_kernel<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
+        Ls.lv[0], (const T*)a.m0, (const T*)a.N0, ms, Ns);
+  }
+  GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
+                  (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
+  for (int it = 0; it < a.M; ++it) {
+    ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+        Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, ms, Ns, (const T*)a.y,
+        (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
+                              (T*)a.mf, (T*)a.Nf, partial, status, s);
+    enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, ms, Ns, status,
+                                s);
+  }
+  if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s);
+}
+
+}  // namespace sqsm

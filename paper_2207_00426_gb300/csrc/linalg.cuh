@@ -1,0 +1,228 @@
+// Small dense linear algebra held in registers (one thread per matrix).
+//
+// Matrices are row-major arrays with compile-time shapes; every loop is fully
+// unrolled so that the arrays stay in registers.  Tria (Sec. 2.2) is an LQ
+// factorisation by Householder reflections applied from the right.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SQSM_DEV __device__ __forceinline__
+
+namespace sqsm {
+
+template <typename T> struct Tiny;
+template <> struct Tiny<float> { static constexpr float value = 1e-30f; };
+template <> struct Tiny<double> { static constexpr double value = 1e-280; };
+
+SQSM_DEV float sq_sqrt(float x) { return sqrtf(x); }
+SQSM_DEV double sq_sqrt(double x) { return sqrt(x); }
+SQSM_DEV float sq_log(float x) { return logf(x); }
+SQSM_DEV double sq_log(double x) { return log(x); }
+
+// Tria(A) for an R x C matrix `a` (Sec. 2.2): on return columns 0..R-1 of
+// `a` hold the lower-triangular L with L L^T = A A^T and diag(L) >= 0 (the
+// strictly upper part of those columns and columns R..C-1 are left as
+// scratch).  Step i reflects row i onto its pivot: v = x + sign(x0)|x| e_0,
+// applied to rows i+1.., after which column i of L is final; its sign is
+// flipped so that L_ii = |x|.  A row whose remaining part is zero (rank
+// deficiency) takes the identity reflector.  With NREF < R only the first
+// NREF reflections are applied: rows 0..NREF-1 of L and columns 0..NREF-1 of
+// the remaining rows are then final (used where only the leading block
+// columns of the factor are needed).
+template <typename T, int R, int C, int NREF = R>
+SQSM_DEV void tria(T* a) {
+  static_assert(R <= C, "tria is only used on R x C blocks with R <= C");
+  static_assert(NREF <= R, "at most R reflections");
+#pragma unroll
+  for (int i = 0; i < NREF; ++i) {
+    T s2 = T(0);
+#pragma unroll
+    for (int j = i; j < C; ++j) s2 += a[i * C + j] * a[i * C + j];
+    const T x0 = a[i * C + i];
+    if (s2 > Tiny<T>::value) {
+      const T alpha = sq_sqrt(s2);
+      const T sgn = x0 >= T(0) ? T(1) : T(-1);
+      const T v0 = x0 + sgn * alpha;
+      const T tau = T(1) / (alpha * (alpha + (x0 >= T(0) ? x0 : -x0)));
+#pragma unroll
+      for (int r = i + 1; r < R; ++r) {
+        T w = a[r * C + i] * v0;
+#pragma unroll
+        for (int j = i + 1; j < C; ++j) w += a[r * C + j] * a[i * C + j];
+        w *= tau;
+        // column i of L, with the sign flip that makes L_ii = alpha > 0
+        a[r * C + i] = -sgn * (a[r * C + i] - w * v0);
+#pragma unroll
+        for (int j = i + 1; j < C; ++j) a[r * C + j] -= w * a[i * C + j];
+      }
+      a[i * C + i] = alpha;
+    } else {
+      a[i * C + i] = T(0);
+    }
+  }
+}
+
+// Copy the R x R lower factor out of the first R columns of an R x C array.
+template <typename T, int R, int C>
+SQSM_DEV void take_lower(const T* a, T* L) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < R; ++j) L[r * R + j] = (j <= r && j < C) ? a[r * C + j] : T(0);
+}
+
+// C[M][N] = A[M][K] B[K][N]
+template <typename T, int M, int K, int N>
+SQSM_DEV void mm(const T* A, const T* B, T* Cm) {
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s += A[i * K + k] * B[k * N + j];
+      Cm[i * N + j] = s;
+    }
+}
+
+// C[M][N] = A[K][M]^T B[K][N]
+template <typename T, int M, int K, int N>
+SQSM_DEV void mtm(const T* A, const T* B, T* Cm) {
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s += A[k * M + i] * B[k * N + j];
+      Cm[i * N + j] = s;
+    }
+}
+
+// C[M][N] = A[M][K] B[N][K]^T
+template <typename T, int M, int K, int N>
+SQSM_DEV void mmt(const T* A, const T* B, T* Cm) {
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s += A[i * K + k] * B[j * K + k];
+      Cm[i * N + j] = s;
+    }
+}
+
+// y[M] = A[M][N] x[N]
+template <typename T, int M, int N>
+SQSM_DEV void mv(const T* A, const T* x, T* y) {
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += A[i * N + k] * x[k];
+    y[i] = s;
+  }
+}
+
+// y[N] = A[M][N]^T x[M]
+template <typename T, int M, int N>
+SQSM_DEV void mtv(const T* A, const T* x, T* y) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < M; ++k) s += A[k * N + i] * x[k];
+    y[i] = s;
+  }
+}
+
+// x = L^{-1} b for lower L (N x N); in place on b.
+template <typename T, int N>
+SQSM_DEV void lsolve(const T* L, T* b) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= L[i * N + k] * b[k];
+    b[i] = s / L[i * N + i];
+  }
+}
+
+// x = L^{-T} b for lower L (N x N); in place on b.
+template <typename T, int N>
+SQSM_DEV void ltsolve(const T* L, T* b) {
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    T s = b[i];
+#pragma unroll
+    for (int k = i + 1; k < N; ++k) s -= L[k * N + i] * b[k];
+    b[i] = s / L[i * N + i];
+  }
+}
+
+// X <- X L^{-1} for X (M x N), lower L (N x N): each row x solves z L = x.
+template <typename T, int M, int N>
+SQSM_DEV void rsolve(T* X, const T* L) {
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+      T s = X[r * N + i];
+#pragma unroll
+      for (int k = i + 1; k < N; ++k) s -= X[r * N + k] * L[k * N + i];
+      X[r * N + i] = s / L[i * N + i];
+    }
+  }
+}
+
+// X <- X L^{-T} for X (M x N), lower L (N x N): each row x solves z L^T = x.
+template <typename T, int M, int N>
+SQSM_DEV void rsolve_t(T* X, const T* L) {
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s = X[r * N + i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s -= X[r * N + k] * L[i * N + k];
+      X[r * N + i] = s / L[i * N + i];
+    }
+  }
+}
+
+template <typename T, int N>
+SQSM_DEV void load(const T* __restrict__ g, T* r) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) r[i] = g[i];
+}
+
+template <typename T, int N>
+SQSM_DEV void store(T* __restrict__ g, const T* r) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) g[i] = r[i];
+}
+
+// Load an N x N lower factor, zeroing the strictly upper part.
+template <typename T, int N>
+SQSM_DEV void load_lower(const T* __restrict__ g, T* r) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) r[i * N + j] = j <= i ? g[i * N + j] : T(0);
+}
+
+// Store an N x N lower factor with explicit zeros above the diagonal.
+template <typename T, int N>
+SQSM_DEV void store_lower(T* __restrict__ g, const T* r) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) g[i * N + j] = j <= i ? r[i * N + j] : T(0);
+}
+
+template <typename T> SQSM_DEV bool finite(T x) { return isfinite(x); }
+
+}  // namespace sqsm

@@ -1,0 +1,341 @@
+// Segmented reduce-then-scan of the square-root filter (Alg. 1) and smoother
+// (Alg. 2) over a batch of independent sequences.
+//
+// Level 0 items are the time steps (filter, k = 1..n_b) or the smoothing
+// elements (smoother, k = 0..n_b) of each sequence; a level-l chunk is a run
+// of consecutive items of one sequence, folded by one thread into one item of
+// level l+1, until every sequence has a single item.  The down-sweep then
+// gives every item the exclusive prefix (filter) or suffix (smoother) of its
+// sequence -- a filtering (resp. smoothing) distribution, i.e. an element
+// with A = 0 (resp. E = 0) -- and the leaves apply it to their own steps.
+// Applying a distribution to an element is Table 3 (resp. Table 5) with that
+// zero block, which is the sequential square-root Kalman (resp. RTS) step.
+//
+// No thread waits on another: levels are separate launches.
+#pragma once
+
+#include "elements.cuh"
+
+namespace sqsm {
+
+// One level of the plan (device arrays).
+struct DevLevel {
+  int64_t n_chunks;
+  const int64_t* first;   // first item of each chunk (global item index)
+  const int32_t* count;   // items in each chunk
+  const int32_t* seq;     // sequence of each chunk
+};
+
+// Sequence bookkeeping: offsets[b] = first observation of sequence b
+// (observations of b are rows offsets[b]..offsets[b+1]-1; its state rows are
+// offsets[b]+b .. offsets[b+1]+b).
+struct DevSeqs {
+  int32_t B;
+  const int64_t* offsets;        // B+1
+  const int64_t* leaf_chunk_off; // B+1: leaf chunks of sequence b
+};
+
+constexpr int kBlock = 128;
+
+template <typename T, int N>
+SQSM_DEV void copy(const T* a, T* b) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) b[i] = a[i];
+}
+
+SQSM_DEV void flag_status(int* status, int code) {
+  if (status) atomicOr(status, code);
+}
+
+// ---------------------------------------------------------------------------
+// Filter
+// ---------------------------------------------------------------------------
+
+// Leaf up-sweep: build the elements of Lemma 1 for the steps of a chunk and
+// fold them left to right with Table 3.
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(kBlock)
+filter_leaf_up(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ y,
+               const T* __restrict__ m0, const T* __restrict__ N0, T* __restrict__ items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = FRec<NX>::size;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t off = sq.offsets[b];
+  T agg[REC], el[REC], tmp[REC];
+  T m0b[NX], N0b[NX * NX];
+  load<T, NX>(m0 + (int64_t)b * NX, m0b);
+  load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N0b);
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t s = s0 + j;
+    Gamma<T, NX, NY> g;
+    g.load_all(gv, s);
+    T ys[NY];
+    load<T, NY>(y + s * NY, ys);
+    if (j == 0) {
+      filter_element<T, NX, NY>(g, ys, s == off, m0b, N0b, agg);
+    } else {
+      filter_element<T, NX, NY>(g, ys, s == off, m0b, N0b, el);
+      filter_combine<T, NX>(agg, el, tmp);
+      copy<T, REC>(tmp, agg);
+    }
+  }
+  store<T, REC>(items + c * REC, agg);
+}
+
+// Upper up-sweep: fold `count` consecutive items left to right.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+filter_up(DevLevel lv, const T* __restrict__ items_in, T* __restrict__ items_out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = FRec<NX>::size;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T agg[REC], el[REC], tmp[REC];
+  load<T, REC>(items_in + i0 * REC, agg);
+  for (int j = 1; j < cnt; ++j) {
+    load<T, REC>(items_in + (i0 + j) * REC, el);
+    filter_combine<T, NX>(agg, el, tmp);
+    copy<T, REC>(tmp, agg);
+  }
+  store<T, REC>(items_out + c * REC, agg);
+}
+
+// Upper down-sweep: item c of level l+1 carries the filtering distribution
+// (b, U) just before its chunk (flag 0: none, the chunk starts the
+// sequence).  Give each item of the chunk its own exclusive prefix.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+filter_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+            const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = FRec<NX>::size;
+  constexpr int CREC = NX + NX * NX;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  int flag = flag_in[c];
+  T cb[NX], cU[NX * NX];
+  load<T, NX>(carry_in + c * CREC, cb);
+  load<T, NX * NX>(carry_in + c * CREC + NX, cU);
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t i = i0 + j;
+    store<T, NX>(carry_out + i * CREC, cb);
+    store<T, NX * NX>(carry_out + i * CREC + NX, cU);
+    flag_out[i] = flag;
+    if (j + 1 < cnt) {
+      const T* it = items + i * REC;
+      if (flag) {
+        T el[REC], nb[NX], nU[NX * NX];
+        load<T, REC>(it, el);
+        filter_apply<T, NX>(cb, cU, el, nb, nU);
+        copy<T, NX>(nb, cb);
+        copy<T, NX * NX>(nU, cU);
+      } else {
+        load<T, NX>(it + FRec<NX>::b, cb);
+        load<T, NX * NX>(it + FRec<NX>::U, cU);
+        flag = 1;
+      }
+    }
+  }
+}
+
+// Leaf down-sweep: sequential square-root Kalman steps from the chunk's
+// carry (or from the prior (m0, N0) for the first chunk of a sequence),
+// writing m^f, N^f and the chunk's partial log-likelihood (FP64 sum).
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(kBlock)
+filter_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ y,
+                 const T* __restrict__ m0, const T* __restrict__ N0,
+                 const T* __restrict__ carry, const int* __restrict__ flag,
+                 T* __restrict__ mf, T* __restrict__ Nf, double* __restrict__ partial,
+                 int* status) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int CREC = NX + NX * NX;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T m[NX], N[NX * NX];
+  if (flag[c]) {
+    load<T, NX>(carry + c * CREC, m);
+    load<T, NX * NX>(carry + c * CREC + NX, N);
+  } else {
+    load<T, NX>(m0 + (int64_t)b * NX, m);
+    load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N);
+    const int64_t row0 = sq.offsets[b] + b;   // k = 0
+    if (mf) store<T, NX>(mf + row0 * NX, m);
+    if (Nf) store_lower<T, NX>(Nf + row0 * NX * NX, N);
+  }
+  double acc = 0.0;
+  bool ok = true;
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t s = s0 + j;
+    Gamma<T, NX, NY> g;
+    g.load_all(gv, s);
+    T ys[NY];
+    load<T, NY>(y + s * NY, ys);
+    const T ll = kf_step<T, NX, NY>(g, ys, m, N);
+    acc += (double)ll;
+    const int64_t row = s + b + 1;
+    if (mf) store<T, NX>(mf + row * NX, m);
+    if (Nf) store_lower<T, NX>(Nf + row * NX * NX, N);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) ok = ok && finite(m[i]);
+  }
+  if (partial) partial[c] = acc;
+  if (!ok) flag_status(status, 8);
+}
+
+// ---------------------------------------------------------------------------
+// Smoother (reverse scan)
+// ---------------------------------------------------------------------------
+
+// Leaf up-sweep: build the elements of Lemma 3 for the chunk's k (state
+// rows) and fold them right to left with Table 5.
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(kBlock)
+smoother_leaf_up(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ mf,
+                 const T* __restrict__ Nf, T* __restrict__ items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = SRec<NX>::size;
+  const int b = lv.seq[c];
+  const int64_t e0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t so = sq.offsets[b] + b;
+  const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
+  T agg[REC], el[REC], tmp[REC];
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t e = e0 + j;
+    const int64_t k = e - so;
+    T m[NX], N[NX * NX];
+    load<T, NX>(mf + e * NX, m);
+    load_lower<T, NX>(Nf + e * NX * NX, N);
+    T* dst = (j == cnt - 1) ? agg : el;
+    if (k == nb) {
+      smoother_element_last<T, NX>(m, N, dst);
+    } else {
+      Gamma<T, NX, NY> g;
+      g.load_transition(gv, sq.offsets[b] + k);
+      smoother_element<T, NX, NY>(g, m, N, dst);
+    }
+    if (j != cnt - 1) {
+      smoother_combine<T, NX>(el, agg, tmp);
+      copy<T, REC>(tmp, agg);
+    }
+  }
+  store<T, REC>(items + c * REC, agg);
+}
+
+// Upper up-sweep: fold `count` items right to left.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+smoother_up(DevLevel lv, const T* __restrict__ items_in, T* __restrict__ items_out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = SRec<NX>::size;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T agg[REC], el[REC], tmp[REC];
+  load<T, REC>(items_in + (i0 + cnt - 1) * REC, agg);
+  for (int j = cnt - 2; j >= 0; --j) {
+    load<T, REC>(items_in + (i0 + j) * REC, el);
+    smoother_combine<T, NX>(el, agg, tmp);
+    copy<T, REC>(tmp, agg);
+  }
+  store<T, REC>(items_out + c * REC, agg);
+}
+
+// Upper down-sweep: item c of level l+1 carries the smoothing distribution
+// (g, D) just after its chunk (flag 0: none, the chunk ends the sequence).
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+              const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = SRec<NX>::size;
+  constexpr int CREC = NX + NX * NX;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  int flag = flag_in[c];
+  T cg[NX], cD[NX * NX];
+  load<T, NX>(carry_in + c * CREC, cg);
+  load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t i = i0 + j;
+    store<T, NX>(carry_out + i * CREC, cg);
+    store<T, NX * NX>(carry_out + i * CREC + NX, cD);
+    flag_out[i] = flag;
+    if (j > 0) {
+      const T* it = items + i * REC;
+      if (flag) {
+        T el[REC];
+        load<T, REC>(it, el);
+        smoother_apply<T, NX>(el, cg, cD);
+      } else {
+        load<T, NX>(it + SRec<NX>::g, cg);
+        load<T, NX * NX>(it + SRec<NX>::D, cD);
+        flag = 1;
+      }
+    }
+  }
+}
+
+// Leaf down-sweep: sequential square-root RTS steps from the chunk's carry
+// (m^s, N^s just after the chunk), writing m^s, N^s.
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(kBlock)
+smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ mf,
+                   const T* __restrict__ Nf, const T* __restrict__ carry,
+                   const int* __restrict__ flag, T* __restrict__ ms, T* __restrict__ Ns,
+                   int* status) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = SRec<NX>::size;
+  constexpr int CREC = NX + NX * NX;
+  const int b = lv.seq[c];
+  const int64_t e0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t so = sq.offsets[b] + b;
+  const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
+  T gm[NX], Dm[NX * NX];
+  if (flag[c]) {
+    load<T, NX>(carry + c * CREC, gm);
+    load<T, NX * NX>(carry + c * CREC + NX, Dm);
+  }
+  bool ok = true;
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t e = e0 + j;
+    const int64_t k = e - so;
+    T m[NX], N[NX * NX];
+    load<T, NX>(mf + e * NX, m);
+    load_lower<T, NX>(Nf + e * NX * NX, N);
+    if (k == nb) {
+      copy<T, NX>(m, gm);
+      copy<T, NX * NX>(N, Dm);
+    } else {
+      Gamma<T, NX, NY> g;
+      g.load_transition(gv, sq.offsets[b] + k);
+      T el[REC];
+      smoother_element<T, NX, NY>(g, m, N, el);
+      smoother_apply<T, NX>(el, gm, Dm);
+    }
+    store<T, NX>(ms + e * NX, gm);
+    store_lower<T, NX>(Ns + e * NX * NX, Dm);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);
+  }
+  if (!ok) flag_status(status, 8);
+}
+
+// Per-sequence FP64 sum of the leaf partial log-likelihoods in a fixed
+// order (deterministic).  One block per sequence.
+__global__ void loglik_reduce(DevSeqs sq, const double* __restrict__ partial,
+                              double* __restrict__ loglik, int* status);
+
+}  // namespace sqsm

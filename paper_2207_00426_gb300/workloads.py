@@ -64,6 +64,8 @@ def random_lgssm(n, nx, ny, seed=0, scale=0.3):
     rng = np.random.default_rng(seed)
     F = np.stack([np.eye(nx) + scale * rng.standard_normal((nx, nx)) / np.sqrt(nx)
                   for _ in range(n)])
+    # keep every transition contractive so long sequences stay bounded
+    F *= np.minimum(1.0, 0.98 / np.linalg.norm(F, ord=2, axis=(1, 2)))[:, None, None]
     c = 0.1 * rng.standard_normal((n, nx))
     SQ = np.stack([_rand_lower(rng, nx, scale) for _ in range(n)])
     H = rng.standard_normal((n, ny, nx))

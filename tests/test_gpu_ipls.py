@@ -1,0 +1,143 @@
+"""Parity of the SLR step and of the IPLS smoother (Alg. 3) for the CT
+bearings-only model against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import ipls as O, models as OM, slr as OS
+from oracle.kalman import sqrt_filter_smoother
+from paper_2207_00426_gb300 import workloads as W
+from gpu_util import rel_mean_err, rel_cov_err, TOL
+
+LIN = {"cubature": 0, "extended": 1}
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2207_00426_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    return B.Context(0)
+
+
+def _dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda:0")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("method", ["cubature", "extended"])
+def test_linearize_matches_oracle(B, ctx, prec, method):
+    d = W.ct_sequence(n=40, seed=11)
+    rng = np.random.default_rng(3)
+    ms = d["x"] + 0.05 * rng.standard_normal(d["x"].shape)
+    Ns = np.stack([np.tril(0.02 * rng.standard_normal((5, 5))) + np.diag(rng.uniform(0.05, 0.2, 5))
+                   for _ in range(41)])
+    dt = torch.float64 if prec == "f64" else torch.float32
+    out = B.sqsm_ct_linearize(ctx, d["theta"], _dev(d["y"], dt), [0, 40], _dev(ms, dt), _dev(Ns, dt),
+                              LIN[method], dt=d["dt"])
+    torch.cuda.synchronize()
+    F, c, SQ, H, dd, SR = [o.cpu().numpy() for o in out]
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    Fr, cr, SQr, Hr, dr, SRr = OS.linearize(ct, ms, Ns, d["y"], method)
+    tol = 1e-10 if prec == "f64" else 2e-5
+    np.testing.assert_allclose(F, Fr, atol=tol * 10)
+    np.testing.assert_allclose(c, cr, atol=tol * 10 * max(1, np.abs(cr).max()))
+    np.testing.assert_allclose(H, Hr, rtol=tol * 10, atol=tol * 10)
+    np.testing.assert_allclose(dd, dr, atol=tol * 100 * max(1, np.abs(dr).max()))
+    P = SQ @ np.swapaxes(SQ, 1, 2)
+    Pr = SQr @ np.swapaxes(SQr, 1, 2)
+    assert np.abs(P - Pr).max() <= (1e-9 if prec == "f64" else 1e-4) * np.abs(Pr).max()
+    R = SR @ np.swapaxes(SR, 1, 2)
+    Rr = SRr @ np.swapaxes(SRr, 1, 2)
+    assert np.abs(R - Rr).max() <= (1e-9 if prec == "f64" else 1e-4) * np.abs(Rr).max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("method", ["cubature", "extended"])
+def test_ipls_single_sequence(B, ctx, prec, method):
+    d = W.ct_sequence(n=97, seed=12)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    M = 6
+    ms, Ns, ll = B.sqsm_ipls_smooth(ctx, d["theta"], _dev(d["y"], dt), [0, 97], _dev(d["m0"][None], dt),
+                                    _dev(d["N0"][None], dt), M, LIN[method], dt=d["dt"])
+    torch.cuda.synchronize()
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    rms, rNs, rll, _ = O.ipls(ct, d["y"], d["m0"], d["N0"], M, method)
+    tol = TOL[prec]
+    assert rel_mean_err(ms.cpu().numpy(), rms) < tol["mean"]
+    assert rel_cov_err(Ns.cpu().numpy(), rNs) < (tol["cov"] if prec == "f64" else 1e-3)
+    assert abs(ll.item() - rll) <= max(tol["ll"], 1e-10) * abs(rll) * (10 if prec == "f32" else 1)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ipls_ragged_batch(B, ctx, prec):
+    lengths = [1, 2, 7, 33, 100, 5]
+    d = W.ct_batch(lengths=lengths, seed=13)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    M = 4
+    ms, Ns, ll = B.sqsm_ipls_smooth(ctx, d["theta"], _dev(d["y"], dt), d["offsets"], _dev(d["m0"], dt),
+                                    _dev(d["N0"], dt), M, 0, dt=d["dt"])
+    torch.cuda.synchronize()
+    ms, Ns, ll = ms.cpu().numpy(), Ns.cpu().numpy(), ll.cpu().numpy()
+    off = d["offsets"]
+    for b, nb in enumerate(lengths):
+        ct = OM.CTBearings(d["theta"], dt=d["dt"])
+        yb = d["y"][off[b]:off[b + 1]]
+        rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
+        rows = slice(off[b] + b, off[b + 1] + b + 1)
+        assert rel_mean_err(ms[rows], rms) < TOL[prec]["mean"]
+        assert abs(ll[b] - rll) <= (1e-9 if prec == "f64" else 1e-4) * abs(rll)
+
+
+def test_graph_replay_and_theta_update(B):
+    """A captured graph replays with new theta (parameters are not baked)."""
+    c2 = B.Context(0, use_graph=True)
+    c3 = B.Context(0, use_graph=False)
+    d = W.ct_sequence(n=50, seed=14)
+    y, m0, N0 = _dev(d["y"], torch.float64), _dev(d["m0"][None], torch.float64), _dev(d["N0"][None], torch.float64)
+    outs = []
+    for th in (d["theta"], d["theta"] + 0.1, d["theta"]):
+        ms, Ns, ll = B.sqsm_ipls_smooth(c2, th, y, [0, 50], m0, N0, 3, 0, dt=d["dt"])
+        ms2, Ns2, ll2 = B.sqsm_ipls_smooth(c3, th, y, [0, 50], m0, N0, 3, 0, dt=d["dt"])
+        torch.cuda.synchronize()
+        assert torch.equal(ms, ms2) and torch.equal(ll, ll2)
+        outs.append(ll.item())
+    assert outs[0] == outs[2] and outs[0] != outs[1]
+
+
+def test_full_size_chain_f32(B, ctx):
+    """n = 100000 (the benchmark workload), FP32, M = 10: the SLR of the
+    iteration-9 trajectory matches the oracle on sampled steps, and the
+    smoother of that linearised model matches the sequential FP64 oracle."""
+    n, M = 100_000, 10
+    d = W.ct_sequence(n=n, seed=1)
+    dt = torch.float32
+    y, m0, N0 = _dev(d["y"], dt), _dev(d["m0"][None], dt), _dev(d["N0"][None], dt)
+    ms9, Ns9, _ = B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M - 1, 0, dt=d["dt"])
+    G = B.sqsm_ct_linearize(ctx, d["theta"], y, [0, n], ms9, Ns9, 0, dt=d["dt"])
+    ms10, Ns10, ll10 = B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, 0, dt=d["dt"])
+    _, _, msl, Nsl, lll = B.sqsm_lgssm_smooth(ctx, *G, m0[0], N0[0], y)
+    torch.cuda.synchronize()
+    # one more IPLS iteration == linearise + linear smoother, on the GPU
+    assert torch.equal(msl, ms10) and abs(lll.item() - ll10.item()) < 1e-9 * abs(ll10.item())
+    # sampled SLR steps against the oracle
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    msn, Nsn = ms9.double().cpu().numpy(), Ns9.double().cpu().numpy()
+    Gn = [g.double().cpu().numpy() for g in G]
+    rng = np.random.default_rng(0)
+    for t in rng.choice(n, 200, replace=False):
+        F, c, S = OS.transition_cubature(ct, msn[t], Nsn[t])
+        np.testing.assert_allclose(Gn[0][t], F, atol=2e-4)
+        P, Pr = Gn[2][t] @ Gn[2][t].T, S @ S.T
+        assert np.abs(P - Pr).max() < 1e-3 * np.abs(Pr).max()
+        H, dd, So = OS.observation_cubature(ct, msn[t + 1], Nsn[t + 1], d["y"][t])
+        np.testing.assert_allclose(Gn[3][t], H, rtol=1e-3, atol=1e-4 * np.abs(H).max())
+    # the linear smoother of the GPU's linearisation against the oracle
+    ref = sqrt_filter_smoother(*Gn, d["y"], d["m0"], d["N0"])
+    assert rel_mean_err(msl.double().cpu().numpy(), ref[2]) < 1e-4
+    assert abs(lll.item() - ref[4]) < 1e-5 * abs(ref[4])
