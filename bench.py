@@ -1,0 +1,360 @@
+"""Benchmark of the GB300 IPLS smoother (CT bearings-only, cubature SLR).
+
+One step = one full iterated posterior linearisation solve (Alg. 3) of
+M = 10 iterations -- SLR, parallel square-root filter scan with the
+log-likelihood, parallel square-root smoother scan -- over one synthetic
+coordinated-turn sequence of n = 100000 observations (n_x = 5, n_y = 2),
+FP32 arithmetic with FP64 log-likelihood accumulation.
+
+Metric: smoothed steps/s = (time steps x IPLS iterations) per second.
+Timing: CUDA events around each step on the launch stream, L2 flushed (a
+256 MiB write) between steps outside the events, max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank smooths its own sequence (weak scaling, no
+data-path collective; a gloo group only aligns the timed region and takes the
+max over ranks).  --impl reference times the FP64 CPU oracle instead (rank 0
+only) on a bounded sample of the same workload.
+"""
+import os
+
+# the oracle legs run single-threaded: pin BLAS threads before numpy loads
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smoothed steps/sec (CT bearings-only IPLS, n=1e5, nx=5)"
+UNIT = "smoothed steps/s"
+N_STEPS = 100_000
+M_ITERS = 10
+SEED = 1
+CPU_SAMPLE_STEPS = 1000          # oracle sample for the CPU baseline leg
+REF_SAMPLE_STEPS = 400           # oracle sample per --impl reference step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_STEPS)
+    ap.add_argument("--M", type=int, default=M_ITERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config(args, world):
+    return {"workload": f"coordinated-turn bearings-only tracking, cubature IPLS, "
+                        f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
+            "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
+            "sequences_total": world, "leaf_chunk": 4, "radix": 4,
+            "l2": "flushed between timed steps (256 MiB write outside the events)",
+            "parallelism": f"independent sequences, {world} GPU(s)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+def oracle_rate(n_sample, M, reps=1):
+    """Time the FP64 oracle's IPLS on the first n_sample observations of the
+    workload (single thread).  Returns (steps/s, seconds, sample text)."""
+    from oracle import ipls as O, models as OM
+    from paper_2207_00426_gb300 import workloads as W
+    d = W.ct_sequence(n=n_sample, seed=SEED)
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        O.ipls(ct, d["y"], d["m0"], d["N0"], M, "cubature")
+    dt = time.perf_counter() - t0
+    return n_sample * M * reps / dt, dt
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_rate(REF_SAMPLE_STEPS // 4, args.M)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(REF_SAMPLE_STEPS, args.M)
+        times.append(dt)
+    tot = sum(times)
+    value = REF_SAMPLE_STEPS * args.M * args.steps / tot
+    sample = (f"first {REF_SAMPLE_STEPS} observations of the n={args.n} sequence, "
+              f"M={args.M}, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+    from paper_2207_00426_gb300 import binding as B
+    from paper_2207_00426_gb300 import costmodel as CM
+    from paper_2207_00426_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return t.item()
+
+    n, M = args.n, args.M
+    d = W.ct_sequence(n=n, seed=SEED + rank)
+    f32 = torch.float32
+    y = torch.tensor(d["y"], dtype=f32, device=dev)
+    m0 = torch.tensor(d["m0"][None], dtype=f32, device=dev)
+    N0 = torch.tensor(d["N0"][None], dtype=f32, device=dev)
+    ms = torch.empty((n + 1, 5), dtype=f32, device=dev)
+    Ns = torch.empty((n + 1, 5, 5), dtype=f32, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    ctx = B.Context(local, use_graph=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, B.CUBATURE, dt=d["dt"],
+                           ms=ms, Ns=Ns, loglik=ll)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert ctx.status() == 0 and np.isfinite(ll.item())
+
+    # ---- timed region: K steps, device time per step, L2 flushed between
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    barrier()
+    t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    t_max = max_over_ranks(t_dev)
+    value = n * M * args.steps * world / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    hy = torch.tensor(d["y"], dtype=f32).pin_memory()
+    hm0 = torch.tensor(d["m0"][None], dtype=f32).pin_memory()
+    hN0 = torch.tensor(d["N0"][None], dtype=f32).pin_memory()
+    hms = torch.empty((n + 1, 5), dtype=f32).pin_memory()
+    hNs = torch.empty((n + 1, 5, 5), dtype=f32).pin_memory()
+    hll = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        y.copy_(hy, non_blocking=True)
+        m0.copy_(hm0, non_blocking=True)
+        N0.copy_(hN0, non_blocking=True)
+        step()
+        hms.copy_(ms, non_blocking=True)
+        hNs.copy_(Ns, non_blocking=True)
+        hll.copy_(ll, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    eevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    barrier()
+    for a, b in eevs:
+        flush.fill_(1)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(sum(a.elapsed_time(b) for a, b in eevs) / 1e3)
+    h2d = hy.numel() * 4 + hm0.numel() * 4 + hN0.numel() * 4
+    d2h = hms.numel() * 4 + hNs.numel() * 4 + 8
+
+    # ---- per-kernel event timing (instrumented replay of the same step)
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    acc = {}
+    nprof = max(3, min(args.steps, 10))
+    for _ in range(nprof):
+        flush.fill_(1)
+        step()
+        for k, (t, c) in ctx.profile_read().items():
+            a0 = acc.setdefault(k, [0.0, 0])
+            a0[0] += t
+            a0[1] += c
+    ctx.profile(False)
+    launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
+    flops = CM.ipls_kernel_flops([n], leaf=4, radix=4)
+    total_ms = sum(t for t, _ in acc.values())
+    kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / nprof,
+                   "share": t / total_ms} for k, (t, c) in acc.items()}
+    top = max(acc, key=lambda k: acc[k][0])
+    f_launch = flops[top][0]
+    t_launch = acc[top][0] / acc[top][1] / 1e3
+    peak = 152 * 128 * 2 * 2070e6 / 1e12        # FP32 FMA lanes x 2 x max SM clock
+    achieved = f_launch / t_launch / 1e12
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "flops_per_launch": f_launch, "peak_basis":
+                "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)"}
+    it_flops = CM.ipls_iteration_flops([n])
+    whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
+    whole["frac_of_fp32_peak"] = whole["achieved_tflops"] / peak
+
+    # ---- FP64 variant of the same step (comparator), few steps
+    f64 = torch.float64
+    y64, m064, N064 = y.double(), m0.double(), N0.double()
+    ms64 = torch.empty((n + 1, 5), dtype=f64, device=dev)
+    Ns64 = torch.empty((n + 1, 5, 5), dtype=f64, device=dev)
+    ll64 = torch.empty(1, dtype=f64, device=dev)
+
+    def step64():
+        B.sqsm_ipls_smooth(ctx, d["theta"], y64, [0, n], m064, N064, M, B.CUBATURE, dt=d["dt"],
+                           ms=ms64, Ns=Ns64, loglik=ll64)
+
+    step64()
+    torch.cuda.synchronize()
+    e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(3)]
+    for a, b in e64:
+        flush.fill_(1)
+        a.record(stream)
+        step64()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t64 = sum(a.elapsed_time(b) for a, b in e64) / 1e3 / 3
+    err_f32 = float((ms.double() - ms64).norm(dim=1).max() / ms64.norm(dim=1).max())
+    ll_rel = abs(ll.item() - ll64.item()) / abs(ll64.item())
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": config(args, world),
+                "wall_s_timed_region": wall,
+                "e2e": {"value": n * M * args.steps * world / t_e2e, "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "clocks": clk.summary(),
+                "roofline": roofline, "whole_step": whole, "kernels": kernels,
+                "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
+                        "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
+                "loglik": ll.item()}
+    ctx.close()
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    line = gpu_arm(args, rank, world, local)
+    if rank == 0 and line is not None:
+        if not args.no_cpu_baseline:
+            rate, dt = oracle_rate(CPU_SAMPLE_STEPS, args.M)
+            line["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"FP64 oracle IPLS on the first {CPU_SAMPLE_STEPS} observations "
+                          f"of the workload, M={args.M}, one thread ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,24 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                       const void* Ns, void* F, void* c, void* SQ, void* H,
                       void* d, void* SR, void* stream);
 
+/* Per-kernel timing (tracing aid; not part of the method).  While enabled,
+ * sqsm_lgssm_smooth and sqsm_ipls_smooth bracket every kernel launch with a
+ * pair of CUDA events on the launch stream; IPLS calls then replay a
+ * separately captured, instrumented graph.  Enabling does not change any
+ * result. */
+int sqsm_profile_enable(sqsm_ctx* ctx, int on);
+
+/* Synchronise ctx's device and sum the event-timed durations of the kernels
+ * launched by the most recent profiled call, per kernel family:
+ * ms[k] (milliseconds) and launches[k] for k = 0..nkinds-1 (host arrays;
+ * families beyond the library's count are set to zero).  Returns the number
+ * of families through *nfamilies if it is not NULL. */
+int sqsm_profile_read(sqsm_ctx* ctx, int nkinds, double* ms, int* launches,
+                      int* nfamilies);
+
+/* Name of kernel family k ("" if out of range). */
+const char* sqsm_kernel_name(int k);
+
 /* 1 if the (nx, ny) pair is compiled into sqsm_lgssm_smooth, else 0. */
 int sqsm_supported_shape(int nx, int ny);
 

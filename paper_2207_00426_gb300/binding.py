@@ -63,9 +63,18 @@ lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTE
                                   _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
 lib.sqsm_ct_linearize.restype = _int
 
+lib.sqsm_profile_enable.argtypes = [_p, _int]
+lib.sqsm_profile_enable.restype = _int
+lib.sqsm_profile_read.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int),
+                                  ctypes.POINTER(_int)]
+lib.sqsm_profile_read.restype = _int
+lib.sqsm_kernel_name.argtypes = [_int]
+lib.sqsm_kernel_name.restype = ctypes.c_char_p
+
 EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
-            "sqsm_ct_linearize"]
+            "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
+            "sqsm_kernel_name"]
 
 
 class SqsmError(RuntimeError):
@@ -128,6 +137,20 @@ class Context:
     def check(self, rc):
         if rc != OK:
             raise SqsmError(rc, lib.sqsm_last_error(self.h).decode())
+
+    def profile(self, on=True):
+        """Enable / disable per-kernel event timing of subsequent calls."""
+        self.check(lib.sqsm_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel family: (total ms, launches)} of the last profiled call."""
+        n = 32
+        ms = (ctypes.c_double * n)()
+        cnt = (_int * n)()
+        nf = _int(0)
+        self.check(lib.sqsm_profile_read(self.h, n, ms, cnt, ctypes.byref(nf)))
+        return {lib.sqsm_kernel_name(k).decode(): (ms[k], cnt[k])
+                for k in range(nf.value) if cnt[k] > 0}
 
     def status(self):
         v = _int(0)

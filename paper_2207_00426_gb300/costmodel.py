@@ -1,0 +1,151 @@
+"""Algorithmic FLOP and byte counts of the kernels, for roofline reporting.
+
+Counts follow the formulas the kernels evaluate (an FMA is 2 flops; an add,
+multiply, divide, square root, log, sine/cosine or atan2 is 1), with the
+triangular structure of the factors taken into account.  Per-launch totals
+use the same chunking as the library's plan (leaf chunks of ``leaf`` steps,
+upper levels of ``radix`` items per thread).
+"""
+import math
+
+
+def tria(R, C, nref=None):
+    """Householder LQ of an R x C block (Tria, Sec. 2.2)."""
+    nref = R if nref is None else nref
+    f = 0
+    for i in range(nref):
+        w = C - i
+        f += 2 * w + 6                      # norm, sqrt, v0, tau
+        f += (R - 1 - i) * (4 * w + 1)      # dot + scale + update per row
+    return f
+
+
+def tri_mm(M, NX):
+    """M x NX times a lower NX x NX factor."""
+    return M * NX * (NX + 1)
+
+
+def kf_step(nx, ny):
+    W = nx + ny
+    return (2 * nx * nx + nx + tri_mm(nx, nx) + tria(nx, 2 * nx) + tri_mm(ny, nx)
+            + tria(W, W) + ny * (2 * nx + 2) + ny * ny + 4 * ny + 3 + nx * 2 * ny)
+
+
+def filter_element(nx, ny):
+    W = nx + ny
+    return (tri_mm(ny, nx) + tria(W, W) + 2 * ny * (2 * nx + 2) + 2 * ny * ny
+            + 2 * nx * ny + 2 * ny * nx * nx + nx * ny * ny + 2 * nx * nx * ny + 2 * nx * ny)
+
+
+def filter_combine(nx):
+    return (nx * nx * (nx + 1) + tria(2 * nx, 2 * nx) + nx ** 3 + nx * nx * (nx + 1)
+            + 4 * nx ** 3 + 6 * nx * nx + 2 * nx
+            + 2 * nx ** 3 + nx ** 3 + tria(nx, 2 * nx)
+            + 10 * nx * nx + 3 * nx
+            + nx * nx * (nx + 1) + tria(nx, 2 * nx))
+
+
+def filter_apply(nx):
+    return (nx * nx * (nx + 1) + tria(2 * nx, 2 * nx, nx) + nx ** 3 + 10 * nx * nx + 2 * nx
+            + 2 * nx ** 3 + nx ** 3 + tria(nx, 2 * nx))
+
+
+def smoother_element(nx):
+    return (tri_mm(nx, nx) + tria(2 * nx, 2 * nx) + nx ** 3 + 4 * nx * nx + 2 * nx)
+
+
+def smoother_combine(nx):
+    return 2 * nx ** 3 + 2 * nx * nx + nx + tri_mm(nx, nx) + tria(nx, 2 * nx)
+
+
+def smoother_apply(nx):
+    return 2 * nx * nx + nx + tri_mm(nx, nx) + tria(nx, 2 * nx)
+
+
+# CT cubature SLR: per sigma point the transition difference costs two turn
+# coefficient evaluations (sincos x2, series or divide) and ~24 flops; a
+# bearing difference costs ~8 flops + atan2 per sensor.
+CT_F_DELTA = 2 * 12 + 24
+CT_H_DELTA = 2 * (9 + 1)
+
+
+def slr_cubature_ct(nx=5, ny=2):
+    tr = (20 + 2 * nx * CT_F_DELTA + nx * nx * 4 + nx * nx * nx + 2 * nx * nx
+          + nx * (2 * nx) + tria(nx, 2 * nx))
+    ob = (2 * 10 + 2 * nx * CT_H_DELTA + ny * nx * 4 + ny * nx * nx + 2 * ny * nx
+          + ny * (nx + ny) + tria(ny, ny + nx) + 2 * 4)
+    return tr + ob
+
+
+def slr_taylor_ct(nx=5, ny=2):
+    return 20 + 40 + 2 * nx * nx + 2 * (10 + 10) + 2 * ny * nx + 8
+
+
+def _chunks(counts, size):
+    """Chunk sizes of one level and the item counts of the next."""
+    sizes, nxt = [], []
+    for c in counts:
+        nch = (c + size - 1) // size
+        sizes += [min(size, c - j * size) for j in range(nch)]
+        nxt.append(nch)
+    return sizes, nxt
+
+
+def _levels(counts0, leaf, radix):
+    levels = []
+    counts = list(counts0)
+    size = leaf
+    while True:
+        sizes, nxt = _chunks(counts, size)
+        levels.append(sizes)
+        counts = nxt
+        size = radix
+        if all(c == 1 for c in counts):
+            return levels
+
+
+def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=4, radix=4, linearization="cubature"):
+    """Algorithmic flops per launch of each kernel family for one IPLS
+    iteration over sequences of the given lengths.  Returns
+    {family: (flops per launch, launches per iteration)}."""
+    out = {}
+    nsteps = sum(lengths)
+    slr = slr_cubature_ct(nx, ny) if linearization == "cubature" else slr_taylor_ct(nx, ny)
+    out["ct_slr"] = (nsteps * slr, 1)
+    fl = _levels(lengths, leaf, radix)
+    sl = _levels([n + 1 for n in lengths], leaf, radix)
+    fe, fc, fa = filter_element(nx, ny), filter_combine(nx), filter_apply(nx)
+    if len(fl) > 1:
+        out["filter_leaf_up"] = (sum(c * fe + (c - 1) * fc for c in fl[0]), 1)
+    ups = [sum((c - 1) * fc for c in lv) for lv in fl[1:]]
+    downs = [sum((c - 1) * fa for c in lv) for lv in fl[1:]]
+    if ups:
+        out["filter_up"] = (sum(ups) / len(ups), len(ups))
+        out["filter_down"] = (sum(downs) / len(downs), len(downs))
+    out["filter_leaf_down"] = (nsteps * kf_step(nx, ny), 1)
+    se, sc, sa = smoother_element(nx), smoother_combine(nx), smoother_apply(nx)
+    nel = nsteps + len(lengths)
+    if len(sl) > 1:
+        out["smoother_leaf_up"] = (sum(c * se + (c - 1) * sc for c in sl[0])
+                                   - len(lengths) * se, 1)
+    ups = [sum((c - 1) * sc for c in lv) for lv in sl[1:]]
+    downs = [sum((c - 1) * sa for c in lv) for lv in sl[1:]]
+    if ups:
+        out["smoother_up"] = (sum(ups) / len(ups), len(ups))
+        out["smoother_down"] = (sum(downs) / len(downs), len(downs))
+    out["smoother_leaf_down"] = ((nel - len(lengths)) * (se + sa), 1)
+    return out
+
+
+def ipls_iteration_flops(lengths, **kw):
+    return sum(f * n for f, n in ipls_kernel_flops(lengths, **kw).values())
+
+
+def ipls_iteration_bytes(lengths, nx=5, ny=2, elem=4):
+    """Algorithmic HBM bytes of one IPLS iteration with every phase's
+    per-step inputs and outputs read / written once: y, the nominal
+    trajectory (mean + packed lower factor) in and out."""
+    tri = nx * (nx + 1) // 2
+    nsteps = sum(lengths)
+    rows = nsteps + len(lengths)
+    return elem * (nsteps * ny + 2 * rows * (nx + tri))

@@ -54,12 +54,18 @@ struct Plan {
 
 struct GraphKey {
   const Plan* plan;
-  int dtype, lin, M;
+  int dtype, lin, M, prof;
   const void *y, *m0, *N0, *ims, *iNs, *ms, *Ns, *ll;
   bool operator<(const GraphKey& o) const {
-    return std::tie(plan, dtype, lin, M, y, m0, N0, ims, iNs, ms, Ns, ll) <
-           std::tie(o.plan, o.dtype, o.lin, o.M, o.y, o.m0, o.N0, o.ims, o.iNs, o.ms, o.Ns, o.ll);
+    return std::tie(plan, dtype, lin, M, prof, y, m0, N0, ims, iNs, ms, Ns, ll) <
+           std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.y, o.m0, o.N0, o.ims, o.iNs, o.ms,
+                    o.Ns, o.ll);
   }
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  std::unique_ptr<Prof> prof;   // events recorded by the instrumented graph
 };
 
 }  // namespace
@@ -71,7 +77,10 @@ struct sqsm_ctx {
   int* d_status = nullptr;
   cudaStream_t capture_stream = nullptr;   // graphs are recorded here
   std::vector<std::unique_ptr<Plan>> plans;
-  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, GraphEntry> graphs;
+  bool prof_on = false;
+  Prof call_prof;                 // events of the last non-graph call
+  Prof* last_prof = nullptr;      // events of the last profiled call
 };
 
 namespace {
@@ -180,7 +189,8 @@ Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
     const Plan* victim = ctx->plans.front().get();
     for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
       if (it->first.plan == victim) {
-        cudaGraphExecDestroy(it->second);
+        if (ctx->last_prof == it->second.prof.get()) ctx->last_prof = nullptr;
+        cudaGraphExecDestroy(it->second.exec);
         it = ctx->graphs.erase(it);
       } else {
         ++it;
@@ -294,7 +304,7 @@ int sqsm_destroy(sqsm_ctx* ctx) {
   {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
     ctx->graphs.clear();
     ctx->plans.clear();
     cudaFree(ctx->d_status);
@@ -321,6 +331,43 @@ int sqsm_get_status(sqsm_ctx* ctx, int* status) {
 
 int sqsm_supported_shape(int nx, int ny) { return lgssm_shape_supported(nx, ny) ? 1 : 0; }
 
+int sqsm_profile_enable(sqsm_ctx* ctx, int on) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  ctx->prof_on = on != 0;
+  return SQSM_OK;
+}
+
+int sqsm_profile_read(sqsm_ctx* ctx, int nkinds, double* ms, int* launches, int* nfamilies) {
+  if (!ctx || nkinds < 0 || (nkinds > 0 && (!ms || !launches))) return SQSM_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_profile_read");
+  for (int k = 0; k < nkinds; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  if (nfamilies) *nfamilies = K_NUM_KINDS;
+  if (!ctx->last_prof) return SQSM_OK;
+  for (const auto& r : ctx->last_prof->rec) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+    if (r.kind < nkinds) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+    }
+  }
+  return SQSM_OK;
+}
+
+const char* sqsm_kernel_name(int k) {
+  static const char* names[K_NUM_KINDS] = {
+      "ct_params", "broadcast_prior", "ct_slr", "filter_leaf_up", "filter_up", "filter_down",
+      "filter_leaf_down", "smoother_leaf_up", "smoother_up", "smoother_down",
+      "smoother_leaf_down", "loglik_reduce"};
+  return (k >= 0 && k < K_NUM_KINDS) ? names[k] : "";
+}
+
 int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const void* F,
                       int64_t sF, const void* c, int64_t sc, const void* SQ, int64_t sSQ,
                       const void* H, int64_t sH, const void* d, int64_t sd, const void* SR,
@@ -344,8 +391,14 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, nx);
   if (!w) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace allocation failed");
+  Prof* prof = nullptr;
+  if (ctx->prof_on) {
+    ctx->call_prof.clear();
+    prof = &ctx->call_prof;
+    ctx->last_prof = prof;
+  }
   LgssmArgs a{nx, ny, F, c, SQ, H, d, SR, sF, sc, sSQ, sH, sd, sSR, m0, N0, y,
-              mf ? mf : w->mf, Nf ? Nf : w->Nf, ms, Ns};
+              mf ? mf : w->mf, Nf ? Nf : w->Nf, ms, Ns, prof};
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   const DevSeqs sq = seqs_of(p);
@@ -355,7 +408,7 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const
                : lgssm_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial,
                                    ctx->d_status, s);
   if (rc) return fail(ctx, rc, "(nx, ny) pair not compiled in");
-  if (loglik) enqueue_loglik_reduce(sq, w->partial, loglik, ctx->d_status, s);
+  if (loglik) enqueue_loglik_reduce(sq, w->partial, loglik, ctx->d_status, s, prof);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_lgssm_smooth launch");
   return SQSM_OK;
@@ -404,6 +457,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   const DevSeqs sq = seqs_of(p);
+  // theta -> model constants, outside any graph so that theta is not baked in
   if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
   auto enqueue = [&](cudaStream_t st) {
     if (dtype == SQSM_F32)
@@ -412,14 +466,26 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
       ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
   };
   if (!ctx->opt.use_graph) {
+    if (ctx->prof_on) {
+      ctx->call_prof.clear();
+      a.prof = &ctx->call_prof;
+      ctx->last_prof = a.prof;
+    }
     enqueue(s);
   } else {
-    GraphKey key{p, dtype, linearization, M, y, m0, N0, init_ms, init_Ns, ms, Ns, loglik};
+    GraphKey key{p, dtype, linearization, M, ctx->prof_on ? 1 : 0, y, m0, N0, init_ms, init_Ns,
+                 ms, Ns, loglik};
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
-      exec = it->second;
+      exec = it->second.exec;
+      if (ctx->prof_on) ctx->last_prof = it->second.prof.get();
     } else {
+      std::unique_ptr<Prof> gprof;
+      if (ctx->prof_on) {
+        gprof = std::make_unique<Prof>();
+        a.prof = gprof.get();
+      }
       // Recording executes nothing, so it happens on the context's own
       // stream (the legacy default stream cannot be captured); the graph is
       // then launched on the caller's stream.
@@ -434,10 +500,14 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
       if (ctx->graphs.size() >= 16) {
-        cudaGraphExecDestroy(ctx->graphs.begin()->second);
+        if (ctx->last_prof == ctx->graphs.begin()->second.prof.get()) ctx->last_prof = nullptr;
+        cudaGraphExecDestroy(ctx->graphs.begin()->second.exec);
         ctx->graphs.erase(ctx->graphs.begin());
       }
-      ctx->graphs[key] = exec;
+      GraphEntry& ge = ctx->graphs[key];
+      ge.exec = exec;
+      ge.prof = std::move(gprof);
+      if (ctx->prof_on) ctx->last_prof = ge.prof.get();
     }
     cudaError_t e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");

@@ -14,6 +14,7 @@ struct LgssmArgs {
   int64_t sF, sc, sSQ, sH, sd, sSR;
   const void *m0, *N0, *y;
   void *mf, *Nf, *ms, *Ns;
+  Prof* prof;
 };
 
 // Returns 0 if (nx, ny) is compiled in and the launches were enqueued,
@@ -35,6 +36,7 @@ struct IplsArgs {
   double* loglik;
   // workspace
   void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params;
+  Prof* prof;   // optional per-kernel events
 };
 
 // Everything of Alg. 3 after the parameter kernel; capturable.
@@ -54,7 +56,7 @@ void ct_linearize_f32(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStr
 void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s);
 
 void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, int* status,
-                           cudaStream_t s);
+                           cudaStream_t s, Prof* P = nullptr);
 
 }  // namespace sqsm
 

@@ -27,43 +27,97 @@ struct ScanBuffers {
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// Kernel families, for per-kernel timing.
+enum KernelKind {
+  K_PARAMS = 0, K_INIT, K_SLR, K_FILTER_LEAF_UP, K_FILTER_UP, K_FILTER_DOWN, K_FILTER_LEAF_DOWN,
+  K_SMOOTHER_LEAF_UP, K_SMOOTHER_UP, K_SMOOTHER_DOWN, K_SMOOTHER_LEAF_DOWN, K_LOGLIK,
+  K_NUM_KINDS
+};
+
+// Optional per-launch CUDA events (recorded as external event nodes when
+// the launches are captured into a graph).  Null = no instrumentation.
+struct Prof {
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> rec;
+  ~Prof() { clear(); }
+  void clear() {
+    for (auto& r : rec) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    rec.clear();
+  }
+  void begin(int kind, cudaStream_t s) {
+    Rec r{kind, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    rec.push_back(r);
+  }
+  void end(cudaStream_t s) { cudaEventRecordWithFlags(rec.back().b, s, cudaEventRecordExternal); }
+};
+
+struct ProfScope {
+  Prof* p;
+  cudaStream_t s;
+  ProfScope(Prof* p_, int kind, cudaStream_t s_) : p(p_), s(s_) {
+    if (p) p->begin(kind, s);
+  }
+  ~ProfScope() {
+    if (p) p->end(s);
+  }
+};
+
 template <typename T, int NX, int NY>
 void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
                     const T* y, const T* m0, const T* N0, T* mf, T* Nf, double* partial,
-                    int* status, cudaStream_t s) {
+                    int* status, cudaStream_t s, Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
-  if (Lc > 1) {
+  if (Lc > 1) {  // with one leaf chunk per sequence every carry is the prior
+    ProfScope ps(P, K_FILTER_LEAF_UP, s);
     filter_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
         L.lv[0], sq, gv, y, m0, N0, (T*)W.items[1]);
-    for (int l = 1; l < Lc; ++l)
-      filter_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-          L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+  }
+  for (int l = 1; l < Lc; ++l) {
+    ProfScope ps(P, K_FILTER_UP, s);
+    filter_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+        L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
   }
   cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
-  for (int l = Lc - 1; l >= 1; --l)
+  for (int l = Lc - 1; l >= 1; --l) {
+    ProfScope ps(P, K_FILTER_DOWN, s);
     filter_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
         L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
         W.flag[l]);
+  }
+  ProfScope ps(P, K_FILTER_LEAF_DOWN, s);
   filter_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
       L.lv[0], sq, gv, y, m0, N0, (const T*)W.carry[1], W.flag[1], mf, Nf, partial, status);
 }
 
 template <typename T, int NX, int NY>
 void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
-                      const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s) {
+                      const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s,
+                      Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
   if (Lc > 1) {
+    ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
     smoother_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
         L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
-    for (int l = 1; l < Lc; ++l)
-      smoother_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-          L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+  }
+  for (int l = 1; l < Lc; ++l) {
+    ProfScope ps(P, K_SMOOTHER_UP, s);
+    smoother_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+        L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
   }
   cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
-  for (int l = Lc - 1; l >= 1; --l)
+  for (int l = Lc - 1; l >= 1; --l) {
+    ProfScope ps(P, K_SMOOTHER_DOWN, s);
     smoother_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
         L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
         W.flag[l]);
+  }
+  ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
   smoother_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
       L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status);
 }

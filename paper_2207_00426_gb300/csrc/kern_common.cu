@@ -25,7 +25,8 @@ __global__ void loglik_reduce(DevSeqs sq, const double* __restrict__ partial,
 }
 
 void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, int* status,
-                           cudaStream_t s) {
+                           cudaStream_t s, Prof* P) {
+  ProfScope ps(P, K_LOGLIK, s);
   loglik_reduce<<<sq.B, 256, 0, s>>>(sq, partial, loglik, status);
 }
 

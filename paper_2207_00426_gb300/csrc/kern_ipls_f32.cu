@@ -29,21 +29,25 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
     cudaMemcpyAsync(ms, a.init_ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(Ns, a.init_Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
   } else {
+    ProfScope ps(a.prof, K_INIT, s);
     broadcast_prior_kernel<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
         Ls.lv[0], (const T*)a.m0, (const T*)a.N0, ms, Ns);
   }
   GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
                   (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
   for (int it = 0; it < a.M; ++it) {
-    ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-        Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, ms, Ns, (const T*)a.y,
-        (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+    {
+      ProfScope ps(a.prof, K_SLR, s);
+      ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+          Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, ms, Ns, (const T*)a.y,
+          (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+    }
     enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
-                              (T*)a.mf, (T*)a.Nf, partial, status, s);
+                              (T*)a.mf, (T*)a.Nf, partial, status, s, a.prof);
     enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, ms, Ns, status,
-                                s);
+                                s, a.prof);
   }
-  if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s);
+  if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s, a.prof);
 }
 
 }  // namespace sqsm
