@@ -54,7 +54,8 @@ typedef enum {
   SQSM_ERR_NOT_PD = 4,           /* device: zero pivot in a triangular solve */
   SQSM_ERR_NONFINITE = 8,        /* device: NaN/Inf in an output             */
   SQSM_ERR_CUDA = 16,            /* a CUDA runtime call failed               */
-  SQSM_ERR_NO_MEMORY = 32        /* workspace allocation failed              */
+  SQSM_ERR_NO_MEMORY = 32,       /* workspace allocation failed              */
+  SQSM_ERR_TOO_LARGE = 64        /* problem exceeds a fixed-size buffer      */
 } sqsm_status;
 
 typedef enum { SQSM_F32 = 0, SQSM_F64 = 1 } sqsm_dtype;
@@ -199,6 +200,41 @@ int sqsm_profile_read(sqsm_ctx* ctx, int nkinds, double* ms, int* launches,
 
 /* Name of kernel family k ("" if out of range). */
 const char* sqsm_kernel_name(int k);
+
+/* The linear smoother of sqsm_lgssm_smooth for callers that cannot
+ * allocate device memory.  The paper has no counterpart of this call; it
+ * exists for code running where cudaMalloc is unavailable or forbidden (an
+ * allocator or memory-pool callback, a process whose device memory a
+ * framework reserved up front, a real-time loop that cannot afford the
+ * device synchronisation of an allocation).  Such callers cannot create an
+ * sqsm_ctx, so this call takes none and allocates nothing: its scratch
+ * buffers live in one fixed array of 32 MiB per device, part of the loaded
+ * library, held until the process exits.
+ *
+ * Arguments and results are those of sqsm_lgssm_smooth (same scan shape,
+ * so the same results), except that mf and Nf must not be NULL and there is
+ * no device status word.  The current CUDA device is used; `stream` must
+ * belong to it.
+ * - Limit: n is bounded by the scratch size (about 280 bytes per step at
+ *   FP32 and nx = 5, i.e. n up to roughly 1.2e5; half that at FP64).
+ *   Larger problems return SQSM_ERR_TOO_LARGE before any GPU work.
+ * - The first call on a device looks up the scratch array's device address
+ *   (this loads the library's device code on that device); make that first
+ *   call before any stream capture.
+ * - All calls on a device share the scratch and its contents persist
+ *   between calls; each call rewrites or clears what it reads.  Calls whose
+ *   GPU work overlaps (different streams, different host threads) race on
+ *   the scratch and must be serialised by the caller.
+ * Returns SQSM_ERR_INVALID_ARG / SQSM_ERR_UNSUPPORTED as sqsm_lgssm_smooth,
+ * SQSM_ERR_TOO_LARGE, or SQSM_ERR_CUDA. */
+int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n,
+                              const void* F, int64_t sF, const void* c,
+                              int64_t sc, const void* SQ, int64_t sSQ,
+                              const void* H, int64_t sH, const void* d,
+                              int64_t sd, const void* SR, int64_t sSR,
+                              const void* m0, const void* N0, const void* y,
+                              void* mf, void* Nf, void* ms, void* Ns,
+                              double* loglik, void* stream);
 
 /* 1 if the (nx, ny) pair is compiled into sqsm_lgssm_smooth, else 0. */
 int sqsm_supported_shape(int nx, int ny);

@@ -20,6 +20,7 @@ ERR_NOT_PD = 4
 ERR_NONFINITE = 8
 ERR_CUDA = 16
 ERR_NO_MEMORY = 32
+ERR_TOO_LARGE = 64
 F32, F64 = 0, 1
 CUBATURE, EXTENDED = 0, 1
 MODEL_CT_BEARINGS = 1
@@ -63,6 +64,9 @@ lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTE
                                   _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
 lib.sqsm_ct_linearize.restype = _int
 
+lib.sqsm_lgssm_smooth_noalloc.argtypes = ([_int, _int, _int, _i64] + [_p, _i64] * 6
+                                          + [_p] * 3 + [_p] * 4 + [_p, _p])
+lib.sqsm_lgssm_smooth_noalloc.restype = _int
 lib.sqsm_profile_enable.argtypes = [_p, _int]
 lib.sqsm_profile_enable.restype = _int
 lib.sqsm_profile_read.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int),
@@ -74,7 +78,7 @@ lib.sqsm_kernel_name.restype = ctypes.c_char_p
 EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
-            "sqsm_kernel_name"]
+            "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc"]
 
 
 class SqsmError(RuntimeError):
