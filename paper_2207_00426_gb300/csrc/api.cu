@@ -39,6 +39,7 @@ struct Workspace {
   void* Nf = nullptr;
   void* gamma[6] = {};       // IPLS linearised model F, c, SQ, H, d, SR
   void* params = nullptr;    // IPLS model constants
+  void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
   bool ipls_ready = false;
 };
 
@@ -251,7 +252,8 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
     if (!w->gamma[i]) return false;
   }
   w->params = w->mem.get(512);
-  if (!w->params) return false;
+  w->dm0 = w->mem.get(es * nx * p->B);
+  if (!w->params || !w->dm0) return false;
   w->ipls_ready = true;
   return true;
 }
@@ -454,6 +456,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   a.F = w->gamma[0]; a.c = w->gamma[1]; a.SQ = w->gamma[2];
   a.H = w->gamma[3]; a.d = w->gamma[4]; a.SR = w->gamma[5];
   a.params = w->params;
+  a.dm0 = w->dm0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   const DevSeqs sq = seqs_of(p);

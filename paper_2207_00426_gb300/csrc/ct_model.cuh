@@ -116,6 +116,21 @@ SQSM_DEV void ct_f(const CTParams<T>& P, const T* x, T* o) {
   o[4] = x[4];
 }
 
+// f(x) - x: the CT step has no position term in it, so this is exact
+// however large the position (1 - cos a = 2 sin^2(a/2)).
+template <typename T>
+SQSM_DEV void ct_f_minus_x(const CTParams<T>& P, const T* x, T* o) {
+  T S, C, ca, sa, sh, ch;
+  turn_coeffs(x[4], P.dt, S, C, ca, sa);
+  sq_sincos(T(0.5) * x[4] * P.dt, &sh, &ch);
+  const T omc = T(2) * sh * sh;
+  o[0] = S * x[2] - C * x[3];
+  o[1] = C * x[2] + S * x[3];
+  o[2] = -omc * x[2] - sa * x[3];
+  o[3] = sa * x[2] - omc * x[3];
+  o[4] = T(0);
+}
+
 // f(m + dl) - f(m) without forming the large position terms twice.
 template <typename T>
 SQSM_DEV void ct_f_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
@@ -186,12 +201,15 @@ SQSM_DEV T branch_shift(T y, T ref) {
   return twopi * sq_floor((y - ref) / twopi + T(0.5));
 }
 
-// Cubature regression of g(x) = ref + delta_g(m, x - m) about (m, N):
-// G = D N^{-1}, off = z_bar - G m, noise factor Tria([Sc, s_i / sqrt(5)]).
-// DG(m, dl, out) returns g(m + dl) - g(m); gm is g(m).
+// Cubature regression of g about (m, N): G = D N^{-1}, noise factor
+// Tria([Sc, s_i / sqrt(5)]) and the offset
+//   off = gm + dbar - G m   (subtract_Gm: absolute form z_bar - G m), or
+//   off = gm + dbar         (deviation form, gm already relative),
+// where dbar is the mean of g(m + dl_i) - g(m).  DG(m, dl, out) returns
+// g(m + dl) - g(m).
 template <typename T, int NO, typename DG>
-SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, const T* Sc, DG dg, T* G,
-                               T* off, T* Sout) {
+SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtract_Gm,
+                               const T* Sc, DG dg, T* G, T* off, T* Sout) {
   constexpr int NX = 5;
   const T sq = sq_sqrt(T(NX));
   T D[NO * NX], Hs[NO * NX], dsum[NO];
@@ -221,8 +239,10 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, const T* Sc,
 #pragma unroll
   for (int r = 0; r < NO; ++r) {
     T s = gm[r] + dbar[r];
+    if (subtract_Gm) {
 #pragma unroll
-    for (int k = 0; k < NX; ++k) s -= D[r * NX + k] * m[k];
+      for (int k = 0; k < NX; ++k) s -= D[r * NX + k] * m[k];
+    }
     off[r] = s;
 #pragma unroll
     for (int k = 0; k < NX; ++k) G[r * NX + k] = D[r * NX + k];
@@ -243,12 +263,20 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, const T* Sc,
 // One thread per leaf chunk of the filter plan: for every step s of the
 // chunk, the transition is linearised at state row s + b (k - 1) and the
 // observation at row s + b + 1 (k) of the nominal trajectory (ms, Ns).
+//
+// centered = 0: eq. Gamma-s as printed (c = z_bar - F m, d = z_bar - H m).
+// centered = 1: the same linear model written for the deviation
+// dx_k = x_k - m_k from the nominal trajectory, which keeps every scan
+// quantity small in FP32 however large the positions:
+//   dx_k = F dx_{k-1} + c~ + q,  c~ = z_bar_x - m_k
+//        = (m_{k-1} - m_k) + (f(m_{k-1}) - m_{k-1}) + dbar_x,
+//   y_k  = H dx_k + d~ + v,      d~ = H m_k + d = z_bar_y (+ branch shift).
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int linearization,
-              const T* __restrict__ ms, const T* __restrict__ Ns, const T* __restrict__ y,
-              T* __restrict__ F, T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H,
-              T* __restrict__ d, T* __restrict__ SRo) {
+              int centered, const T* __restrict__ ms, const T* __restrict__ Ns,
+              const T* __restrict__ y, T* __restrict__ F, T* __restrict__ c,
+              T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d, T* __restrict__ SRo) {
   const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (ch >= lv.n_chunks) return;
   constexpr int NX = 5, NY = 2;
@@ -264,21 +292,29 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
     load<T, NX>(ms + rp * NX, m);
     load_lower<T, NX>(Ns + rp * NX * NX, N);
     T Fm[NX * NX], cm[NX], Sl[NX * NX];
-    if (linearization == 0) {
-      T fm[NX];
+    T fm[NX];    // f(m_{k-1}) (absolute) or f(m_{k-1}) - m_k (deviation form)
+    if (centered) {
+      T mk[NX];
+      load<T, NX>(ms + rk * NX, mk);
+      ct_f_minus_x(P, m, fm);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) fm[r] += m[r] - mk[r];
+    } else {
       ct_f(P, m, fm);
-      cubature_regress<T, NX>(m, N, fm, P.SQ,
+    }
+    if (linearization == 0) {
+      cubature_regress<T, NX>(m, N, fm, !centered, P.SQ,
                               [&](const T* mm_, const T* dl, T* o) { ct_f_delta(P, mm_, dl, o); },
                               Fm, cm, Sl);
     } else {
-      T fm[NX];
-      ct_f(P, m, fm);
       ct_jac_f(P, m, Fm);
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         T sacc = fm[r];
+        if (!centered) {
 #pragma unroll
-        for (int k = 0; k < NX; ++k) sacc -= Fm[r * NX + k] * m[k];
+          for (int k = 0; k < NX; ++k) sacc -= Fm[r * NX + k] * m[k];
+        }
         cm[r] = sacc;
       }
 #pragma unroll
@@ -295,7 +331,7 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
     ct_h(P, m, hm);
     if (linearization == 0) {
       const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
-      cubature_regress<T, NY>(m, N, hm, Sr,
+      cubature_regress<T, NY>(m, N, hm, !centered, Sr,
                               [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
                               Hm, dm, So);
     } else {
@@ -303,8 +339,10 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
         T sacc = hm[r];
+        if (!centered) {
 #pragma unroll
-        for (int k = 0; k < NX; ++k) sacc -= Hm[r * NX + k] * m[k];
+          for (int k = 0; k < NX; ++k) sacc -= Hm[r * NX + k] * m[k];
+        }
         dm[r] = sacc;
       }
       So[0] = P.sigma; So[1] = T(0); So[2] = T(0); So[3] = P.sigma;
@@ -334,6 +372,17 @@ broadcast_prior_kernel(DevLevel lv, const T* __restrict__ m0, const T* __restric
     store<T, NX>(ms + e * NX, m);
     store_lower<T, NX>(Ns + e * NX * NX, N);
   }
+}
+
+// Prior of the deviation model: dm0[b] = m0[b] - m_0 (nominal row 0 of b).
+template <typename T, int NX>
+__global__ void center_prior_kernel(DevSeqs sq, const T* __restrict__ m0,
+                                    const T* __restrict__ ms, T* __restrict__ dm0) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= sq.B) return;
+  const int64_t row0 = sq.offsets[b] + b;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) dm0[(int64_t)b * NX + i] = m0[(int64_t)b * NX + i] - ms[row0 * NX + i];
 }
 
 }  // namespace sqsm

@@ -35,7 +35,7 @@ struct IplsArgs {
   void *ms, *Ns;
   double* loglik;
   // workspace
-  void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params;
+  void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params, *dm0;
   Prof* prof;   // optional per-kernel events
 };
 

@@ -98,7 +98,7 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
 template <typename T, int NX, int NY>
 void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
                       const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s,
-                      Prof* P = nullptr) {
+                      Prof* P = nullptr, const T* nominal = nullptr) {
   const int Lc = (int)L.lv.size();
   if (Lc > 1) {
     ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
@@ -119,7 +119,7 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
   }
   ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
   smoother_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-      L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status);
+      L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status, nominal);
 }
 
 // Record sizes (elements) of the scan buffers.

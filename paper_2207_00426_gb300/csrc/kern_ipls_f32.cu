@@ -13,7 +13,7 @@ void ipls_params_f32(const IplsArgs& a, cudaStream_t s) {
 void ct_linearize_f32(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
   using T = float;
   ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-      Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, (const T*)a.ms,
+      Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, 0, (const T*)a.ms,
       (const T*)a.Ns, (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
 }
 
@@ -35,17 +35,26 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   }
   GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
                   (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
+  // Each iteration smooths the linearised model in deviation coordinates
+  // dx_k = x_k - m_k about its own nominal trajectory m (the previous
+  // smoothing means, held in ms): the SLR writes c~, d~ of that form, the
+  // prior becomes m0 - m_0, and the smoother adds m back when it writes ms.
   for (int it = 0; it < a.M; ++it) {
     {
       ProfScope ps(a.prof, K_SLR, s);
       ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-          Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, ms, Ns, (const T*)a.y,
-          (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+          Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, 1, ms, Ns,
+          (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
     }
-    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
+    {
+      ProfScope ps(a.prof, K_INIT, s);
+      center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, ms,
+                                                                     (T*)a.dm0);
+    }
+    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0,
                               (T*)a.mf, (T*)a.Nf, partial, status, s, a.prof);
     enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, ms, Ns, status,
-                                s, a.prof);
+                                s, a.prof, ms);
   }
   if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s, a.prof);
 }

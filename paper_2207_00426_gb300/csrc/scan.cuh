@@ -287,13 +287,16 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
 }
 
 // Leaf down-sweep: sequential square-root RTS steps from the chunk's carry
-// (m^s, N^s just after the chunk), writing m^s, N^s.
+// (m^s, N^s just after the chunk), writing m^s, N^s.  With `nominal` set the
+// scan runs on deviations from a nominal trajectory and the written mean is
+// nominal + deviation (nominal may alias ms: each row is read, then written,
+// by the same thread).
 template <typename T, int NX, int NY>
 __global__ void __launch_bounds__(kBlock)
 smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ mf,
                    const T* __restrict__ Nf, const T* __restrict__ carry,
-                   const int* __restrict__ flag, T* __restrict__ ms, T* __restrict__ Ns,
-                   int* status) {
+                   const int* __restrict__ flag, T* ms, T* __restrict__ Ns, int* status,
+                   const T* nominal) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
@@ -325,7 +328,14 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict
       smoother_element<T, NX, NY>(g, m, N, el);
       smoother_apply<T, NX>(el, gm, Dm);
     }
-    store<T, NX>(ms + e * NX, gm);
+    if (nominal) {
+      T out[NX];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) out[i] = nominal[e * NX + i] + gm[i];
+      store<T, NX>(ms + e * NX, out);
+    } else {
+      store<T, NX>(ms + e * NX, gm);
+    }
     store_lower<T, NX>(Ns + e * NX * NX, Dm);
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);

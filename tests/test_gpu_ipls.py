@@ -123,8 +123,10 @@ def test_full_size_chain_f32(B, ctx):
     ms10, Ns10, ll10 = B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, 0, dt=d["dt"])
     _, _, msl, Nsl, lll = B.sqsm_lgssm_smooth(ctx, *G, m0[0], N0[0], y)
     torch.cuda.synchronize()
-    # one more IPLS iteration == linearise + linear smoother, on the GPU
-    assert torch.equal(msl, ms10) and abs(lll.item() - ll10.item()) < 1e-9 * abs(ll10.item())
+    # one more IPLS iteration (smoothed in deviation coordinates) agrees with
+    # linearise (printed absolute form) + linear smoother, on the GPU
+    assert rel_mean_err(msl.double().cpu().numpy(), ms10.double().cpu().numpy()) < 1e-4
+    assert abs(lll.item() - ll10.item()) < 1e-5 * abs(ll10.item())
     # sampled SLR steps against the oracle
     ct = OM.CTBearings(d["theta"], dt=d["dt"])
     msn, Nsn = ms9.double().cpu().numpy(), Ns9.double().cpu().numpy()
