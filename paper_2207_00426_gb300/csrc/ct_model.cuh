@@ -19,10 +19,11 @@
 //    Tria([S, s_1/sqrt(nx), ..., s_nx/sqrt(nx)]) with
 //    s_i = (Z_i^+ + Z_i^-)/2 - z_bar (the residual Z_i - z_bar - F(X_i - m)
 //    of both points of pair i); this needs no downdate and cannot fail.
-// Transformed points are evaluated as differences f(m + delta) - f(m) in a
-// form without cancellation against large positions, and bearings of the
-// points as the signed angle from the mean's line of sight, which also takes
-// them on the branch nearest h(m).  d absorbs the 2 pi multiple that moves y
+// Transformed points are evaluated as differences from the mean's image in
+// a form without cancellation (for f, of its non-identity part f(x) - x, whose
+// regression is added to I), and bearings of the points as the signed angle
+// from the mean's line of sight, which also takes them on the branch nearest
+// h(m).  d absorbs the 2 pi multiple that moves y
 // onto that branch.
 #pragma once
 
@@ -131,18 +132,31 @@ SQSM_DEV void ct_f_minus_x(const CTParams<T>& P, const T* x, T* o) {
   o[4] = T(0);
 }
 
-// f(m + dl) - f(m) without forming the large position terms twice.
+// g(m + dl) - g(m) for g(x) = f(x) - x, the part of the CT step that is not
+// the identity, written so that no term cancels against a larger one:
+//   positions:  K(w_x) dl_v + (K(w_x) - K(w_m)) v_m,  K = [[S, -C], [C, S]],
+//   velocities: (R(a_x) - I) dl_v + R(a_m) (R(da) - I) v_m,
+//   with R(b) - I = [[-2 sin^2(b/2), -sin b], [sin b, -2 sin^2(b/2)]] and
+//   da = dl_w dt formed from the small increment itself; omega: 0.
+// (The cubature regression of f is then I + the regression of g.)
 template <typename T>
-SQSM_DEV void ct_f_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
-  T Sm, Cm, cam, sam, Sx, Cx, cax, sax;
-  turn_coeffs(m[4], P.dt, Sm, Cm, cam, sam);
-  turn_coeffs(m[4] + dl[4], P.dt, Sx, Cx, cax, sax);
-  const T vx = m[2] + dl[2], vy = m[3] + dl[3];
-  o[0] = dl[0] + (Sx * vx - Cx * vy) - (Sm * m[2] - Cm * m[3]);
-  o[1] = dl[1] + (Cx * vx + Sx * vy) - (Cm * m[2] + Sm * m[3]);
-  o[2] = (cax * vx - sax * vy) - (cam * m[2] - sam * m[3]);
-  o[3] = (sax * vx + cax * vy) - (sam * m[2] + cam * m[3]);
-  o[4] = dl[4];
+SQSM_DEV void ct_g_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
+  T Sm, Cm, cam, sam, Sx, Cx, cax, sax, shx, chx, sd, cd, shd, chd;
+  const T dt = P.dt;
+  turn_coeffs(m[4], dt, Sm, Cm, cam, sam);
+  turn_coeffs(m[4] + dl[4], dt, Sx, Cx, cax, sax);
+  sq_sincos(T(0.5) * (m[4] + dl[4]) * dt, &shx, &chx);
+  const T omx = T(2) * shx * shx;
+  const T da = dl[4] * dt;
+  sq_sincos(da, &sd, &cd);
+  sq_sincos(T(0.5) * da, &shd, &chd);
+  const T omd = T(2) * shd * shd;
+  const T ux = -omd * m[2] - sd * m[3], uy = sd * m[2] - omd * m[3];
+  o[0] = (Sx * dl[2] - Cx * dl[3]) + ((Sx - Sm) * m[2] - (Cx - Cm) * m[3]);
+  o[1] = (Cx * dl[2] + Sx * dl[3]) + ((Cx - Cm) * m[2] + (Sx - Sm) * m[3]);
+  o[2] = (-omx * dl[2] - sax * dl[3]) + (cam * ux - sam * uy);
+  o[3] = (sax * dl[2] - omx * dl[3]) + (sam * ux + cam * uy);
+  o[4] = T(0);
 }
 
 template <typename T>
@@ -201,13 +215,15 @@ SQSM_DEV T branch_shift(T y, T ref) {
   return twopi * sq_floor((y - ref) / twopi + T(0.5));
 }
 
-// Cubature regression of g about (m, N): G = D N^{-1}, noise factor
-// Tria([Sc, s_i / sqrt(5)]) and the offset
+// Cubature regression of a function about (m, N): G = D N^{-1} (+ I when
+// ADD_I), noise factor Tria([Sc, s_i / sqrt(5)]) and the offset
 //   off = gm + dbar - G m   (subtract_Gm: absolute form z_bar - G m), or
 //   off = gm + dbar         (deviation form, gm already relative),
-// where dbar is the mean of g(m + dl_i) - g(m).  DG(m, dl, out) returns
-// g(m + dl) - g(m).
-template <typename T, int NO, typename DG>
+// where dbar is the mean of the point differences.  DG(m, dl, out) returns
+// the difference at m + dl; with ADD_I it returns that difference minus dl
+// (the regression of x itself is exactly I, and the pair means and
+// residuals are unchanged because the +-dl of a pair cancel).
+template <typename T, int NO, bool ADD_I, typename DG>
 SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtract_Gm,
                                const T* Sc, DG dg, T* G, T* off, T* Sout) {
   constexpr int NX = 5;
@@ -236,6 +252,11 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 #pragma unroll
   for (int r = 0; r < NO; ++r) dbar[r] = dsum[r] / T(2 * NX);
   rsolve<T, NO, NX>(D, N);           // G = D N^{-1}
+  if constexpr (ADD_I) {
+    static_assert(NO == NX, "identity split needs a square regression");
+#pragma unroll
+    for (int r = 0; r < NO; ++r) D[r * NX + r] += T(1);
+  }
 #pragma unroll
   for (int r = 0; r < NO; ++r) {
     T s = gm[r] + dbar[r];
@@ -303,9 +324,9 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
       ct_f(P, m, fm);
     }
     if (linearization == 0) {
-      cubature_regress<T, NX>(m, N, fm, !centered, P.SQ,
-                              [&](const T* mm_, const T* dl, T* o) { ct_f_delta(P, mm_, dl, o); },
-                              Fm, cm, Sl);
+      cubature_regress<T, NX, true>(m, N, fm, !centered, P.SQ,
+                                    [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, mm_, dl, o); },
+                                    Fm, cm, Sl);
     } else {
       ct_jac_f(P, m, Fm);
 #pragma unroll
@@ -331,7 +352,7 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
     ct_h(P, m, hm);
     if (linearization == 0) {
       const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
-      cubature_regress<T, NY>(m, N, hm, !centered, Sr,
+      cubature_regress<T, NY, false>(m, N, hm, !centered, Sr,
                               [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
                               Hm, dm, So);
     } else {

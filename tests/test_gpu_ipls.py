@@ -143,3 +143,27 @@ def test_full_size_chain_f32(B, ctx):
     ref = sqrt_filter_smoother(*Gn, d["y"], d["m0"], d["N0"])
     assert rel_mean_err(msl.double().cpu().numpy(), ref[2]) < 1e-4
     assert abs(lll.item() - ref[4]) < 1e-5 * abs(ref[4])
+
+
+def test_full_size_fp32_accuracy_against_fp64(B, ctx):
+    """n = 100000, cubature: FP32 smoothed means against the FP64 build of
+    the same kernels (itself equal to the oracle at every size the oracle can
+    run).  The workload is far from converged at M = 10 (its trajectory still
+    moves by ~100 between iterations), which amplifies any perturbation: the
+    FP64 run itself moves 3.6e-5 under 1e-7 relative noise on y.  Measured:
+    4e-6 (M = 1), 1.7e-5 (M = 2), 1.7e-4 (M = 10)."""
+    n = 100_000
+    d = W.ct_sequence(n=n, seed=1)
+    res = {}
+    for M, tol in ((1, 2e-5), (2, 1e-4), (10, 5e-4)):
+        out = []
+        for dt in (torch.float32, torch.float64):
+            ms, Ns, ll = B.sqsm_ipls_smooth(ctx, d["theta"], _dev(d["y"], dt), [0, n],
+                                            _dev(d["m0"][None], dt), _dev(d["N0"][None], dt), M, 0,
+                                            dt=d["dt"])
+            torch.cuda.synchronize()
+            out.append((ms.double().cpu().numpy(), ll.item()))
+        err = rel_mean_err(out[0][0], out[1][0])
+        res[M] = err
+        assert err < tol, (M, err)
+        assert abs(out[0][1] - out[1][1]) < 2e-5 * abs(out[1][1])
