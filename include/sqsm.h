@@ -166,6 +166,37 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                      const void* init_Ns, void* ms, void* Ns, double* loglik,
                      void* stream);
 
+/* Negative pseudo log-likelihood and its gradient with respect to theta
+ * through the fixed point of Alg. 3 (Sec. 5.2: eq. implicity_function_theorem
+ * and Alg. 4, in reverse / vector-Jacobian form), summed over the batch.
+ *
+ * Runs M iterations of Alg. 3 (as sqsm_ipls_smooth; M = 0 takes
+ * init_ms/init_Ns as the trajectory), linearises once more at the result
+ * n* and filters/smooths that model (Sec. 5.1: nll = -sum_b l_b of this
+ * last filter), then iterates the adjoint fixed point
+ *   lambda <- (dKS/dn)^T lambda + d nll/dn      (adj_iters times, from 0)
+ * and returns grad = d nll/d theta + (dKS/d theta)^T lambda.  The adjoint
+ * pass is hand-written: reverse recurrences of the smoother and the filter
+ * (as parallel scans), the Cholesky adjoint of the smoother factors and the
+ * adjoint of the cubature regression.  Only SQSM_CUBATURE is supported
+ * (SQSM_ERR_UNSUPPORTED otherwise).
+ *
+ *   ms, Ns      outputs: the trajectory n* (state layout), as
+ *               sqsm_ipls_smooth with the same M.
+ *   nll         device double[1]; grad device double[3] (theta order).
+ *   adj_change  device double[1] or NULL: max-norm change of lambda in the
+ *               last adjoint iteration relative to its max-norm (a
+ *               convergence measure; the gradient assumes n* is a fixed
+ *               point and lambda converged).
+ * Other arguments as sqsm_ipls_smooth. */
+int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
+                       const double* theta, int linearization, int M,
+                       int adj_iters, int64_t batch, const int64_t* offsets,
+                       const void* y, const void* m0, const void* N0,
+                       const void* init_ms, const void* init_Ns, void* ms,
+                       void* Ns, double* nll, double* grad, double* adj_change,
+                       void* stream);
+
 /* Statistical linear regression of a compiled-in model about a nominal
  * trajectory (one application of Sec. 4.2 / 4.3 to every step, the first
  * half of one iteration of Alg. 3).  Same batch layout as

@@ -64,6 +64,9 @@ lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTE
                                   _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
 lib.sqsm_ct_linearize.restype = _int
 
+lib.sqsm_ipls_nll_grad.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
+                                   _int, _int, _int, _i64, ctypes.POINTER(_i64)] + [_p] * 10 + [_p]
+lib.sqsm_ipls_nll_grad.restype = _int
 lib.sqsm_lgssm_smooth_noalloc.argtypes = ([_int, _int, _int, _i64] + [_p, _i64] * 6
                                           + [_p] * 3 + [_p] * 4 + [_p, _p])
 lib.sqsm_lgssm_smooth_noalloc.restype = _int
@@ -78,7 +81,7 @@ lib.sqsm_kernel_name.restype = ctypes.c_char_p
 EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
-            "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc"]
+            "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad"]
 
 
 class SqsmError(RuntimeError):
@@ -264,3 +267,35 @@ def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt
                                *[_ptr(o, dtp) for o in out], _stream())
     ctx.check(rc)
     return tuple(out)
+
+
+def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, sensors=None,
+                       init_ms=None, init_Ns=None, ms=None, Ns=None, nll=None, grad=None,
+                       change=None):
+    """Call sqsm_ipls_nll_grad (cubature).  Returns (nll, grad, change, ms,
+    Ns) as device tensors (nll [1], grad [3], change [1] float64)."""
+    import numpy as np
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    if sensors is None:
+        sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    off, batch = _offsets(offsets)
+    rows = int(off[batch]) + batch
+    dev = y.device
+    if ms is None:
+        ms = torch.empty((rows, 5), dtype=dtp, device=dev)
+    if Ns is None:
+        Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
+    f64 = torch.float64
+    nll = torch.empty(1, dtype=f64, device=dev) if nll is None else nll
+    grad = torch.empty(3, dtype=f64, device=dev) if grad is None else grad
+    change = torch.empty(1, dtype=f64, device=dev) if change is None else change
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = _model(dt, np.asarray(sensors))
+    rc = lib.sqsm_ipls_nll_grad(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), int(adj_iters),
+                                batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"),
+                                _ptr(init_ms, dtp, "init_ms"), _ptr(init_Ns, dtp, "init_Ns"),
+                                _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"), _ptr(nll, f64, "nll"),
+                                _ptr(grad, f64, "grad"), _ptr(change, f64, "change"), _stream())
+    ctx.check(rc)
+    return nll, grad, change, ms, Ns

@@ -1,0 +1,96 @@
+// Enqueue of one NLL + gradient evaluation (forward IPLS, the linearisation
+// pass at the final trajectory, and the fixed-point adjoint iterations).
+#pragma once
+
+#include "adjoint_kernels.cuh"
+#include "dispatch.h"
+
+namespace sqsm {
+
+template <typename T>
+void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const ScanBuffers& Wf,
+                 const LevelSet& Ls, const ScanBuffers& Ws, const ScanBuffers& Wa, DevSeqs sq,
+                 double* partial, int* status, cudaStream_t s) {
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size, MREC = MapRec<NX>::size;
+  const int64_t rows = Ls.n_items[0];
+  // 1. Alg. 3 for M iterations: the nominal trajectory lands in a.ms / a.Ns.
+  IplsArgs fw = a;
+  fw.loglik = nullptr;
+  if (a.M > 0) {
+    if (sizeof(T) == 4) ipls_enqueue_f32(fw, Lf, Wf, Ls, Ws, sq, partial, status, s);
+    else ipls_enqueue_f64(fw, Lf, Wf, Ls, Ws, sq, partial, status, s);
+  } else {
+    cudaMemcpyAsync(a.ms, a.init_ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(a.Ns, a.init_Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
+  }
+  // 2. linearise at it (printed absolute form), filter and smoother once more,
+  //    and the pseudo log-likelihood of that linearisation.
+  cudaMemcpyAsync(g.nom_m, a.ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
+  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+      Lf.lv[0], sq, (const CTParams<T>*)a.params, 0, 0, (const T*)g.nom_m, (const T*)g.nom_N,
+      (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+  GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
+                  (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
+  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
+                            (T*)a.mf, (T*)a.Nf, partial, status, s);
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, (T*)g.ms2,
+                              (T*)g.Ns2, status, s);
+  enqueue_loglik_reduce(sq, partial, g.ll, status, s);
+  adj_nll_kernel<<<1, 1, 0, s>>>(sq.B, g.ll, -1.0, g.nll);
+  // 3. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)
+  AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F, a.c, a.SQ, a.H, a.d, a.SR,
+             g.dir, g.dfilt, g.gbar};
+  const T lbar = T(-1);
+  T* lam_a = (T*)g.lam_a;
+  T* lam_b = (T*)g.lam_b;
+  cudaMemsetAsync(lam_a, 0, sizeof(T) * X * rows, s);
+  const int Lc = (int)Lf.lv.size();
+  for (int it = 0; it < g.iters; ++it) {
+    adj_direct_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, (const T*)g.Ns2, lam_a,
+                                                               (T*)g.dir);
+    // smoother adjoint: forward-in-time scan of maps
+    if (Lc > 1) {
+      adj_smoother_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab,
+                                                                             (T*)Wa.items[1]);
+      for (int l = 1; l < Lc; ++l)
+        adj_up<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+    }
+    cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
+    for (int l = Lc - 1; l >= 1; --l)
+      adj_down<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+          Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+          (T*)Wa.carry[l], Wa.flag[l]);
+    adj_smoother_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+        Lf.lv[0], sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
+    // filter adjoint: backward-in-time scan of maps
+    if (Lc > 1) {
+      adj_filter_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab, lbar,
+                                                                           (T*)Wa.items[1]);
+      for (int l = 1; l < Lc; ++l)
+        adj_up<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+    }
+    cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
+    for (int l = Lc - 1; l >= 1; --l)
+      adj_down<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+          Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+          (T*)Wa.carry[l], Wa.flag[l]);
+    adj_filter_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
+        Lf.lv[0], sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
+    // SLR adjoint -> next cotangent of the nominal trajectory, theta partials
+    adj_slr_kernel<T><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
+        Ls.lv[0], sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
+    if (it + 1 == g.iters && g.change)
+      adj_change_reduce<T><<<1, 256, 0, s>>>(X * rows, lam_b, lam_a, g.change);
+    T* t = lam_a;
+    lam_a = lam_b;
+    lam_b = t;
+  }
+  if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(Ls.lv[0].n_chunks, g.th_partial, 1.0, g.grad);
+  else cudaMemsetAsync(g.grad, 0, 3 * sizeof(double), s);
+  (void)MREC;
+}
+
+}  // namespace sqsm

@@ -1,0 +1,633 @@
+// Reverse-mode adjoint of one iteration of Alg. 3 and of the pseudo
+// log-likelihood, for the gradient of Sec. 5.2 (eq. implicity_function_theorem,
+// Alg. 4) in its reverse (vector-Jacobian) form:
+//   lambda <- (dKS/dn)^T lambda + (d l/dn)^T   (fixed point),
+//   d l/d theta = (d l/d theta)^T + (dKS/d theta)^T lambda.
+//
+// One reverse pass, with cotangents lambda on the smoother output
+// (m^s_k, N^s_k) and lbar on the log-likelihood, runs in covariance form
+// (the square-root and covariance recursions are the same function):
+//  1. N^s = chol(P^s): P^s-bar = sym(L^{-T} Phi(L^T L-bar) L^{-1}), Phi = lower
+//     triangle with half diagonal (the factors are full rank here);
+//  2. the RTS recursion read backwards is a forward linear recurrence
+//     x_{k+1} = (G_k^T m, G_k^T P G_k) + direct_{k+1};
+//  3. local VJP of each RTS step;
+//  4. the filter recursion read backwards is a backward linear recurrence
+//     x_{k-1} = (A_k^T m + s_k, A_k^T P A_k + sym(A_k^T m w_k^T) + S_k) with
+//     A_k = (I - K_k H_k) F_{k-1}, w_k = F^T H^T S_k^{-1} v_k and sources from
+//     lbar and from step 3;
+//  5. local VJP of each Kalman step (-> linearised-model cotangents) and of
+//     the cubature SLR (-> nominal-trajectory cotangents and theta).
+// Both recurrences use one family of affine maps
+//   x = (m, P) -> (B^T m + s, B^T P B + sym(B^T m r^T) + S),
+// closed under composition, so they run as the same segmented
+// reduce-then-scan as the forward filter and smoother (no thread waits on
+// another).  The first map of the forward recurrence and the last of the
+// backward one absorb their boundary value (B = 0), which makes a chunk that
+// holds them independent of its carry.
+#pragma once
+
+#include "ct_model.cuh"
+
+namespace sqsm {
+
+template <int NX> struct MapRec {
+  static constexpr int B = 0, r = NX * NX, s = NX * NX + NX, S = NX * NX + 2 * NX,
+                       size = 2 * NX * NX + 2 * NX;
+};
+template <int NX> struct XRec {
+  static constexpr int m = 0, P = NX, size = NX + NX * NX;
+};
+
+// x_out = map(x_in)
+template <typename T, int NX>
+SQSM_DEV void map_apply(const T* mp, const T* xin, T* xout) {
+  using R = MapRec<NX>;
+  T bm[NX];
+  mtv<T, NX, NX>(mp + R::B, xin, bm);             // B^T m
+  T BP[NX * NX];
+  mtm<T, NX, NX, NX>(mp + R::B, xin + NX, BP);    // B^T P
+#pragma unroll
+  for (int i = 0; i < NX; ++i) xout[i] = bm[i] + mp[R::s + i];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += BP[i * NX + k] * mp[R::B + k * NX + j];
+      xout[NX + i * NX + j] =
+          acc + T(0.5) * (bm[i] * mp[R::r + j] + mp[R::r + i] * bm[j]) + mp[R::S + i * NX + j];
+    }
+}
+
+// out = second o first (first applied first):
+//   B = B_f B_s, r = B_s^T r_f + r_s, s = B_s^T s_f + s_s,
+//   S = B_s^T S_f B_s + sym(B_s^T s_f r_s^T) + S_s.
+template <typename T, int NX>
+SQSM_DEV void map_compose(const T* f, const T* sc, T* out) {
+  using R = MapRec<NX>;
+  mm<T, NX, NX, NX>(f + R::B, sc + R::B, out + R::B);
+  T t[NX];
+  mtv<T, NX, NX>(sc + R::B, f + R::r, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) out[R::r + i] = t[i] + sc[R::r + i];
+  T bs[NX];
+  mtv<T, NX, NX>(sc + R::B, f + R::s, bs);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) out[R::s + i] = bs[i] + sc[R::s + i];
+  T BS[NX * NX];
+  mtm<T, NX, NX, NX>(sc + R::B, f + R::S, BS);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += BS[i * NX + k] * sc[R::B + k * NX + j];
+      out[R::S + i * NX + j] =
+          acc + T(0.5) * (bs[i] * sc[R::r + j] + sc[R::r + i] * bs[j]) + sc[R::S + i * NX + j];
+    }
+}
+
+// Fold a boundary value into a map: the result ignores its input.
+template <typename T, int NX>
+SQSM_DEV void map_make_constant(T* mp, const T* x0) {
+  using R = MapRec<NX>;
+  T x1[XRec<NX>::size];
+  map_apply<T, NX>(mp, x0, x1);
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) {
+    mp[R::B + i] = T(0);
+    mp[R::S + i] = x1[NX + i];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    mp[R::r + i] = T(0);
+    mp[R::s + i] = x1[i];
+  }
+}
+
+// A A^T for lower A.
+template <typename T, int N>
+SQSM_DEV void gram_lower(const T* A, T* P) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k <= i && k <= j) s += A[i * N + k] * A[j * N + k];
+      P[i * N + j] = s;
+    }
+}
+
+// Inverse of a lower-triangular N x N matrix (lower).
+template <typename T, int N>
+SQSM_DEV void inv_lower(const T* L, T* Li) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T col[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) col[i] = i == j ? T(1) : T(0);
+    lsolve<T, N>(L, col);
+#pragma unroll
+    for (int i = 0; i < N; ++i) Li[i * N + j] = col[i];
+  }
+}
+
+// (F N) with N lower (NX x NX), then N^- = Tria([F N, SQ]).
+template <typename T, int NX>
+SQSM_DEV void predict_factor(const T* F, const T* N, const T* SQ, T* Nm) {
+  T P[NX * 2 * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < NX; ++k) s += F[i * NX + k] * N[k * NX + j];
+      P[i * 2 * NX + j] = s;
+      P[i * 2 * NX + NX + j] = SQ[i * NX + j];
+    }
+  tria<T, NX, 2 * NX>(P);
+  take_lower<T, NX, 2 * NX>(P, Nm);
+}
+
+// Covariance quantities of the Kalman step k (t = k-1) from the filter
+// output at k-1: m^- = F m + c, P^- = N^- N^-^T, S = H P^- H^T + Omega,
+// W = S^{-1}, U = P^- H^T, K = U W, v = y - H m^- - d.
+template <typename T, int NX, int NY>
+struct KfQ {
+  T mp[NX], Pp[NX * NX], W[NY * NY], U[NX * NY], K[NX * NY], v[NY], Pprev[NX * NX];
+
+  SQSM_DEV void compute(const Gamma<T, NX, NY>& g, const T* y, const T* mprev, const T* Nprev) {
+    mv<T, NX, NX>(g.F, mprev, mp);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
+    gram_lower<T, NX>(Nprev, Pprev);
+    T Nm[NX * NX];
+    predict_factor<T, NX>(g.F, Nprev, g.SQ, Nm);
+    gram_lower<T, NX>(Nm, Pp);
+    mmt<T, NX, NX, NY>(Pp, g.H, U);                  // P^- H^T
+    T S[NY * NY];
+    mm<T, NY, NX, NY>(g.H, U, S);                    // H P^- H^T
+    T R[NY * NY];
+    gram_lower<T, NY>(g.SR, R);
+#pragma unroll
+    for (int i = 0; i < NY * NY; ++i) S[i] += R[i];
+    // W = S^{-1} through its Cholesky factor
+    T Ls[NY * NY];
+#pragma unroll
+    for (int i = 0; i < NY * NY; ++i) Ls[i] = S[i];
+    chol_inplace<NY>(Ls);
+    T Li[NY * NY];
+    inv_lower<T, NY>(Ls, Li);
+    mtm<T, NY, NY, NY>(Li, Li, W);
+    mm<T, NX, NY, NY>(U, W, K);
+#pragma unroll
+    for (int i = 0; i < NY; ++i) {
+      T s = y[i] - g.d[i];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) s -= g.H[i * NX + k] * mp[k];
+      v[i] = s;
+    }
+  }
+
+  template <int N>
+  SQSM_DEV static void chol_inplace(T* A) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = A[j * N + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[j * N + k] * A[j * N + k];
+      const T d = sq_sqrt(s);
+      A[j * N + j] = d;
+#pragma unroll
+      for (int i = j + 1; i < N; ++i) {
+        T t = A[i * N + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) t -= A[i * N + k] * A[j * N + k];
+        A[i * N + j] = t / d;
+      }
+#pragma unroll
+      for (int i = 0; i < j; ++i) A[i * N + j] = T(0);
+    }
+  }
+};
+
+// Linearised-model cotangent record of one step: F | c | Lambda | H | d | Omega.
+template <int NX, int NY> struct GRec {
+  static constexpr int F = 0, c = NX * NX, L = NX * NX + NX, H = 2 * NX * NX + NX,
+                       d = 2 * NX * NX + NX + NY * NX, O = 2 * NX * NX + NX + NY * NX + NY,
+                       size = 2 * NX * NX + NX + NY * NX + NY + NY * NY;
+};
+
+// ---------------------------------------------------------------------------
+// Step 1: direct cotangents of the smoother output, per state row.
+// ---------------------------------------------------------------------------
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+adj_direct_kernel(int64_t rows, const T* __restrict__ Ns, const T* __restrict__ lam,
+                  T* __restrict__ dir) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows) return;
+  constexpr int X = XRec<NX>::size;
+  T L[NX * NX], Lb[NX * NX];
+  load_lower<T, NX>(Ns + e * NX * NX, L);
+  load_lower<T, NX>(lam + e * X + NX, Lb);
+  T M[NX * NX];
+  mtm<T, NX, NX, NX>(L, Lb, M);                    // L^T Lbar
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) M[i * NX + j] = j < i ? M[i * NX + j] : (j == i ? T(0.5) * M[i * NX + j] : T(0));
+  T Li[NX * NX];
+  inv_lower<T, NX>(L, Li);
+  T A[NX * NX], P[NX * NX];
+  mtm<T, NX, NX, NX>(Li, M, A);                    // L^{-T} Phi
+  mm<T, NX, NX, NX>(A, Li, P);                     // ... L^{-1}
+  T* o = dir + e * X;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) o[i] = lam[e * X + i];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) o[NX + i * NX + j] = T(0.5) * (P[i * NX + j] + P[j * NX + i]);
+}
+
+// ---------------------------------------------------------------------------
+// Map builders (one per time step s of sequence b; state rows e = s + b
+// (k - 1) and e + 1 (k)).
+// ---------------------------------------------------------------------------
+struct AdjCtx {
+  int64_t gF, gc, gL, gH, gd, gO;   // unused placeholder for layout clarity
+};
+
+// Smoother gain G_k = P^f_k F^T (P^-_{k+1})^{-1} and the intermediate
+// quantities of the RTS step, from the filter output at row e.
+template <typename T, int NX, int NY>
+struct RtsQ {
+  T Pf[NX * NX], mp[NX], Pp[NX * NX], Wp[NX * NX], G[NX * NX];
+  SQSM_DEV void compute(const Gamma<T, NX, NY>& g, const T* mf, const T* Nf) {
+    gram_lower<T, NX>(Nf, Pf);
+    mv<T, NX, NX>(g.F, mf, mp);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
+    T Nm[NX * NX];
+    predict_factor<T, NX>(g.F, Nf, g.SQ, Nm);
+    gram_lower<T, NX>(Nm, Pp);
+    T Li[NX * NX];
+    inv_lower<T, NX>(Nm, Li);
+    mtm<T, NX, NX, NX>(Li, Li, Wp);
+    T PFt[NX * NX];
+    mmt<T, NX, NX, NX>(Pf, g.F, PFt);
+    mm<T, NX, NX, NX>(PFt, Wp, G);
+  }
+};
+
+// Forward-recurrence map of step s: x(row e) -> x(row e + 1),
+// B = G_{k-1}, r = 0, s = direct_m(e+1), S = direct_P(e+1).
+template <typename T, int NX, int NY>
+SQSM_DEV void smoother_adj_map(const RtsQ<T, NX, NY>& q, const T* dnext, T* mp) {
+  using R = MapRec<NX>;
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) {
+    mp[R::B + i] = q.G[i];
+    mp[R::S + i] = dnext[NX + i];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    mp[R::r + i] = T(0);
+    mp[R::s + i] = dnext[i];
+  }
+}
+
+// Backward-recurrence map of Kalman step k: x(row e + 1) -> x(row e),
+// B = A = (I - K H) F, r = w = F^T H^T W v,
+// s = lbar w + dfilt_m(e), S = -lbar/2 (F^T H^T W H F - w w^T) + dfilt_P(e).
+template <typename T, int NX, int NY>
+SQSM_DEV void filter_adj_map(const KfQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, T lbar,
+                             const T* dprev, T* mp) {
+  using R = MapRec<NX>;
+  T KH[NX * NX];
+  mm<T, NX, NY, NX>(q.K, g.H, KH);
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) KH[i] = ((i / NX) == (i % NX) ? T(1) : T(0)) - KH[i];
+  mm<T, NX, NX, NX>(KH, g.F, mp + R::B);
+  T HF[NY * NX], al[NY];
+  mm<T, NY, NX, NX>(g.H, g.F, HF);
+  mv<T, NY, NY>(q.W, q.v, al);
+  T w[NX];
+  mtv<T, NY, NX>(HF, al, w);
+  T WHF[NY * NX];
+  mm<T, NY, NY, NX>(q.W, HF, WHF);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    mp[R::r + i] = w[i];
+    mp[R::s + i] = lbar * w[i] + dprev[i];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < NY; ++k) s += HF[k * NX + i] * WHF[k * NX + j];
+      mp[R::S + i * NX + j] = T(-0.5) * lbar * (s - w[i] * w[j]) + dprev[NX + i * NX + j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Local VJPs
+// ---------------------------------------------------------------------------
+
+// RTS step at row e (k < n) with total cotangent x = (mt, Pt): writes the
+// direct filter cotangents of row e and the smoother part of the
+// linearised-model cotangents of step t (F, c, Lambda).
+template <typename T, int NX, int NY>
+SQSM_DEV void rts_vjp(const RtsQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const T* mf,
+                      const T* msn, const T* Nsn, const T* x, T* dfilt, T* gbar) {
+  using GR = GRec<NX, NY>;
+  const T* mt = x;
+  const T* Pt = x + NX;
+  T Ps1[NX * NX];
+  gram_lower<T, NX>(Nsn, Ps1);
+  T dm_[NX], D[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) dm_[i] = msn[i] - q.mp[i];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) D[i] = Ps1[i] - q.Pp[i];
+  // Gb = mt dm^T + 2 Pt G D
+  T PtG[NX * NX], Gb[NX * NX], tmp[NX * NX];
+  mm<T, NX, NX, NX>(Pt, q.G, PtG);
+  mm<T, NX, NX, NX>(PtG, D, tmp);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Gb[i * NX + j] = mt[i] * dm_[j] + T(2) * tmp[i * NX + j];
+  // dmp = -G^T mt ; dPp = -G^T Pt G - sym(G^T Gb Wp)
+  T dmp[NX];
+  mtv<T, NX, NX>(q.G, mt, dmp);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) dmp[i] = -dmp[i];
+  T dPp[NX * NX], GtPtG[NX * NX], GtGb[NX * NX], GtGbW[NX * NX];
+  mtm<T, NX, NX, NX>(q.G, PtG, GtPtG);
+  mtm<T, NX, NX, NX>(q.G, Gb, GtGb);
+  mm<T, NX, NX, NX>(GtGb, q.Wp, GtGbW);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+      dPp[i * NX + j] = -GtPtG[i * NX + j] - T(0.5) * (GtGbW[i * NX + j] + GtGbW[j * NX + i]);
+  // direct filter cotangents: dmf = mt + F^T dmp ; dPf = Pt + sym(Gb Wp F) + F^T dPp F
+  T Ftd[NX];
+  mtv<T, NX, NX>(g.F, dmp, Ftd);
+  T GbW[NX * NX], GbWF[NX * NX], FtdPp[NX * NX], FtdPpF[NX * NX];
+  mm<T, NX, NX, NX>(Gb, q.Wp, GbW);
+  mm<T, NX, NX, NX>(GbW, g.F, GbWF);
+  mtm<T, NX, NX, NX>(g.F, dPp, FtdPp);
+  mm<T, NX, NX, NX>(FtdPp, g.F, FtdPpF);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    dfilt[i] = mt[i] + Ftd[i];
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+      dfilt[NX + i * NX + j] = Pt[i * NX + j] + T(0.5) * (GbWF[i * NX + j] + GbWF[j * NX + i]) +
+                               FtdPpF[i * NX + j];
+  }
+  // gF = Wp Gb^T Pf + dmp mf^T + 2 dPp F Pf ; gc = dmp ; gL = dPp
+  T WGbt[NX * NX], A1[NX * NX], FPf[NX * NX], A2[NX * NX];
+  mmt<T, NX, NX, NX>(q.Wp, Gb, WGbt);
+  mm<T, NX, NX, NX>(WGbt, q.Pf, A1);
+  mm<T, NX, NX, NX>(g.F, q.Pf, FPf);
+  mm<T, NX, NX, NX>(dPp, FPf, A2);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      gbar[GR::F + i * NX + j] = A1[i * NX + j] + dmp[i] * mf[j] + T(2) * A2[i * NX + j];
+      gbar[GR::L + i * NX + j] = dPp[i * NX + j];
+    }
+    gbar[GR::c + i] = dmp[i];
+  }
+}
+
+// Kalman step k (t = k - 1) with total cotangent x = (ym, yP) of its output
+// and lbar of l_k: adds the filter part of the linearised-model cotangents
+// of step t to gbar (F, c, Lambda: +=; H, d, Omega: =).
+template <typename T, int NX, int NY>
+SQSM_DEV void kf_vjp(const KfQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const T* mprev, T lbar,
+                     const T* x, T* gbar) {
+  using GR = GRec<NX, NY>;
+  const T* ym = x;
+  const T* yP = x + NX;
+  T al[NY];
+  mv<T, NY, NY>(q.W, q.v, al);
+  T vb[NY], Sb[NY * NY];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) vb[i] = -lbar * al[i];
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Sb[i * NY + j] = T(-0.5) * lbar * (q.W[i * NY + j] - al[i] * al[j]);
+  // m' = m^- + K v
+  T mpb[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) mpb[i] = ym[i];
+  T Ktym[NY];
+  mtv<T, NX, NY>(q.K, ym, Ktym);
+#pragma unroll
+  for (int i = 0; i < NY; ++i) vb[i] += Ktym[i];
+  // Kb = ym v^T ; Ub = -2 yP K + Kb W ; Wb = -U^T yP U + U^T Kb
+  T Ub[NX * NY], yPK[NX * NY];
+  mm<T, NX, NX, NY>(yP, q.K, yPK);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      T kw = T(0);
+#pragma unroll
+      for (int k = 0; k < NY; ++k) kw += q.v[k] * q.W[k * NY + j];
+      Ub[i * NY + j] = T(-2) * yPK[i * NY + j] + ym[i] * kw;
+    }
+  T yPU[NX * NY], Wb[NY * NY];
+  mm<T, NX, NX, NY>(yP, q.U, yPU);
+  T Utym[NY];
+  mtv<T, NX, NY>(q.U, ym, Utym);
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) s += q.U[k * NY + i] * yPU[k * NY + j];
+      Wb[i * NY + j] = -s + Utym[i] * q.v[j];
+    }
+  // Sb -= sym(W Wb W)
+  T WWb[NY * NY], WWbW[NY * NY];
+  mm<T, NY, NY, NY>(q.W, Wb, WWb);
+  mm<T, NY, NY, NY>(WWb, q.W, WWbW);
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) Sb[i * NY + j] -= T(0.5) * (WWbW[i * NY + j] + WWbW[j * NY + i]);
+  // v = y - H m^- - d
+  T gH[NY * NX];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    gbar[GR::d + i] = -vb[i];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) gH[i * NX + j] = -vb[i] * q.mp[j];
+  }
+  T Htvb[NX];
+  mtv<T, NY, NX>(g.H, vb, Htvb);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) mpb[i] -= Htvb[i];
+  // U = P^- H^T: Ppb += sym(Ub H); gH += Ub^T P^-
+  // S = H P^- H^T + Omega: Ppb += H^T Sb H; gH += 2 Sb H P^-; gO = Sb
+  T Ppb[NX * NX], UbH[NX * NX];
+  mm<T, NX, NY, NX>(Ub, g.H, UbH);
+  T SbH[NY * NX], HtSbH[NX * NX];
+  mm<T, NY, NY, NX>(Sb, g.H, SbH);
+  mtm<T, NX, NY, NX>(g.H, SbH, HtSbH);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+      Ppb[i * NX + j] = yP[i * NX + j] + T(0.5) * (UbH[i * NX + j] + UbH[j * NX + i]) + HtSbH[i * NX + j];
+  T UbtPp[NY * NX], SbHPp[NY * NX];
+  mtm<T, NY, NX, NX>(Ub, q.Pp, UbtPp);
+  mm<T, NY, NX, NX>(SbH, q.Pp, SbHPp);
+#pragma unroll
+  for (int i = 0; i < NY; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) gbar[GR::H + i * NX + j] = gH[i * NX + j] + UbtPp[i * NX + j] + T(2) * SbHPp[i * NX + j];
+#pragma unroll
+  for (int i = 0; i < NY * NY; ++i) gbar[GR::O + i] = Sb[i];
+  // m^- = F m + c ; P^- = F P F^T + Lambda
+  T FPprev[NX * NX], PpbFP[NX * NX];
+  mm<T, NX, NX, NX>(g.F, q.Pprev, FPprev);
+  mm<T, NX, NX, NX>(Ppb, FPprev, PpbFP);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    gbar[GR::c + i] += mpb[i];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      gbar[GR::F + i * NX + j] += mpb[i] * mprev[j] + T(2) * PpbFP[i * NX + j];
+      gbar[GR::L + i * NX + j] += Ppb[i * NX + j];
+    }
+  }
+}
+
+// VJP of the cubature regression of one function about (m, N) (Sec. 4.3 in
+// the form of the forward kernel): given cotangents Gb of the regression
+// matrix, ob of the offset (absolute form z_bar - G m) and Lb of the noise
+// covariance, accumulate into mb, Nb.  JAC(x, J) writes the Jacobian of
+// the regressed function at x; G, s (residual columns) are recomputed.
+template <typename T, int NO, typename JAC>
+SQSM_DEV void cubature_vjp(const T* m, const T* N, const T* G, const T* sres, const T* Gb,
+                           const T* ob, const T* Lb, JAC jac, T* mb, T* Nb) {
+  constexpr int NX = 5;
+  const T sq = sq_sqrt(T(NX));
+  // m-part of the offset: off = z_bar - G m
+  T Fp[NO * NX];
+#pragma unroll
+  for (int r = 0; r < NO; ++r)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Fp[r * NX + j] = Gb[r * NX + j] - ob[r] * m[j];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) s += G[r * NX + j] * ob[r];
+    mb[j] -= s;
+  }
+  // G = D N^{-1}: Db = Fp N^{-T}; Nb -= G^T Fp N^{-T}
+  T Db[NO * NX];
+#pragma unroll
+  for (int i = 0; i < NO * NX; ++i) Db[i] = Fp[i];
+  rsolve_t<T, NO, NX>(Db, N);
+  T GtDb[NX * NX];
+  mtm<T, NX, NO, NX>(G, Db, GtDb);
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) Nb[i] -= GtDb[i];
+  // residual columns: sb_i = (2/NX) Lb s_i ; common = (ob - sum sb_i) / (2 NX)
+  T sb[NO * NX], sum[NO];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) sum[r] = T(0);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < NO; ++k) s += Lb[r * NO + k] * sres[k * NX + i];
+      sb[r * NX + i] = T(2) / T(NX) * s;
+      sum[r] += sb[r * NX + i];
+    }
+  T common[NO];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) common[r] = (ob[r] - sum[r]) / T(2 * NX);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T X[NX], J[NO * NX], zp[NO], zn[NO], xp[NX], xn[NX];
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      zp[r] = Db[r * NX + i] / (T(2) * sq) + T(0.5) * sb[r * NX + i] + common[r];
+      zn[r] = -Db[r * NX + i] / (T(2) * sq) + T(0.5) * sb[r * NX + i] + common[r];
+    }
+#pragma unroll
+    for (int j = 0; j < NX; ++j) X[j] = m[j] + sq * N[j * NX + i];
+    jac(X, J);
+    mtv<T, NO, NX>(J, zp, xp);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) X[j] = m[j] - sq * N[j * NX + i];
+    jac(X, J);
+    mtv<T, NO, NX>(J, zn, xn);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      mb[j] += xp[j] + xn[j];
+      Nb[j * NX + i] += sq * (xp[j] - xn[j]);
+    }
+  }
+}
+
+// Forward quantities of the cubature regression needed by its VJP: G and
+// the residual columns s_i, from the same difference formulas as the
+// forward kernel.
+template <typename T, int NO, bool ADD_I, typename DG>
+SQSM_DEV void cubature_fwd(const T* m, const T* N, DG dg, T* G, T* sres) {
+  constexpr int NX = 5;
+  const T sq = sq_sqrt(T(NX));
+  T Hs[NO * NX], dsum[NO];
+#pragma unroll
+  for (int r = 0; r < NO; ++r) dsum[r] = T(0);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T dp[NX], dn[NX], zp[NO], zn[NO];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      dp[r] = sq * N[r * NX + i];
+      dn[r] = -dp[r];
+    }
+    dg(m, dp, zp);
+    dg(m, dn, zn);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      G[r * NX + i] = (zp[r] - zn[r]) / (T(2) * sq);
+      Hs[r * NX + i] = T(0.5) * (zp[r] + zn[r]);
+      dsum[r] += zp[r] + zn[r];
+    }
+  }
+  rsolve<T, NO, NX>(G, N);
+  if constexpr (ADD_I) {
+#pragma unroll
+    for (int r = 0; r < NO; ++r) G[r * NX + r] += T(1);
+  }
+#pragma unroll
+  for (int r = 0; r < NO; ++r)
+#pragma unroll
+    for (int i = 0; i < NX; ++i) sres[r * NX + i] = Hs[r * NX + i] - dsum[r] / T(2 * NX);
+}
+
+}  // namespace sqsm

@@ -1,0 +1,368 @@
+// Kernels of the reverse pass (see adjoint.cuh) for the CT bearings model.
+//
+// Per time step s of sequence b: state rows e = s + b (k - 1) and e + 1 (k).
+// Buffers (state layout unless noted):
+//   nom      nominal trajectory (m, N) the linearisation was taken at,
+//   gam      linearised model of the step (absolute form, per step),
+//   mf, Nf   filter output, ms, Ns smoother output of that linearisation,
+//   dir      direct cotangents (m, P) of the smoother output,
+//   dfilt    direct cotangents (m, P) of the filter output (from the RTS VJP),
+//   gbar     cotangents of the linearised model (GRec, per step),
+//   lam      cotangent of the nominal trajectory (m, lower N).
+#pragma once
+
+#include "adjoint.cuh"
+
+namespace sqsm {
+
+struct AdjBufs {
+  const void *mf, *Nf, *ms, *Ns, *nom_m, *nom_N, *y;
+  const void *F, *c, *SQ, *H, *d, *SR;
+  void *dir, *dfilt, *gbar;
+};
+
+template <typename T>
+SQSM_DEV GammaView<T> gview(const AdjBufs& a) {
+  return GammaView<T>{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
+                      (const T*)a.d, (const T*)a.SR, 25, 5, 25, 10, 2, 4};
+}
+
+// --------------------------- smoother adjoint (forward in time) -----------
+
+template <typename T>
+SQSM_DEV void build_smoother_map(const AdjBufs& a, int64_t s, int64_t e, bool first, T* mp) {
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
+  Gamma<T, NX, NY> g;
+  g.load_transition(gview<T>(a), s);
+  T mf[NX], Nf[NX * NX];
+  load<T, NX>((const T*)a.mf + e * NX, mf);
+  load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nf);
+  RtsQ<T, NX, NY> q;
+  q.compute(g, mf, Nf);
+  smoother_adj_map<T, NX, NY>(q, (const T*)a.dir + (e + 1) * X, mp);
+  if (first) {
+    T x0[X];
+    load<T, X>((const T*)a.dir + e * X, x0);
+    map_make_constant<T, NX>(mp, x0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_smoother_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T* __restrict__ items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = MapRec<5>::size;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t off = sq.offsets[b];
+  T agg[REC], mp[REC], tmp[REC];
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t s = s0 + j;
+    build_smoother_map<T>(a, s, s + b, s == off, j == 0 ? agg : mp);
+    if (j > 0) {
+      map_compose<T, 5>(agg, mp, tmp);
+      copy<T, REC>(tmp, agg);
+    }
+  }
+  store<T, REC>(items + c * REC, agg);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_smoother_leaf_down(DevLevel lv, DevSeqs sq, AdjBufs a, const T* __restrict__ carry,
+                       const int* __restrict__ flag) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
+  using GR = GRec<NX, NY>;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t last = sq.offsets[b + 1] - 1;
+  T x[X];
+  if (flag[c]) load<T, X>(carry + c * X, x);
+  else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t s = s0 + j, e = s + b;
+    Gamma<T, NX, NY> g;
+    g.load_transition(gview<T>(a), s);
+    T mf[NX], Nf[NX * NX], msn[NX], Nsn[NX * NX];
+    load<T, NX>((const T*)a.mf + e * NX, mf);
+    load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nf);
+    load<T, NX>((const T*)a.ms + (e + 1) * NX, msn);
+    load_lower<T, NX>((const T*)a.Ns + (e + 1) * NX * NX, Nsn);
+    RtsQ<T, NX, NY> q;
+    q.compute(g, mf, Nf);
+    T df[X], gb[GR::size];
+    rts_vjp<T, NX, NY>(q, g, mf, msn, Nsn, x, df, gb);
+    store<T, X>((T*)a.dfilt + e * X, df);
+    T* go = (T*)a.gbar + s * GR::size;
+    store<T, NX * NX>(go + GR::F, gb + GR::F);
+    store<T, NX>(go + GR::c, gb + GR::c);
+    store<T, NX * NX>(go + GR::L, gb + GR::L);
+    T mp[REC], xn[X];
+    smoother_adj_map<T, NX, NY>(q, (const T*)a.dir + (e + 1) * X, mp);
+    map_apply<T, NX>(mp, x, xn);
+    copy<T, X>(xn, x);
+    if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
+  }
+}
+
+// --------------------------- filter adjoint (backward in time) ------------
+
+template <typename T>
+SQSM_DEV void build_filter_map(const AdjBufs& a, int64_t s, int64_t e, bool lastb, T lbar, T* mp) {
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
+  Gamma<T, NX, NY> g;
+  g.load_all(gview<T>(a), s);
+  T ys[NY], mprev[NX], Nprev[NX * NX];
+  load<T, NY>((const T*)a.y + s * NY, ys);
+  load<T, NX>((const T*)a.mf + e * NX, mprev);
+  load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nprev);
+  KfQ<T, NX, NY> q;
+  q.compute(g, ys, mprev, Nprev);
+  filter_adj_map<T, NX, NY>(q, g, lbar, (const T*)a.dfilt + e * X, mp);
+  if (lastb) {
+    T xn[X];
+    load<T, X>((const T*)a.dfilt + (e + 1) * X, xn);
+    map_make_constant<T, NX>(mp, xn);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_filter_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, T* __restrict__ items) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = MapRec<5>::size;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  const int64_t last = sq.offsets[b + 1] - 1;
+  T agg[REC], mp[REC], tmp[REC];
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t s = s0 + j;
+    build_filter_map<T>(a, s, s + b, s == last, lbar, j == cnt - 1 ? agg : mp);
+    if (j < cnt - 1) {
+      map_compose<T, 5>(agg, mp, tmp);
+      copy<T, REC>(tmp, agg);
+    }
+  }
+  store<T, REC>(items + c * REC, agg);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_filter_leaf_down(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, const T* __restrict__ carry,
+                     const int* __restrict__ flag) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
+  using GR = GRec<NX, NY>;
+  const int b = lv.seq[c];
+  const int64_t s0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T x[X];
+  if (flag[c]) load<T, X>(carry + c * X, x);
+  else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t s = s0 + j, e = s + b;
+    Gamma<T, NX, NY> g;
+    g.load_all(gview<T>(a), s);
+    T ys[NY], mprev[NX], Nprev[NX * NX];
+    load<T, NY>((const T*)a.y + s * NY, ys);
+    load<T, NX>((const T*)a.mf + e * NX, mprev);
+    load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nprev);
+    KfQ<T, NX, NY> q;
+    q.compute(g, ys, mprev, Nprev);
+    T gb[GR::size];
+    T* go = (T*)a.gbar + s * GR::size;
+    load<T, GR::size>(go, gb);
+    kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
+    store<T, GR::size>(go, gb);
+    T mp[REC], xn[X];
+    filter_adj_map<T, NX, NY>(q, g, lbar, (const T*)a.dfilt + e * X, mp);
+    map_apply<T, NX>(mp, x, xn);
+    copy<T, X>(xn, x);
+  }
+}
+
+// --------------------------- upper levels (both directions) ---------------
+
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kBlock)
+adj_up(DevLevel lv, const T* __restrict__ in, T* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = MapRec<5>::size;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T agg[REC], mp[REC], tmp[REC];
+  load<T, REC>(in + (FWD ? i0 : i0 + cnt - 1) * REC, agg);
+  for (int j = 1; j < cnt; ++j) {
+    load<T, REC>(in + (FWD ? i0 + j : i0 + cnt - 1 - j) * REC, mp);
+    map_compose<T, 5>(agg, mp, tmp);
+    copy<T, REC>(tmp, agg);
+  }
+  store<T, REC>(out + c * REC, agg);
+}
+
+// carry = the cotangent vector entering the chunk (forward: before its
+// first item; backward: after its last); flag 0: none, the chunk holds the
+// constant boundary map.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kBlock)
+adj_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
+         const int* __restrict__ fin, T* __restrict__ cout, int* __restrict__ fout) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n_chunks) return;
+  constexpr int REC = MapRec<5>::size, X = XRec<5>::size;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  int flag = fin[c];
+  T x[X];
+  load<T, X>(cin + c * X, x);
+  if (!flag) {
+#pragma unroll
+    for (int i = 0; i < X; ++i) x[i] = T(0);
+  }
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t i = FWD ? i0 + j : i0 + cnt - 1 - j;
+    store<T, X>(cout + i * X, x);
+    fout[i] = flag;
+    if (j + 1 < cnt) {
+      T mp[REC], xn[X];
+      load<T, REC>(items + i * REC, mp);
+      map_apply<T, 5>(mp, x, xn);
+      copy<T, X>(xn, x);
+      flag = 1;
+    }
+  }
+}
+
+// --------------------------- SLR VJP and reductions ------------------------
+
+// One thread per smoother leaf chunk (state rows): nominal-trajectory
+// cotangent of row k from the transition regression of step k (k < n) and
+// the observation regression of step k - 1 (k >= 1); theta partial sums.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
+               T* __restrict__ lam_out, double* __restrict__ th_partial) {
+  const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ch >= lv.n_chunks) return;
+  constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
+  using GR = GRec<NX, NY>;
+  const CTParams<T> P = *Pp;
+  const int b = lv.seq[ch];
+  const int64_t so = sq.offsets[b] + b;
+  const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
+  T Q[NX * NX];
+  gram_lower<T, NX>(P.SQ, Q);
+  double th[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < lv.count[ch]; ++j) {
+    const int64_t e = lv.first[ch] + j;
+    const int64_t k = e - so;
+    T m[NX], N[NX * NX], mb[NX], Nb[NX * NX];
+    load<T, NX>((const T*)a.nom_m + e * NX, m);
+    load_lower<T, NX>((const T*)a.nom_N + e * NX * NX, N);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mb[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) Nb[i] = T(0);
+    if (k < nb) {
+      const T* gb = (const T*)a.gbar + (sq.offsets[b] + k) * GR::size;
+      T G[NX * NX], sres[NX * NX], Lb[NX * NX];
+      cubature_fwd<T, NX, true>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, mm_, dl, o); },
+                                G, sres);
+#pragma unroll
+      for (int i = 0; i < NX; ++i)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) Lb[i * NX + q] = T(0.5) * (gb[GR::L + i * NX + q] + gb[GR::L + q * NX + i]);
+      cubature_vjp<T, NX>(m, N, G, sres, gb + GR::F, gb + GR::c, Lb,
+                          [&](const T* xx, T* J) { ct_jac_f(P, xx, J); }, mb, Nb);
+      double tq = 0.0;
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) tq += (double)Lb[i] * (double)Q[i];
+      const double t44 = (double)Lb[24] * (double)Q[24];
+      th[1] += tq - t44;
+      th[2] += t44;
+    }
+    if (k >= 1) {
+      const T* gb = (const T*)a.gbar + (sq.offsets[b] + k - 1) * GR::size;
+      T G[NY * NX], sres[NY * NX], Lb[NY * NY];
+      cubature_fwd<T, NY, false>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
+                                 G, sres);
+#pragma unroll
+      for (int i = 0; i < NY; ++i)
+#pragma unroll
+        for (int q = 0; q < NY; ++q) Lb[i * NY + q] = T(0.5) * (gb[GR::O + i * NY + q] + gb[GR::O + q * NY + i]);
+      cubature_vjp<T, NY>(m, N, G, sres, gb + GR::H, gb + GR::d, Lb,
+                          [&](const T* xx, T* J) { ct_jac_h(P, xx, J); }, mb, Nb);
+      th[0] += 2.0 * (double)P.sigma * (double)P.sigma * ((double)Lb[0] + (double)Lb[3]);
+    }
+    T* o = lam_out + e * X;
+    store<T, NX>(o, mb);
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = 0; q < NX; ++q) o[NX + r * NX + q] = q <= r ? Nb[r * NX + q] : T(0);
+  }
+  th_partial[ch * 3 + 0] = th[0];
+  th_partial[ch * 3 + 1] = th[1];
+  th_partial[ch * 3 + 2] = th[2];
+}
+
+// Fixed-order sums of the theta partials (one block): out[j] = sign * sum.
+static __global__ void adj_theta_reduce(int64_t n, const double* __restrict__ part, double sign,
+                                        double* __restrict__ out) {
+  __shared__ double buf[3][256];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int j = 0; j < 3; ++j) acc[j] += part[i * 3 + j];
+  for (int j = 0; j < 3; ++j) buf[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int j = 0; j < 3; ++j) buf[j][threadIdx.x] += buf[j][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 3; ++j) out[j] = sign * buf[j][0];
+}
+
+// Relative max-norm change between two cotangent iterates (one block).
+template <typename T>
+static __global__ void adj_change_reduce(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
+                                  double* __restrict__ out) {
+  __shared__ double s1[256], s2[256];
+  double d = 0.0, m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    d = fmax(d, fabs((double)a[i] - (double)b[i]));
+    m = fmax(m, fabs((double)a[i]));
+  }
+  s1[threadIdx.x] = d;
+  s2[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = s2[0] > 0.0 ? s1[0] / s2[0] : s1[0];
+}
+
+// Sum of the per-sequence log-likelihoods times sign (one thread, fixed order).
+static __global__ void adj_nll_kernel(int B, const double* __restrict__ ll, double sign,
+                                      double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < B; ++b) s += ll[b];
+  out[0] = sign * s;
+}
+
+}  // namespace sqsm

@@ -41,6 +41,10 @@ struct Workspace {
   void* params = nullptr;    // IPLS model constants
   void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
   bool ipls_ready = false;
+  // NLL + gradient
+  AdjArgs adj{};
+  ScanBuffers adj_scan;
+  bool adj_ready = false;
 };
 
 struct Plan {
@@ -55,12 +59,12 @@ struct Plan {
 
 struct GraphKey {
   const Plan* plan;
-  int dtype, lin, M, prof;
+  int dtype, lin, M, prof, adj;     // adj: adjoint iterations + 1 (0 = smoother only)
   const void *y, *m0, *N0, *ims, *iNs, *ms, *Ns, *ll;
   bool operator<(const GraphKey& o) const {
-    return std::tie(plan, dtype, lin, M, prof, y, m0, N0, ims, iNs, ms, Ns, ll) <
-           std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.y, o.m0, o.N0, o.ims, o.iNs, o.ms,
-                    o.Ns, o.ll);
+    return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll) <
+           std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.adj, o.y, o.m0, o.N0, o.ims, o.iNs,
+                    o.ms, o.Ns, o.ll);
   }
 };
 
@@ -255,6 +259,32 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
   w->dm0 = w->mem.get(es * nx * p->B);
   if (!w->params || !w->dm0) return false;
   w->ipls_ready = true;
+  return true;
+}
+
+bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
+  if (w->adj_ready) return true;
+  const size_t es = dtype == SQSM_F64 ? 8 : 4;
+  const int64_t rows = p->smth.n_items[0], steps = p->filt.n_items[0];
+  const int nx = 5, ny = 2, X = nx + nx * nx;
+  const int grec = 2 * nx * nx + nx + ny * nx + ny + ny * ny;
+  AdjArgs& g = w->adj;
+  g.nom_m = w->mem.get(es * nx * rows);
+  g.nom_N = w->mem.get(es * nx * nx * rows);
+  g.ms2 = w->mem.get(es * nx * rows);
+  g.Ns2 = w->mem.get(es * nx * nx * rows);
+  g.dir = w->mem.get(es * X * rows);
+  g.dfilt = w->mem.get(es * X * rows);
+  g.lam_a = w->mem.get(es * X * rows);
+  g.lam_b = w->mem.get(es * X * rows);
+  g.gbar = w->mem.get(es * grec * steps);
+  g.th_partial = (double*)w->mem.get(sizeof(double) * 3 * p->smth.lv[0].n_chunks);
+  g.ll = (double*)w->mem.get(sizeof(double) * p->B);
+  if (!g.nom_m || !g.nom_N || !g.ms2 || !g.Ns2 || !g.dir || !g.dfilt || !g.lam_a || !g.lam_b ||
+      !g.gbar || !g.th_partial || !g.ll)
+    return false;
+  if (!alloc_scan(w->mem, p->filt, w->adj_scan, es * (2 * nx * nx + 2 * nx), es * X)) return false;
+  w->adj_ready = true;
   return true;
 }
 
@@ -476,7 +506,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
     }
     enqueue(s);
   } else {
-    GraphKey key{p, dtype, linearization, M, ctx->prof_on ? 1 : 0, y, m0, N0, init_ms, init_Ns,
+    GraphKey key{p, dtype, linearization, M, ctx->prof_on ? 1 : 0, 0, y, m0, N0, init_ms, init_Ns,
                  ms, Ns, loglik};
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
@@ -517,6 +547,103 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth launch");
+  return SQSM_OK;
+}
+
+int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                       int linearization, int M, int adj_iters, int64_t batch,
+                       const int64_t* offsets, const void* y, const void* m0, const void* N0,
+                       const void* init_ms, const void* init_Ns, void* ms, void* Ns,
+                       double* nll, double* grad, double* adj_change, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization != SQSM_CUBATURE)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the gradient is implemented for cubature SLR only");
+  if (M < 0 || adj_iters < 0) return fail(ctx, SQSM_ERR_INVALID_ARG, "M, adj_iters must be >= 0");
+  if (M == 0 && (!init_ms || !init_Ns))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "M = 0 needs an initial trajectory");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !m0 || !N0 || !ms || !Ns || !nll || !grad)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
+  if ((init_ms == nullptr) != (init_Ns == nullptr))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  DeviceGuard g(ctx->device);
+  Plan* p = get_plan(ctx, offsets, batch);
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, 5);
+  if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype))
+    return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  IplsArgs a{};
+  a.linearization = linearization;
+  a.M = M;
+  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  a.dt = model->dt;
+  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
+  a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
+  a.ms = ms; a.Ns = Ns; a.loglik = nullptr;
+  a.mf = w->mf; a.Nf = w->Nf;
+  a.F = w->gamma[0]; a.c = w->gamma[1]; a.SQ = w->gamma[2];
+  a.H = w->gamma[3]; a.d = w->gamma[4]; a.SR = w->gamma[5];
+  a.params = w->params;
+  a.dm0 = w->dm0;
+  AdjArgs adj = w->adj;
+  adj.iters = adj_iters;
+  adj.nll = nll;
+  adj.grad = grad;
+  adj.change = adj_change;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
+  auto enqueue = [&](cudaStream_t st) {
+    if (dtype == SQSM_F32)
+      adj_enqueue_f32(a, adj, p->filt, w->filt, p->smth, w->smth, w->adj_scan, sq, w->partial,
+                      ctx->d_status, st);
+    else
+      adj_enqueue_f64(a, adj, p->filt, w->filt, p->smth, w->smth, w->adj_scan, sq, w->partial,
+                      ctx->d_status, st);
+  };
+  if (!ctx->opt.use_graph) {
+    enqueue(s);
+  } else {
+    GraphKey key{p, dtype, linearization, M, 0, adj_iters + 1, y, m0, N0, init_ms, init_Ns,
+                 ms, Ns, nll};
+    auto it = ctx->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != ctx->graphs.end() && it->first.adj == adj_iters + 1 && key.ll == nll) {
+      exec = it->second.exec;
+    } else {
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cs = ctx->capture_stream;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+      enqueue(cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      if (ctx->graphs.size() >= 16) {
+        if (ctx->last_prof == ctx->graphs.begin()->second.prof.get()) ctx->last_prof = nullptr;
+        cudaGraphExecDestroy(ctx->graphs.begin()->second.exec);
+        ctx->graphs.erase(ctx->graphs.begin());
+      }
+      ctx->graphs[key].exec = exec;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_nll_grad launch");
   return SQSM_OK;
 }
 

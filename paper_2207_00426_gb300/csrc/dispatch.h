@@ -51,6 +51,22 @@ void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
 void ipls_params_f32(const IplsArgs& a, cudaStream_t s);
 void ipls_params_f64(const IplsArgs& a, cudaStream_t s);
 
+// Buffers of the NLL + gradient evaluation (all device).
+struct AdjArgs {
+  int iters;                          // adjoint fixed-point iterations
+  void *nom_m, *nom_N, *ms2, *Ns2;    // linearisation point, its smoother output
+  void *dir, *dfilt, *gbar, *lam_a, *lam_b;
+  double *th_partial, *ll, *nll, *grad, *change;
+};
+void adj_enqueue_f32(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf,
+                     const ScanBuffers& Wf, const LevelSet& Ls, const ScanBuffers& Ws,
+                     const ScanBuffers& Wa, DevSeqs sq, double* partial, int* status,
+                     cudaStream_t s);
+void adj_enqueue_f64(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf,
+                     const ScanBuffers& Wf, const LevelSet& Ls, const ScanBuffers& Ws,
+                     const ScanBuffers& Wa, DevSeqs sq, double* partial, int* status,
+                     cudaStream_t s);
+
 // One SLR pass (Sec. 4.2 / 4.3) of the CT model into caller arrays.
 void ct_linearize_f32(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s);
 void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s);

@@ -1,0 +1,13 @@
+// NLL + gradient through the IPLS fixed point (Sec. 5.2), float.
+#include "adj_impl.cuh"
+
+namespace sqsm {
+
+void adj_enqueue_f32(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf,
+                    const ScanBuffers& Wf, const LevelSet& Ls, const ScanBuffers& Ws,
+                    const ScanBuffers& Wa, DevSeqs sq, double* partial, int* status,
+                    cudaStream_t s) {
+  adj_enqueue<float>(a, g, Lf, Wf, Ls, Ws, Wa, sq, partial, status, s);
+}
+
+}  // namespace sqsm

@@ -1,0 +1,98 @@
+"""Gradient of the negative pseudo log-likelihood through the IPLS fixed
+point (Sec. 5.2), hand-written adjoint on the GPU, against the oracle's
+central finite differences of the converged pseudo log-likelihood."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import ipls as O, models as OM
+from paper_2207_00426_gb300 import workloads as W
+
+THETA = np.log([0.05, 0.01, 0.1])
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2207_00426_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    return B.Context(0)
+
+
+def _dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda:0")
+
+
+def _oracle(d, theta, y=None, m0=None, N0=None):
+    y = d["y"] if y is None else y
+    m0 = d["m0"] if m0 is None else m0
+    N0 = d["N0"] if N0 is None else N0
+    nll = O.nll(OM.CTBearings, theta, y, m0, N0, "cubature", tol=1e-13, dt=d["dt"])
+    g = O.nll_grad_fd(OM.CTBearings, theta, y, m0, N0, "cubature", h=1e-5, tol=1e-13, dt=d["dt"])
+    return nll, g
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-6), ("f32", 1e-3)])
+@pytest.mark.parametrize("n", [30, 131])
+def test_gradient_matches_oracle_fd(B, ctx, prec, tol, n):
+    d = W.ct_sequence(n=n, seed=31 + n)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    theta = THETA + np.array([0.2, -0.3, 0.25])
+    nll, grad, change, ms, _ = B.sqsm_ipls_nll_grad(ctx, theta, _dev(d["y"], dt), [0, n],
+                                                    _dev(d["m0"][None], dt), _dev(d["N0"][None], dt),
+                                                    M=40, adj_iters=40, dt=d["dt"])
+    torch.cuda.synchronize()
+    rnll, rg = _oracle(d, theta)
+    g = grad.cpu().numpy()
+    assert abs(nll.item() - rnll) <= (1e-9 if prec == "f64" else 1e-5) * abs(rnll)
+    assert np.linalg.norm(g - rg) <= tol * np.linalg.norm(rg), (g, rg)
+    assert change.item() < (1e-8 if prec == "f64" else 1e-3)
+
+
+def test_batched_gradient_is_sum(B, ctx):
+    lengths = [17, 40, 3]
+    d = W.ct_batch(lengths=lengths, seed=41)
+    dt = torch.float64
+    nll, grad, _, _, _ = B.sqsm_ipls_nll_grad(ctx, THETA, _dev(d["y"], dt), d["offsets"],
+                                              _dev(d["m0"], dt), _dev(d["N0"], dt), M=40,
+                                              adj_iters=40, dt=d["dt"])
+    torch.cuda.synchronize()
+    off = d["offsets"]
+    tot_nll, tot_g = 0.0, np.zeros(3)
+    for b in range(len(lengths)):
+        rn, rg = _oracle(d, THETA, d["y"][off[b]:off[b + 1]], d["m0"][b], d["N0"][b])
+        tot_nll += rn
+        tot_g += rg
+    assert abs(nll.item() - tot_nll) <= 1e-9 * abs(tot_nll)
+    np.testing.assert_allclose(grad.cpu().numpy(), tot_g, rtol=1e-6, atol=1e-8 * np.abs(tot_g).max())
+
+
+def test_autograd_function(B, ctx):
+    from paper_2207_00426_gb300.autograd import ipls_nll
+    d = W.ct_sequence(n=50, seed=43)
+    dt = torch.float64
+    theta = torch.tensor(THETA, dtype=torch.float64, requires_grad=True)
+    val = ipls_nll(theta, ctx, _dev(d["y"], dt), [0, 50], _dev(d["m0"][None], dt),
+                   _dev(d["N0"][None], dt), M=40, adj_iters=40, dt=d["dt"])
+    (3.0 * val).backward()
+    _, rg = _oracle(d, THETA)
+    np.testing.assert_allclose(theta.grad.numpy(), 3.0 * rg, rtol=1e-6, atol=1e-9)
+
+
+def test_extended_is_rejected(B, ctx):
+    d = W.ct_sequence(n=10, seed=44)
+    dt = torch.float64
+    import ctypes
+    th = (ctypes.c_double * 3)(*THETA)
+    mdl = B._model(d["dt"], d["sensors"])
+    off, batch = B._offsets([0, 10])
+    z = torch.zeros(64, dtype=dt, device="cuda:0")
+    p = z.data_ptr()
+    rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, B.EXTENDED, 5, 5, batch, off,
+                                  p, p, p, None, None, p, p, p, p, None, None)
+    assert rc == B.ERR_UNSUPPORTED
