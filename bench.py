@@ -288,12 +288,88 @@ def gpu_arm(args, rank, world, local):
     peak = 152 * 128 * 2 * 2070e6 / 1e12        # FP32 FMA lanes x 2 x max SM clock
     achieved = f_launch / t_launch / 1e12
     roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
+                "peak_note": "derived",
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "flops_per_launch": f_launch, "peak_basis":
                 "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)"}
     it_flops = CM.ipls_iteration_flops([n])
     whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
     whole["frac_of_fp32_peak"] = whole["achieved_tflops"] / peak
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / k
+
+    # ---- NLL + gradient (Sec. 5.2) at the same size: M IPLS iterations, the
+    #      final linearisation pass and ADJ adjoint fixed-point iterations
+    ADJ = 10
+    grads = {}
+
+    def nll_grad_rate(dtype, k):
+        yy, mm0, NN0 = y.to(dtype), m0.to(dtype), N0.to(dtype)
+        out = {}
+
+        def ev():
+            out["r"] = B.sqsm_ipls_nll_grad(ctx, d["theta"], yy, [0, n], mm0, NN0, M, ADJ, dt=d["dt"])
+        ev()
+        torch.cuda.synchronize()
+        t = timed(ev, k)
+        nll_, g_, ch_, _, _ = out["r"]
+        return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "nll": nll_.item(),
+                "grad": g_.cpu().tolist(), "adjoint_iterations": ADJ,
+                "adjoint_last_rel_change": ch_.item()}
+
+    grads["f32"] = nll_grad_rate(torch.float32, max(2, min(args.steps, 5)))
+    grads["f64"] = nll_grad_rate(torch.float64, 2)
+
+    # ---- batched: 4096 independent sequences, lengths U{100..5000} (ragged)
+    db = W.ct_batch(batch=4096, lo=100, hi=5000, seed=3)
+    yb = torch.tensor(db["y"], dtype=f32, device=dev)
+    m0b = torch.tensor(db["m0"], dtype=f32, device=dev)
+    N0b = torch.tensor(db["N0"], dtype=f32, device=dev)
+    nb_tot = int(db["offsets"][-1])
+    rows_b = nb_tot + 4096
+    msb = torch.empty((rows_b, 5), dtype=f32, device=dev)
+    Nsb = torch.empty((rows_b, 5, 5), dtype=f32, device=dev)
+    llb = torch.empty(4096, dtype=torch.float64, device=dev)
+
+    def bstep():
+        B.sqsm_ipls_smooth(ctx, db["theta"], yb, db["offsets"], m0b, N0b, M, B.CUBATURE, dt=db["dt"],
+                           ms=msb, Ns=Nsb, loglik=llb)
+    bstep()
+    torch.cuda.synchronize()
+    tb = timed(bstep, 3)
+    ctx.profile(True)
+    bstep()
+    torch.cuda.synchronize()
+    bacc = {}
+    for _ in range(2):
+        bstep()
+        for k, (t, c) in ctx.profile_read().items():
+            a0 = bacc.setdefault(k, [0.0, 0])
+            a0[0] += t
+            a0[1] += c
+    ctx.profile(False)
+    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])), leaf=4, radix=4)
+    btot = sum(t for t, _ in bacc.values())
+    btop = max(bacc, key=lambda k: bacc[k][0])
+    bach = bflops[btop][0] / (bacc[btop][0] / bacc[btop][1] / 1e3) / 1e12
+    batched = {"workload": "4096 CT sequences, lengths U{100..5000}, cubature IPLS, M=10",
+               "steps_total": nb_tot, "value": nb_tot * M / tb, "unit": UNIT,
+               "ms_per_step": 1e3 * tb,
+               "roofline": {"bound": "alu", "kernel": btop, "achieved": bach, "peak": peak,
+                            "unit": "TFLOP/s", "frac": bach / peak},
+               "shares": {k: t / btot for k, (t, _) in bacc.items()},
+               "whole_step_tflops": CM.ipls_iteration_flops(list(np.diff(db["offsets"]))) * M
+               / tb / 1e12}
+    del yb, msb, Nsb
 
     # ---- FP64 variant of the same step (comparator), few steps
     f64 = torch.float64
@@ -332,6 +408,7 @@ def gpu_arm(args, rank, world, local):
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "clocks": clk.summary(),
                 "roofline": roofline, "whole_step": whole, "kernels": kernels,
+                "nll_grad": grads, "batched": batched,
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
                 "loglik": ll.item()}

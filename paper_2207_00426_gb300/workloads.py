@@ -134,19 +134,42 @@ def ct_sequence(n=10_000, seed=1, dt=CT_DT, theta=CT_THETA_TRUE,
 def ct_batch(batch=4096, lo=100, hi=5000, seed=3, dt=CT_DT, theta=CT_THETA_TRUE,
              sensors=CT_SENSORS, prior_std=0.1, lengths=None):
     """Independent CT sequences; y rows of sequence b are
-    y[offsets[b]:offsets[b+1]], its prior m0[b], N0[b]."""
+    y[offsets[b]:offsets[b+1]], its prior m0[b], N0[b].  All sequences are
+    simulated together (vectorised over the batch)."""
     rng = np.random.default_rng(seed)
     sigma, qc, qw = np.exp(theta)
     if lengths is None:
         lengths = rng.integers(lo, hi + 1, size=batch)
     lengths = np.asarray(lengths, dtype=np.int64)
-    offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
+    B = len(lengths)
+    offsets = np.zeros(B + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(lengths)
-    ys, m0, xs = [], [], []
-    for nb in lengths:
-        x, y = _simulate_ct(rng, int(nb), dt, sigma, qc, qw, sensors)
-        ys.append(y); m0.append(x[0]); xs.append(x)
-    N0 = np.tile(prior_std * np.eye(5), (len(lengths), 1, 1))
-    return dict(y=np.concatenate(ys), offsets=offsets, m0=np.array(m0), N0=N0,
-                x=xs, theta=np.array(theta, dtype=np.float64), dt=dt,
+    speed = rng.uniform(0.5, 2.0, B)
+    heading = rng.uniform(0.0, 2.0 * np.pi, B)
+    w0 = 0.3 * rng.standard_normal(B)
+    x = np.stack([np.zeros(B), np.zeros(B), speed * np.cos(heading), speed * np.sin(heading), w0], 1)
+    m0 = x.copy()
+    L = _ct_noise_factor(dt, qc, qw)
+    nmax = int(lengths.max())
+    y = np.zeros((int(offsets[-1]), 2))
+    for t in range(nmax):
+        px, py, vx, vy, w = x.T
+        a = w * dt
+        small = np.abs(a) < 1e-9
+        wsafe = np.where(small, 1.0, w)
+        S = np.where(small, dt, np.sin(a) / wsafe)
+        C = np.where(small, 0.5 * w * dt * dt, (1.0 - np.cos(a)) / wsafe)
+        ca, sa = np.cos(a), np.sin(a)
+        x = np.stack([px + S * vx - C * vy, py + C * vx + S * vy,
+                      ca * vx - sa * vy, sa * vx + ca * vy, w], 1)
+        x = x + rng.standard_normal((B, 5)) @ L.T
+        bear = np.arctan2(x[:, 1:2] - sensors[None, :, 1], x[:, 0:1] - sensors[None, :, 0])
+        bear = bear + sigma * rng.standard_normal((B, 2))
+        bear = bear - 2.0 * np.pi * np.floor(bear / (2.0 * np.pi) + 0.5)
+        live = t < lengths
+        rows = offsets[:-1][live] + t
+        y[rows] = bear[live]
+    N0 = np.tile(prior_std * np.eye(5), (B, 1, 1))
+    return dict(y=y, offsets=offsets, m0=m0, N0=N0,
+                theta=np.array(theta, dtype=np.float64), dt=dt,
                 sensors=np.array(sensors, dtype=np.float64))
