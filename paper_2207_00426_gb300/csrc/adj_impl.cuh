@@ -27,8 +27,8 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   //    and the pseudo log-likelihood of that linearisation.
   cudaMemcpyAsync(g.nom_m, a.ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
-  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-      Lf.lv[0], sq, (const CTParams<T>*)a.params, 0, 0, (const T*)g.nom_m, (const T*)g.nom_N,
+  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, 0, 0, (const T*)g.nom_m, (const T*)g.nom_N,
       (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
   GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
                   (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};

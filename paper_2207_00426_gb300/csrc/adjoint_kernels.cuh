@@ -275,7 +275,8 @@ adj_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjB
     if (k < nb) {
       const T* gb = (const T*)a.gbar + (sq.offsets[b] + k) * GR::size;
       T G[NX * NX], sres[NX * NX], Lb[NX * NX];
-      cubature_fwd<T, NX, true>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, mm_, dl, o); },
+      const Turn<T> tm = turn(m[4], P.dt);
+      cubature_fwd<T, NX, true>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
                                 G, sres);
 #pragma unroll
       for (int i = 0; i < NX; ++i)

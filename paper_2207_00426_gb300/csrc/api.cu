@@ -117,6 +117,7 @@ int cuda_fail(sqsm_ctx* ctx, cudaError_t e, const char* where) {
 // sequence has one item.
 bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
   std::vector<int64_t> counts = counts0;
+  L.B = (int)counts0.size();
   int level = 0;
   int64_t total = 0;
   for (int64_t v : counts) total += v;
@@ -153,6 +154,24 @@ bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
     d.seq = ds;
     L.lv.push_back(d);
     L.n_items.push_back(d.n_chunks);
+    // items of level+1 per sequence = chunks per sequence at this level
+    {
+      std::vector<int64_t> so(counts.size() + 1, 0);
+      int64_t mx = 0;
+      for (size_t b = 0; b < counts.size(); ++b) {
+        so[b + 1] = so[b] + next[b];
+        mx = std::max<int64_t>(mx, next[b]);
+      }
+      int64_t* dso = (int64_t*)p.mem.get(sizeof(int64_t) * so.size());
+      if (!dso) return false;
+      cudaMemcpy(dso, so.data(), sizeof(int64_t) * so.size(), cudaMemcpyHostToDevice);
+      if (L.seq_item_off.empty()) {   // index 0 (steps) is not used
+        L.seq_item_off.push_back(nullptr);
+        L.max_seq_items.push_back(0);
+      }
+      L.seq_item_off.push_back(dso);
+      L.max_seq_items.push_back(mx);
+    }
     if (level == 0) {
       std::vector<int64_t> lco(counts.size() + 1, 0);
       for (size_t b = 0; b < counts.size(); ++b) lco[b + 1] = lco[b] + next[b];
@@ -476,6 +495,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   IplsArgs a{};
   a.linearization = linearization;
+  a.leaf = p->L0;
   a.M = M;
   for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
   a.dt = model->dt;
@@ -584,6 +604,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   IplsArgs a{};
   a.linearization = linearization;
+  a.leaf = p->L0;
   a.M = M;
   for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
   a.dt = model->dt;
@@ -674,6 +695,7 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   IplsArgs a{};
   a.linearization = linearization;
+  a.leaf = p->L0;
   for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
   a.dt = model->dt;
   for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];

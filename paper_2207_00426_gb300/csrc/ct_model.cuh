@@ -70,20 +70,42 @@ __global__ void ct_params_kernel(double th0, double th1, double th2, double dt, 
   *P = p;
 }
 
+// Turn coefficients of a = w dt from one sincos of a/2 (double-angle
+// identities sin a = 2 s c, cos a = 1 - 2 s^2, 1 - cos a = 2 s^2):
+// S = sin(a)/w, C = (1 - cos a)/w, ca = cos a, sa = sin a, omc = 1 - cos a;
+// S and C by their series for |a| < 1e-3.
 template <typename T>
-SQSM_DEV void turn_coeffs(T w, T dt, T& S, T& C, T& ca, T& sa) {
+struct Turn {
+  T S, C, ca, sa, omc;
+};
+
+template <typename T>
+SQSM_DEV Turn<T> turn(T w, T dt) {
+  Turn<T> r;
   const T a = w * dt;
-  sq_sincos(a, &sa, &ca);
+  T sh, ch;
+  sq_sincos(T(0.5) * a, &sh, &ch);
+  r.sa = T(2) * sh * ch;
+  r.omc = T(2) * sh * sh;
+  r.ca = T(1) - r.omc;
   if (fabs(a) < T(1e-3)) {
     const T a2 = a * a;
-    S = dt * (T(1) - a2 / T(6) + a2 * a2 / T(120));
-    C = dt * a * (T(0.5) - a2 / T(24) + a2 * a2 / T(720));
+    r.S = dt * (T(1) - a2 / T(6) + a2 * a2 / T(120));
+    r.C = dt * a * (T(0.5) - a2 / T(24) + a2 * a2 / T(720));
   } else {
-    T sh, ch;
-    sq_sincos(T(0.5) * a, &sh, &ch);
-    S = sa / w;
-    C = T(2) * sh * sh / w;
+    r.S = r.sa / w;
+    r.C = r.omc / w;
   }
+  return r;
+}
+
+template <typename T>
+SQSM_DEV void turn_coeffs(T w, T dt, T& S, T& C, T& ca, T& sa) {
+  const Turn<T> r = turn(w, dt);
+  S = r.S;
+  C = r.C;
+  ca = r.ca;
+  sa = r.sa;
 }
 
 // dS/dw and dC/dw: series in a for |a| < 0.1, closed forms otherwise.
@@ -96,11 +118,11 @@ SQSM_DEV void turn_coeff_derivs(T w, T dt, T& dS, T& dC) {
     dsa = a * (T(-1) / T(3) + a2 * (T(1) / T(30) + a2 * (T(-1) / T(840) + a2 / T(45360))));
     dca = T(0.5) + a2 * (T(-1) / T(8) + a2 * (T(1) / T(144) + a2 * (T(-1) / T(5760) + a2 / T(403200))));
   } else {
-    T sa, ca, sh, ch;
-    sq_sincos(a, &sa, &ca);
+    T sh, ch;
     sq_sincos(T(0.5) * a, &sh, &ch);
-    dsa = (a * ca - sa) / (a * a);
-    dca = (a * sa - T(2) * sh * sh) / (a * a);
+    const T sa = T(2) * sh * ch, omc = T(2) * sh * sh;
+    dsa = (a * (T(1) - omc) - sa) / (a * a);
+    dca = (a * sa - omc) / (a * a);
   }
   dS = dt * dt * dsa;
   dC = dt * dt * dca;
@@ -121,14 +143,11 @@ SQSM_DEV void ct_f(const CTParams<T>& P, const T* x, T* o) {
 // however large the position (1 - cos a = 2 sin^2(a/2)).
 template <typename T>
 SQSM_DEV void ct_f_minus_x(const CTParams<T>& P, const T* x, T* o) {
-  T S, C, ca, sa, sh, ch;
-  turn_coeffs(x[4], P.dt, S, C, ca, sa);
-  sq_sincos(T(0.5) * x[4] * P.dt, &sh, &ch);
-  const T omc = T(2) * sh * sh;
-  o[0] = S * x[2] - C * x[3];
-  o[1] = C * x[2] + S * x[3];
-  o[2] = -omc * x[2] - sa * x[3];
-  o[3] = sa * x[2] - omc * x[3];
+  const Turn<T> t = turn(x[4], P.dt);
+  o[0] = t.S * x[2] - t.C * x[3];
+  o[1] = t.C * x[2] + t.S * x[3];
+  o[2] = -t.omc * x[2] - t.sa * x[3];
+  o[3] = t.sa * x[2] - t.omc * x[3];
   o[4] = T(0);
 }
 
@@ -140,22 +159,16 @@ SQSM_DEV void ct_f_minus_x(const CTParams<T>& P, const T* x, T* o) {
 //   da = dl_w dt formed from the small increment itself; omega: 0.
 // (The cubature regression of f is then I + the regression of g.)
 template <typename T>
-SQSM_DEV void ct_g_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
-  T Sm, Cm, cam, sam, Sx, Cx, cax, sax, shx, chx, sd, cd, shd, chd;
-  const T dt = P.dt;
-  turn_coeffs(m[4], dt, Sm, Cm, cam, sam);
-  turn_coeffs(m[4] + dl[4], dt, Sx, Cx, cax, sax);
-  sq_sincos(T(0.5) * (m[4] + dl[4]) * dt, &shx, &chx);
-  const T omx = T(2) * shx * shx;
-  const T da = dl[4] * dt;
-  sq_sincos(da, &sd, &cd);
-  sq_sincos(T(0.5) * da, &shd, &chd);
-  const T omd = T(2) * shd * shd;
+SQSM_DEV void ct_g_delta(const CTParams<T>& P, const Turn<T>& tm, const T* m, const T* dl, T* o) {
+  const Turn<T> tx = turn(m[4] + dl[4], P.dt);
+  T shd, chd;
+  sq_sincos(T(0.5) * dl[4] * P.dt, &shd, &chd);
+  const T sd = T(2) * shd * chd, omd = T(2) * shd * shd;
   const T ux = -omd * m[2] - sd * m[3], uy = sd * m[2] - omd * m[3];
-  o[0] = (Sx * dl[2] - Cx * dl[3]) + ((Sx - Sm) * m[2] - (Cx - Cm) * m[3]);
-  o[1] = (Cx * dl[2] + Sx * dl[3]) + ((Cx - Cm) * m[2] + (Sx - Sm) * m[3]);
-  o[2] = (-omx * dl[2] - sax * dl[3]) + (cam * ux - sam * uy);
-  o[3] = (sax * dl[2] - omx * dl[3]) + (sam * ux + cam * uy);
+  o[0] = (tx.S * dl[2] - tx.C * dl[3]) + ((tx.S - tm.S) * m[2] - (tx.C - tm.C) * m[3]);
+  o[1] = (tx.C * dl[2] + tx.S * dl[3]) + ((tx.C - tm.C) * m[2] + (tx.S - tm.S) * m[3]);
+  o[2] = (-tx.omc * dl[2] - tx.sa * dl[3]) + (tm.ca * ux - tm.sa * uy);
+  o[3] = (tx.sa * dl[2] - tx.omc * dl[3]) + (tm.sa * ux + tm.ca * uy);
   o[4] = T(0);
 }
 
@@ -292,21 +305,26 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 //   dx_k = F dx_{k-1} + c~ + q,  c~ = z_bar_x - m_k
 //        = (m_{k-1} - m_k) + (f(m_{k-1}) - m_{k-1}) + dbar_x,
 //   y_k  = H dx_k + d~ + v,      d~ = H m_k + d = z_bar_y (+ branch shift).
+// Steps are independent: one thread per step, addressed as (leaf chunk,
+// position in chunk) so that the chunk table gives the sequence; launch
+// n_chunks * leaf threads.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int linearization,
-              int centered, const T* __restrict__ ms, const T* __restrict__ Ns,
-              const T* __restrict__ y, T* __restrict__ F, T* __restrict__ c,
-              T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d, T* __restrict__ SRo) {
-  const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
+              int linearization, int centered, const T* __restrict__ ms,
+              const T* __restrict__ Ns, const T* __restrict__ y, T* __restrict__ F,
+              T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d,
+              T* __restrict__ SRo) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ch = tid / leaf;
   if (ch >= lv.n_chunks) return;
+  const int j = (int)(tid - ch * leaf);
+  if (j >= lv.count[ch]) return;
   constexpr int NX = 5, NY = 2;
   const CTParams<T> P = *Pp;
   const int b = lv.seq[ch];
-  const int64_t s0 = lv.first[ch];
-  const int cnt = lv.count[ch];
-  for (int j = 0; j < cnt; ++j) {
-    const int64_t s = s0 + j;
+  {
+    const int64_t s = lv.first[ch] + j;
     const int64_t rp = s + b, rk = s + b + 1;
     T m[NX], N[NX * NX];
     // transition at k - 1
@@ -324,9 +342,10 @@ ct_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, int l
       ct_f(P, m, fm);
     }
     if (linearization == 0) {
-      cubature_regress<T, NX, true>(m, N, fm, !centered, P.SQ,
-                                    [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, mm_, dl, o); },
-                                    Fm, cm, Sl);
+      const Turn<T> tm = turn(m[4], P.dt);
+      cubature_regress<T, NX, true>(
+          m, N, fm, !centered, P.SQ,
+          [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); }, Fm, cm, Sl);
     } else {
       ct_jac_f(P, m, Fm);
 #pragma unroll

@@ -30,6 +30,7 @@ bool lgssm_shape_supported(int nx, int ny);
 
 struct IplsArgs {
   int linearization, M;
+  int leaf;            // leaf chunk length of the plan
   double theta[3], dt, sensors[4];
   const void *y, *m0, *N0, *init_ms, *init_Ns;
   void *ms, *Ns;

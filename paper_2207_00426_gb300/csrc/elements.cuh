@@ -229,14 +229,20 @@ SQSM_DEV void filter_element(const Gamma<T, NX, NY>& g, const T* y, bool first, 
   // Wm = Y^{-1} H F (NY x NX); Z = Wm^T; eta = Wm^T Y^{-1} (y - H c - d)
   T Wm[NY * NX];
   mm<T, NY, NX, NX>(g.H, g.F, Wm);
+  {
+    T inv[NY];
 #pragma unroll
-  for (int j = 0; j < NX; ++j) {
-    T col[NY];
+    for (int i = 0; i < NY; ++i) inv[i] = T(1) / Y[i * NY + i];
 #pragma unroll
-    for (int i = 0; i < NY; ++i) col[i] = Wm[i * NX + j];
-    lsolve<T, NY>(Y, col);
+    for (int j = 0; j < NX; ++j) {
 #pragma unroll
-    for (int i = 0; i < NY; ++i) Wm[i * NX + j] = col[i];
+      for (int i = 0; i < NY; ++i) {
+        T sacc = Wm[i * NX + j];
+#pragma unroll
+        for (int k = 0; k < i; ++k) sacc -= Y[i * NY + k] * Wm[k * NX + j];
+        Wm[i * NX + j] = sacc * inv[i];
+      }
+    }
   }
   // A = (I - K H) F = F - Psi21 Wm  (k > 1);  A = 0 (k = 1)
 #pragma unroll

@@ -5,7 +5,7 @@
 
 #include <vector>
 
-#include "scan.cuh"
+#include "wscan.cuh"
 
 namespace sqsm {
 
@@ -16,6 +16,19 @@ struct LevelSet {
   std::vector<DevLevel> lv;
   std::vector<int64_t> n_items;
   int64_t* leaf_chunk_off = nullptr;   // device, B+1
+  // per item level l >= 1: first item of each sequence (device, B+1) and the
+  // largest number of items any sequence has there (host)
+  std::vector<int64_t*> seq_item_off;
+  std::vector<int64_t> max_seq_items;
+  int B = 0;
+
+  // Lowest item level whose per-sequence item count fits one Kogge-Stone block.
+  int ks_level(int ks_max) const {
+    const int Lc = (int)lv.size();
+    for (int l = 1; l < Lc; ++l)
+      if (max_seq_items[l] <= ks_max) return l;
+    return Lc;
+  }
 };
 
 // Device buffers of one scan for one (dtype, nx): items[l], carry[l],
@@ -73,22 +86,40 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
                     const T* y, const T* m0, const T* N0, T* mf, T* Nf, double* partial,
                     int* status, cudaStream_t s, Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
+  constexpr int KS = KsMax<T, FRec<NX>::size>::value;
+  const int Lk = L.ks_level(KS);
   if (Lc > 1) {  // with one leaf chunk per sequence every carry is the prior
-    ProfScope ps(P, K_FILTER_LEAF_UP, s);
-    filter_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-        L.lv[0], sq, gv, y, m0, N0, (T*)W.items[1]);
-  }
-  for (int l = 1; l < Lc; ++l) {
+    {
+      ProfScope ps(P, K_FILTER_LEAF_UP, s);
+      filter_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+          L.lv[0], sq, gv, y, m0, N0, (T*)W.items[1]);
+    }
+    for (int l = 1; l < Lk; ++l) {
+      ProfScope ps(P, K_FILTER_UP, s);
+      if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+        filter_up_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
+            L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+      else
+        filter_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+            L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+    }
     ProfScope ps(P, K_FILTER_UP, s);
-    filter_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-        L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+    filter_top_ks<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk],
+                                                        (const T*)W.items[Lk], (T*)W.carry[Lk],
+                                                        W.flag[Lk]);
+  } else {
+    cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
   }
-  cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
-  for (int l = Lc - 1; l >= 1; --l) {
+  for (int l = (Lc > 1 ? Lk : Lc) - 1; l >= 1; --l) {
     ProfScope ps(P, K_FILTER_DOWN, s);
-    filter_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-        L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
-        W.flag[l]);
+    if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+      filter_down_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
+    else
+      filter_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_FILTER_LEAF_DOWN, s);
   filter_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
@@ -100,22 +131,40 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
                       const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s,
                       Prof* P = nullptr, const T* nominal = nullptr) {
   const int Lc = (int)L.lv.size();
+  constexpr int KS = KsMax<T, SRec<NX>::size>::value;
+  const int Lk = L.ks_level(KS);
   if (Lc > 1) {
-    ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
-    smoother_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-        L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
-  }
-  for (int l = 1; l < Lc; ++l) {
+    {
+      ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
+      smoother_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+          L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
+    }
+    for (int l = 1; l < Lk; ++l) {
+      ProfScope ps(P, K_SMOOTHER_UP, s);
+      if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+        smoother_up_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
+            L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+      else
+        smoother_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+            L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+    }
     ProfScope ps(P, K_SMOOTHER_UP, s);
-    smoother_up<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-        L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
+    smoother_top_ks<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk],
+                                                          (const T*)W.items[Lk], (T*)W.carry[Lk],
+                                                          W.flag[Lk]);
+  } else {
+    cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
   }
-  cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
-  for (int l = Lc - 1; l >= 1; --l) {
+  for (int l = (Lc > 1 ? Lk : Lc) - 1; l >= 1; --l) {
     ProfScope ps(P, K_SMOOTHER_DOWN, s);
-    smoother_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
-        L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
-        W.flag[l]);
+    if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+      smoother_down_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
+    else
+      smoother_down<T, NX><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
   smoother_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(

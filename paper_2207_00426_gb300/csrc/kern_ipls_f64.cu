@@ -12,8 +12,8 @@ void ipls_params_f64(const IplsArgs& a, cudaStream_t s) {
 
 void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
   using T = double;
-  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-      Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, 0, (const T*)a.ms,
+  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 0, (const T*)a.ms,
       (const T*)a.Ns, (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
 }
 
@@ -42,8 +42,8 @@ void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   for (int it = 0; it < a.M; ++it) {
     {
       ProfScope ps(a.prof, K_SLR, s);
-      ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-          Lf.lv[0], sq, (const CTParams<T>*)a.params, a.linearization, 1, ms, Ns,
+      ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+          Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, ms, Ns,
           (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
     }
     {

@@ -139,6 +139,9 @@ SQSM_DEV void mtv(const T* A, const T* x, T* y) {
   }
 }
 
+// Triangular solves divide once per diagonal entry and multiply by the
+// reciprocal elsewhere.
+
 // x = L^{-1} b for lower L (N x N); in place on b.
 template <typename T, int N>
 SQSM_DEV void lsolve(const T* L, T* b) {
@@ -166,6 +169,9 @@ SQSM_DEV void ltsolve(const T* L, T* b) {
 // X <- X L^{-1} for X (M x N), lower L (N x N): each row x solves z L = x.
 template <typename T, int M, int N>
 SQSM_DEV void rsolve(T* X, const T* L) {
+  T inv[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) inv[i] = T(1) / L[i * N + i];
 #pragma unroll
   for (int r = 0; r < M; ++r) {
 #pragma unroll
@@ -173,7 +179,7 @@ SQSM_DEV void rsolve(T* X, const T* L) {
       T s = X[r * N + i];
 #pragma unroll
       for (int k = i + 1; k < N; ++k) s -= X[r * N + k] * L[k * N + i];
-      X[r * N + i] = s / L[i * N + i];
+      X[r * N + i] = s * inv[i];
     }
   }
 }
@@ -181,6 +187,9 @@ SQSM_DEV void rsolve(T* X, const T* L) {
 // X <- X L^{-T} for X (M x N), lower L (N x N): each row x solves z L^T = x.
 template <typename T, int M, int N>
 SQSM_DEV void rsolve_t(T* X, const T* L) {
+  T inv[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) inv[i] = T(1) / L[i * N + i];
 #pragma unroll
   for (int r = 0; r < M; ++r) {
 #pragma unroll
@@ -188,7 +197,7 @@ SQSM_DEV void rsolve_t(T* X, const T* L) {
       T s = X[r * N + i];
 #pragma unroll
       for (int k = 0; k < i; ++k) s -= X[r * N + k] * L[i * N + k];
-      X[r * N + i] = s / L[i * N + i];
+      X[r * N + i] = s * inv[i];
     }
   }
 }

@@ -63,6 +63,9 @@ struct TableDesc {
   int64_t* offsets;         // {0, n}
   int64_t* leaf_chunk_off;  // {0, filter leaf chunks}
   int64_t n, leaf_chunks;
+  int nso;                  // per-level sequence item offsets {0, items}
+  int64_t* so[2 * kMaxLevels];
+  int64_t so_val[2 * kMaxLevels];
 };
 
 __global__ void fill_tables(TableDesc t) {
@@ -72,6 +75,10 @@ __global__ void fill_tables(TableDesc t) {
     t.offsets[1] = t.n;
     t.leaf_chunk_off[0] = 0;
     t.leaf_chunk_off[1] = t.leaf_chunks;
+    for (int l = 0; l < t.nso; ++l) {
+      t.so[l][0] = 0;
+      t.so[l][1] = t.so_val[l];
+    }
   }
   for (int l = 0; l < t.nlev; ++l) {
     const int64_t nch = (t.items[l] + t.size[l] - 1) / t.size[l];
@@ -100,6 +107,9 @@ struct Carver {
 bool carve_scan(Carver& cv, int64_t items0, int L0, int R, size_t es, size_t rec, size_t crec,
                 LevelSet& L, ScanBuffers& W, TableDesc& td) {
   L.lv.clear();
+  L.seq_item_off.clear();
+  L.max_seq_items.clear();
+  L.B = 1;
   L.n_items.assign(1, items0);
   int64_t items = items0;
   int size = L0;
@@ -119,6 +129,17 @@ bool carve_scan(Carver& cv, int64_t items0, int L0, int R, size_t es, size_t rec
     ++td.nlev;
     L.lv.push_back(d);
     L.n_items.push_back(nch);
+    // one sequence: its items at the next level are [0, nch)
+    int64_t* so = (int64_t*)cv.take(2 * sizeof(int64_t));
+    td.so[td.nso] = so;
+    td.so_val[td.nso] = nch;
+    ++td.nso;
+    if (L.seq_item_off.empty()) {
+      L.seq_item_off.push_back(nullptr);
+      L.max_seq_items.push_back(0);
+    }
+    L.seq_item_off.push_back(so);
+    L.max_seq_items.push_back(nch);
     items = nch;
     size = R;
     if (nch == 1) break;

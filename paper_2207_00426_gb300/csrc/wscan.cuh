@@ -1,0 +1,249 @@
+// Upper scan levels with one warp per chunk (see warp_ops.cuh); used for the
+// levels that hold few chunks, where one thread per chunk leaves most of the
+// GPU idle and each combine's latency sets the time.
+#pragma once
+
+#include "scan.cuh"
+#include "warp_ops.cuh"
+
+namespace sqsm {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int64_t kWarpLevelMaxChunks = 2048;
+
+template <typename T, int NX> struct WFilterBuf {
+  T a[FRec<NX>::size], b[FRec<NX>::size], c[FRec<NX>::size];
+  T cb[NX], cU[NX * NX], nb[NX], nU[NX * NX];
+  WFilterWs<T, NX> ws;
+};
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
+filter_up_w(DevLevel lv, const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int REC = FRec<NX>::size;
+  __shared__ WFilterBuf<T, NX> sh[kWarpsPerBlock];
+  const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
+  if (c >= lv.n_chunks) return;   // uniform per warp
+  WFilterBuf<T, NX>& B = sh[wid];
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T* agg = B.a;
+  T* el = B.b;
+  T* tmp = B.c;
+  for (int i = lane; i < REC; i += kWarp) agg[i] = in[i0 * REC + i];
+  __syncwarp();
+  for (int j = 1; j < cnt; ++j) {
+    for (int i = lane; i < REC; i += kWarp) el[i] = in[(i0 + j) * REC + i];
+    __syncwarp();
+    wfilter_combine<T, NX>(agg, el, tmp, B.ws, lane);
+    T* t = agg;
+    agg = tmp;
+    tmp = t;
+  }
+  for (int i = lane; i < REC; i += kWarp) out[c * REC + i] = agg[i];
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
+filter_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+              const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX;
+  __shared__ WFilterBuf<T, NX> sh[kWarpsPerBlock];
+  const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
+  if (c >= lv.n_chunks) return;
+  WFilterBuf<T, NX>& B = sh[wid];
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  int flag = flag_in[c];
+  for (int i = lane; i < CREC; i += kWarp) {
+    const T v = carry_in[c * CREC + i];
+    if (i < NX) B.cb[i] = v; else B.cU[i - NX] = v;
+  }
+  __syncwarp();
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t it = i0 + j;
+    for (int i = lane; i < CREC; i += kWarp) carry_out[it * CREC + i] = i < NX ? B.cb[i] : B.cU[i - NX];
+    if (lane == 0) flag_out[it] = flag;
+    __syncwarp();
+    if (j + 1 < cnt) {
+      if (flag) {
+        for (int i = lane; i < REC; i += kWarp) B.a[i] = items[it * REC + i];
+        __syncwarp();
+        wfilter_apply<T, NX>(B.cb, B.cU, B.a, B.nb, B.nU, B.ws, lane);
+        for (int i = lane; i < NX * NX; i += kWarp) B.cU[i] = B.nU[i];
+        if (lane < NX) B.cb[lane] = B.nb[lane];
+      } else {
+        for (int i = lane; i < NX; i += kWarp) B.cb[i] = items[it * REC + FRec<NX>::b + i];
+        for (int i = lane; i < NX * NX; i += kWarp) B.cU[i] = items[it * REC + FRec<NX>::U + i];
+        flag = 1;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T, int NX> struct WSmootherBuf {
+  T a[SRec<NX>::size], b[SRec<NX>::size], c[SRec<NX>::size];
+  T cg[NX], cD[NX * NX];
+  WSmootherWs<T, NX> ws;
+};
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
+smoother_up_w(DevLevel lv, const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int REC = SRec<NX>::size;
+  __shared__ WSmootherBuf<T, NX> sh[kWarpsPerBlock];
+  const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
+  if (c >= lv.n_chunks) return;
+  WSmootherBuf<T, NX>& B = sh[wid];
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T* agg = B.a;
+  T* el = B.b;
+  T* tmp = B.c;
+  for (int i = lane; i < REC; i += kWarp) agg[i] = in[(i0 + cnt - 1) * REC + i];
+  __syncwarp();
+  for (int j = cnt - 2; j >= 0; --j) {
+    for (int i = lane; i < REC; i += kWarp) el[i] = in[(i0 + j) * REC + i];
+    __syncwarp();
+    wsmoother_combine<T, NX>(el, agg, tmp, B.ws, lane);
+    T* t = agg;
+    agg = tmp;
+    tmp = t;
+  }
+  for (int i = lane; i < REC; i += kWarp) out[c * REC + i] = agg[i];
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
+smoother_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+                const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
+  __shared__ WSmootherBuf<T, NX> sh[kWarpsPerBlock];
+  const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+  const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
+  if (c >= lv.n_chunks) return;
+  WSmootherBuf<T, NX>& B = sh[wid];
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  int flag = flag_in[c];
+  for (int i = lane; i < CREC; i += kWarp) {
+    const T v = carry_in[c * CREC + i];
+    if (i < NX) B.cg[i] = v; else B.cD[i - NX] = v;
+  }
+  __syncwarp();
+  for (int j = cnt - 1; j >= 0; --j) {
+    const int64_t it = i0 + j;
+    for (int i = lane; i < CREC; i += kWarp) carry_out[it * CREC + i] = i < NX ? B.cg[i] : B.cD[i - NX];
+    if (lane == 0) flag_out[it] = flag;
+    __syncwarp();
+    if (j > 0) {
+      if (flag) {
+        for (int i = lane; i < REC; i += kWarp) B.a[i] = items[it * REC + i];
+        __syncwarp();
+        wsmoother_apply<T, NX>(B.a, B.cg, B.cD, B.ws, lane);
+      } else {
+        for (int i = lane; i < NX; i += kWarp) B.cg[i] = items[it * REC + SRec<NX>::g + i];
+        for (int i = lane; i < NX * NX; i += kWarp) B.cD[i] = items[it * REC + SRec<NX>::D + i];
+        flag = 1;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+inline unsigned wgrid_for(int64_t chunks) {
+  return (unsigned)((chunks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+}
+
+}  // namespace sqsm
+
+namespace sqsm {
+
+// Top of the tree in one launch: when every sequence has at most KS items at
+// a level, one block per sequence runs a Kogge-Stone inclusive scan of them in
+// shared memory (ceil(log2 KS) dependent combines) and writes each item's
+// exclusive prefix (filter) / suffix (smoother) as its carry, replacing all
+// higher up- and down-levels.
+// Block width: 128 (FP32) / 64 (FP64) items, fewer if the records would not
+// fit in 48 KB of static shared memory.
+template <typename T, int REC> struct KsMax {
+  static constexpr int cap = sizeof(T) == 4 ? 128 : 64;
+  static constexpr int fit = (int)((48 * 1024) / (REC * sizeof(T)) / 32 * 32);
+  static constexpr int value = cap < fit ? cap : fit;
+};
+
+template <typename T, int NX>
+__global__ void __launch_bounds__((KsMax<T, FRec<NX>::size>::value))
+filter_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
+              T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = FRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
+  __shared__ T S[KS * REC];
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int64_t i0 = seq_item_off[b];
+  const int c = (int)(seq_item_off[b + 1] - i0);
+  T mine[REC], tmp[REC];
+  if (t < c) load<T, REC>(items + (i0 + t) * REC, mine);
+  for (int d = 1; d < c; d <<= 1) {
+    if (t < c) store<T, REC>(S + t * REC, mine);
+    __syncthreads();
+    if (t < c && t >= d) {
+      filter_combine<T, NX>(S + (t - d) * REC, mine, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncthreads();
+  }
+  if (t < c) store<T, REC>(S + t * REC, mine);
+  __syncthreads();
+  if (t < c) {
+    T* co = carry_out + (i0 + t) * CREC;
+    if (t > 0) {
+      const T* p = S + (t - 1) * REC;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) co[i] = p[FRec<NX>::b + i];
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[FRec<NX>::U + i];
+    }
+    flag_out[i0 + t] = t > 0 ? 1 : 0;
+  }
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__((KsMax<T, SRec<NX>::size>::value))
+smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
+                T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = SRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
+  __shared__ T S[KS * REC];
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int64_t i0 = seq_item_off[b];
+  const int c = (int)(seq_item_off[b + 1] - i0);
+  T mine[REC], tmp[REC];
+  if (t < c) load<T, REC>(items + (i0 + t) * REC, mine);
+  for (int d = 1; d < c; d <<= 1) {
+    if (t < c) store<T, REC>(S + t * REC, mine);
+    __syncthreads();
+    if (t + d < c) {
+      smoother_combine<T, NX>(mine, S + (t + d) * REC, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncthreads();
+  }
+  if (t < c) store<T, REC>(S + t * REC, mine);
+  __syncthreads();
+  if (t < c) {
+    T* co = carry_out + (i0 + t) * CREC;
+    if (t + 1 < c) {
+      const T* p = S + (t + 1) * REC;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) co[i] = p[SRec<NX>::g + i];
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[SRec<NX>::D + i];
+    }
+    flag_out[i0 + t] = t + 1 < c ? 1 : 0;
+  }
+}
+
+}  // namespace sqsm
