@@ -183,11 +183,8 @@ def gpu_arm(args, rank, world, local):
             pg.barrier()
 
     def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return t.item()
+        from paper_2207_00426_gb300 import dist as D
+        return D.allreduce_max(x)
 
     n, M = args.n, args.M
     d = W.ct_sequence(n=n, seed=SEED + rank)
