@@ -67,7 +67,8 @@ def config(args, world):
     return {"workload": f"coordinated-turn bearings-only tracking, cubature IPLS, "
                         f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
             "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
-            "sequences_total": world, "leaf_chunk": 4, "radix": 4,
+            "sequences_total": world, "leaf_chunk": 4,
+            "upper_levels": "folds of 4 above 160000 items, 32-item warp scans below",
             "l2": "flushed between timed steps (256 MiB write outside the events)",
             "parallelism": f"independent sequences, {world} GPU(s)"}
 
@@ -275,12 +276,14 @@ def gpu_arm(args, rank, world, local):
             a0[1] += c
     ctx.profile(False)
     launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
-    flops = CM.ipls_kernel_flops([n], leaf=4, radix=4)
+    flops = CM.ipls_kernel_flops([n], leaf=4)
     total_ms = sum(t for t, _ in acc.values())
     kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / nprof,
                    "share": t / total_ms} for k, (t, c) in acc.items()}
     top = max(acc, key=lambda k: acc[k][0])
-    f_launch = flops[top][0]
+    # algorithmic flops of the family per step, spread over its launches
+    fam_flops = flops[top][0] * flops[top][1] * M
+    f_launch = fam_flops / (acc[top][1] / nprof)
     t_launch = acc[top][0] / acc[top][1] / 1e3
     peak = 152 * 128 * 2 * 2070e6 / 1e12        # FP32 FMA lanes x 2 x max SM clock
     achieved = f_launch / t_launch / 1e12
@@ -354,10 +357,10 @@ def gpu_arm(args, rank, world, local):
             a0[0] += t
             a0[1] += c
     ctx.profile(False)
-    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])), leaf=4, radix=4)
+    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])), leaf=4)
     btot = sum(t for t, _ in bacc.values())
     btop = max(bacc, key=lambda k: bacc[k][0])
-    bach = bflops[btop][0] / (bacc[btop][0] / bacc[btop][1] / 1e3) / 1e12
+    bach = bflops[btop][0] * bflops[btop][1] * M / (bacc[btop][0] / 2 / 1e3) / 1e12
     batched = {"workload": "4096 CT sequences, lengths U{100..5000}, cubature IPLS, M=10",
                "steps_total": nb_tot, "value": nb_tot * M / tb, "unit": UNIT,
                "ms_per_step": 1e3 * tb,

@@ -4,7 +4,9 @@ Counts follow the formulas the kernels evaluate (an FMA is 2 flops; an add,
 multiply, divide, square root, log, sine/cosine or atan2 is 1), with the
 triangular structure of the factors taken into account.  Per-launch totals
 use the same chunking as the library's plan (leaf chunks of ``leaf`` steps,
-upper levels of ``radix`` items per thread).
+upper levels of ``radix`` items, or the adaptive 4 / 32 choice for radix 0).
+Upper levels count the work-efficient number of combines (c - 1 per chunk of
+c items); the warp-scanned chunks do more.
 """
 import math
 
@@ -91,6 +93,11 @@ def _chunks(counts, size):
     return sizes, nxt
 
 
+# Adaptive plans (radix 0) fold a level of more items than this 4 per thread
+# and scan smaller levels in chunks of 32 (one warp per chunk).
+FOLD_ABOVE_ITEMS = 160000
+
+
 def _levels(counts0, leaf, radix):
     levels = []
     counts = list(counts0)
@@ -99,12 +106,15 @@ def _levels(counts0, leaf, radix):
         sizes, nxt = _chunks(counts, size)
         levels.append(sizes)
         counts = nxt
-        size = radix
+        if radix > 1:
+            size = radix
+        else:
+            size = 32 if sum(counts) <= FOLD_ABOVE_ITEMS else 4
         if all(c == 1 for c in counts):
             return levels
 
 
-def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=4, radix=4, linearization="cubature"):
+def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=4, radix=0, linearization="cubature"):
     """Algorithmic flops per launch of each kernel family for one IPLS
     iteration over sequences of the given lengths.  Returns
     {family: (flops per launch, launches per iteration)}."""

@@ -54,14 +54,23 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
       adj_smoother_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab,
                                                                              (T*)Wa.items[1]);
       for (int l = 1; l < Lc; ++l)
-        adj_up<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+        if (Lf.chunk_scan(l))
+          adj_up_cs<T, true><<<(unsigned)Lf.lv[l].n_chunks, kChunkScan, 0, s>>>(
+              Lf.lv[l], (T*)Wa.items[l], (T*)Wa.items[l + 1]);
+        else
+          adj_up<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+              Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
     }
     cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     for (int l = Lc - 1; l >= 1; --l)
-      adj_down<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-          Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-          (T*)Wa.carry[l], Wa.flag[l]);
+      if (Lf.chunk_scan(l))
+        adj_down_cs<T, true><<<cs_down_grid(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+            (T*)Wa.carry[l], Wa.flag[l]);
+      else
+        adj_down<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+            (T*)Wa.carry[l], Wa.flag[l]);
     adj_smoother_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
         Lf.lv[0], sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
     // filter adjoint: backward-in-time scan of maps
@@ -69,14 +78,23 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
       adj_filter_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab, lbar,
                                                                            (T*)Wa.items[1]);
       for (int l = 1; l < Lc; ++l)
-        adj_up<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+        if (Lf.chunk_scan(l))
+          adj_up_cs<T, false><<<(unsigned)Lf.lv[l].n_chunks, kChunkScan, 0, s>>>(
+              Lf.lv[l], (T*)Wa.items[l], (T*)Wa.items[l + 1]);
+        else
+          adj_up<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+              Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
     }
     cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     for (int l = Lc - 1; l >= 1; --l)
-      adj_down<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-          Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-          (T*)Wa.carry[l], Wa.flag[l]);
+      if (Lf.chunk_scan(l))
+        adj_down_cs<T, false><<<cs_down_grid(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+            (T*)Wa.carry[l], Wa.flag[l]);
+      else
+        adj_down<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
+            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
+            (T*)Wa.carry[l], Wa.flag[l]);
     adj_filter_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
         Lf.lv[0], sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
     // SLR adjoint -> next cotangent of the nominal trajectory, theta partials

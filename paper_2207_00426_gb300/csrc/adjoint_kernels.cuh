@@ -242,6 +242,66 @@ adj_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
   }
 }
 
+// Chunk-scan variant of an upper level: one warp per chunk of at most 32
+// maps computes, in place, the composition of the chunk's maps from its
+// first (in scan order) through each item, and writes the chunk's total.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kChunkScan)
+adj_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
+  constexpr int REC = MapRec<5>::size;
+  __shared__ T S[kChunkScan * REC];
+  const int64_t c = blockIdx.x;
+  const int t = threadIdx.x;   // position in scan order
+  const int cnt = lv.count[c];
+  const int64_t i = lv.first[c] + (FWD ? t : cnt - 1 - t);
+  T mine[REC], tmp[REC];
+  if (t < cnt) load<T, REC>(items + i * REC, mine);
+  for (int d = 1; d < cnt; d <<= 1) {
+    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    __syncwarp();
+    if (t < cnt && t >= d) {
+      map_compose<T, 5>(S + (t - d) * REC, mine, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncwarp();
+  }
+  if (t < cnt) store<T, REC>(items + i * REC, mine);
+  if (t == cnt - 1) store<T, REC>(out + c * REC, mine);
+}
+
+// One thread per item of a chunk-scanned level: the cotangent entering item
+// i is the chunk's carry pushed through the composed maps of the items
+// before i (in scan order).
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(kBlock)
+adj_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
+            const int* __restrict__ fin, T* __restrict__ cout, int* __restrict__ fout) {
+  constexpr int REC = MapRec<5>::size, X = XRec<5>::size;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = tid / kChunkScan;
+  if (c >= lv.n_chunks) return;
+  const int j = (int)(tid - c * kChunkScan);
+  const int cnt = lv.count[c];
+  if (j >= cnt) return;
+  const int64_t i = lv.first[c] + j;
+  const bool head = FWD ? j == 0 : j == cnt - 1;
+  const int flag = fin[c];
+  T x[X];
+  load<T, X>(cin + c * X, x);
+  if (!flag) {
+#pragma unroll
+    for (int k = 0; k < X; ++k) x[k] = T(0);
+  }
+  if (!head) {
+    T mp[REC], xn[X];
+    load<T, REC>(items + (FWD ? i - 1 : i + 1) * REC, mp);
+    map_apply<T, 5>(mp, x, xn);
+    copy<T, X>(xn, x);
+  }
+  store<T, X>(cout + i * X, x);
+  fout[i] = head ? flag : 1;
+}
+
 // --------------------------- SLR VJP and reductions ------------------------
 
 // One thread per smoother leaf chunk (state rows): nominal-trajectory

@@ -112,9 +112,15 @@ int cuda_fail(sqsm_ctx* ctx, cudaError_t e, const char* where) {
   return fail(ctx, SQSM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Adaptive plans fold a level with more items than this (4 per thread)
+// rather than chunk-scanning it: its folds alone give > 40k threads, enough
+// to fill the GPU.
+constexpr int64_t kFoldAboveItems = 160000;
+
 // Levels of a segmented scan whose level-0 items are `counts[b]` per
-// sequence: chunks of L0 items at the leaf, R items above, until each
-// sequence has one item.
+// sequence: chunks of L0 items at the leaf, then chunks of R items (or, for
+// R == 0, of 4 or 32 items chosen per level) until each sequence has one item.
+
 bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
   std::vector<int64_t> counts = counts0;
   L.B = (int)counts0.size();
@@ -122,8 +128,19 @@ bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
   int64_t total = 0;
   for (int64_t v : counts) total += v;
   L.n_items.push_back(total);
+  L.cs.assign(1, 0);
   for (;;) {
-    const int64_t size = level == 0 ? p.L0 : p.R;
+    int64_t size = level == 0 ? p.L0 : p.R;
+    if (level > 0) {
+      bool cs = false;
+      if (p.R == 0) {                       // adaptive: see get_plan
+        int64_t items = 0;
+        for (int64_t v : counts) items += v;
+        cs = items <= kFoldAboveItems;
+        size = cs ? kChunkScan : 4;
+      }
+      L.cs.push_back(cs ? 1 : 0);
+    }
     std::vector<int64_t> first;
     std::vector<int32_t> count, seq;
     std::vector<int64_t> next(counts.size());
@@ -189,7 +206,13 @@ bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
 
 Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
   const int L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk : 4;
-  const int R = ctx->opt.radix > 1 ? ctx->opt.radix : 4;
+  // default (radix 0): a level with many items is folded 4 items per thread
+  // (enough threads to fill the GPU, least work); a level with few items is
+  // scanned in one-warp Kogge-Stone chunks of 32 (shortest chain of
+  // dependent combines).  An explicit radix folds that many items per
+  // thread at every level.
+  const bool chunk_scan = ctx->opt.radix <= 1;
+  const int R = chunk_scan ? 0 : ctx->opt.radix;
   for (auto& p : ctx->plans)
     if (p->B == batch && p->L0 == L0 && p->R == R &&
         std::memcmp(p->offsets.data(), offsets, sizeof(int64_t) * (batch + 1)) == 0)

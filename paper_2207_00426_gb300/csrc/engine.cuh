@@ -21,6 +21,10 @@ struct LevelSet {
   std::vector<int64_t*> seq_item_off;
   std::vector<int64_t> max_seq_items;
   int B = 0;
+  // per chunk level l >= 1: 1 = one-warp Kogge-Stone chunks of 32 items,
+  // 0 = sequential folds (one thread per chunk)
+  std::vector<char> cs;
+  bool chunk_scan(int l) const { return l < (int)cs.size() && cs[l]; }
 
   // Lowest item level whose per-sequence item count fits one Kogge-Stone block.
   int ks_level(int ks_max) const {
@@ -96,7 +100,10 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_FILTER_UP, s);
-      if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+      if (L.chunk_scan(l))
+        filter_up_cs<T, NX><<<(unsigned)L.lv[l].n_chunks, kChunkScan, 0, s>>>(
+            L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
+      else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
         filter_up_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
             L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
       else
@@ -112,7 +119,11 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
   }
   for (int l = (Lc > 1 ? Lk : Lc) - 1; l >= 1; --l) {
     ProfScope ps(P, K_FILTER_DOWN, s);
-    if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+    if (L.chunk_scan(l))
+      filter_down_cs<T, NX><<<cs_down_grid(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
+    else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
       filter_down_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
           L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
           (T*)W.carry[l], W.flag[l]);
@@ -141,7 +152,10 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_SMOOTHER_UP, s);
-      if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+      if (L.chunk_scan(l))
+        smoother_up_cs<T, NX><<<(unsigned)L.lv[l].n_chunks, kChunkScan, 0, s>>>(
+            L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
+      else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
         smoother_up_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
             L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
       else
@@ -157,7 +171,11 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
   }
   for (int l = (Lc > 1 ? Lk : Lc) - 1; l >= 1; --l) {
     ProfScope ps(P, K_SMOOTHER_DOWN, s);
-    if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
+    if (L.chunk_scan(l))
+      smoother_down_cs<T, NX><<<cs_down_grid(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
+          (T*)W.carry[l], W.flag[l]);
+    else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
       smoother_down_w<T, NX><<<wgrid_for(L.lv[l].n_chunks), kWarp * kWarpsPerBlock, 0, s>>>(
           L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1],
           (T*)W.carry[l], W.flag[l]);

@@ -247,3 +247,130 @@ smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ 
 }
 
 }  // namespace sqsm
+
+namespace sqsm {
+
+// Upper levels in "chunk scan" form (radix kChunkScan = one warp): the up
+// kernel scans each chunk with Kogge-Stone inside one warp, overwriting the
+// items with their in-chunk inclusive prefixes (filter) / suffixes (smoother)
+// and writing the chunk total; the down kernel gives every item its carry in
+// one step, the chunk's carry applied to the neighbour's in-chunk prefix.
+constexpr int kChunkScan = 32;
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kChunkScan)
+filter_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
+  constexpr int REC = FRec<NX>::size;
+  __shared__ T S[kChunkScan * REC];
+  const int64_t c = blockIdx.x;
+  const int t = threadIdx.x;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T mine[REC], tmp[REC];
+  if (t < cnt) load<T, REC>(items + (i0 + t) * REC, mine);
+  for (int d = 1; d < cnt; d <<= 1) {
+    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    __syncwarp();
+    if (t < cnt && t >= d) {
+      filter_combine<T, NX>(S + (t - d) * REC, mine, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncwarp();
+  }
+  if (t < cnt) store<T, REC>(items + (i0 + t) * REC, mine);
+  if (t == cnt - 1) store<T, REC>(out + c * REC, mine);
+}
+
+// One thread per item of the level.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+               const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = tid / kChunkScan;
+  if (c >= lv.n_chunks) return;
+  const int j = (int)(tid - c * kChunkScan);
+  if (j >= lv.count[c]) return;
+  const int64_t i = lv.first[c] + j;
+  const int flag = flag_in[c];
+  T cb[NX], cU[NX * NX];
+  if (j == 0) {
+    load<T, NX>(carry_in + c * CREC, cb);
+    load<T, NX * NX>(carry_in + c * CREC + NX, cU);
+  } else if (flag) {
+    T pb[NX], pU[NX * NX], el[REC];
+    load<T, NX>(carry_in + c * CREC, pb);
+    load<T, NX * NX>(carry_in + c * CREC + NX, pU);
+    load<T, REC>(items + (i - 1) * REC, el);
+    filter_apply<T, NX>(pb, pU, el, cb, cU);
+  } else {
+    load<T, NX>(items + (i - 1) * REC + FRec<NX>::b, cb);
+    load<T, NX * NX>(items + (i - 1) * REC + FRec<NX>::U, cU);
+  }
+  store<T, NX>(carry_out + i * CREC, cb);
+  store<T, NX * NX>(carry_out + i * CREC + NX, cU);
+  flag_out[i] = j == 0 ? flag : 1;
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kChunkScan)
+smoother_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
+  constexpr int REC = SRec<NX>::size;
+  __shared__ T S[kChunkScan * REC];
+  const int64_t c = blockIdx.x;
+  const int t = threadIdx.x;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  T mine[REC], tmp[REC];
+  if (t < cnt) load<T, REC>(items + (i0 + t) * REC, mine);
+  for (int d = 1; d < cnt; d <<= 1) {
+    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    __syncwarp();
+    if (t + d < cnt) {
+      smoother_combine<T, NX>(mine, S + (t + d) * REC, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncwarp();
+  }
+  if (t < cnt) store<T, REC>(items + (i0 + t) * REC, mine);
+  if (t == 0 && cnt > 0) store<T, REC>(out + c * REC, mine);
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kBlock)
+smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
+                 const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = tid / kChunkScan;
+  if (c >= lv.n_chunks) return;
+  const int j = (int)(tid - c * kChunkScan);
+  const int cnt = lv.count[c];
+  if (j >= cnt) return;
+  const int64_t i = lv.first[c] + j;
+  const int flag = flag_in[c];
+  T cg[NX], cD[NX * NX];
+  if (j == cnt - 1) {
+    load<T, NX>(carry_in + c * CREC, cg);
+    load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+  } else if (flag) {
+    T el[REC];
+    load<T, NX>(carry_in + c * CREC, cg);
+    load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+    load<T, REC>(items + (i + 1) * REC, el);
+    smoother_apply<T, NX>(el, cg, cD);
+  } else {
+    load<T, NX>(items + (i + 1) * REC + SRec<NX>::g, cg);
+    load<T, NX * NX>(items + (i + 1) * REC + SRec<NX>::D, cD);
+  }
+  store<T, NX>(carry_out + i * CREC, cg);
+  store<T, NX * NX>(carry_out + i * CREC + NX, cD);
+  flag_out[i] = j == cnt - 1 ? flag : 1;
+}
+
+inline unsigned cs_down_grid(int64_t chunks) {
+  return (unsigned)((chunks * kChunkScan + kBlock - 1) / kBlock);
+}
+
+}  // namespace sqsm

@@ -54,6 +54,24 @@ def test_gradient_matches_oracle_fd(B, ctx, prec, tol, n):
     assert change.item() < (1e-8 if prec == "f64" else 1e-3)
 
 
+@pytest.mark.parametrize("leaf,radix", [(4, 4), (2, 3)])
+def test_gradient_fold_levels(B, leaf, radix):
+    """The adjoint's map scans with every upper level folded (explicit radix)
+    instead of warp-scanned."""
+    c2 = B.Context(0, leaf_chunk=leaf, radix=radix)
+    n = 131
+    d = W.ct_sequence(n=n, seed=31 + n)
+    theta = THETA + np.array([0.2, -0.3, 0.25])
+    nll, grad, _, _, _ = B.sqsm_ipls_nll_grad(c2, theta, _dev(d["y"], torch.float64), [0, n],
+                                              _dev(d["m0"][None], torch.float64),
+                                              _dev(d["N0"][None], torch.float64),
+                                              M=40, adj_iters=40, dt=d["dt"])
+    torch.cuda.synchronize()
+    rnll, rg = _oracle(d, theta)
+    assert abs(nll.item() - rnll) <= 1e-9 * abs(rnll)
+    assert np.linalg.norm(grad.cpu().numpy() - rg) <= 1e-6 * np.linalg.norm(rg)
+
+
 def test_batched_gradient_is_sum(B, ctx):
     lengths = [17, 40, 3]
     d = W.ct_batch(lengths=lengths, seed=41)

@@ -94,6 +94,32 @@ def test_ipls_ragged_batch(B, ctx, prec):
         assert abs(ll[b] - rll) <= (1e-9 if prec == "f64" else 1e-4) * abs(rll)
 
 
+def test_large_batch_folds_and_warp_scans(B, ctx):
+    """A batch of about 8e5 steps: the first upper level has more than 1.6e5
+    items and is folded 4 per thread, the levels above are warp-scanned in
+    chunks of 32.  Three short sequences placed among the long ones are
+    checked against the oracle."""
+    lengths = [600] + [4000] * 100 + [37] + [4000] * 99 + [1]
+    d = W.ct_batch(lengths=lengths, seed=21)
+    M = 2
+    ms, Ns, ll = B.sqsm_ipls_smooth(ctx, d["theta"], _dev(d["y"], torch.float32), d["offsets"],
+                                    _dev(d["m0"], torch.float32), _dev(d["N0"], torch.float32),
+                                    M, 0, dt=d["dt"])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    ms, Ns, ll = ms.cpu().numpy(), Ns.cpu().numpy(), ll.cpu().numpy()
+    assert np.all(np.isfinite(ms)) and np.all(np.isfinite(ll))
+    off = d["offsets"]
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    for b in (0, 101, len(lengths) - 1):
+        yb = d["y"][off[b]:off[b + 1]]
+        rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
+        rows = slice(off[b] + b, off[b + 1] + b + 1)
+        assert rel_mean_err(ms[rows], rms) < TOL["f32"]["mean"]
+        assert rel_cov_err(Ns[rows], rNs) < 1e-3
+        assert abs(ll[b] - rll) <= 1e-4 * abs(rll)
+
+
 def test_graph_replay_and_theta_update(B):
     """A captured graph replays with new theta (parameters are not baked)."""
     c2 = B.Context(0, use_graph=True)
