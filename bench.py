@@ -64,10 +64,11 @@ def dist_env():
 
 
 def config(args, world):
+    from paper_2207_00426_gb300.costmodel import default_leaf
     return {"workload": f"coordinated-turn bearings-only tracking, cubature IPLS, "
                         f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
             "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
-            "sequences_total": world, "leaf_chunk": 4,
+            "sequences_total": world, "leaf_chunk": default_leaf(args.n),
             "upper_levels": "folds of 4 above 160000 items, 32-item warp scans below",
             "l2": "flushed between timed steps (256 MiB write outside the events)",
             "parallelism": f"independent sequences, {world} GPU(s)"}
@@ -276,7 +277,7 @@ def gpu_arm(args, rank, world, local):
             a0[1] += c
     ctx.profile(False)
     launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
-    flops = CM.ipls_kernel_flops([n], leaf=4)
+    flops = CM.ipls_kernel_flops([n])
     total_ms = sum(t for t, _ in acc.values())
     kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / nprof,
                    "share": t / total_ms} for k, (t, c) in acc.items()}
@@ -357,7 +358,7 @@ def gpu_arm(args, rank, world, local):
             a0[0] += t
             a0[1] += c
     ctx.profile(False)
-    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])), leaf=4)
+    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])))
     btot = sum(t for t, _ in bacc.values())
     btop = max(bacc, key=lambda k: bacc[k][0])
     bach = bflops[btop][0] * bflops[btop][1] * M / (bacc[btop][0] / 2 / 1e3) / 1e12

@@ -83,7 +83,10 @@ typedef struct {
   double sensors[4];    /* s_x^1, s_y^1, s_x^2, s_y^2               */
 } sqsm_model;
 
-/* Scan shape.  Zero fields take defaults. */
+/* Scan shape.  Zero fields take defaults: leaf_chunk 3 when all leaf chunks
+ * of a call fit one wave of 256 threads per SM, else 4; radix 0 folds upper
+ * levels of more than 160000 items 4 per thread and scans smaller levels in
+ * one-warp chunks of 32. */
 typedef struct {
   int leaf_chunk;       /* time steps folded by one thread at the leaf  */
   int radix;            /* items folded by one thread at upper levels   */

@@ -98,6 +98,12 @@ def _chunks(counts, size):
 FOLD_ABOVE_ITEMS = 160000
 
 
+def default_leaf(steps, sm_count=152):
+    """Leaf chunk the library picks when none is given: 3 while the leaf
+    chunks fit one wave of 256 threads per SM, else 4."""
+    return 3 if steps <= 3 * 256 * sm_count else 4
+
+
 def _levels(counts0, leaf, radix):
     levels = []
     counts = list(counts0)
@@ -114,12 +120,13 @@ def _levels(counts0, leaf, radix):
             return levels
 
 
-def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=4, radix=0, linearization="cubature"):
+def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cubature"):
     """Algorithmic flops per launch of each kernel family for one IPLS
     iteration over sequences of the given lengths.  Returns
     {family: (flops per launch, launches per iteration)}."""
     out = {}
     nsteps = sum(lengths)
+    leaf = default_leaf(nsteps) if leaf is None else leaf
     slr = slr_cubature_ct(nx, ny) if linearization == "cubature" else slr_taylor_ct(nx, ny)
     out["ct_slr"] = (nsteps * slr, 1)
     fl = _levels(lengths, leaf, radix)

@@ -27,11 +27,10 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   //    and the pseudo log-likelihood of that linearisation.
   cudaMemcpyAsync(g.nom_m, a.ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
-  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+  ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
       Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, 0, 0, (const T*)g.nom_m, (const T*)g.nom_N,
-      (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
-  GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
-                  (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
+      (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
+  const GammaPacked<T> gv{(T*)a.F};
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
                             (T*)a.mf, (T*)a.Nf, partial, status, s);
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, (T*)g.ms2,
@@ -39,7 +38,7 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   enqueue_loglik_reduce(sq, partial, g.ll, status, s);
   adj_nll_kernel<<<1, 1, 0, s>>>(sq.B, g.ll, -1.0, g.nll);
   // 3. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)
-  AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F, a.c, a.SQ, a.H, a.d, a.SR,
+  AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F,
              g.dir, g.dfilt, g.gbar};
   const T lbar = T(-1);
   T* lam_a = (T*)g.lam_a;

@@ -3,7 +3,7 @@
 // Per time step s of sequence b: state rows e = s + b (k - 1) and e + 1 (k).
 // Buffers (state layout unless noted):
 //   nom      nominal trajectory (m, N) the linearisation was taken at,
-//   gam      linearised model of the step (absolute form, per step),
+//   gam      linearised model of the step (absolute form, PRec per step),
 //   mf, Nf   filter output, ms, Ns smoother output of that linearisation,
 //   dir      direct cotangents (m, P) of the smoother output,
 //   dfilt    direct cotangents (m, P) of the filter output (from the RTS VJP),
@@ -17,14 +17,13 @@ namespace sqsm {
 
 struct AdjBufs {
   const void *mf, *Nf, *ms, *Ns, *nom_m, *nom_N, *y;
-  const void *F, *c, *SQ, *H, *d, *SR;
+  const void* gam;   // linearised model, PRec records
   void *dir, *dfilt, *gbar;
 };
 
 template <typename T>
-SQSM_DEV GammaView<T> gview(const AdjBufs& a) {
-  return GammaView<T>{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
-                      (const T*)a.d, (const T*)a.SR, 25, 5, 25, 10, 2, 4};
+SQSM_DEV GammaPacked<T> gview(const AdjBufs& a) {
+  return GammaPacked<T>{(T*)a.gam};
 }
 
 // --------------------------- smoother adjoint (forward in time) -----------

@@ -37,7 +37,7 @@ struct Workspace {
   double* partial = nullptr;
   void* mf = nullptr;        // filter outputs when the caller wants none / IPLS
   void* Nf = nullptr;
-  void* gamma[6] = {};       // IPLS linearised model F, c, SQ, H, d, SR
+  void* gamma = nullptr;     // IPLS linearised model, PRec<5, 2> records per step
   void* params = nullptr;    // IPLS model constants
   void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
   bool ipls_ready = false;
@@ -77,6 +77,7 @@ struct GraphEntry {
 
 struct sqsm_ctx {
   int device = 0;
+  int sm_count = 152;
   sqsm_options opt{};
   std::string err;
   int* d_status = nullptr;
@@ -205,7 +206,12 @@ bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
 }
 
 Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
-  const int L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk : 4;
+  // default leaf: 3 steps per thread while the leaf chunks fit one wave of
+  // the leaf kernels (256 threads per SM at their register use), so that the
+  // latency-bound leaf chains are short; 4 above that, fewer upper items.
+  const int64_t steps = offsets[batch] - offsets[0];
+  const int L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk
+                 : steps <= 3 * int64_t(256) * ctx->sm_count ? 3 : 4;
   // default (radix 0): a level with many items is folded 4 items per thread
   // (enough threads to fill the GPU, least work); a level with few items is
   // scanned in one-warp Kogge-Stone chunks of 32 (shortest chain of
@@ -290,13 +296,10 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
   if (w->ipls_ready) return true;
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
   const int64_t n = p->filt.n_items[0];
-  const int nx = 5, ny = 2;
-  const size_t sizes[6] = {(size_t)nx * nx, (size_t)nx, (size_t)nx * nx,
-                           (size_t)ny * nx, (size_t)ny, (size_t)ny * ny};
-  for (int i = 0; i < 6; ++i) {
-    w->gamma[i] = w->mem.get(es * sizes[i] * n);
-    if (!w->gamma[i]) return false;
-  }
+  const int nx = 5;
+  // the linearised model of every step as packed records
+  w->gamma = w->mem.get(es * PRec<5, 2>::size * n);
+  if (!w->gamma) return false;
   w->params = w->mem.get(512);
   w->dm0 = w->mem.get(es * nx * p->B);
   if (!w->params || !w->dm0) return false;
@@ -364,6 +367,7 @@ int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
     return SQSM_ERR_CUDA;
   }
   cudaMemset(ctx->d_status, 0, sizeof(int));
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaFree(ctx->d_status);
     delete ctx;
@@ -526,8 +530,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
   a.ms = ms; a.Ns = Ns; a.loglik = loglik;
   a.mf = w->mf; a.Nf = w->Nf;
-  a.F = w->gamma[0]; a.c = w->gamma[1]; a.SQ = w->gamma[2];
-  a.H = w->gamma[3]; a.d = w->gamma[4]; a.SR = w->gamma[5];
+  a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
   a.params = w->params;
   a.dm0 = w->dm0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -635,8 +638,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
   a.ms = ms; a.Ns = Ns; a.loglik = nullptr;
   a.mf = w->mf; a.Nf = w->Nf;
-  a.F = w->gamma[0]; a.c = w->gamma[1]; a.SQ = w->gamma[2];
-  a.H = w->gamma[3]; a.d = w->gamma[4]; a.SR = w->gamma[5];
+  a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
   a.params = w->params;
   a.dm0 = w->dm0;
   AdjArgs adj = w->adj;

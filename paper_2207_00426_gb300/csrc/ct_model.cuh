@@ -294,9 +294,11 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
   take_lower<T, NO, C>(B, Sout);
 }
 
-// One thread per leaf chunk of the filter plan: for every step s of the
-// chunk, the transition is linearised at state row s + b (k - 1) and the
-// observation at row s + b + 1 (k) of the nominal trajectory (ms, Ns).
+// One thread per step s: the transition is linearised at state row s + b
+// (k - 1) and the observation at row s + b + 1 (k) of the nominal trajectory
+// (ms, Ns).  PACKED writes one PRec record per step to F (c, SQ, H, d, SR
+// unused); otherwise the six arrays are written in the sqsm_ct_linearize
+// layout (full matrices, row-major, one per step).
 //
 // centered = 0: eq. Gamma-s as printed (c = z_bar - F m, d = z_bar - H m).
 // centered = 1: the same linear model written for the deviation
@@ -308,7 +310,7 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 // Steps are independent: one thread per step, addressed as (leaf chunk,
 // position in chunk) so that the chunk table gives the sequence; launch
 // n_chunks * leaf threads.
-template <typename T>
+template <typename T, bool PACKED>
 __global__ void __launch_bounds__(kBlock)
 ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
               int linearization, int centered, const T* __restrict__ ms,
@@ -360,9 +362,17 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
 #pragma unroll
       for (int i = 0; i < NX * NX; ++i) Sl[i] = P.SQ[i];
     }
-    store<T, NX * NX>(F + s * NX * NX, Fm);
-    store<T, NX>(c + s * NX, cm);
-    store_lower<T, NX>(SQo + s * NX * NX, Sl);
+    if constexpr (PACKED) {
+      Gamma<T, NX, NY> gg;
+      copy<T, NX * NX>(Fm, gg.F);
+      copy<T, NX>(cm, gg.c);
+      copy<T, NX * NX>(Sl, gg.SQ);
+      gg.store_transition(GammaPacked<T>{F}, s);
+    } else {
+      store<T, NX * NX>(F + s * NX * NX, Fm);
+      store<T, NX>(c + s * NX, cm);
+      store_lower<T, NX>(SQo + s * NX * NX, Sl);
+    }
     // observation at k
     load<T, NX>(ms + rk * NX, m);
     load_lower<T, NX>(Ns + rk * NX * NX, N);
@@ -389,9 +399,17 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
     }
 #pragma unroll
     for (int r = 0; r < NY; ++r) dm[r] += branch_shift(ys[r], hm[r]);
-    store<T, NY * NX>(H + s * NY * NX, Hm);
-    store<T, NY>(d + s * NY, dm);
-    store_lower<T, NY>(SRo + s * NY * NY, So);
+    if constexpr (PACKED) {
+      Gamma<T, NX, NY> gg;
+      copy<T, NY * NX>(Hm, gg.H);
+      copy<T, NY>(dm, gg.d);
+      copy<T, NY * NY>(So, gg.SR);
+      gg.store_observation(GammaPacked<T>{F}, s);
+    } else {
+      store<T, NY * NX>(H + s * NY * NX, Hm);
+      store<T, NY>(d + s * NY, dm);
+      store_lower<T, NY>(SRo + s * NY * NY, So);
+    }
   }
 }
 

@@ -22,9 +22,88 @@ struct GammaView {
   int64_t sF, sc, sSQ, sH, sd, sSR;
 };
 
+// Packed per-step record of the linearised model, the layout the iterated
+// smoother keeps internally: 16-byte aligned, transition part first so that
+// the smoother reads only that part,
+//   F (NX x NX) | c | S_Lambda (lower, row-packed) | pad |
+//   H (NY x NX) | d | S_Omega (lower, row-packed) | pad.
+template <int NX, int NY> struct PRec {
+  static constexpr int F = 0, c = NX * NX, SQ = NX * NX + NX;
+  static constexpr int H = (SQ + NX * (NX + 1) / 2 + 3) / 4 * 4;   // also the transition size
+  static constexpr int d = H + NY * NX, SR = d + NY;
+  static constexpr int size = (SR + NY * (NY + 1) / 2 + 3) / 4 * 4;
+};
+
+template <typename T>
+struct GammaPacked {
+  T* rec;   // PRec records, one per step
+};
+
 template <typename T, int NX, int NY>
 struct Gamma {
   T F[NX * NX], c[NX], SQ[NX * NX], H[NY * NX], d[NY], SR[NY * NY];
+
+  SQSM_DEV void load_transition(const GammaPacked<T>& g, int64_t t) {
+    using P = PRec<NX, NY>;
+    T v[P::H];
+    vload<T, P::H>(g.rec + t * P::size, v);
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) F[i] = v[P::F + i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) c[i] = v[P::c + i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) SQ[i * NX + j] = j <= i ? v[P::SQ + i * (i + 1) / 2 + j] : T(0);
+  }
+  SQSM_DEV void load_observation(const GammaPacked<T>& g, int64_t t) {
+    using P = PRec<NX, NY>;
+    T v[P::size - P::H];
+    vload<T, P::size - P::H>(g.rec + t * P::size + P::H, v);
+#pragma unroll
+    for (int i = 0; i < NY * NX; ++i) H[i] = v[i];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) d[i] = v[P::d - P::H + i];
+#pragma unroll
+    for (int i = 0; i < NY; ++i)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) SR[i * NY + j] = j <= i ? v[P::SR - P::H + i * (i + 1) / 2 + j] : T(0);
+  }
+  SQSM_DEV void load_all(const GammaPacked<T>& g, int64_t t) {
+    load_transition(g, t);
+    load_observation(g, t);
+  }
+  // Write this step's record (lower triangles of S_Lambda, S_Omega).
+  SQSM_DEV void store_transition(const GammaPacked<T>& g, int64_t t) const {
+    using P = PRec<NX, NY>;
+    T v[P::H];
+#pragma unroll
+    for (int i = 0; i < P::H; ++i) v[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) v[P::F + i] = F[i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) v[P::c + i] = c[i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) v[P::SQ + i * (i + 1) / 2 + j] = SQ[i * NX + j];
+    vstore<T, P::H>(g.rec + t * P::size, v);
+  }
+  SQSM_DEV void store_observation(const GammaPacked<T>& g, int64_t t) const {
+    using P = PRec<NX, NY>;
+    T v[P::size - P::H];
+#pragma unroll
+    for (int i = 0; i < P::size - P::H; ++i) v[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NY * NX; ++i) v[i] = H[i];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) v[P::d - P::H + i] = d[i];
+#pragma unroll
+    for (int i = 0; i < NY; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) v[P::SR - P::H + i * (i + 1) / 2 + j] = SR[i * NY + j];
+    vstore<T, P::size - P::H>(g.rec + t * P::size + P::H, v);
+  }
 
   SQSM_DEV void load_transition(const GammaView<T>& g, int64_t t) {
     load<T, NX * NX>(g.F + t * g.sF, F);

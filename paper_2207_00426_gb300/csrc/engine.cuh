@@ -85,8 +85,8 @@ struct ProfScope {
   }
 };
 
-template <typename T, int NX, int NY>
-void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
+template <typename T, int NX, int NY, typename GV>
+void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
                     const T* y, const T* m0, const T* N0, T* mf, T* Nf, double* partial,
                     int* status, cudaStream_t s, Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
@@ -95,7 +95,7 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
   if (Lc > 1) {  // with one leaf chunk per sequence every carry is the prior
     {
       ProfScope ps(P, K_FILTER_LEAF_UP, s);
-      filter_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      filter_leaf_up<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
           L.lv[0], sq, gv, y, m0, N0, (T*)W.items[1]);
     }
     for (int l = 1; l < Lk; ++l) {
@@ -133,12 +133,12 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaVi
           (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_FILTER_LEAF_DOWN, s);
-  filter_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+  filter_leaf_down<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
       L.lv[0], sq, gv, y, m0, N0, (const T*)W.carry[1], W.flag[1], mf, Nf, partial, status);
 }
 
-template <typename T, int NX, int NY>
-void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GammaView<T> gv,
+template <typename T, int NX, int NY, typename GV>
+void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
                       const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s,
                       Prof* P = nullptr, const T* nominal = nullptr) {
   const int Lc = (int)L.lv.size();
@@ -147,7 +147,7 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
   if (Lc > 1) {
     {
       ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
-      smoother_leaf_up<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      smoother_leaf_up<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
           L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
     }
     for (int l = 1; l < Lk; ++l) {
@@ -185,7 +185,7 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, Gamma
           (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
-  smoother_leaf_down<T, NX, NY><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+  smoother_leaf_down<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
       L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status, nominal);
 }
 

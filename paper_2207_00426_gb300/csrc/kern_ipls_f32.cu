@@ -12,7 +12,7 @@ void ipls_params_f32(const IplsArgs& a, cudaStream_t s) {
 
 void ct_linearize_f32(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
   using T = float;
-  ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+  ct_slr_kernel<T, false><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
       Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 0, (const T*)a.ms,
       (const T*)a.Ns, (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
 }
@@ -33,8 +33,8 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
     broadcast_prior_kernel<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
         Ls.lv[0], (const T*)a.m0, (const T*)a.N0, ms, Ns);
   }
-  GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
-                  (const T*)a.d, (const T*)a.SR, NX * NX, NX, NX * NX, NY * NX, NY, NY * NY};
+  // the linearised model of every step, packed (a.F holds the PRec records)
+  const GammaPacked<T> gv{(T*)a.F};
   // Each iteration smooths the linearised model in deviation coordinates
   // dx_k = x_k - m_k about its own nominal trajectory m (the previous
   // smoothing means, held in ms): the SLR writes c~, d~ of that form, the
@@ -42,9 +42,9 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   for (int it = 0; it < a.M; ++it) {
     {
       ProfScope ps(a.prof, K_SLR, s);
-      ct_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+      ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
           Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, ms, Ns,
-          (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+          (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
     {
       ProfScope ps(a.prof, K_INIT, s);

@@ -223,6 +223,40 @@ SQSM_DEV void load_lower(const T* __restrict__ g, T* r) {
     for (int j = 0; j < N; ++j) r[i * N + j] = j <= i ? g[i * N + j] : T(0);
 }
 
+// N consecutive elements through 16-byte vector accesses (g 16-byte aligned,
+// N * sizeof(T) a multiple of 16).
+template <typename T, int N>
+SQSM_DEV void vload(const T* __restrict__ g, T* r) {
+  static_assert((N * sizeof(T)) % 16 == 0, "vector access of whole 16-byte words");
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(g)[i];
+      r[4 * i] = v.x; r[4 * i + 1] = v.y; r[4 * i + 2] = v.z; r[4 * i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 v = reinterpret_cast<const double2*>(g)[i];
+      r[2 * i] = v.x; r[2 * i + 1] = v.y;
+    }
+  }
+}
+
+template <typename T, int N>
+SQSM_DEV void vstore(T* __restrict__ g, const T* r) {
+  static_assert((N * sizeof(T)) % 16 == 0, "vector access of whole 16-byte words");
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+      reinterpret_cast<float4*>(g)[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i)
+      reinterpret_cast<double2*>(g)[i] = make_double2(r[2 * i], r[2 * i + 1]);
+  }
+}
+
 // Store an N x N lower factor with explicit zeros above the diagonal.
 template <typename T, int N>
 SQSM_DEV void store_lower(T* __restrict__ g, const T* r) {

@@ -53,9 +53,9 @@ SQSM_DEV void flag_status(int* status, int code) {
 
 // Leaf up-sweep: build the elements of Lemma 1 for the steps of a chunk and
 // fold them left to right with Table 3.
-template <typename T, int NX, int NY>
+template <typename T, int NX, int NY, typename GV>
 __global__ void __launch_bounds__(kBlock)
-filter_leaf_up(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ y,
+filter_leaf_up(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
                const T* __restrict__ m0, const T* __restrict__ N0, T* __restrict__ items) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
@@ -146,9 +146,9 @@ filter_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carr
 // Leaf down-sweep: sequential square-root Kalman steps from the chunk's
 // carry (or from the prior (m0, N0) for the first chunk of a sequence),
 // writing m^f, N^f and the chunk's partial log-likelihood (FP64 sum).
-template <typename T, int NX, int NY>
+template <typename T, int NX, int NY, typename GV>
 __global__ void __launch_bounds__(kBlock)
-filter_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ y,
+filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
                  const T* __restrict__ m0, const T* __restrict__ N0,
                  const T* __restrict__ carry, const int* __restrict__ flag,
                  T* __restrict__ mf, T* __restrict__ Nf, double* __restrict__ partial,
@@ -196,9 +196,9 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__
 
 // Leaf up-sweep: build the elements of Lemma 3 for the chunk's k (state
 // rows) and fold them right to left with Table 5.
-template <typename T, int NX, int NY>
+template <typename T, int NX, int NY, typename GV>
 __global__ void __launch_bounds__(kBlock)
-smoother_leaf_up(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ mf,
+smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
                  const T* __restrict__ Nf, T* __restrict__ items) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
@@ -291,9 +291,9 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
 // scan runs on deviations from a nominal trajectory and the written mean is
 // nominal + deviation (nominal may alias ms: each row is read, then written,
 // by the same thread).
-template <typename T, int NX, int NY>
+template <typename T, int NX, int NY, typename GV>
 __global__ void __launch_bounds__(kBlock)
-smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaView<T> gv, const T* __restrict__ mf,
+smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
                    const T* __restrict__ Nf, const T* __restrict__ carry,
                    const int* __restrict__ flag, T* ms, T* __restrict__ Ns, int* status,
                    const T* nominal) {
