@@ -27,14 +27,15 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   //    and the pseudo log-likelihood of that linearisation.
   cudaMemcpyAsync(g.nom_m, a.ms, sizeof(T) * NX * rows, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
+  const RowsSplit<T, NX> nom{(T*)g.nom_m, (T*)g.nom_N}, fo{(T*)a.mf, (T*)a.Nf},
+      so{(T*)g.ms2, (T*)g.Ns2};
   ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, 0, 0, (const T*)g.nom_m, (const T*)g.nom_N,
-      (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
+      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, 0, 0, nom, (const T*)a.y, (T*)a.F,
+      nullptr, nullptr, nullptr, nullptr, nullptr);
   const GammaPacked<T> gv{(T*)a.F};
-  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
-                            (T*)a.mf, (T*)a.Nf, partial, status, s);
-  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, (T*)g.ms2,
-                              (T*)g.Ns2, status, s);
+  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0, fo,
+                            partial, status, s);
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fo, so, status, s);
   enqueue_loglik_reduce(sq, partial, g.ll, status, s);
   adj_nll_kernel<<<1, 1, 0, s>>>(sq.B, g.ll, -1.0, g.nll);
   // 3. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)

@@ -38,6 +38,8 @@ struct Workspace {
   void* mf = nullptr;        // filter outputs when the caller wants none / IPLS
   void* Nf = nullptr;
   void* gamma = nullptr;     // IPLS linearised model, PRec<5, 2> records per step
+  void* frows = nullptr;     // IPLS filter output, packed rows
+  void* nrows = nullptr;     // IPLS nominal trajectory, packed rows
   void* params = nullptr;    // IPLS model constants
   void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
   bool ipls_ready = false;
@@ -299,7 +301,10 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
   const int nx = 5;
   // the linearised model of every step as packed records
   w->gamma = w->mem.get(es * PRec<5, 2>::size * n);
-  if (!w->gamma) return false;
+  const int64_t rows = p->smth.n_items[0];
+  w->frows = w->mem.get(es * XRow<5>::size * rows);
+  w->nrows = w->mem.get(es * XRow<5>::size * rows);
+  if (!w->gamma || !w->frows || !w->nrows) return false;
   w->params = w->mem.get(512);
   w->dm0 = w->mem.get(es * nx * p->B);
   if (!w->params || !w->dm0) return false;
@@ -531,6 +536,8 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   a.ms = ms; a.Ns = Ns; a.loglik = loglik;
   a.mf = w->mf; a.Nf = w->Nf;
   a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
+  a.frows = w->frows;
+  a.nrows = w->nrows;
   a.params = w->params;
   a.dm0 = w->dm0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -639,6 +646,8 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   a.ms = ms; a.Ns = Ns; a.loglik = nullptr;
   a.mf = w->mf; a.Nf = w->Nf;
   a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
+  a.frows = w->frows;
+  a.nrows = w->nrows;
   a.params = w->params;
   a.dm0 = w->dm0;
   AdjArgs adj = w->adj;

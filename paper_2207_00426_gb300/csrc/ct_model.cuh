@@ -296,7 +296,7 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 
 // One thread per step s: the transition is linearised at state row s + b
 // (k - 1) and the observation at row s + b + 1 (k) of the nominal trajectory
-// (ms, Ns).  PACKED writes one PRec record per step to F (c, SQ, H, d, SR
+// `nom`.  PACKED writes one PRec record per step to F (c, SQ, H, d, SR
 // unused); otherwise the six arrays are written in the sqsm_ct_linearize
 // layout (full matrices, row-major, one per step).
 //
@@ -310,11 +310,10 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 // Steps are independent: one thread per step, addressed as (leaf chunk,
 // position in chunk) so that the chunk table gives the sequence; launch
 // n_chunks * leaf threads.
-template <typename T, bool PACKED>
+template <typename T, bool PACKED, typename NO>
 __global__ void __launch_bounds__(kBlock)
 ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
-              int linearization, int centered, const T* __restrict__ ms,
-              const T* __restrict__ Ns, const T* __restrict__ y, T* __restrict__ F,
+              int linearization, int centered, NO nom, const T* __restrict__ y, T* __restrict__ F,
               T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d,
               T* __restrict__ SRo) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -330,13 +329,12 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
     const int64_t rp = s + b, rk = s + b + 1;
     T m[NX], N[NX * NX];
     // transition at k - 1
-    load<T, NX>(ms + rp * NX, m);
-    load_lower<T, NX>(Ns + rp * NX * NX, N);
+    nom.load(rp, m, N);
     T Fm[NX * NX], cm[NX], Sl[NX * NX];
     T fm[NX];    // f(m_{k-1}) (absolute) or f(m_{k-1}) - m_k (deviation form)
     if (centered) {
       T mk[NX];
-      load<T, NX>(ms + rk * NX, mk);
+      nom.load_mean(rk, mk);
       ct_f_minus_x(P, m, fm);
 #pragma unroll
       for (int r = 0; r < NX; ++r) fm[r] += m[r] - mk[r];
@@ -374,8 +372,7 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
       store_lower<T, NX>(SQo + s * NX * NX, Sl);
     }
     // observation at k
-    load<T, NX>(ms + rk * NX, m);
-    load_lower<T, NX>(Ns + rk * NX * NX, N);
+    nom.load(rk, m, N);
     T hm[NY], Hm[NY * NX], dm[NY], So[NY * NY], ys[NY];
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
@@ -415,10 +412,9 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
 
 // Initial nominal trajectory (Alg. 3 input): the prior of each sequence
 // broadcast to all of its state rows.  One thread per smoother leaf chunk.
-template <typename T, int NX>
+template <typename T, int NX, typename SO>
 __global__ void __launch_bounds__(kBlock)
-broadcast_prior_kernel(DevLevel lv, const T* __restrict__ m0, const T* __restrict__ N0,
-                       T* __restrict__ ms, T* __restrict__ Ns) {
+broadcast_prior_kernel(DevLevel lv, const T* __restrict__ m0, const T* __restrict__ N0, SO so) {
   const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (ch >= lv.n_chunks) return;
   const int b = lv.seq[ch];
@@ -426,21 +422,30 @@ broadcast_prior_kernel(DevLevel lv, const T* __restrict__ m0, const T* __restric
   load<T, NX>(m0 + (int64_t)b * NX, m);
   load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N);
   for (int j = 0; j < lv.count[ch]; ++j) {
-    const int64_t e = lv.first[ch] + j;
-    store<T, NX>(ms + e * NX, m);
-    store_lower<T, NX>(Ns + e * NX * NX, N);
+    so.store(lv.first[ch] + j, m, N);
   }
 }
 
+// Copy of state rows between layouts, one thread per row.
+template <typename T, int NX, typename RI, typename RO>
+__global__ void __launch_bounds__(kBlock) rows_copy_kernel(int64_t rows, RI in, RO out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows) return;
+  T m[NX], N[NX * NX];
+  in.load(e, m, N);
+  out.store(e, m, N);
+}
+
 // Prior of the deviation model: dm0[b] = m0[b] - m_0 (nominal row 0 of b).
-template <typename T, int NX>
-__global__ void center_prior_kernel(DevSeqs sq, const T* __restrict__ m0,
-                                    const T* __restrict__ ms, T* __restrict__ dm0) {
+template <typename T, int NX, typename RI>
+__global__ void center_prior_kernel(DevSeqs sq, const T* __restrict__ m0, RI nom,
+                                    T* __restrict__ dm0) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= sq.B) return;
-  const int64_t row0 = sq.offsets[b] + b;
+  T mn[NX];
+  nom.load_mean(sq.offsets[b] + b, mn);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) dm0[(int64_t)b * NX + i] = m0[(int64_t)b * NX + i] - ms[row0 * NX + i];
+  for (int i = 0; i < NX; ++i) dm0[(int64_t)b * NX + i] = m0[(int64_t)b * NX + i] - mn[i];
 }
 
 }  // namespace sqsm

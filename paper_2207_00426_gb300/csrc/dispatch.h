@@ -37,6 +37,7 @@ struct IplsArgs {
   double* loglik;
   // workspace
   void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params, *dm0;
+  void *frows, *nrows;   // packed filter output and nominal trajectory (RowsPacked)
   Prof* prof;   // optional per-kernel events
 };
 

@@ -39,6 +39,67 @@ struct GammaPacked {
   T* rec;   // PRec records, one per step
 };
 
+// State rows (m_k, N_k) of a trajectory, rows k = 0..n of each sequence.
+// RowsSplit is the API layout: m as NX values and N as a full NX x NX lower
+// factor (zeros above the diagonal) per row; a null array is not written.
+// RowsPacked is the iterated smoother's own layout: one 16-byte-aligned
+// record per row, m | N (lower, row-packed) | pad.
+template <int NX> struct XRow {
+  static constexpr int size = (NX + NX * (NX + 1) / 2 + 3) / 4 * 4;
+  static constexpr int mvec = (NX + 3) / 4 * 4;   // leading words that hold m
+};
+
+template <typename T, int NX>
+struct RowsSplit {
+  T* m;
+  T* N;
+  SQSM_DEV void load(int64_t e, T* mo, T* No) const {
+    sqsm::load<T, NX>(m + e * NX, mo);
+    load_lower<T, NX>(N + e * NX * NX, No);
+  }
+  SQSM_DEV void load_mean(int64_t e, T* mo) const { sqsm::load<T, NX>(m + e * NX, mo); }
+  SQSM_DEV void store(int64_t e, const T* mi, const T* Ni) const {
+    if (m) sqsm::store<T, NX>(m + e * NX, mi);
+    if (N) store_lower<T, NX>(N + e * NX * NX, Ni);
+  }
+};
+
+template <typename T, int NX>
+struct RowsPacked {
+  T* rec;
+  SQSM_DEV void load(int64_t e, T* mo, T* No) const {
+    using R = XRow<NX>;
+    T v[R::size];
+    vload<T, R::size>(rec + e * R::size, v);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mo[i] = v[i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) No[i * NX + j] = j <= i ? v[NX + i * (i + 1) / 2 + j] : T(0);
+  }
+  SQSM_DEV void load_mean(int64_t e, T* mo) const {
+    using R = XRow<NX>;
+    T v[R::mvec];
+    vload<T, R::mvec>(rec + e * R::size, v);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) mo[i] = v[i];
+  }
+  SQSM_DEV void store(int64_t e, const T* mi, const T* Ni) const {
+    using R = XRow<NX>;
+    T v[R::size];
+#pragma unroll
+    for (int i = 0; i < R::size; ++i) v[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) v[i] = mi[i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) v[NX + i * (i + 1) / 2 + j] = Ni[i * NX + j];
+    vstore<T, R::size>(rec + e * R::size, v);
+  }
+};
+
 template <typename T, int NX, int NY>
 struct Gamma {
   T F[NX * NX], c[NX], SQ[NX * NX], H[NY * NX], d[NY], SR[NY * NY];

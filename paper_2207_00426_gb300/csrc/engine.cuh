@@ -85,9 +85,9 @@ struct ProfScope {
   }
 };
 
-template <typename T, int NX, int NY, typename GV>
+template <typename T, int NX, int NY, typename GV, typename FO>
 void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
-                    const T* y, const T* m0, const T* N0, T* mf, T* Nf, double* partial,
+                    const T* y, const T* m0, const T* N0, FO fo, double* partial,
                     int* status, cudaStream_t s, Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
   constexpr int KS = KsMax<T, FRec<NX>::size>::value;
@@ -133,22 +133,21 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
           (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_FILTER_LEAF_DOWN, s);
-  filter_leaf_down<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-      L.lv[0], sq, gv, y, m0, N0, (const T*)W.carry[1], W.flag[1], mf, Nf, partial, status);
+  filter_leaf_down<T, NX, NY, GV, FO><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      L.lv[0], sq, gv, y, m0, N0, (const T*)W.carry[1], W.flag[1], fo, partial, status);
 }
 
-template <typename T, int NX, int NY, typename GV>
-void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
-                      const T* mf, const T* Nf, T* ms, T* Ns, int* status, cudaStream_t s,
-                      Prof* P = nullptr, const T* nominal = nullptr) {
+template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
+void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv, FO fo, SO so,
+                      int* status, cudaStream_t s, Prof* P = nullptr, bool add_nominal = false) {
   const int Lc = (int)L.lv.size();
   constexpr int KS = KsMax<T, SRec<NX>::size>::value;
   const int Lk = L.ks_level(KS);
   if (Lc > 1) {
     {
       ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
-      smoother_leaf_up<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-          L.lv[0], sq, gv, mf, Nf, (T*)W.items[1]);
+      smoother_leaf_up<T, NX, NY, GV, FO><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+          L.lv[0], sq, gv, fo, (T*)W.items[1]);
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_SMOOTHER_UP, s);
@@ -185,8 +184,8 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv
           (T*)W.carry[l], W.flag[l]);
   }
   ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
-  smoother_leaf_down<T, NX, NY, GV><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-      L.lv[0], sq, gv, mf, Nf, (const T*)W.carry[1], W.flag[1], ms, Ns, status, nominal);
+  smoother_leaf_down<T, NX, NY, GV, FO, SO><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
+      L.lv[0], sq, gv, fo, (const T*)W.carry[1], W.flag[1], so, status, add_nominal);
 }
 
 // Record sizes (elements) of the scan buffers.

@@ -1,0 +1,76 @@
+// Iterated posterior linearisation smoother (Alg. 3) for the CT model.
+//
+// The iterations keep the nominal trajectory and the filter output as packed
+// state rows (RowsPacked) and the linearised model as packed records (PRec);
+// the caller's arrays are read once (warm start) and written once (result).
+#pragma once
+
+#include "ct_model.cuh"
+#include "dispatch.h"
+
+namespace sqsm {
+
+template <typename T>
+void ipls_params(const IplsArgs& a, cudaStream_t s) {
+  ct_params_kernel<T><<<1, 1, 0, s>>>(a.theta[0], a.theta[1], a.theta[2], a.dt, a.sensors[0],
+                                      a.sensors[1], a.sensors[2], a.sensors[3],
+                                      (CTParams<T>*)a.params);
+}
+
+// sqsm_ct_linearize: the printed (absolute) form, caller's layout in and out.
+template <typename T>
+void ct_linearize(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
+  const RowsSplit<T, 5> nom{(T*)a.ms, (T*)a.Ns};
+  ct_slr_kernel<T, false><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 0, nom,
+      (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+}
+
+template <typename T>
+void ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                  const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                  int* status, cudaStream_t s) {
+  constexpr int NX = 5, NY = 2;
+  const int64_t rows = Ls.n_items[0];
+  const RowsPacked<T, NX> nom{(T*)a.nrows}, fr{(T*)a.frows};
+  const RowsSplit<T, NX> user{(T*)a.ms, (T*)a.Ns};
+  {
+    ProfScope ps(a.prof, K_INIT, s);
+    if (a.init_ms) {
+      const RowsSplit<T, NX> init{(T*)a.init_ms, (T*)a.init_Ns};
+      rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, init, nom);
+    } else {
+      broadcast_prior_kernel<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
+          Ls.lv[0], (const T*)a.m0, (const T*)a.N0, nom);
+    }
+  }
+  // the linearised model of every step, packed (a.F holds the PRec records)
+  const GammaPacked<T> gv{(T*)a.F};
+  // Each iteration smooths the linearised model in deviation coordinates
+  // dx_k = x_k - m_k about its own nominal trajectory m (the previous
+  // smoothing means): the SLR writes c~, d~ of that form, the prior becomes
+  // m0 - m_0, and the smoother adds m back when it writes the new nominal.
+  for (int it = 0; it < a.M; ++it) {
+    {
+      ProfScope ps(a.prof, K_SLR, s);
+      ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+          Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, nom,
+          (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
+    }
+    {
+      ProfScope ps(a.prof, K_INIT, s);
+      center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
+                                                                     (T*)a.dm0);
+    }
+    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
+                              partial, status, s, a.prof);
+    enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true);
+  }
+  {
+    ProfScope ps(a.prof, K_INIT, s);
+    rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, user);
+  }
+  if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s, a.prof);
+}
+
+}  // namespace sqsm

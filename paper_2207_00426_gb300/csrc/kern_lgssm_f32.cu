@@ -10,10 +10,10 @@ void run(const LgssmArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, const Le
   using T = float;
   GammaView<T> gv{(const T*)a.F, (const T*)a.c, (const T*)a.SQ, (const T*)a.H,
                   (const T*)a.d, (const T*)a.SR, a.sF, a.sc, a.sSQ, a.sH, a.sd, a.sSR};
-  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0,
-                            (T*)a.mf, (T*)a.Nf, partial, status, s, a.prof);
-  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, (const T*)a.mf, (const T*)a.Nf, (T*)a.ms,
-                              (T*)a.Ns, status, s, a.prof);
+  const RowsSplit<T, NX> fo{(T*)a.mf, (T*)a.Nf}, so{(T*)a.ms, (T*)a.Ns};
+  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0, fo,
+                            partial, status, s, a.prof);
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fo, so, status, s, a.prof);
 }
 
 }  // namespace

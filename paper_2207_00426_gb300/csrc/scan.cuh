@@ -146,13 +146,12 @@ filter_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carr
 // Leaf down-sweep: sequential square-root Kalman steps from the chunk's
 // carry (or from the prior (m0, N0) for the first chunk of a sequence),
 // writing m^f, N^f and the chunk's partial log-likelihood (FP64 sum).
-template <typename T, int NX, int NY, typename GV>
+template <typename T, int NX, int NY, typename GV, typename FO>
 __global__ void __launch_bounds__(kBlock)
 filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
                  const T* __restrict__ m0, const T* __restrict__ N0,
                  const T* __restrict__ carry, const int* __restrict__ flag,
-                 T* __restrict__ mf, T* __restrict__ Nf, double* __restrict__ partial,
-                 int* status) {
+                 FO fo, double* __restrict__ partial, int* status) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int CREC = NX + NX * NX;
@@ -166,9 +165,7 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
   } else {
     load<T, NX>(m0 + (int64_t)b * NX, m);
     load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N);
-    const int64_t row0 = sq.offsets[b] + b;   // k = 0
-    if (mf) store<T, NX>(mf + row0 * NX, m);
-    if (Nf) store_lower<T, NX>(Nf + row0 * NX * NX, N);
+    fo.store(sq.offsets[b] + b, m, N);   // k = 0
   }
   double acc = 0.0;
   bool ok = true;
@@ -180,9 +177,7 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
     load<T, NY>(y + s * NY, ys);
     const T ll = kf_step<T, NX, NY>(g, ys, m, N);
     acc += (double)ll;
-    const int64_t row = s + b + 1;
-    if (mf) store<T, NX>(mf + row * NX, m);
-    if (Nf) store_lower<T, NX>(Nf + row * NX * NX, N);
+    fo.store(s + b + 1, m, N);
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(m[i]);
   }
@@ -196,10 +191,9 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
 
 // Leaf up-sweep: build the elements of Lemma 3 for the chunk's k (state
 // rows) and fold them right to left with Table 5.
-template <typename T, int NX, int NY, typename GV>
+template <typename T, int NX, int NY, typename GV, typename FO>
 __global__ void __launch_bounds__(kBlock)
-smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
-                 const T* __restrict__ Nf, T* __restrict__ items) {
+smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, FO fo, T* __restrict__ items) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
@@ -213,8 +207,7 @@ smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
     const int64_t e = e0 + j;
     const int64_t k = e - so;
     T m[NX], N[NX * NX];
-    load<T, NX>(mf + e * NX, m);
-    load_lower<T, NX>(Nf + e * NX * NX, N);
+    fo.load(e, m, N);
     T* dst = (j == cnt - 1) ? agg : el;
     if (k == nb) {
       smoother_element_last<T, NX>(m, N, dst);
@@ -287,16 +280,14 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
 }
 
 // Leaf down-sweep: sequential square-root RTS steps from the chunk's carry
-// (m^s, N^s just after the chunk), writing m^s, N^s.  With `nominal` set the
-// scan runs on deviations from a nominal trajectory and the written mean is
-// nominal + deviation (nominal may alias ms: each row is read, then written,
-// by the same thread).
-template <typename T, int NX, int NY, typename GV>
+// (m^s, N^s just after the chunk), writing m^s, N^s to `out_rows`.  With
+// add_nominal the scan runs on deviations from a nominal trajectory held in
+// `out_rows` itself, and the written mean is nominal + deviation (each row is
+// read, then written, by the same thread).
+template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
 __global__ void __launch_bounds__(kBlock)
-smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
-                   const T* __restrict__ Nf, const T* __restrict__ carry,
-                   const int* __restrict__ flag, T* ms, T* __restrict__ Ns, int* status,
-                   const T* nominal) {
+smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ carry,
+                   const int* __restrict__ flag, SO out_rows, int* status, bool add_nominal) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
@@ -304,7 +295,7 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
   const int b = lv.seq[c];
   const int64_t e0 = lv.first[c];
   const int cnt = lv.count[c];
-  const int64_t so = sq.offsets[b] + b;
+  const int64_t r0 = sq.offsets[b] + b;
   const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
   T gm[NX], Dm[NX * NX];
   if (flag[c]) {
@@ -314,10 +305,9 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
   bool ok = true;
   for (int j = cnt - 1; j >= 0; --j) {
     const int64_t e = e0 + j;
-    const int64_t k = e - so;
+    const int64_t k = e - r0;
     T m[NX], N[NX * NX];
-    load<T, NX>(mf + e * NX, m);
-    load_lower<T, NX>(Nf + e * NX * NX, N);
+    fo.load(e, m, N);
     if (k == nb) {
       copy<T, NX>(m, gm);
       copy<T, NX * NX>(N, Dm);
@@ -328,15 +318,15 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ mf,
       smoother_element<T, NX, NY>(g, m, N, el);
       smoother_apply<T, NX>(el, gm, Dm);
     }
-    if (nominal) {
+    if (add_nominal) {
       T out[NX];
+      out_rows.load_mean(e, out);
 #pragma unroll
-      for (int i = 0; i < NX; ++i) out[i] = nominal[e * NX + i] + gm[i];
-      store<T, NX>(ms + e * NX, out);
+      for (int i = 0; i < NX; ++i) out[i] += gm[i];
+      out_rows.store(e, out, Dm);
     } else {
-      store<T, NX>(ms + e * NX, gm);
+      out_rows.store(e, gm, Dm);
     }
-    store_lower<T, NX>(Ns + e * NX * NX, Dm);
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);
   }
