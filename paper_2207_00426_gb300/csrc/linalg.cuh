@@ -21,6 +21,25 @@ SQSM_DEV double sq_sqrt(double x) { return sqrt(x); }
 SQSM_DEV float sq_log(float x) { return logf(x); }
 SQSM_DEV double sq_log(double x) { return log(x); }
 
+// Square root and reciprocal for the reflector of one Householder step
+// (normal x > 0).  FP32 starts from the hardware reciprocal square root and
+// reciprocal estimates and takes one Newton step each (on y^2 = x from
+// y = x rsqrt(x), and on 1/x, as in Markstein's refinements), which keeps
+// them within about an ulp without the slow-path branch of the IEEE
+// operations, so that a whole Tria is one branch-free block the compiler can
+// schedule across reflections.  FP64 keeps the correctly rounded operations.
+SQSM_DEV float hh_sqrt(float x) {
+  const float r = rsqrtf(x);
+  const float y = x * r;
+  return fmaf(fmaf(-y, y, x), 0.5f * r, y);
+}
+SQSM_DEV double hh_sqrt(double x) { return sqrt(x); }
+SQSM_DEV float hh_rcp(float x) {
+  const float r = __fdividef(1.0f, x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+SQSM_DEV double hh_rcp(double x) { return 1.0 / x; }
+
 // Tria(A) for an R x C matrix `a` (Sec. 2.2): on return columns 0..R-1 of
 // `a` hold the lower-triangular L with L L^T = A A^T and diag(L) >= 0 (the
 // strictly upper part of those columns and columns R..C-1 are left as
@@ -35,32 +54,39 @@ template <typename T, int R, int C, int NREF = R>
 SQSM_DEV void tria(T* a) {
   static_assert(R <= C, "tria is only used on R x C blocks with R <= C");
   static_assert(NREF <= R, "at most R reflections");
+  // Branch-free: a zero row selects the identity reflector (tau = 0, column
+  // left as is).  Dot products use two partial sums to halve their chains.
 #pragma unroll
   for (int i = 0; i < NREF; ++i) {
-    T s2 = T(0);
+    T s2a = T(0), s2b = T(0);
 #pragma unroll
-    for (int j = i; j < C; ++j) s2 += a[i * C + j] * a[i * C + j];
-    const T x0 = a[i * C + i];
-    if (s2 > Tiny<T>::value) {
-      const T alpha = sq_sqrt(s2);
-      const T sgn = x0 >= T(0) ? T(1) : T(-1);
-      const T v0 = x0 + sgn * alpha;
-      const T tau = T(1) / (alpha * (alpha + (x0 >= T(0) ? x0 : -x0)));
-#pragma unroll
-      for (int r = i + 1; r < R; ++r) {
-        T w = a[r * C + i] * v0;
-#pragma unroll
-        for (int j = i + 1; j < C; ++j) w += a[r * C + j] * a[i * C + j];
-        w *= tau;
-        // column i of L, with the sign flip that makes L_ii = alpha > 0
-        a[r * C + i] = -sgn * (a[r * C + i] - w * v0);
-#pragma unroll
-        for (int j = i + 1; j < C; ++j) a[r * C + j] -= w * a[i * C + j];
-      }
-      a[i * C + i] = alpha;
-    } else {
-      a[i * C + i] = T(0);
+    for (int j = i; j < C; j += 2) {
+      s2a += a[i * C + j] * a[i * C + j];
+      if (j + 1 < C) s2b += a[i * C + j + 1] * a[i * C + j + 1];
     }
+    const T s2 = s2a + s2b;
+    const T x0 = a[i * C + i];
+    const bool nz = s2 > Tiny<T>::value;
+    const T alpha = hh_sqrt(nz ? s2 : T(1));
+    const T sgn = x0 >= T(0) ? T(1) : T(-1);
+    const T v0 = x0 + sgn * alpha;
+    const T tau = nz ? hh_rcp(alpha * (alpha + (x0 >= T(0) ? x0 : -x0))) : T(0);
+#pragma unroll
+    for (int r = i + 1; r < R; ++r) {
+      T wa = a[r * C + i] * v0, wb = T(0);
+#pragma unroll
+      for (int j = i + 1; j < C; j += 2) {
+        wa += a[r * C + j] * a[i * C + j];
+        if (j + 1 < C) wb += a[r * C + j + 1] * a[i * C + j + 1];
+      }
+      const T w = (wa + wb) * tau;
+      // column i of L, with the sign flip that makes L_ii = alpha > 0
+      const T ci = -sgn * (a[r * C + i] - w * v0);
+      a[r * C + i] = nz ? ci : a[r * C + i];
+#pragma unroll
+      for (int j = i + 1; j < C; ++j) a[r * C + j] -= w * a[i * C + j];
+    }
+    a[i * C + i] = nz ? alpha : T(0);
   }
 }
 
