@@ -65,7 +65,7 @@ adj_smoother_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T* __restrict__ items) 
       copy<T, REC>(tmp, agg);
     }
   }
-  store<T, REC>(items + c * REC, agg);
+  vstore<T, REC>(items + c * REC, agg);
 }
 
 template <typename T>
@@ -149,7 +149,7 @@ adj_filter_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, T* __restrict__ i
       copy<T, REC>(tmp, agg);
     }
   }
-  store<T, REC>(items + c * REC, agg);
+  vstore<T, REC>(items + c * REC, agg);
 }
 
 template <typename T>
@@ -199,13 +199,13 @@ adj_up(DevLevel lv, const T* __restrict__ in, T* __restrict__ out) {
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   T agg[REC], mp[REC], tmp[REC];
-  load<T, REC>(in + (FWD ? i0 : i0 + cnt - 1) * REC, agg);
+  vload<T, REC>(in + (FWD ? i0 : i0 + cnt - 1) * REC, agg);
   for (int j = 1; j < cnt; ++j) {
-    load<T, REC>(in + (FWD ? i0 + j : i0 + cnt - 1 - j) * REC, mp);
+    vload<T, REC>(in + (FWD ? i0 + j : i0 + cnt - 1 - j) * REC, mp);
     map_compose<T, 5>(agg, mp, tmp);
     copy<T, REC>(tmp, agg);
   }
-  store<T, REC>(out + c * REC, agg);
+  vstore<T, REC>(out + c * REC, agg);
 }
 
 // carry = the cotangent vector entering the chunk (forward: before its
@@ -233,7 +233,7 @@ adj_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
     fout[i] = flag;
     if (j + 1 < cnt) {
       T mp[REC], xn[X];
-      load<T, REC>(items + i * REC, mp);
+      vload<T, REC>(items + i * REC, mp);
       map_apply<T, 5>(mp, x, xn);
       copy<T, X>(xn, x);
       flag = 1;
@@ -248,15 +248,15 @@ template <typename T, bool FWD>
 __global__ void __launch_bounds__(kChunkScan)
 adj_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   constexpr int REC = MapRec<5>::size;
-  __shared__ T S[kChunkScan * REC];
+  __shared__ __align__(16) T S[kChunkScan * REC];
   const int64_t c = blockIdx.x;
   const int t = threadIdx.x;   // position in scan order
   const int cnt = lv.count[c];
   const int64_t i = lv.first[c] + (FWD ? t : cnt - 1 - t);
   T mine[REC], tmp[REC];
-  if (t < cnt) load<T, REC>(items + i * REC, mine);
+  if (t < cnt) vload<T, REC>(items + i * REC, mine);
   for (int d = 1; d < cnt; d <<= 1) {
-    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    if (t < cnt) vstore<T, REC>(S + t * REC, mine);
     __syncwarp();
     if (t < cnt && t >= d) {
       map_compose<T, 5>(S + (t - d) * REC, mine, tmp);
@@ -264,8 +264,8 @@ adj_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
     }
     __syncwarp();
   }
-  if (t < cnt) store<T, REC>(items + i * REC, mine);
-  if (t == cnt - 1) store<T, REC>(out + c * REC, mine);
+  if (t < cnt) vstore<T, REC>(items + i * REC, mine);
+  if (t == cnt - 1) vstore<T, REC>(out + c * REC, mine);
 }
 
 // One thread per item of a chunk-scanned level: the cotangent entering item
@@ -293,7 +293,7 @@ adj_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
   }
   if (!head) {
     T mp[REC], xn[X];
-    load<T, REC>(items + (FWD ? i - 1 : i + 1) * REC, mp);
+    vload<T, REC>(items + (FWD ? i - 1 : i + 1) * REC, mp);
     map_apply<T, 5>(mp, x, xn);
     copy<T, X>(xn, x);
   }

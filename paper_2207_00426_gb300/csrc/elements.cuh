@@ -182,13 +182,25 @@ struct Gamma {
   }
 };
 
+// Record sizes are padded to whole 16-byte words (4 elements) so that
+// records move with vector accesses.
 template <int NX> struct FRec {
   static constexpr int A = 0, b = NX * NX, U = NX * NX + NX, eta = 2 * NX * NX + NX,
-                       Z = 2 * NX * NX + 2 * NX, size = 3 * NX * NX + 2 * NX;
+                       Z = 2 * NX * NX + 2 * NX, size = (3 * NX * NX + 2 * NX + 3) / 4 * 4;
 };
 template <int NX> struct SRec {
-  static constexpr int E = 0, g = NX * NX, D = NX * NX + NX, size = 2 * NX * NX + NX;
+  static constexpr int E = 0, g = NX * NX, D = NX * NX + NX,
+                       size = (2 * NX * NX + NX + 3) / 4 * 4;
 };
+inline int frec_size(int nx) { return (3 * nx * nx + 2 * nx + 3) / 4 * 4; }
+inline int srec_size(int nx) { return (2 * nx * nx + nx + 3) / 4 * 4; }
+
+// Clear the padding words of a record after its fields are written.
+template <typename T, int USED, int SIZE>
+SQSM_DEV void zero_pad(T* rec) {
+#pragma unroll
+  for (int i = USED; i < SIZE; ++i) rec[i] = T(0);
+}
 
 constexpr double kLog2Pi = 1.8378770664093454835606594728112;
 
@@ -410,6 +422,7 @@ SQSM_DEV void filter_element(const Gamma<T, NX, NY>& g, const T* y, bool first, 
 #pragma unroll
     for (int j = 0; j < NY; ++j) Zr[i * NY + j] = Wm[j * NX + i];
   square_Z<T, NX, NY>(Zr, e + R::Z);
+  zero_pad<T, R::Z + NX * NX, R::size>(e);
 }
 
 // Xi of eq. sqrt-filter-com-2 from U_i and Z_j: the 2NX x 2NX matrix
@@ -530,6 +543,7 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     tria<T, NX, C2>(B);
     take_lower<T, NX, C2>(B, out + R::Z);
   }
+  zero_pad<T, R::Z + NX * NX, R::size>(out);
 }
 
 // Table 3 with a left operand that is a filtering distribution (A_i = 0):
@@ -625,6 +639,7 @@ SQSM_DEV void smoother_element(const Gamma<T, NX, NY>& g, const T* mf, const T* 
     for (int j = 0; j < NX; ++j)
       e[R::D + i * NX + j] = j <= i ? Phi[(NX + i) * C2 + NX + j] : T(0);
   }
+  zero_pad<T, R::D + NX * NX, R::size>(e);
 }
 
 // Caption of Table 4: E_n = 0, g_n = m^f_n, D_n = N^f_n.
@@ -638,6 +653,7 @@ SQSM_DEV void smoother_element_last(const T* mf, const T* Nf, T* e) {
   }
 #pragma unroll
   for (int i = 0; i < NX; ++i) e[R::g + i] = mf[i];
+  zero_pad<T, R::D + NX * NX, R::size>(e);
 }
 
 // Smoother operator of Lemma 4 / Table 5 (right column): out = e_i (x) e_j,
@@ -664,6 +680,7 @@ SQSM_DEV void smoother_combine(const T* ei, const T* ej, T* out) {
     }
   tria<T, NX, C2>(B);
   take_lower<T, NX, C2>(B, out + R::D);
+  zero_pad<T, R::D + NX * NX, R::size>(out);
 }
 
 // Table 5 with a right operand whose E is 0 (a smoothing distribution

@@ -172,7 +172,7 @@ extern "C" int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n, c
   if (sF < 0 || sc < 0 || sSQ < 0 || sH < 0 || sd < 0 || sSR < 0) return SQSM_ERR_INVALID_ARG;
   const int L0 = 4, R = 4;   // the default scan shape of sqsm_lgssm_smooth
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
-  const size_t frec = 3 * nx * nx + 2 * nx, srec = 2 * nx * nx + nx, crec = nx + nx * nx;
+  const size_t frec = frec_size(nx), srec = srec_size(nx), crec = nx + nx * nx;
 
   // measure first: reject problems that do not fit before touching the GPU
   for (int pass = 0; pass < 2; ++pass) {

@@ -82,7 +82,7 @@ filter_leaf_up(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
       copy<T, REC>(tmp, agg);
     }
   }
-  store<T, REC>(items + c * REC, agg);
+  vstore<T, REC>(items + c * REC, agg);
 }
 
 // Upper up-sweep: fold `count` consecutive items left to right.
@@ -95,13 +95,13 @@ filter_up(DevLevel lv, const T* __restrict__ items_in, T* __restrict__ items_out
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   T agg[REC], el[REC], tmp[REC];
-  load<T, REC>(items_in + i0 * REC, agg);
+  vload<T, REC>(items_in + i0 * REC, agg);
   for (int j = 1; j < cnt; ++j) {
-    load<T, REC>(items_in + (i0 + j) * REC, el);
+    vload<T, REC>(items_in + (i0 + j) * REC, el);
     filter_combine<T, NX>(agg, el, tmp);
     copy<T, REC>(tmp, agg);
   }
-  store<T, REC>(items_out + c * REC, agg);
+  vstore<T, REC>(items_out + c * REC, agg);
 }
 
 // Upper down-sweep: item c of level l+1 carries the filtering distribution
@@ -130,7 +130,7 @@ filter_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carr
       const T* it = items + i * REC;
       if (flag) {
         T el[REC], nb[NX], nU[NX * NX];
-        load<T, REC>(it, el);
+        vload<T, REC>(it, el);
         filter_apply<T, NX>(cb, cU, el, nb, nU);
         copy<T, NX>(nb, cb);
         copy<T, NX * NX>(nU, cU);
@@ -221,7 +221,7 @@ smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, FO fo, T* __restrict__ items) {
       copy<T, REC>(tmp, agg);
     }
   }
-  store<T, REC>(items + c * REC, agg);
+  vstore<T, REC>(items + c * REC, agg);
 }
 
 // Upper up-sweep: fold `count` items right to left.
@@ -234,13 +234,13 @@ smoother_up(DevLevel lv, const T* __restrict__ items_in, T* __restrict__ items_o
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   T agg[REC], el[REC], tmp[REC];
-  load<T, REC>(items_in + (i0 + cnt - 1) * REC, agg);
+  vload<T, REC>(items_in + (i0 + cnt - 1) * REC, agg);
   for (int j = cnt - 2; j >= 0; --j) {
-    load<T, REC>(items_in + (i0 + j) * REC, el);
+    vload<T, REC>(items_in + (i0 + j) * REC, el);
     smoother_combine<T, NX>(el, agg, tmp);
     copy<T, REC>(tmp, agg);
   }
-  store<T, REC>(items_out + c * REC, agg);
+  vstore<T, REC>(items_out + c * REC, agg);
 }
 
 // Upper down-sweep: item c of level l+1 carries the smoothing distribution
@@ -268,7 +268,7 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
       const T* it = items + i * REC;
       if (flag) {
         T el[REC];
-        load<T, REC>(it, el);
+        vload<T, REC>(it, el);
         smoother_apply<T, NX>(el, cg, cD);
       } else {
         load<T, NX>(it + SRec<NX>::g, cg);

@@ -181,14 +181,14 @@ __global__ void __launch_bounds__((KsMax<T, FRec<NX>::size>::value))
 filter_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
               T* __restrict__ carry_out, int* __restrict__ flag_out) {
   constexpr int REC = FRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
-  __shared__ T S[KS * REC];
+  __shared__ __align__(16) T S[KS * REC];
   const int b = blockIdx.x, t = threadIdx.x;
   const int64_t i0 = seq_item_off[b];
   const int c = (int)(seq_item_off[b + 1] - i0);
   T mine[REC], tmp[REC];
-  if (t < c) load<T, REC>(items + (i0 + t) * REC, mine);
+  if (t < c) vload<T, REC>(items + (i0 + t) * REC, mine);
   for (int d = 1; d < c; d <<= 1) {
-    if (t < c) store<T, REC>(S + t * REC, mine);
+    if (t < c) vstore<T, REC>(S + t * REC, mine);
     __syncthreads();
     if (t < c && t >= d) {
       filter_combine<T, NX>(S + (t - d) * REC, mine, tmp);
@@ -196,7 +196,7 @@ filter_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ it
     }
     __syncthreads();
   }
-  if (t < c) store<T, REC>(S + t * REC, mine);
+  if (t < c) vstore<T, REC>(S + t * REC, mine);
   __syncthreads();
   if (t < c) {
     T* co = carry_out + (i0 + t) * CREC;
@@ -216,14 +216,14 @@ __global__ void __launch_bounds__((KsMax<T, SRec<NX>::size>::value))
 smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
                 T* __restrict__ carry_out, int* __restrict__ flag_out) {
   constexpr int REC = SRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
-  __shared__ T S[KS * REC];
+  __shared__ __align__(16) T S[KS * REC];
   const int b = blockIdx.x, t = threadIdx.x;
   const int64_t i0 = seq_item_off[b];
   const int c = (int)(seq_item_off[b + 1] - i0);
   T mine[REC], tmp[REC];
-  if (t < c) load<T, REC>(items + (i0 + t) * REC, mine);
+  if (t < c) vload<T, REC>(items + (i0 + t) * REC, mine);
   for (int d = 1; d < c; d <<= 1) {
-    if (t < c) store<T, REC>(S + t * REC, mine);
+    if (t < c) vstore<T, REC>(S + t * REC, mine);
     __syncthreads();
     if (t + d < c) {
       smoother_combine<T, NX>(mine, S + (t + d) * REC, tmp);
@@ -231,7 +231,7 @@ smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ 
     }
     __syncthreads();
   }
-  if (t < c) store<T, REC>(S + t * REC, mine);
+  if (t < c) vstore<T, REC>(S + t * REC, mine);
   __syncthreads();
   if (t < c) {
     T* co = carry_out + (i0 + t) * CREC;
@@ -261,15 +261,15 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kChunkScan)
 filter_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   constexpr int REC = FRec<NX>::size;
-  __shared__ T S[kChunkScan * REC];
+  __shared__ __align__(16) T S[kChunkScan * REC];
   const int64_t c = blockIdx.x;
   const int t = threadIdx.x;
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   T mine[REC], tmp[REC];
-  if (t < cnt) load<T, REC>(items + (i0 + t) * REC, mine);
+  if (t < cnt) vload<T, REC>(items + (i0 + t) * REC, mine);
   for (int d = 1; d < cnt; d <<= 1) {
-    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    if (t < cnt) vstore<T, REC>(S + t * REC, mine);
     __syncwarp();
     if (t < cnt && t >= d) {
       filter_combine<T, NX>(S + (t - d) * REC, mine, tmp);
@@ -277,8 +277,8 @@ filter_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
     }
     __syncwarp();
   }
-  if (t < cnt) store<T, REC>(items + (i0 + t) * REC, mine);
-  if (t == cnt - 1) store<T, REC>(out + c * REC, mine);
+  if (t < cnt) vstore<T, REC>(items + (i0 + t) * REC, mine);
+  if (t == cnt - 1) vstore<T, REC>(out + c * REC, mine);
 }
 
 // One thread per item of the level.
@@ -302,7 +302,7 @@ filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ c
     T pb[NX], pU[NX * NX], el[REC];
     load<T, NX>(carry_in + c * CREC, pb);
     load<T, NX * NX>(carry_in + c * CREC + NX, pU);
-    load<T, REC>(items + (i - 1) * REC, el);
+    vload<T, REC>(items + (i - 1) * REC, el);
     filter_apply<T, NX>(pb, pU, el, cb, cU);
   } else {
     load<T, NX>(items + (i - 1) * REC + FRec<NX>::b, cb);
@@ -317,15 +317,15 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kChunkScan)
 smoother_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   constexpr int REC = SRec<NX>::size;
-  __shared__ T S[kChunkScan * REC];
+  __shared__ __align__(16) T S[kChunkScan * REC];
   const int64_t c = blockIdx.x;
   const int t = threadIdx.x;
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   T mine[REC], tmp[REC];
-  if (t < cnt) load<T, REC>(items + (i0 + t) * REC, mine);
+  if (t < cnt) vload<T, REC>(items + (i0 + t) * REC, mine);
   for (int d = 1; d < cnt; d <<= 1) {
-    if (t < cnt) store<T, REC>(S + t * REC, mine);
+    if (t < cnt) vstore<T, REC>(S + t * REC, mine);
     __syncwarp();
     if (t + d < cnt) {
       smoother_combine<T, NX>(mine, S + (t + d) * REC, tmp);
@@ -333,8 +333,8 @@ smoother_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
     }
     __syncwarp();
   }
-  if (t < cnt) store<T, REC>(items + (i0 + t) * REC, mine);
-  if (t == 0 && cnt > 0) store<T, REC>(out + c * REC, mine);
+  if (t < cnt) vstore<T, REC>(items + (i0 + t) * REC, mine);
+  if (t == 0 && cnt > 0) vstore<T, REC>(out + c * REC, mine);
 }
 
 template <typename T, int NX>
@@ -358,7 +358,7 @@ smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__
     T el[REC];
     load<T, NX>(carry_in + c * CREC, cg);
     load<T, NX * NX>(carry_in + c * CREC + NX, cD);
-    load<T, REC>(items + (i + 1) * REC, el);
+    vload<T, REC>(items + (i + 1) * REC, el);
     smoother_apply<T, NX>(el, cg, cD);
   } else {
     load<T, NX>(items + (i + 1) * REC + SRec<NX>::g, cg);
