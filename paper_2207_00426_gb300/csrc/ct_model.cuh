@@ -5,8 +5,8 @@
 // Model: x = (p_x, p_y, v_x, v_y, w), a = w dt,
 //   p' = p + [[S, -C], [C, S]] v,  v' = [[cos a, -sin a], [sin a, cos a]] v,
 //   w' = w,  S = sin(a)/w,  C = (1 - cos a)/w = 2 sin^2(a/2)/w
-//   (series S = dt(1 - a^2/6 + a^4/120), C = dt(a/2 - a^3/24 + a^5/720) for
-//   |a| < 1e-3); process noise factor in closed form; bearings
+//   (Taylor series of sin(a)/a and (1 - cos a)/a^2 for |a| <= 1/4);
+//   process noise factor in closed form; bearings
 //   atan2(p_y - s_y, p_x - s_x) with noise sigma.
 //
 // Cubature (third-degree spherical-radial rule, points m +- sqrt(nx) N e_i,
@@ -70,10 +70,46 @@ __global__ void ct_params_kernel(double th0, double th1, double th2, double dt, 
   *P = p;
 }
 
-// Turn coefficients of a = w dt from one sincos of a/2 (double-angle
-// identities sin a = 2 s c, cos a = 1 - 2 s^2, 1 - cos a = 2 s^2):
-// S = sin(a)/w, C = (1 - cos a)/w, ca = cos a, sa = sin a, omc = 1 - cos a;
-// S and C by their series for |a| < 1e-3.
+// sin(a)/a and (1 - cos a)/a^2 by their Taylor series in a^2, for
+// |a| <= kSeriesMaxAngle: the first omitted term is below half an ulp of the
+// result (a^2 <= 1/16; FP32 keeps 4 terms, FP64 7).
+constexpr double kSeriesMaxAngle = 0.25;
+
+template <typename T>
+SQSM_DEV void sinc_cosc(T a2, T& sinc, T& cosc) {
+  if constexpr (sizeof(T) == 4) {
+    sinc = T(1) + a2 * (T(-1.0 / 6) + a2 * (T(1.0 / 120) + a2 * T(-1.0 / 5040)));
+    cosc = T(0.5) + a2 * (T(-1.0 / 24) + a2 * (T(1.0 / 720) + a2 * T(-1.0 / 40320)));
+  } else {
+    sinc = T(1) + a2 * (T(-1.0 / 6) + a2 * (T(1.0 / 120) + a2 * (T(-1.0 / 5040) +
+           a2 * (T(1.0 / 362880) + a2 * (T(-1.0 / 39916800) + a2 * T(1.0 / 6227020800.0))))));
+    cosc = T(0.5) + a2 * (T(-1.0 / 24) + a2 * (T(1.0 / 720) + a2 * (T(-1.0 / 40320) +
+           a2 * (T(1.0 / 3628800) + a2 * (T(-1.0 / 479001600) + a2 * T(1.0 / 87178291200.0))))));
+  }
+}
+
+// sin a and 1 - cos a of a small angle (series), else from one sincos of
+// a/2 (sin a = 2 s c, 1 - cos a = 2 s^2): both without cancellation.
+template <typename T>
+SQSM_DEV void sin_omc(T a, T& sa, T& omc) {
+  if (fabs(a) <= T(kSeriesMaxAngle)) {
+    T sinc, cosc;
+    sinc_cosc(a * a, sinc, cosc);
+    sa = a * sinc;
+    omc = a * a * cosc;
+  } else {
+    T sh, ch;
+    sq_sincos(T(0.5) * a, &sh, &ch);
+    sa = T(2) * sh * ch;
+    omc = T(2) * sh * sh;
+  }
+}
+
+// Turn coefficients of a = w dt: S = sin(a)/w, C = (1 - cos a)/w,
+// ca = cos a, sa = sin a, omc = 1 - cos a.  Small angles (the usual case:
+// |w| dt <= 1/4) take the series of sin(a)/a and (1 - cos a)/a^2, which need
+// neither a sincos nor a division; larger ones one sincos of a/2 and two
+// divisions.
 template <typename T>
 struct Turn {
   T S, C, ca, sa, omc;
@@ -83,19 +119,22 @@ template <typename T>
 SQSM_DEV Turn<T> turn(T w, T dt) {
   Turn<T> r;
   const T a = w * dt;
-  T sh, ch;
-  sq_sincos(T(0.5) * a, &sh, &ch);
-  r.sa = T(2) * sh * ch;
-  r.omc = T(2) * sh * sh;
-  r.ca = T(1) - r.omc;
-  if (fabs(a) < T(1e-3)) {
-    const T a2 = a * a;
-    r.S = dt * (T(1) - a2 / T(6) + a2 * a2 / T(120));
-    r.C = dt * a * (T(0.5) - a2 / T(24) + a2 * a2 / T(720));
+  if (fabs(a) <= T(kSeriesMaxAngle)) {
+    T sinc, cosc;
+    sinc_cosc(a * a, sinc, cosc);
+    r.sa = a * sinc;
+    r.omc = a * a * cosc;
+    r.S = dt * sinc;
+    r.C = dt * a * cosc;
   } else {
+    T sh, ch;
+    sq_sincos(T(0.5) * a, &sh, &ch);
+    r.sa = T(2) * sh * ch;
+    r.omc = T(2) * sh * sh;
     r.S = r.sa / w;
     r.C = r.omc / w;
   }
+  r.ca = T(1) - r.omc;
   return r;
 }
 
@@ -161,9 +200,8 @@ SQSM_DEV void ct_f_minus_x(const CTParams<T>& P, const T* x, T* o) {
 template <typename T>
 SQSM_DEV void ct_g_delta(const CTParams<T>& P, const Turn<T>& tm, const T* m, const T* dl, T* o) {
   const Turn<T> tx = turn(m[4] + dl[4], P.dt);
-  T shd, chd;
-  sq_sincos(T(0.5) * dl[4] * P.dt, &shd, &chd);
-  const T sd = T(2) * shd * chd, omd = T(2) * shd * shd;
+  T sd, omd;
+  sin_omc(dl[4] * P.dt, sd, omd);
   const T ux = -omd * m[2] - sd * m[3], uy = sd * m[2] - omd * m[3];
   o[0] = (tx.S * dl[2] - tx.C * dl[3]) + ((tx.S - tm.S) * m[2] - (tx.C - tm.C) * m[3]);
   o[1] = (tx.C * dl[2] + tx.S * dl[3]) + ((tx.C - tm.C) * m[2] + (tx.S - tm.S) * m[3]);
