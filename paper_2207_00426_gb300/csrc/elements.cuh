@@ -455,37 +455,43 @@ SQSM_DEV void make_xi(const T* Ui, const T* Zj, T* X) {
 //   U_ij = Tria([A_j U_i Xi_11^{-T}, U_j]),
 //   eta_ij = A_i^T (I - G U_i^T)(eta_j - Z_j Z_j^T b_i) + eta_i,
 //   Z_ij = Tria([A_i^T Xi_22, Z_i]).
-template <typename T, int NX>
+// PARTS selects the fields computed (bit 0: A, b; bit 1: U; bit 2: eta, Z),
+// so that three threads can each take one part of a combine; Xi_22 (the
+// last NX reflections) is formed only for eta, Z.
+template <typename T, int NX, int PARTS = 7>
 SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
   using R = FRec<NX>;
   constexpr int C2 = 2 * NX;
+  constexpr bool AB = PARTS & 1, UU = PARTS & 2, EZ = PARTS & 4;
   T X[C2 * C2];
-  make_xi<T, NX, C2>(ei + R::U, ej + R::Z, X);
-  T G[NX * NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i)
-#pragma unroll
-    for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
+  make_xi<T, NX, EZ ? C2 : NX>(ei + R::U, ej + R::Z, X);
   T X11[NX * NX];
   take_lower<T, NX, C2>(X, X11);
-  rsolve<T, NX, NX>(G, X11);
   const T* Ui = ei + R::U;
-  // Minv = I - U_i G^T
-  T Mi[NX * NX];
+  T G[NX * NX];
+  if constexpr (AB || EZ) {
 #pragma unroll
-  for (int i = 0; i < NX; ++i)
+    for (int i = 0; i < NX; ++i)
 #pragma unroll
-    for (int j = 0; j < NX; ++j) {
-      T s = i == j ? T(1) : T(0);
+      for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
+    rsolve<T, NX, NX>(G, X11);
+  }
+  if constexpr (AB) {
+    // Minv = I - U_i G^T
+    T Mi[NX * NX];
 #pragma unroll
-      for (int k = 0; k <= i; ++k) s -= Ui[i * NX + k] * G[j * NX + k];
-      Mi[i * NX + j] = s;
-    }
-  T AjM[NX * NX];
-  mm<T, NX, NX, NX>(ej + R::A, Mi, AjM);
-  mm<T, NX, NX, NX>(AjM, ei + R::A, out + R::A);
-  // b_ij
-  {
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        T s = i == j ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) s -= Ui[i * NX + k] * G[j * NX + k];
+        Mi[i * NX + j] = s;
+      }
+    T AjM[NX * NX];
+    mm<T, NX, NX, NX>(ej + R::A, Mi, AjM);
+    mm<T, NX, NX, NX>(AjM, ei + R::A, out + R::A);
+    // b_ij
     T t[NX], u[NX];
     mtv<T, NX, NX>(Ui, ej + R::eta, t);
     mv<T, NX, NX>(Ui, t, u);
@@ -495,8 +501,8 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
 #pragma unroll
     for (int i = 0; i < NX; ++i) out[R::b + i] = t[i] + ej[R::b + i];
   }
-  // U_ij = Tria([A_j U_i Xi11^{-T}, U_j])
-  {
+  if constexpr (UU) {
+    // U_ij = Tria([A_j U_i Xi11^{-T}, U_j])
     T V[NX * NX];
     mm<T, NX, NX, NX>(ej + R::A, Ui, V);
     rsolve_t<T, NX, NX>(V, X11);
@@ -511,8 +517,8 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     tria<T, NX, C2>(B);
     take_lower<T, NX, C2>(B, out + R::U);
   }
-  // eta_ij
-  {
+  if constexpr (EZ) {
+    // eta_ij
     const T* Zj = ej + R::Z;
     T s[NX], r[NX], t[NX];
     mtv<T, NX, NX>(Zj, ei + R::b, s);
@@ -526,24 +532,22 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     mtv<T, NX, NX>(ei + R::A, r, t);
 #pragma unroll
     for (int i = 0; i < NX; ++i) out[R::eta + i] = t[i] + ei[R::eta + i];
-  }
-  // Z_ij = Tria([A_i^T Xi22, Z_i])
-  {
+    // Z_ij = Tria([A_i^T Xi22, Z_i])
     T B[NX * C2];
 #pragma unroll
     for (int i = 0; i < NX; ++i)
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
-        T s = T(0);
+        T a = T(0);
 #pragma unroll
-        for (int k = j; k < NX; ++k) s += ei[R::A + k * NX + i] * X[(NX + k) * C2 + NX + j];
-        B[i * C2 + j] = s;
+        for (int k = j; k < NX; ++k) a += ei[R::A + k * NX + i] * X[(NX + k) * C2 + NX + j];
+        B[i * C2 + j] = a;
         B[i * C2 + NX + j] = ei[R::Z + i * NX + j];
       }
     tria<T, NX, C2>(B);
     take_lower<T, NX, C2>(B, out + R::Z);
   }
-  zero_pad<T, R::Z + NX * NX, R::size>(out);
+  if constexpr (PARTS == 7) zero_pad<T, R::Z + NX * NX, R::size>(out);
 }
 
 // Table 3 with a left operand that is a filtering distribution (A_i = 0):

@@ -85,12 +85,19 @@ struct ProfScope {
   }
 };
 
+// Chunk-scanned filter levels of at most this many chunks use three threads
+// per combine (latency-bound); larger ones one (throughput-bound).
+constexpr int64_t kCs3MaxChunks = 512;
+
 template <typename T, int NX, int NY, typename GV, typename FO>
 void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
                     const T* y, const T* m0, const T* N0, FO fo, double* partial,
                     int* status, cudaStream_t s, Prof* P = nullptr) {
   const int Lc = (int)L.lv.size();
-  constexpr int KS = KsMax<T, FRec<NX>::size>::value;
+  // FP32 takes three threads per combine at the top of the tree; FP64 records
+  // and factors do not fit three such threads' registers.
+  constexpr bool R3 = sizeof(T) == 4;
+  constexpr int KS = R3 ? Ks3Max<T, FRec<NX>::size>::value : KsMax<T, FRec<NX>::size>::value;
   const int Lk = L.ks_level(KS);
   if (Lc > 1) {  // with one leaf chunk per sequence every carry is the prior
     {
@@ -100,7 +107,10 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_FILTER_UP, s);
-      if (L.chunk_scan(l))
+      if (R3 && L.chunk_scan(l) && L.lv[l].n_chunks <= kCs3MaxChunks)
+        filter_up_cs3<T, NX><<<(unsigned)L.lv[l].n_chunks, 3 * kChunkScan, 0, s>>>(
+            L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
+      else if (L.chunk_scan(l))
         filter_up_cs<T, NX><<<(unsigned)L.lv[l].n_chunks, kChunkScan, 0, s>>>(
             L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
       else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
@@ -111,9 +121,12 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
             L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
     }
     ProfScope ps(P, K_FILTER_UP, s);
-    filter_top_ks<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk],
-                                                        (const T*)W.items[Lk], (T*)W.carry[Lk],
-                                                        W.flag[Lk]);
+    if constexpr (R3)
+      filter_top_ks3<T, NX><<<L.B, 3 * KS, 0, s>>>(L.seq_item_off[Lk], (const T*)W.items[Lk],
+                                                  (T*)W.carry[Lk], W.flag[Lk]);
+    else
+      filter_top_ks<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk], (const T*)W.items[Lk],
+                                              (T*)W.carry[Lk], W.flag[Lk]);
   } else {
     cudaMemsetAsync(W.flag[Lc], 0, sizeof(int) * L.n_items[Lc], s);
   }

@@ -21,8 +21,8 @@ SQSM_DEV double sq_sqrt(double x) { return sqrt(x); }
 SQSM_DEV float sq_log(float x) { return logf(x); }
 SQSM_DEV double sq_log(double x) { return log(x); }
 
-// Square root and reciprocal for the reflector of one Householder step
-// (normal x > 0).  FP32 starts from the hardware reciprocal square root and
+// Square root and reciprocal for the reflector of one Householder step and
+// the diagonal of triangular solves (normal x > 0).  FP32 starts from the hardware reciprocal square root and
 // reciprocal estimates and takes one Newton step each (on y^2 = x from
 // y = x rsqrt(x), and on 1/x, as in Markstein's refinements), which keeps
 // them within about an ulp without the slow-path branch of the IEEE
@@ -197,7 +197,7 @@ template <typename T, int M, int N>
 SQSM_DEV void rsolve(T* X, const T* L) {
   T inv[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) inv[i] = T(1) / L[i * N + i];
+  for (int i = 0; i < N; ++i) inv[i] = hh_rcp(L[i * N + i]);
 #pragma unroll
   for (int r = 0; r < M; ++r) {
 #pragma unroll
@@ -215,7 +215,7 @@ template <typename T, int M, int N>
 SQSM_DEV void rsolve_t(T* X, const T* L) {
   T inv[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) inv[i] = T(1) / L[i * N + i];
+  for (int i = 0; i < N; ++i) inv[i] = hh_rcp(L[i * N + i]);
 #pragma unroll
   for (int r = 0; r < M; ++r) {
 #pragma unroll

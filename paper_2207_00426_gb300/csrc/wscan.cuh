@@ -373,4 +373,101 @@ inline unsigned cs_down_grid(int64_t chunks) {
   return (unsigned)((chunks * kChunkScan + kBlock - 1) / kBlock);
 }
 
+// Filter scans with three threads per combine.  In the latency-bound top
+// levels (few chunks, one warp per SM or less) a combine's chain of dependent
+// instructions sets the time per Kogge-Stone round.  Thread (role r, item t)
+// computes only part r of S[t - d] (x) S[t] (r = 0: A, b; 1: U; 2: eta, Z;
+// each forms the Xi factor it needs itself), which shortens that chain; role
+// r runs in warps of its own, so no warp diverges.
+template <typename T, int NX, int CAP>
+SQSM_DEV void filter_ks3(T* S, int c) {
+  using R = FRec<NX>;
+  constexpr int REC = R::size;
+  static_assert(CAP % 32 == 0, "roles in whole warps");
+  const int role = threadIdx.x / CAP, t = threadIdx.x - role * CAP;
+  for (int d = 1; d < c; d <<= 1) {
+    T part[REC];
+    const bool act = t < c && t >= d;
+    if (act) {
+      const T* ei = S + (t - d) * REC;
+      const T* ej = S + t * REC;
+      if (role == 0) filter_combine<T, NX, 1>(ei, ej, part);
+      else if (role == 1) filter_combine<T, NX, 2>(ei, ej, part);
+      else filter_combine<T, NX, 4>(ei, ej, part);
+    }
+    __syncthreads();
+    if (act) {
+      T* o = S + t * REC;
+      if (role == 0) {
+#pragma unroll
+        for (int i = R::A; i < R::U; ++i) o[i] = part[i];
+      } else if (role == 1) {
+#pragma unroll
+        for (int i = R::U; i < R::eta; ++i) o[i] = part[i];
+      } else {
+#pragma unroll
+        for (int i = R::eta; i < R::Z + NX * NX; ++i) o[i] = part[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Chunk-scan up level (see filter_up_cs) with three threads per combine: one
+// block of 3 x 32 threads per chunk.
+template <typename T, int NX>
+__global__ void __launch_bounds__(3 * kChunkScan)
+filter_up_cs3(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
+  constexpr int REC = FRec<NX>::size, W = REC * sizeof(T) / 16;   // 16-byte words
+  __shared__ __align__(16) T S[kChunkScan * REC];
+  const int64_t c = blockIdx.x;
+  const int64_t i0 = lv.first[c];
+  const int cnt = lv.count[c];
+  float4* S4 = reinterpret_cast<float4*>(S);
+  float4* I4 = reinterpret_cast<float4*>(items + i0 * REC);
+  for (int w = threadIdx.x; w < cnt * W; w += blockDim.x) S4[w] = I4[w];
+  __syncthreads();
+  filter_ks3<T, NX, kChunkScan>(S, cnt);
+  for (int w = threadIdx.x; w < cnt * W; w += blockDim.x) I4[w] = S4[w];
+  float4* O4 = reinterpret_cast<float4*>(out + c * REC);
+  for (int w = threadIdx.x; w < W; w += blockDim.x) O4[w] = S4[(cnt - 1) * W + w];
+}
+
+// Top of the tree (see filter_top_ks) with three threads per combine, for
+// sequences of at most Ks3Max items at that level (64, fewer where the
+// records would not fit 48 KB of static shared memory).
+template <typename T, int REC> struct Ks3Max {
+  static constexpr int fit = (int)((48 * 1024) / (REC * sizeof(T)) / 32 * 32);
+  static constexpr int value = 64 < fit ? 64 : fit;
+};
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(3 * Ks3Max<T, FRec<NX>::size>::value)
+filter_top_ks3(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
+               T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX, W = REC * sizeof(T) / 16;
+  constexpr int KS = Ks3Max<T, REC>::value;
+  __shared__ __align__(16) T S[KS * REC];
+  const int b = blockIdx.x;
+  const int64_t i0 = seq_item_off[b];
+  const int c = (int)(seq_item_off[b + 1] - i0);
+  float4* S4 = reinterpret_cast<float4*>(S);
+  const float4* I4 = reinterpret_cast<const float4*>(items + i0 * REC);
+  for (int w = threadIdx.x; w < c * W; w += blockDim.x) S4[w] = I4[w];
+  __syncthreads();
+  filter_ks3<T, NX, KS>(S, c);
+  const int t = threadIdx.x;
+  if (t < c) {
+    T* co = carry_out + (i0 + t) * CREC;
+    if (t > 0) {
+      const T* p = S + (t - 1) * REC;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) co[i] = p[FRec<NX>::b + i];
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[FRec<NX>::U + i];
+    }
+    flag_out[i0 + t] = t > 0 ? 1 : 0;
+  }
+}
+
 }  // namespace sqsm
