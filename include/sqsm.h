@@ -86,14 +86,30 @@ typedef struct {
 /* Scan shape.  Zero fields take defaults: leaf_chunk 3 when all leaf chunks
  * of a call fit one wave of 256 threads per SM, else 4; radix 0 folds upper
  * levels of more than 160000 items 4 per thread and scans smaller levels in
- * one-warp chunks of 32. */
+ * one-warp chunks of 32.
+ *
+ * autotune = 1 (with leaf_chunk = radix = 0): the first sqsm_ipls_smooth or
+ * sqsm_ipls_nll_grad call of each workload shape (dtype, linearisation,
+ * batch size, log2 of the total and of the longest sequence length) times
+ * one IPLS iteration for each candidate scan shape on the caller's inputs
+ * and stream, keeps the fastest for the context, then runs the call.  That
+ * first call synchronises the stream and overwrites the outputs before
+ * writing the final ones; later calls of the shape use the stored choice. */
 typedef struct {
   int leaf_chunk;       /* time steps folded by one thread at the leaf  */
   int radix;            /* items folded by one thread at upper levels   */
   int use_graph;        /* 1: replay the IPLS iterations as a CUDA graph */
+  int autotune;         /* 1: measure and keep the fastest scan shape   */
 } sqsm_options;
 
 typedef struct sqsm_ctx sqsm_ctx;
+
+/* The scan shape (leaf_chunk, radix; radix 0 = the adaptive upper levels)
+ * that IPLS calls on this context use for a batch of sequences with the
+ * given host offsets (batch + 1 values) and dtype: the options', the
+ * autotuned choice if one is stored, else the default.  No GPU work. */
+int sqsm_scan_shape(sqsm_ctx* ctx, int dtype, int linearization, int64_t batch,
+                    const int64_t* offsets, int* leaf_chunk, int* radix);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).
  * The context owns scan workspaces, cached plans and captured graphs; they

@@ -37,7 +37,7 @@ _int = ctypes.c_int
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int)]
+    _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int), ("autotune", _int)]
 
 
 class Model(ctypes.Structure):
@@ -77,11 +77,15 @@ lib.sqsm_profile_read.argtypes = [_p, _int, ctypes.POINTER(ctypes.c_double), cty
 lib.sqsm_profile_read.restype = _int
 lib.sqsm_kernel_name.argtypes = [_int]
 lib.sqsm_kernel_name.restype = ctypes.c_char_p
+lib.sqsm_scan_shape.argtypes = [_p, _int, _int, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_int),
+                                ctypes.POINTER(_int)]
+lib.sqsm_scan_shape.restype = _int
 
 EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
-            "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad"]
+            "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad",
+            "sqsm_scan_shape"]
 
 
 class SqsmError(RuntimeError):
@@ -119,12 +123,12 @@ def _stream():
 class Context:
     """Owns an sqsm_ctx (workspaces, plans, graphs) on one device."""
 
-    def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True):
+    def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True, autotune=False):
         if device is None:
             device = torch.cuda.current_device()
         self.device = int(device)
         h = _p()
-        opt = Options(leaf_chunk, radix, 1 if use_graph else 0)
+        opt = Options(leaf_chunk, radix, 1 if use_graph else 0, 1 if autotune else 0)
         rc = lib.sqsm_create(ctypes.byref(h), self.device, ctypes.byref(opt))
         if rc != OK:
             raise SqsmError(rc, "sqsm_create failed")
@@ -163,6 +167,15 @@ class Context:
         v = _int(0)
         self.check(lib.sqsm_get_status(self.h, ctypes.byref(v)))
         return v.value
+
+    def scan_shape(self, offsets, dtype=torch.float32, linearization=0):
+        """(leaf_chunk, radix) that IPLS calls with these sequence offsets use."""
+        off = (_i64 * len(offsets))(*[int(v) for v in offsets])
+        leaf, radix = _int(0), _int(0)
+        self.check(lib.sqsm_scan_shape(self.h, _dtype_code(dtype), int(linearization),
+                                       len(offsets) - 1, off, ctypes.byref(leaf),
+                                       ctypes.byref(radix)))
+        return leaf.value, radix.value
 
 
 def supported_shape(nx, ny):

@@ -1,6 +1,7 @@
 // C ABI of include/sqsm.h: argument validation, plans (per batch layout),
 // workspaces (per plan, dtype and nx) and captured graphs, all owned by the
 // context.  Host code only builds index tables and enqueues kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -77,9 +78,21 @@ struct GraphEntry {
 
 }  // namespace
 
+// Workload shape an autotuned scan shape is stored for.
+struct TuneKey {
+  int dtype, lin;
+  int64_t batch;
+  int lg_total, lg_max;   // floor(log2) of the total and of the longest length
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dtype, lin, batch, lg_total, lg_max) <
+           std::tie(o.dtype, o.lin, o.batch, o.lg_total, o.lg_max);
+  }
+};
+
 struct sqsm_ctx {
   int device = 0;
   int sm_count = 152;
+  std::map<TuneKey, std::pair<int, int>> tuned;   // autotuned (leaf_chunk, radix)
   sqsm_options opt{};
   std::string err;
   int* d_status = nullptr;
@@ -207,24 +220,50 @@ bool build_levels(Plan& p, const std::vector<int64_t>& counts0, LevelSet& L) {
   return true;
 }
 
-Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
-  // default leaf: 3 steps per thread while the leaf chunks fit one wave of
-  // the leaf kernels (256 threads per SM at their register use), so that the
-  // latency-bound leaf chains are short; 4 above that, fewer upper items.
+// Scan shape from the options, else the default: leaf 3 steps per thread
+// while the leaf chunks fit one wave of the leaf kernels (256 threads per SM
+// at their register use), so that the latency-bound leaf chains are short, 4
+// above that (fewer upper items); radix 0: a level with many items is folded
+// 4 items per thread (enough threads to fill the GPU, least work), a level
+// with few items is scanned in one-warp Kogge-Stone chunks of 32 (shortest
+// chain of dependent combines).  An explicit radix folds that many items per
+// thread at every level.
+void default_shape(const sqsm_ctx* ctx, const int64_t* offsets, int64_t batch, int* L0, int* R) {
   const int64_t steps = offsets[batch] - offsets[0];
-  const int L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk
-                 : steps <= 3 * int64_t(256) * ctx->sm_count ? 3 : 4;
-  // default (radix 0): a level with many items is folded 4 items per thread
-  // (enough threads to fill the GPU, least work); a level with few items is
-  // scanned in one-warp Kogge-Stone chunks of 32 (shortest chain of
-  // dependent combines).  An explicit radix folds that many items per
-  // thread at every level.
-  const bool chunk_scan = ctx->opt.radix <= 1;
-  const int R = chunk_scan ? 0 : ctx->opt.radix;
+  *L0 = ctx->opt.leaf_chunk > 0 ? ctx->opt.leaf_chunk
+        : steps <= 3 * int64_t(256) * ctx->sm_count ? 3 : 4;
+  *R = ctx->opt.radix <= 1 ? 0 : ctx->opt.radix;
+}
+
+Plan* find_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch, int L0, int R) {
   for (auto& p : ctx->plans)
     if (p->B == batch && p->L0 == L0 && p->R == R &&
         std::memcmp(p->offsets.data(), offsets, sizeof(int64_t) * (batch + 1)) == 0)
       return p.get();
+  return nullptr;
+}
+
+// Free a plan, its workspaces and the graphs that replay its buffers.
+void drop_plan(sqsm_ctx* ctx, const Plan* victim) {
+  for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+    if (it->first.plan == victim) {
+      if (ctx->last_prof == it->second.prof.get()) ctx->last_prof = nullptr;
+      cudaGraphExecDestroy(it->second.exec);
+      it = ctx->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  cudaDeviceSynchronize();
+  for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it)
+    if (it->get() == victim) {
+      ctx->plans.erase(it);
+      break;
+    }
+}
+
+Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch, int L0, int R) {
+  if (Plan* q = find_plan(ctx, offsets, batch, L0, R)) return q;
   auto p = std::make_unique<Plan>();
   p->B = (int)batch;
   p->L0 = L0;
@@ -239,23 +278,15 @@ Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
     ns[b] = nf[b] + 1;
   }
   if (!build_levels(*p, nf, p->filt) || !build_levels(*p, ns, p->smth)) return nullptr;
-  if (ctx->plans.size() >= 8) {
-    // graphs replaying the evicted plan's buffers go with it
-    const Plan* victim = ctx->plans.front().get();
-    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
-      if (it->first.plan == victim) {
-        if (ctx->last_prof == it->second.prof.get()) ctx->last_prof = nullptr;
-        cudaGraphExecDestroy(it->second.exec);
-        it = ctx->graphs.erase(it);
-      } else {
-        ++it;
-      }
-    }
-    cudaDeviceSynchronize();
-    ctx->plans.erase(ctx->plans.begin());
-  }
+  if (ctx->plans.size() >= 8) drop_plan(ctx, ctx->plans.front().get());
   ctx->plans.push_back(std::move(p));
   return ctx->plans.back().get();
+}
+
+Plan* get_plan(sqsm_ctx* ctx, const int64_t* offsets, int64_t batch) {
+  int L0, R;
+  default_shape(ctx, offsets, batch, &L0, &R);
+  return get_plan(ctx, offsets, batch, L0, R);
 }
 
 bool alloc_scan(Alloc& mem, const LevelSet& L, ScanBuffers& W, size_t item_bytes,
@@ -497,6 +528,149 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const
   return SQSM_OK;
 }
 
+namespace {
+
+// Arguments of one IPLS enqueue on plan p's workspace w.
+IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* model,
+                        const double* theta, int lin, int M, const void* y, const void* m0,
+                        const void* N0, const void* init_ms, const void* init_Ns, void* ms,
+                        void* Ns, double* loglik) {
+  IplsArgs a{};
+  a.linearization = lin;
+  a.leaf = p->L0;
+  a.M = M;
+  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  a.dt = model->dt;
+  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
+  a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
+  a.ms = ms; a.Ns = Ns; a.loglik = loglik;
+  a.mf = w->mf; a.Nf = w->Nf;
+  a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
+  a.frows = w->frows;
+  a.nrows = w->nrows;
+  a.params = w->params;
+  a.dm0 = w->dm0;
+  return a;
+}
+
+void enqueue_ipls(sqsm_ctx* ctx, int dtype, const Plan* p, const Workspace* w, const IplsArgs& a,
+                  cudaStream_t st) {
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32)
+    ipls_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
+  else
+    ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
+}
+
+int floor_log2(int64_t v) {
+  int l = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++l;
+  }
+  return l;
+}
+
+TuneKey tune_key(int dtype, int lin, int64_t batch, const int64_t* offsets) {
+  int64_t longest = 0;
+  for (int64_t b = 0; b < batch; ++b) longest = std::max(longest, offsets[b + 1] - offsets[b]);
+  return TuneKey{dtype, lin, batch, floor_log2(offsets[batch] - offsets[0]), floor_log2(longest)};
+}
+
+// Candidate scan shapes (leaf_chunk, radix) the autotuner measures.
+constexpr int kTuneShapes[][2] = {{2, 0}, {3, 0}, {4, 0}, {6, 0}, {8, 0}, {4, 4}};
+
+// Scan shape of an IPLS call: the options' or the default, or with
+// autotune the fastest candidate for the workload shape, measured once per
+// context (one IPLS iteration per candidate on the call's inputs, best of two
+// after a warm-up run) and stored.  Plans made only for the measurement are
+// freed as soon as a faster candidate is found.
+int choose_ipls_shape(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                      int lin, int64_t batch, const int64_t* offsets, const void* y,
+                      const void* m0, const void* N0, const void* init_ms, const void* init_Ns,
+                      void* ms, void* Ns, cudaStream_t s, int* L0, int* R) {
+  default_shape(ctx, offsets, batch, L0, R);
+  if (!ctx->opt.autotune || ctx->opt.leaf_chunk > 0 || ctx->opt.radix > 0) return SQSM_OK;
+  const TuneKey key = tune_key(dtype, lin, batch, offsets);
+  auto found = ctx->tuned.find(key);
+  if (found != ctx->tuned.end()) {
+    *L0 = found->second.first;
+    *R = found->second.second;
+    return SQSM_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(ctx, SQSM_ERR_CUDA, "autotune: cudaEventCreate failed");
+  }
+  float best = INFINITY;
+  int bl = *L0, br = *R;
+  bool best_made = false;   // the best plan was made only for the measurement
+  int rc = SQSM_OK;
+  for (const auto& c : kTuneShapes) {
+    const bool existed = find_plan(ctx, offsets, batch, c[0], c[1]) != nullptr;
+    Plan* p = get_plan(ctx, offsets, batch, c[0], c[1]);
+    if (!p) continue;
+    Workspace* w = get_ws(p, dtype, 5);
+    if (!w || !ensure_ipls(w, p, dtype)) {
+      if (!existed) drop_plan(ctx, p);
+      continue;
+    }
+    const IplsArgs a = make_ipls_args(p, w, model, theta, lin, 1, y, m0, N0, init_ms, init_Ns,
+                                      ms, Ns, nullptr);
+    if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
+    float t = INFINITY;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      enqueue_ipls(ctx, dtype, p, w, a, s);
+      cudaEventRecord(e1, s);
+      const cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(ctx, e, "autotune");
+        break;
+      }
+      float ms_ = 0.f;
+      cudaEventElapsedTime(&ms_, e0, e1);
+      if (rep > 0) t = std::min(t, ms_);
+    }
+    if (rc != SQSM_OK) break;
+    if (t < best) {
+      if (best_made) drop_plan(ctx, find_plan(ctx, offsets, batch, bl, br));
+      best = t;
+      bl = c[0];
+      br = c[1];
+      best_made = !existed;
+    } else if (!existed) {
+      drop_plan(ctx, p);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SQSM_OK) return rc;
+  ctx->tuned[key] = {bl, br};
+  *L0 = bl;
+  *R = br;
+  return SQSM_OK;
+}
+
+}  // namespace
+
+extern "C" int sqsm_scan_shape(sqsm_ctx* ctx, int dtype, int linearization, int64_t batch,
+                               const int64_t* offsets, int* leaf_chunk, int* radix) {
+  if (!ctx || !leaf_chunk || !radix) return SQSM_ERR_INVALID_ARG;
+  if (batch < 1 || batch > (1 << 30) || !valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  default_shape(ctx, offsets, batch, leaf_chunk, radix);
+  if (ctx->opt.autotune && ctx->opt.leaf_chunk <= 0 && ctx->opt.radix <= 0) {
+    auto it = ctx->tuned.find(tune_key(dtype, linearization, batch, offsets));
+    if (it != ctx->tuned.end()) {
+      *leaf_chunk = it->second.first;
+      *radix = it->second.second;
+    }
+  }
+  return SQSM_OK;
+}
+
 int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
                      int linearization, int M, int64_t batch, const int64_t* offsets,
                      const void* y, const void* m0, const void* N0, const void* init_ms,
@@ -521,36 +695,21 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
-  Plan* p = get_plan(ctx, offsets, batch);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  int L0 = 0, R = 0;
+  const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
+                                    m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
+  if (trc != SQSM_OK) return trc;
+  Plan* p = get_plan(ctx, offsets, batch, L0, R);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a{};
-  a.linearization = linearization;
-  a.leaf = p->L0;
-  a.M = M;
-  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
-  a.dt = model->dt;
-  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
-  a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
-  a.ms = ms; a.Ns = Ns; a.loglik = loglik;
-  a.mf = w->mf; a.Nf = w->Nf;
-  a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
-  a.frows = w->frows;
-  a.nrows = w->nrows;
-  a.params = w->params;
-  a.dm0 = w->dm0;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaGetLastError();
-  const DevSeqs sq = seqs_of(p);
+  IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+                              ms, Ns, loglik);
   // theta -> model constants, outside any graph so that theta is not baked in
   if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
-  auto enqueue = [&](cudaStream_t st) {
-    if (dtype == SQSM_F32)
-      ipls_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
-    else
-      ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
-  };
+  auto enqueue = [&](cudaStream_t st) { enqueue_ipls(ctx, dtype, p, w, a, st); };
   if (!ctx->opt.use_graph) {
     if (ctx->prof_on) {
       ctx->call_prof.clear();
@@ -630,33 +789,24 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
-  Plan* p = get_plan(ctx, offsets, batch);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  int L0 = 0, R = 0;
+  const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
+                                    m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
+  if (trc != SQSM_OK) return trc;
+  Plan* p = get_plan(ctx, offsets, batch, L0, R);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a{};
-  a.linearization = linearization;
-  a.leaf = p->L0;
-  a.M = M;
-  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
-  a.dt = model->dt;
-  for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
-  a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
-  a.ms = ms; a.Ns = Ns; a.loglik = nullptr;
-  a.mf = w->mf; a.Nf = w->Nf;
-  a.F = w->gamma;   // PRec records; c, SQ, H, d, SR unused
-  a.frows = w->frows;
-  a.nrows = w->nrows;
-  a.params = w->params;
-  a.dm0 = w->dm0;
+  IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+                              ms, Ns, nullptr);
   AdjArgs adj = w->adj;
   adj.iters = adj_iters;
   adj.nll = nll;
   adj.grad = grad;
   adj.change = adj_change;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaGetLastError();
   const DevSeqs sq = seqs_of(p);
   if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
   auto enqueue = [&](cudaStream_t st) {
