@@ -288,9 +288,15 @@ def gpu_arm(args, rank, world, local):
     t_launch = acc[top][0] / acc[top][1] / 1e3
     peak = 152 * 128 * 2 * 2070e6 / 1e12        # FP32 FMA lanes x 2 x max SM clock
     achieved = f_launch / t_launch / 1e12
+    # DRAM bytes per launch of the filter scan's upper family at this
+    # workload (n = 1e5, FP32, default scan shape), from an ncu capture of the
+    # same kernels (dram__bytes_read.sum + dram__bytes_write.sum, 12.35 MB
+    # per iteration over its three launches); other workloads: not measured
+    traffic = 4.12e6 if (top == "filter_up" and n == N_STEPS) else None
     roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
                 "peak_note": "derived",
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch",
                 "flops_per_launch": f_launch, "peak_basis":
                 "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)"}
     it_flops = CM.ipls_iteration_flops([n])
