@@ -39,17 +39,26 @@ def filter_element(nx, ny):
             + 2 * nx * ny + 2 * ny * nx * nx + nx * ny * ny + 2 * nx * nx * ny + 2 * nx * ny)
 
 
+def xi_blocks(nx):
+    """M = U_i^T Z_j (U_i lower), Xi_11 = Tria([M, I]) and the gain
+    G = Z_j M^T Xi_11^{-T} Xi_11^{-1} (product, two triangular solves)."""
+    tri = nx * nx * (nx + 1)            # a triangular solve / product, 2 flops per FMA
+    return tri + tria(nx, 2 * nx) + 2 * nx ** 3 + 2 * tri
+
+
 def filter_combine(nx):
-    return (nx * nx * (nx + 1) + tria(2 * nx, 2 * nx) + nx ** 3 + nx * nx * (nx + 1)
-            + 4 * nx ** 3 + 6 * nx * nx + 2 * nx
-            + 2 * nx ** 3 + nx ** 3 + tria(nx, 2 * nx)
-            + 10 * nx * nx + 3 * nx
-            + nx * nx * (nx + 1) + tria(nx, 2 * nx))
+    tri = nx * nx * (nx + 1)
+    ab = tri + 4 * nx ** 3 + 2 * (nx * (nx + 1) + nx * nx) + 2 * nx       # I - U G^T, A, b
+    eta = 2 * (3 * nx * nx + nx * (nx + 1)) + 3 * nx
+    u = 2 * nx ** 3 + tri + tria(nx, 2 * nx)                              # A_j U_i Xi_11^{-T}
+    z = tria(nx, 2 * nx) + tri + 2 * nx ** 3 + tria(nx, 2 * nx)            # L, W, A_i^T W
+    return xi_blocks(nx) + ab + eta + u + z
 
 
 def filter_apply(nx):
-    return (nx * nx * (nx + 1) + tria(2 * nx, 2 * nx, nx) + nx ** 3 + 10 * nx * nx + 2 * nx
-            + 2 * nx ** 3 + nx ** 3 + tria(nx, 2 * nx))
+    tri = nx * nx * (nx + 1)
+    b = 2 * (nx * (nx + 1) + 2 * nx * nx) + 3 * nx
+    return xi_blocks(nx) + b + 2 * nx ** 3 + tri + tria(nx, 2 * nx)
 
 
 def smoother_element(nx):

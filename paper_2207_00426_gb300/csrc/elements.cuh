@@ -425,25 +425,51 @@ SQSM_DEV void filter_element(const Gamma<T, NX, NY>& g, const T* y, bool first, 
   zero_pad<T, R::Z + NX * NX, R::size>(e);
 }
 
-// Xi of eq. sqrt-filter-com-2 from U_i and Z_j: the 2NX x 2NX matrix
-// [[U_i^T Z_j, I], [Z_j, 0]] triangularised (NREF reflections).
-template <typename T, int NX, int NREF>
-SQSM_DEV void make_xi(const T* Ui, const T* Zj, T* X) {
-  constexpr int C2 = 2 * NX;
+// The blocks of Xi (eq. sqrt-filter-com-2), Xi = Tria([[M, I], [Z_j, 0]])
+// with M = U_i^T Z_j, from two NX x 2NX Trias instead of one 2NX x 2NX one.
+// Multiplying out Xi Xi^T = [[I + M M^T, M Z_j^T], [Z_j M^T, Z_j Z_j^T]]:
+//   Xi_11 = Tria([M, I]),
+//   Xi_21 = Z_j M^T Xi_11^{-T},
+//   Xi_22 Xi_22^T = Z_j Z_j^T - Xi_21 Xi_21^T = Z_j (I + M^T M)^{-1} Z_j^T
+//                 = W W^T  with  W = Z_j L^{-T},  L = Tria([M^T, I]),
+// (the push-through identity); Xi_22 enters the operator only through
+// Tria([A_i^T Xi_22, Z_i]), which W gives the same product.  Xi_11 and L
+// are >= I, so the triangular solves are well conditioned.
+template <typename T, int NX>
+SQSM_DEV void xi_m(const T* Ui, const T* Zj, T* Mx) {
 #pragma unroll
-  for (int i = 0; i < NX; ++i) {
+  for (int i = 0; i < NX; ++i)
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       T s = T(0);
 #pragma unroll
-      for (int k = i; k < NX; ++k) s += Ui[k * NX + i] * Zj[k * NX + j];   // U_i^T Z_j
-      X[i * C2 + j] = s;
-      X[i * C2 + NX + j] = i == j ? T(1) : T(0);
-      X[(NX + i) * C2 + j] = Zj[i * NX + j];
-      X[(NX + i) * C2 + NX + j] = T(0);
+      for (int k = i; k < NX; ++k) s += Ui[k * NX + i] * Zj[k * NX + j];   // U_i lower
+      Mx[i * NX + j] = s;
     }
-  }
-  tria<T, C2, C2, NREF>(X);
+}
+
+// Tria([A, I]) for A (NX x NX), or Tria([A^T, I]) with TRANS.
+template <typename T, int NX, bool TRANS>
+SQSM_DEV void tria_with_identity(const T* A, T* L) {
+  constexpr int C2 = 2 * NX;
+  T B[NX * C2];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      B[i * C2 + j] = TRANS ? A[j * NX + i] : A[i * NX + j];
+      B[i * C2 + NX + j] = i == j ? T(1) : T(0);
+    }
+  tria<T, NX, C2>(B);
+  take_lower<T, NX, C2>(B, L);
+}
+
+// G = Xi_21 Xi_11^{-1} = Z_j M^T Xi_11^{-T} Xi_11^{-1}.
+template <typename T, int NX>
+SQSM_DEV void xi_gain(const T* Zj, const T* Mx, const T* X11, T* G) {
+  mmt<T, NX, NX, NX>(Zj, Mx, G);
+  rsolve_t<T, NX, NX>(G, X11);
+  rsolve<T, NX, NX>(G, X11);
 }
 
 // Filter operator of Lemma 2 / Table 3 (right column) on full elements:
@@ -454,39 +480,34 @@ SQSM_DEV void make_xi(const T* Ui, const T* Zj, T* X) {
 //   b_ij = A_j (I - U_i G^T)(b_i + U_i U_i^T eta_j) + b_j,
 //   U_ij = Tria([A_j U_i Xi_11^{-T}, U_j]),
 //   eta_ij = A_i^T (I - G U_i^T)(eta_j - Z_j Z_j^T b_i) + eta_i,
-//   Z_ij = Tria([A_i^T Xi_22, Z_i]).
-// PARTS selects the fields computed (bit 0: A, b; bit 1: U; bit 2: eta, Z),
-// so that three threads can each take one part of a combine; Xi_22 (the
-// last NX reflections) is formed only for eta, Z.
+//   Z_ij = Tria([A_i^T Xi_22, Z_i])  (with Xi_22 -> W, see above).
+// PARTS selects the fields computed (bit 0: A, b, eta; bit 1: U; bit 2: Z),
+// so that three threads can each take one part of a combine, each forming
+// only the factors its part needs.
 template <typename T, int NX, int PARTS = 7>
 SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
   using R = FRec<NX>;
   constexpr int C2 = 2 * NX;
-  constexpr bool AB = PARTS & 1, UU = PARTS & 2, EZ = PARTS & 4;
-  T X[C2 * C2];
-  make_xi<T, NX, EZ ? C2 : NX>(ei + R::U, ej + R::Z, X);
-  T X11[NX * NX];
-  take_lower<T, NX, C2>(X, X11);
+  constexpr bool ABE = PARTS & 1, UU = PARTS & 2, ZZ = PARTS & 4;
   const T* Ui = ei + R::U;
-  T G[NX * NX];
-  if constexpr (AB || EZ) {
-#pragma unroll
-    for (int i = 0; i < NX; ++i)
-#pragma unroll
-      for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
-    rsolve<T, NX, NX>(G, X11);
-  }
-  if constexpr (AB) {
+  const T* Zj = ej + R::Z;
+  T Mx[NX * NX];
+  xi_m<T, NX>(Ui, Zj, Mx);
+  T X11[NX * NX];
+  if constexpr (ABE || UU) tria_with_identity<T, NX, false>(Mx, X11);
+  if constexpr (ABE) {
+    T G[NX * NX];
+    xi_gain<T, NX>(Zj, Mx, X11, G);
     // Minv = I - U_i G^T
     T Mi[NX * NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i)
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
-        T s = i == j ? T(1) : T(0);
+        T a = i == j ? T(1) : T(0);
 #pragma unroll
-        for (int k = 0; k <= i; ++k) s -= Ui[i * NX + k] * G[j * NX + k];
-        Mi[i * NX + j] = s;
+        for (int k = 0; k <= i; ++k) a -= Ui[i * NX + k] * G[j * NX + k];
+        Mi[i * NX + j] = a;
       }
     T AjM[NX * NX];
     mm<T, NX, NX, NX>(ej + R::A, Mi, AjM);
@@ -500,6 +521,19 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     mv<T, NX, NX>(AjM, u, t);
 #pragma unroll
     for (int i = 0; i < NX; ++i) out[R::b + i] = t[i] + ej[R::b + i];
+    // eta_ij
+    T sv[NX], r[NX];
+    mtv<T, NX, NX>(Zj, ei + R::b, sv);
+    mv<T, NX, NX>(Zj, sv, r);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[i] = ej[R::eta + i] - r[i];
+    mtv<T, NX, NX>(Ui, r, t);
+    mv<T, NX, NX>(G, t, sv);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) r[i] -= sv[i];
+    mtv<T, NX, NX>(ei + R::A, r, t);
+#pragma unroll
+    for (int i = 0; i < NX; ++i) out[R::eta + i] = t[i] + ei[R::eta + i];
   }
   if constexpr (UU) {
     // U_ij = Tria([A_j U_i Xi11^{-T}, U_j])
@@ -517,22 +551,13 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     tria<T, NX, C2>(B);
     take_lower<T, NX, C2>(B, out + R::U);
   }
-  if constexpr (EZ) {
-    // eta_ij
-    const T* Zj = ej + R::Z;
-    T s[NX], r[NX], t[NX];
-    mtv<T, NX, NX>(Zj, ei + R::b, s);
-    mv<T, NX, NX>(Zj, s, r);
+  if constexpr (ZZ) {
+    // Z_ij = Tria([A_i^T W, Z_i]),  W = Z_j L^{-T},  L = Tria([M^T, I])
+    T L[NX * NX], W[NX * NX];
+    tria_with_identity<T, NX, true>(Mx, L);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) r[i] = ej[R::eta + i] - r[i];
-    mtv<T, NX, NX>(Ui, r, t);
-    mv<T, NX, NX>(G, t, s);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) r[i] -= s[i];
-    mtv<T, NX, NX>(ei + R::A, r, t);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) out[R::eta + i] = t[i] + ei[R::eta + i];
-    // Z_ij = Tria([A_i^T Xi22, Z_i])
+    for (int i = 0; i < NX * NX; ++i) W[i] = Zj[i];
+    rsolve_t<T, NX, NX>(W, L);
     T B[NX * C2];
 #pragma unroll
     for (int i = 0; i < NX; ++i)
@@ -540,7 +565,7 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
       for (int j = 0; j < NX; ++j) {
         T a = T(0);
 #pragma unroll
-        for (int k = j; k < NX; ++k) a += ei[R::A + k * NX + i] * X[(NX + k) * C2 + NX + j];
+        for (int k = 0; k < NX; ++k) a += ei[R::A + k * NX + i] * W[k * NX + j];
         B[i * C2 + j] = a;
         B[i * C2 + NX + j] = ei[R::Z + i * NX + j];
       }
@@ -551,21 +576,16 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
 }
 
 // Table 3 with a left operand that is a filtering distribution (A_i = 0):
-// only b_ij and U_ij are needed, so Xi_22 (the last NX reflections) and
-// eta_ij, Z_ij are skipped.  (bi, Ui) -> (bo, Uo).
+// only b_ij and U_ij are needed (Xi_11 and G), so Xi_22, eta_ij and Z_ij are
+// skipped.  (bi, Ui) -> (bo, Uo).
 template <typename T, int NX>
 SQSM_DEV void filter_apply(const T* bi, const T* Ui, const T* ej, T* bo, T* Uo) {
   using R = FRec<NX>;
   constexpr int C2 = 2 * NX;
-  T X[C2 * C2];
-  make_xi<T, NX, NX>(Ui, ej + R::Z, X);
-  T G[NX * NX], X11[NX * NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i)
-#pragma unroll
-    for (int j = 0; j < NX; ++j) G[i * NX + j] = X[(NX + i) * C2 + j];
-  take_lower<T, NX, C2>(X, X11);
-  rsolve<T, NX, NX>(G, X11);
+  T Mx[NX * NX], X11[NX * NX], G[NX * NX];
+  xi_m<T, NX>(Ui, ej + R::Z, Mx);
+  tria_with_identity<T, NX, false>(Mx, X11);
+  xi_gain<T, NX>(ej + R::Z, Mx, X11, G);
   T t[NX], u[NX], w[NX];
   mtv<T, NX, NX>(Ui, ej + R::eta, t);
   mv<T, NX, NX>(Ui, t, u);

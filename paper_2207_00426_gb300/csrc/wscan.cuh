@@ -376,8 +376,8 @@ inline unsigned cs_down_grid(int64_t chunks) {
 // Filter scans with three threads per combine.  In the latency-bound top
 // levels (few chunks, one warp per SM or less) a combine's chain of dependent
 // instructions sets the time per Kogge-Stone round.  Thread (role r, item t)
-// computes only part r of S[t - d] (x) S[t] (r = 0: A, b; 1: U; 2: eta, Z;
-// each forms the Xi factor it needs itself), which shortens that chain; role
+// computes only part r of S[t - d] (x) S[t] (r = 0: A, b, eta; 1: U; 2: Z;
+// each forms the factors it needs itself), which shortens that chain; role
 // r runs in warps of its own, so no warp diverges.
 template <typename T, int NX, int CAP>
 SQSM_DEV void filter_ks3(T* S, int c) {
@@ -400,13 +400,15 @@ SQSM_DEV void filter_ks3(T* S, int c) {
       T* o = S + t * REC;
       if (role == 0) {
 #pragma unroll
-        for (int i = R::A; i < R::U; ++i) o[i] = part[i];
+        for (int i = R::A; i < R::U; ++i) o[i] = part[i];      // A, b
+#pragma unroll
+        for (int i = R::eta; i < R::Z; ++i) o[i] = part[i];    // eta
       } else if (role == 1) {
 #pragma unroll
         for (int i = R::U; i < R::eta; ++i) o[i] = part[i];
       } else {
 #pragma unroll
-        for (int i = R::eta; i < R::Z + NX * NX; ++i) o[i] = part[i];
+        for (int i = R::Z; i < R::Z + NX * NX; ++i) o[i] = part[i];
       }
     }
     __syncthreads();
