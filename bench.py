@@ -403,6 +403,36 @@ def gpu_arm(args, rank, world, local):
                / tb / 1e12}
     del yb, msb, Nsb
 
+    # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
+    #      for cubature and extended SLR in FP32 and cubature in FP64, and
+    #      the whole-step fraction of the FP32 peak (cubature FP32)
+    sweep = {}
+    for lg in range(10, 21, 2):
+        ns = 1 << lg
+        ds = W.ct_sequence(n=ns, seed=2 + lg)
+        row = {}
+        for name, dtp, lin in (("f32_cubature", torch.float32, B.CUBATURE),
+                               ("f32_extended", torch.float32, B.EXTENDED),
+                               ("f64_cubature", torch.float64, B.CUBATURE)):
+            ys = torch.tensor(ds["y"], dtype=dtp, device=dev)
+            m0s = torch.tensor(ds["m0"][None], dtype=dtp, device=dev)
+            N0s = torch.tensor(ds["N0"][None], dtype=dtp, device=dev)
+            mss = torch.empty((ns + 1, 5), dtype=dtp, device=dev)
+            Nss = torch.empty((ns + 1, 5, 5), dtype=dtp, device=dev)
+            lls = torch.empty(1, dtype=torch.float64, device=dev)
+
+            def sstep():
+                B.sqsm_ipls_smooth(ctx, ds["theta"], ys, [0, ns], m0s, N0s, M, lin, dt=ds["dt"],
+                                   ms=mss, Ns=Nss, loglik=lls)
+            sstep()
+            torch.cuda.synchronize()
+            ts = timed(sstep, 3 if dtp == torch.float32 else 1)
+            row[name] = ns * M / ts
+            if name == "f32_cubature":
+                row["f32_cubature_frac_of_fp32_peak"] = (CM.ipls_iteration_flops([ns]) * M / ts
+                                                         / 1e12 / peak)
+        sweep[str(ns)] = row
+
     # ---- FP64 variant of the same step (comparator), few steps
     f64 = torch.float64
     y64, m064, N064 = y.double(), m0.double(), N0.double()
@@ -441,6 +471,7 @@ def gpu_arm(args, rank, world, local):
                 "clocks": clk.summary(),
                 "roofline": roofline, "whole_step": whole, "kernels": kernels,
                 "nll_grad": grads, "batched": batched,
+                "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
                 "loglik": ll.item()}

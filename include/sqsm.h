@@ -185,6 +185,25 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                      const void* init_Ns, void* ms, void* Ns, double* loglik,
                      void* stream);
 
+/* sqsm_ipls_smooth run until convergence (Alg. 3 "until convergence"):
+ * iterations continue while the largest change of any smoothing mean
+ * component between consecutive iterations, max_k |m^(i)_k - m^(i-1)_k|,
+ * is >= tol, at most max_iters times (>= 1; the change after iteration 1 is
+ * measured from the initial trajectory).  iters_done: device int, the
+ * number of iterations run.  ms, Ns, loglik: as sqsm_ipls_smooth after the
+ * last iteration.  With use_graph the whole loop is one CUDA graph whose
+ * iterations are the body of a conditional WHILE node, so the host never
+ * waits; without it the host reads a continue flag after every iteration
+ * (one stream synchronisation per iteration).  The change is compared in
+ * FP32.  Errors as sqsm_ipls_smooth; SQSM_ERR_INVALID_ARG also for tol < 0
+ * or a null iters_done. */
+int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
+                         const double* theta, int linearization, int max_iters,
+                         double tol, int64_t batch, const int64_t* offsets,
+                         const void* y, const void* m0, const void* N0,
+                         const void* init_ms, const void* init_Ns, void* ms,
+                         void* Ns, double* loglik, int* iters_done, void* stream);
+
 /* Negative pseudo log-likelihood and its gradient with respect to theta
  * through the fixed point of Alg. 3 (Sec. 5.2: eq. implicity_function_theorem
  * and Alg. 4, in reverse / vector-Jacobian form), summed over the batch.

@@ -60,6 +60,11 @@ lib.sqsm_lgssm_smooth.restype = _int
 lib.sqsm_ipls_smooth.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
                                  _int, _int, _i64, ctypes.POINTER(_i64)] + [_p] * 8 + [_p]
 lib.sqsm_ipls_smooth.restype = _int
+lib.sqsm_ipls_smooth_tol.argtypes = ([_p, _int, ctypes.POINTER(Model),
+                                      ctypes.POINTER(ctypes.c_double), _int, _int,
+                                      ctypes.c_double, _i64, ctypes.POINTER(_i64)]
+                                     + [_p] * 9 + [_p])
+lib.sqsm_ipls_smooth_tol.restype = _int
 lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
                                   _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
 lib.sqsm_ct_linearize.restype = _int
@@ -85,7 +90,7 @@ EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
             "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad",
-            "sqsm_scan_shape"]
+            "sqsm_scan_shape", "sqsm_ipls_smooth_tol"]
 
 
 class SqsmError(RuntimeError):
@@ -257,6 +262,36 @@ def sqsm_ipls_smooth(ctx, theta, y, offsets, m0, N0, M, linearization=CUBATURE, 
                               _stream())
     ctx.check(rc)
     return ms, Ns, loglik
+
+
+def sqsm_ipls_smooth_tol(ctx, theta, y, offsets, m0, N0, max_iters, tol, linearization=CUBATURE,
+                         dt=0.01, sensors=None, init_ms=None, init_Ns=None):
+    """Call sqsm_ipls_smooth_tol (iterate until the largest change of a
+    smoothing mean is below tol, at most max_iters times).  Returns (ms, Ns,
+    loglik, iters_done) as device tensors (iters_done int32 [1])."""
+    import numpy as np
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    if sensors is None:
+        sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    off, batch = _offsets(offsets)
+    rows = int(off[batch]) + batch
+    dev = y.device
+    ms = torch.empty((rows, 5), dtype=dtp, device=dev)
+    Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
+    loglik = torch.empty(batch, dtype=torch.float64, device=dev)
+    iters = torch.zeros(1, dtype=torch.int32, device=dev)
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = _model(dt, np.asarray(sensors))
+    rc = lib.sqsm_ipls_smooth_tol(ctx.h, code, ctypes.byref(mdl), th, int(linearization),
+                                  int(max_iters), float(tol), batch, off, _ptr(y, dtp, "y"),
+                                  _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"),
+                                  _ptr(init_ms, dtp, "init_ms"), _ptr(init_Ns, dtp, "init_Ns"),
+                                  _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"),
+                                  _ptr(loglik, torch.float64, "loglik"),
+                                  _ptr(iters, torch.int32, "iters_done"), _stream())
+    ctx.check(rc)
+    return ms, Ns, loglik, iters
 
 
 def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt=0.01,

@@ -41,6 +41,8 @@ struct Workspace {
   void* gamma = nullptr;     // IPLS linearised model, PRec<5, 2> records per step
   void* frows = nullptr;     // IPLS filter output, packed rows
   void* nrows = nullptr;     // IPLS nominal trajectory, packed rows
+  int* tol_words = nullptr;  // tolerance mode: [0] iterations run, [1] continue flag,
+                             // [2] largest change of the nominal means (float bits)
   void* params = nullptr;    // IPLS model constants
   void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
   bool ipls_ready = false;
@@ -64,10 +66,12 @@ struct GraphKey {
   const Plan* plan;
   int dtype, lin, M, prof, adj;     // adj: adjoint iterations + 1 (0 = smoother only)
   const void *y, *m0, *N0, *ims, *iNs, *ms, *Ns, *ll;
+  double tol = -1.0;                // tolerance mode (M = iteration cap), else -1
+  const void* iters = nullptr;
   bool operator<(const GraphKey& o) const {
-    return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll) <
+    return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll, tol, iters) <
            std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.adj, o.y, o.m0, o.N0, o.ims, o.iNs,
-                    o.ms, o.Ns, o.ll);
+                    o.ms, o.Ns, o.ll, o.tol, o.iters);
   }
 };
 
@@ -97,6 +101,7 @@ struct sqsm_ctx {
   std::string err;
   int* d_status = nullptr;
   cudaStream_t capture_stream = nullptr;   // graphs are recorded here
+  cudaStream_t body_stream = nullptr;      // bodies of conditional graph nodes
   std::vector<std::unique_ptr<Plan>> plans;
   std::map<GraphKey, GraphEntry> graphs;
   bool prof_on = false;
@@ -338,7 +343,8 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
   if (!w->gamma || !w->frows || !w->nrows) return false;
   w->params = w->mem.get(512);
   w->dm0 = w->mem.get(es * nx * p->B);
-  if (!w->params || !w->dm0) return false;
+  w->tol_words = (int*)w->mem.get(4 * sizeof(int));
+  if (!w->params || !w->dm0 || !w->tol_words) return false;
   w->ipls_ready = true;
   return true;
 }
@@ -404,7 +410,9 @@ int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
   }
   cudaMemset(ctx->d_status, 0, sizeof(int));
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
-  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_status);
     delete ctx;
     return SQSM_ERR_CUDA;
@@ -423,6 +431,7 @@ int sqsm_destroy(sqsm_ctx* ctx) {
     ctx->plans.clear();
     cudaFree(ctx->d_status);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   }
   delete ctx;
   return SQSM_OK;
@@ -759,6 +768,150 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth launch");
+  return SQSM_OK;
+}
+
+int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                         int linearization, int max_iters, double tol, int64_t batch,
+                         const int64_t* offsets, const void* y, const void* m0, const void* N0,
+                         const void* init_ms, const void* init_Ns, void* ms, void* Ns,
+                         double* loglik, int* iters_done, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
+  if (max_iters < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "max_iters must be >= 1");
+  if (!(tol >= 0.0) || !std::isfinite(tol))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !m0 || !N0 || !ms || !Ns || !iters_done)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
+  if ((init_ms == nullptr) != (init_Ns == nullptr))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  int L0 = 0, R = 0;
+  const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
+                                    m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
+  if (trc != SQSM_OK) return trc;
+  Plan* p = get_plan(ctx, offsets, batch, L0, R);
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, 5);
+  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  const IplsArgs a = make_ipls_args(p, w, model, theta, linearization, max_iters, y, m0, N0,
+                                    init_ms, init_Ns, ms, Ns, loglik);
+  int* iters = w->tol_words;
+  int* go = w->tol_words + 1;
+  unsigned* dmax = (unsigned*)(w->tol_words + 2);
+  const DevSeqs sq = seqs_of(p);
+  auto phase = [&](int ph, cudaStream_t st) {
+    if (dtype == SQSM_F32)
+      ipls_phase_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, ph,
+                     ph == IPLS_ITER ? dmax : nullptr);
+    else
+      ipls_phase_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, ph,
+                     ph == IPLS_ITER ? dmax : nullptr);
+  };
+  if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
+  if (!ctx->opt.use_graph) {
+    // host-driven loop: one device-to-host read of the continue flag per iteration
+    phase(IPLS_PRE, s);
+    cudaMemsetAsync(w->tol_words, 0, 4 * sizeof(int), s);
+    for (int it = 0; it < max_iters; ++it) {
+      phase(IPLS_ITER, s);
+      enqueue_tol_check(dmax, iters, max_iters, (float)tol, 0, 0, go, s);
+      int more = 0;
+      cudaMemcpyAsync(&more, go, sizeof(int), cudaMemcpyDeviceToHost, s);
+      const cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth_tol");
+      if (!more) break;
+    }
+    phase(IPLS_POST, s);
+    cudaMemcpyAsync(iters_done, iters, sizeof(int), cudaMemcpyDeviceToDevice, s);
+  } else {
+    // one graph: the initial trajectory, a conditional WHILE node whose body is
+    // one iteration followed by the check that sets the loop's condition, then
+    // the result and the log-likelihood
+    GraphKey key{p, dtype, linearization, max_iters, 0, 0, y, m0, N0, init_ms, init_Ns,
+                 ms, Ns, loglik};
+    key.tol = tol;
+    key.iters = iters_done;
+    auto it = ctx->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != ctx->graphs.end()) {
+      exec = it->second.exec;
+    } else {
+      cudaStream_t cs = ctx->capture_stream;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+      phase(IPLS_PRE, cs);
+      cudaMemsetAsync(w->tol_words, 0, 4 * sizeof(int), cs);
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t graph = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+      cudaGraphConditionalHandle handle = 0;
+      if (e == cudaSuccess)
+        e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode = nullptr;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp);
+      if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies);
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(ctx->body_stream, cp.conditional.phGraph_out[0], nullptr,
+                                          nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaGraph_t dead = nullptr;
+        cudaStreamEndCapture(cs, &dead);
+        if (dead) cudaGraphDestroy(dead);
+        return cuda_fail(ctx, e, "conditional graph node");
+      }
+      phase(IPLS_ITER, ctx->body_stream);
+      enqueue_tol_check(dmax, iters, max_iters, (float)tol, handle, 1, nullptr, ctx->body_stream);
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(ctx->body_stream, &body);
+      if (e != cudaSuccess) {
+        cudaGraph_t dead = nullptr;
+        cudaStreamEndCapture(cs, &dead);
+        if (dead) cudaGraphDestroy(dead);
+        return cuda_fail(ctx, e, "conditional body capture");
+      }
+      phase(IPLS_POST, cs);
+      cudaMemcpyAsync(iters_done, iters, sizeof(int), cudaMemcpyDeviceToDevice, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      if (ctx->graphs.size() >= 16) {
+        if (ctx->last_prof == ctx->graphs.begin()->second.prof.get()) ctx->last_prof = nullptr;
+        cudaGraphExecDestroy(ctx->graphs.begin()->second.exec);
+        ctx->graphs.erase(ctx->graphs.begin());
+      }
+      ctx->graphs[key].exec = exec;
+    }
+    const cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth_tol launch");
   return SQSM_OK;
 }
 

@@ -48,6 +48,22 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
 void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                       const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                       int* status, cudaStream_t s);
+// Phases of Alg. 3 for the tolerance mode (see ipls_phase).
+enum { IPLS_PRE = 0, IPLS_ITER = 1, IPLS_POST = 2 };
+void ipls_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                    const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                    int* status, cudaStream_t s, int phase, unsigned* dmax);
+void ipls_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                    const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                    int* status, cudaStream_t s, int phase, unsigned* dmax);
+// After one iteration of the tolerance mode: counts it in *iters, compares
+// the largest change *dmax (float bits) with tol, clears *dmax, and sets
+// whether the loop continues (change >= tol and fewer than max_iters
+// iterations): into the conditional handle when use_handle, into *go when
+// go is set.
+void enqueue_tol_check(unsigned* dmax, int* iters, int max_iters, float tol,
+                       cudaGraphConditionalHandle handle, int use_handle, int* go, cudaStream_t s);
+
 // The parameter kernel (theta -> model constants), launched before each
 // replay so that theta is not baked into a captured graph.
 void ipls_params_f32(const IplsArgs& a, cudaStream_t s);

@@ -152,7 +152,8 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
 
 template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
 void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv, FO fo, SO so,
-                      int* status, cudaStream_t s, Prof* P = nullptr, bool add_nominal = false) {
+                      int* status, cudaStream_t s, Prof* P = nullptr, bool add_nominal = false,
+                      unsigned* dmax = nullptr) {
   const int Lc = (int)L.lv.size();
   constexpr int KS = KsMax<T, SRec<NX>::size>::value;
   const int Lk = L.ks_level(KS);
@@ -198,7 +199,7 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv
   }
   ProfScope ps(P, K_SMOOTHER_LEAF_DOWN, s);
   smoother_leaf_down<T, NX, NY, GV, FO, SO><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-      L.lv[0], sq, gv, fo, (const T*)W.carry[1], W.flag[1], so, status, add_nominal);
+      L.lv[0], sq, gv, fo, (const T*)W.carry[1], W.flag[1], so, status, add_nominal, dmax);
 }
 
 // Record sizes (elements) of the scan buffers.

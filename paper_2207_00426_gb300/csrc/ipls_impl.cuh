@@ -26,15 +26,17 @@ void ct_linearize(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_
       (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
 }
 
+// One phase of Alg. 3 (IPLS_PRE: initial nominal trajectory; IPLS_ITER: one
+// iteration, with dmax set also the largest change of the nominal means;
+// IPLS_POST: the result into the caller's arrays and the log-likelihood).
 template <typename T>
-void ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
-                  const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
-                  int* status, cudaStream_t s) {
+void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, const LevelSet& Ls,
+                const ScanBuffers& Ws, DevSeqs sq, double* partial, int* status, cudaStream_t s,
+                int phase, unsigned* dmax) {
   constexpr int NX = 5, NY = 2;
   const int64_t rows = Ls.n_items[0];
   const RowsPacked<T, NX> nom{(T*)a.nrows}, fr{(T*)a.frows};
-  const RowsSplit<T, NX> user{(T*)a.ms, (T*)a.Ns};
-  {
+  if (phase == IPLS_PRE) {
     ProfScope ps(a.prof, K_INIT, s);
     if (a.init_ms) {
       const RowsSplit<T, NX> init{(T*)a.init_ms, (T*)a.init_Ns};
@@ -43,6 +45,16 @@ void ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
       broadcast_prior_kernel<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
           Ls.lv[0], (const T*)a.m0, (const T*)a.N0, nom);
     }
+    return;
+  }
+  if (phase == IPLS_POST) {
+    {
+      ProfScope ps(a.prof, K_INIT, s);
+      const RowsSplit<T, NX> user{(T*)a.ms, (T*)a.Ns};
+      rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, user);
+    }
+    if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s, a.prof);
+    return;
   }
   // the linearised model of every step, packed (a.F holds the PRec records)
   const GammaPacked<T> gv{(T*)a.F};
@@ -50,27 +62,31 @@ void ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
   // dx_k = x_k - m_k about its own nominal trajectory m (the previous
   // smoothing means): the SLR writes c~, d~ of that form, the prior becomes
   // m0 - m_0, and the smoother adds m back when it writes the new nominal.
-  for (int it = 0; it < a.M; ++it) {
-    {
-      ProfScope ps(a.prof, K_SLR, s);
-      ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-          Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, nom,
-          (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
-    }
-    {
-      ProfScope ps(a.prof, K_INIT, s);
-      center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
-                                                                     (T*)a.dm0);
-    }
-    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
-                              partial, status, s, a.prof);
-    enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true);
+  {
+    ProfScope ps(a.prof, K_SLR, s);
+    ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, nom,
+        (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
   }
   {
     ProfScope ps(a.prof, K_INIT, s);
-    rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, user);
+    center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
+                                                                   (T*)a.dm0);
   }
-  if (a.loglik) enqueue_loglik_reduce(sq, partial, a.loglik, status, s, a.prof);
+  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
+                            partial, status, s, a.prof);
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, dmax);
+}
+
+// M iterations of Alg. 3.
+template <typename T>
+void ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                  const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                  int* status, cudaStream_t s) {
+  ipls_phase<T>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, IPLS_PRE, nullptr);
+  for (int it = 0; it < a.M; ++it)
+    ipls_phase<T>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, IPLS_ITER, nullptr);
+  ipls_phase<T>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, IPLS_POST, nullptr);
 }
 
 }  // namespace sqsm

@@ -30,4 +30,24 @@ void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, in
   loglik_reduce<<<sq.B, 256, 0, s>>>(sq, partial, loglik, status);
 }
 
+namespace {
+
+__global__ void ipls_tol_check(unsigned* dmax, int* iters, int max_iters, float tol,
+                               cudaGraphConditionalHandle handle, int use_handle, int* go) {
+  const float d = __uint_as_float(*dmax);
+  const int it = *iters + 1;
+  *iters = it;
+  *dmax = 0u;
+  const unsigned more = (!(d < tol) && it < max_iters) ? 1u : 0u;
+  if (use_handle) cudaGraphSetConditional(handle, more);
+  if (go) *go = (int)more;
+}
+
+}  // namespace
+
+void enqueue_tol_check(unsigned* dmax, int* iters, int max_iters, float tol,
+                       cudaGraphConditionalHandle handle, int use_handle, int* go, cudaStream_t s) {
+  ipls_tol_check<<<1, 1, 0, s>>>(dmax, iters, max_iters, tol, handle, use_handle, go);
+}
+
 }  // namespace sqsm

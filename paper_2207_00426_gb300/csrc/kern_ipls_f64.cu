@@ -9,6 +9,12 @@ void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStr
   ct_linearize<double>(a, Lf, sq, s);
 }
 
+void ipls_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                    const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                    int* status, cudaStream_t s, int phase, unsigned* dmax) {
+  ipls_phase<double>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax);
+}
+
 void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                       const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                       int* status, cudaStream_t s) {

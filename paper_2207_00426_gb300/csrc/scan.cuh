@@ -283,11 +283,13 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
 // (m^s, N^s just after the chunk), writing m^s, N^s to `out_rows`.  With
 // add_nominal the scan runs on deviations from a nominal trajectory held in
 // `out_rows` itself, and the written mean is nominal + deviation (each row is
-// read, then written, by the same thread).
+// read, then written, by the same thread); with dmax set, the largest
+// |deviation| over all rows is max-reduced into *dmax (float bits).
 template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
 __global__ void __launch_bounds__(kBlock)
 smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ carry,
-                   const int* __restrict__ flag, SO out_rows, int* status, bool add_nominal) {
+                   const int* __restrict__ flag, SO out_rows, int* status, bool add_nominal,
+                   unsigned* dmax) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
@@ -297,6 +299,7 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
   const int cnt = lv.count[c];
   const int64_t r0 = sq.offsets[b] + b;
   const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
+  float change = 0.f;
   T gm[NX], Dm[NX * NX];
   if (flag[c]) {
     load<T, NX>(carry + c * CREC, gm);
@@ -329,8 +332,20 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
     }
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);
+    if (dmax) {
+#pragma unroll
+      for (int i = 0; i < NX; ++i) change = fmaxf(change, fabsf((float)gm[i]));
+    }
   }
   if (!ok) flag_status(status, 8);
+  if (dmax) {
+    // max over the grid of |deviation| = |new - previous nominal mean|, as
+    // the bits of a non-negative float (ordered like the values)
+    unsigned bits = __float_as_uint(ok ? change : INFINITY);
+    const unsigned mask = __activemask();
+    bits = __reduce_max_sync(mask, bits);
+    if ((int)(threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(dmax, bits);
+  }
 }
 
 // Per-sequence FP64 sum of the leaf partial log-likelihoods in a fixed
