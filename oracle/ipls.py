@@ -13,8 +13,8 @@ Readings:
 """
 import numpy as np
 
-from .kalman import sqrt_filter, sqrt_smoother
-from .slr import linearize
+from .kalman import cov_filter, cov_smoother, sqrt_filter, sqrt_smoother
+from .slr import linearize, linearize_std
 
 
 def ipls(model, y, m0, N0, M, method="cubature", init=None, tol=None):
@@ -62,3 +62,29 @@ def nll_grad_fd(model_cls, theta, y, m0, N0, method="cubature", h=1e-4,
         fm = nll(model_cls, theta - e, y, m0, N0, method, M, tol, init, **model_kw)
         g[j] = (fp - fm) / (2.0 * h)
     return g
+
+
+def ipls_std(model, y, m0, P0, M, init=None, tol=None):
+    """Alg. 3 in the standard (covariance) form: M times {covariance-form
+    cubature linearisation; covariance Kalman filter; covariance RTS
+    smoother}.  Same readings and stopping rule as ipls.  Returns ms, Ps,
+    loglik, iterations."""
+    n = y.shape[0]
+    if init is None:
+        ms = np.tile(m0, (n + 1, 1))
+        Ps = np.tile(P0, (n + 1, 1, 1))
+    else:
+        ms, Ps = (np.array(a, dtype=np.float64) for a in init)
+    loglik = np.nan
+    it = 0
+    for it in range(1, M + 1):
+        F, c, Q, H, d, R = linearize_std(model, ms, Ps, y)
+        mf, Pf, _, ell = cov_filter(F, c, Q, H, d, R, y, m0, P0)
+        ms_new, Ps_new = cov_smoother(F, c, Q, mf, Pf)
+        loglik = float(np.sum(ell))
+        delta = np.max(np.abs(ms_new - ms))
+        ms, Ps = ms_new, Ps_new
+        if tol is not None and delta < tol:
+            break
+    return ms, Ps, loglik, it
+

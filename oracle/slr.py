@@ -108,3 +108,53 @@ def linearize(model, ms, Ns, y, method):
         else:
             raise ValueError(method)
     return F, c, SQ, H, d, SR
+
+
+# --------------------------------------------------------------------------
+# Standard (covariance) form of the same regressions, for the standard
+# parallel filter and smoother (left columns of Tables 1-5): Sec. 4.1's
+# statistical linear regression written with covariances,
+#   F = Psi^T P^{-1},  c = z_bar - F m,  Lambda = Phi - F P F^T + Q,
+# Psi = sum_i w (X_i - m)(Z_i - z_bar)^T, Phi = sum_i w (Z_i - z_bar)(...)^T.
+# --------------------------------------------------------------------------
+def _gslr_cov(m, P, Zs, w, Q):
+    N = np.linalg.cholesky(P)
+    X, _ = cubature_points(m, N)
+    zbar = np.sum(w[:, None] * Zs, axis=0)
+    Psi = sum(w[i] * np.outer(X[i] - m, Zs[i] - zbar) for i in range(len(w)))
+    Phi = sum(w[i] * np.outer(Zs[i] - zbar, Zs[i] - zbar) for i in range(len(w)))
+    G = np.linalg.solve(P, Psi).T
+    return G, zbar - G @ m, Phi - G @ P @ G.T + Q
+
+
+def transition_cubature_std(model, m, P):
+    """(F, c, Lambda) from (m^s_{k-1}, P^s_{k-1}), covariance form."""
+    X, w = cubature_points(m, np.linalg.cholesky(P))
+    Zs = np.array([model.f(x) for x in X])
+    SQ = model.SQ()
+    return _gslr_cov(m, P, Zs, w, SQ @ SQ.T)
+
+
+def observation_cubature_std(model, m, P, y):
+    """(H, d, Omega) from (m^s_k, P^s_k), covariance form, bearings on the
+    branch nearest h(m) as in observation_cubature."""
+    X, w = cubature_points(m, np.linalg.cholesky(P))
+    ref = model.h(m)
+    Zs = np.array([model.branch(model.h(x), ref) for x in X])
+    SR = model.SR()
+    H, d, R = _gslr_cov(m, P, Zs, w, SR @ SR.T)
+    return H, d + (y - model.branch(y, ref)), R
+
+
+def linearize_std(model, ms, Ps, y):
+    """The covariance-form linearisation of every step (cubature):
+    transition t from (ms[t], Ps[t]), observation from (ms[t+1], Ps[t+1])."""
+    n = y.shape[0]
+    nx, ny = model.nx, model.ny
+    F = np.zeros((n, nx, nx)); c = np.zeros((n, nx)); Q = np.zeros((n, nx, nx))
+    H = np.zeros((n, ny, nx)); d = np.zeros((n, ny)); R = np.zeros((n, ny, ny))
+    for t in range(n):
+        F[t], c[t], Q[t] = transition_cubature_std(model, ms[t], Ps[t])
+        H[t], d[t], R[t] = observation_cubature_std(model, ms[t + 1], Ps[t + 1], y[t])
+    return F, c, Q, H, d, R
+
