@@ -185,6 +185,23 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                      const void* init_Ns, void* ms, void* Ns, double* loglik,
                      void* stream);
 
+/* Alg. 3 in the standard (covariance) form: the left columns of Tables
+ * 1-5 for the parallel filter and smoother and the covariance form of the
+ * cubature SLR (Sec. 4.1), otherwise as sqsm_ipls_smooth (same batch layout,
+ * deviation coordinates, prior broadcast as the initial trajectory).  It is
+ * the comparator of the square-root form's numerical stability (Sec. 6): in
+ * FP32 its covariances can lose positive definiteness, which shows as NaN in
+ * ms / loglik and SQSM_ERR_NONFINITE in the status word.
+ *   P0  [batch][nx][nx]: prior covariances (full, symmetric).
+ *   Ps  output covariances P^s_k (full, symmetric), state layout.
+ * Cubature only (SQSM_ERR_UNSUPPORTED otherwise); scan levels fold 4 items
+ * per thread; no graph capture. */
+int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
+                         const double* theta, int linearization, int M,
+                         int64_t batch, const int64_t* offsets, const void* y,
+                         const void* m0, const void* P0, void* ms, void* Ps,
+                         double* loglik, void* stream);
+
 /* sqsm_ipls_smooth run until convergence (Alg. 3 "until convergence"):
  * iterations continue while the largest change of any smoothing mean
  * component between consecutive iterations, max_k |m^(i)_k - m^(i-1)_k|,

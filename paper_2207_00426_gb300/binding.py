@@ -65,6 +65,10 @@ lib.sqsm_ipls_smooth_tol.argtypes = ([_p, _int, ctypes.POINTER(Model),
                                       ctypes.c_double, _i64, ctypes.POINTER(_i64)]
                                      + [_p] * 9 + [_p])
 lib.sqsm_ipls_smooth_tol.restype = _int
+lib.sqsm_ipls_smooth_std.argtypes = ([_p, _int, ctypes.POINTER(Model),
+                                      ctypes.POINTER(ctypes.c_double), _int, _int, _i64,
+                                      ctypes.POINTER(_i64)] + [_p] * 6 + [_p])
+lib.sqsm_ipls_smooth_std.restype = _int
 lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
                                   _int, _i64, ctypes.POINTER(_i64)] + [_p] * 9 + [_p]
 lib.sqsm_ct_linearize.restype = _int
@@ -90,7 +94,7 @@ EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
             "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad",
-            "sqsm_scan_shape", "sqsm_ipls_smooth_tol"]
+            "sqsm_scan_shape", "sqsm_ipls_smooth_tol", "sqsm_ipls_smooth_std"]
 
 
 class SqsmError(RuntimeError):
@@ -292,6 +296,30 @@ def sqsm_ipls_smooth_tol(ctx, theta, y, offsets, m0, N0, max_iters, tol, lineari
                                   _ptr(iters, torch.int32, "iters_done"), _stream())
     ctx.check(rc)
     return ms, Ns, loglik, iters
+
+
+def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, dt=0.01, sensors=None):
+    """Call sqsm_ipls_smooth_std (standard covariance form, cubature).
+    P0 [batch, 5, 5] prior covariances.  Returns (ms, Ps, loglik)."""
+    import numpy as np
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    if sensors is None:
+        sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    off, batch = _offsets(offsets)
+    rows = int(off[batch]) + batch
+    dev = y.device
+    ms = torch.empty((rows, 5), dtype=dtp, device=dev)
+    Ps = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
+    loglik = torch.empty(batch, dtype=torch.float64, device=dev)
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = _model(dt, np.asarray(sensors))
+    rc = lib.sqsm_ipls_smooth_std(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), batch,
+                                  off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
+                                  _ptr(P0, dtp, "P0"), _ptr(ms, dtp, "ms"), _ptr(Ps, dtp, "Ps"),
+                                  _ptr(loglik, torch.float64, "loglik"), _stream())
+    ctx.check(rc)
+    return ms, Ps, loglik
 
 
 def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt=0.01,

@@ -915,6 +915,52 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   return SQSM_OK;
 }
 
+int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                         int linearization, int M, int64_t batch, const int64_t* offsets,
+                         const void* y, const void* m0, const void* P0, void* ms, void* Ps,
+                         double* loglik, void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization != SQSM_CUBATURE)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the standard form is implemented for cubature SLR");
+  if (M < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "M must be >= 1");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !m0 || !P0 || !ms || !Ps)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGetLastError();
+  int L0 = 0, R = 0;
+  default_shape(ctx, offsets, batch, &L0, &R);
+  Plan* p = get_plan(ctx, offsets, batch, L0, 4);   // fold-only levels
+  if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
+  Workspace* w = get_ws(p, dtype, 5);
+  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  // a.N0 carries the prior covariances, a.Ns the covariance output
+  const IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, P0, nullptr,
+                                    nullptr, ms, Ps, loglik);
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32) {
+    ipls_params_f32(a, s);
+    std_ipls_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, s);
+  } else {
+    ipls_params_f64(a, s);
+    std_ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, s);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_smooth_std launch");
+  return SQSM_OK;
+}
+
 int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
                        int linearization, int M, int adj_iters, int64_t batch,
                        const int64_t* offsets, const void* y, const void* m0, const void* N0,

@@ -48,6 +48,15 @@ void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
 void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                       const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                       int* status, cudaStream_t s);
+// Alg. 3 in the standard (covariance) form on a fold-only plan (radix 4);
+// a.N0 holds prior covariances P0, a.Ns receives full covariances.
+void std_ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                          const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                          int* status, cudaStream_t s);
+void std_ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                          const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                          int* status, cudaStream_t s);
+
 // Phases of Alg. 3 for the tolerance mode (see ipls_phase).
 enum { IPLS_PRE = 0, IPLS_ITER = 1, IPLS_POST = 2 };
 void ipls_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
