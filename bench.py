@@ -433,6 +433,54 @@ def gpu_arm(args, rank, world, local):
                                                          / 1e12 / peak)
         sweep[str(ns)] = row
 
+    # ---- FP32 stability of the square-root form against the standard
+    #      (covariance) form, as in the paper's robustness experiment: 15
+    #      sequences per length, M = 20, cubature and extended SLR, share of
+    #      sequences whose log-likelihood is not finite; both in the printed
+    #      absolute coordinates and in the deviation coordinates used here,
+    #      with the means' error against the FP64 square-root run (finite runs)
+    cabs = B.Context(local, use_graph=True, absolute=True)
+    stability = {}
+    noise_sets = {"q_c=0.01,q_w=0.1": W.CT_THETA_TRUE,
+                  "q_c=0.1,q_w=0.1": (W.CT_THETA_TRUE[0], float(np.log(0.1)), float(np.log(0.1)))}
+    for ns, (noise, theta_s) in [(ns, kv) for kv in noise_sets.items()
+                                 for ns in (100, 500, 1000, 2000, 4000, 8000)]:
+        dsb = W.ct_batch(lengths=[ns] * 15, seed=1000 + ns, theta=theta_s)
+        offs = [int(v) for v in dsb["offsets"]]
+        P0s = dsb["N0"] @ np.swapaxes(dsb["N0"], 1, 2)
+        t64 = {k: torch.tensor(dsb[k], dtype=torch.float64, device=dev) for k in ("y", "m0", "N0")}
+        t32 = {k: torch.tensor(dsb[k], dtype=f32, device=dev) for k in ("y", "m0", "N0")}
+        P032 = torch.tensor(P0s, dtype=f32, device=dev)
+        res = {}
+        for lin_name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED)):
+            ms64, _, _ = B.sqsm_ipls_smooth(ctx, dsb["theta"], t64["y"], offs, t64["m0"],
+                                            t64["N0"], 20, lin, dt=dsb["dt"])
+            for coords, c in (("absolute", cabs), ("deviation", ctx)):
+                for form in ("sqrt", "standard"):
+                    if form == "sqrt":
+                        msf, _, llf = B.sqsm_ipls_smooth(c, dsb["theta"], t32["y"], offs,
+                                                         t32["m0"], t32["N0"], 20, lin,
+                                                         dt=dsb["dt"])
+                    else:
+                        msf, _, llf = B.sqsm_ipls_smooth_std(c, dsb["theta"], t32["y"], offs,
+                                                             t32["m0"], P032, 20, lin,
+                                                             dt=dsb["dt"])
+                    torch.cuda.synchronize()
+                    c.status()   # clears the non-finite flag a diverged run raises
+                    llf = llf.cpu().numpy()
+                    fin = np.isfinite(llf)
+                    errs = []
+                    for b in np.nonzero(fin)[0]:
+                        rows = slice(offs[b] + b, offs[b + 1] + b + 1)
+                        ref = ms64[rows].cpu().numpy()
+                        errs.append(float(np.abs(msf[rows].double().cpu().numpy() - ref).max()
+                                          / np.abs(ref).max()))
+                    res[f"{form}_{lin_name}_{coords}"] = {
+                        "divergence_rate": float(1.0 - fin.mean()),
+                        "median_mean_rel_err_vs_f64": float(np.median(errs)) if errs else None}
+        stability.setdefault(noise, {})[str(ns)] = res
+    cabs.close()
+
     # ---- FP64 variant of the same step (comparator), few steps
     f64 = torch.float64
     y64, m064, N064 = y.double(), m0.double(), N0.double()
@@ -472,6 +520,7 @@ def gpu_arm(args, rank, world, local):
                 "roofline": roofline, "whole_step": whole, "kernels": kernels,
                 "nll_grad": grads, "batched": batched,
                 "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
+                "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
                 "loglik": ll.item()}

@@ -100,6 +100,10 @@ typedef struct {
   int radix;            /* items folded by one thread at upper levels   */
   int use_graph;        /* 1: replay the IPLS iterations as a CUDA graph */
   int autotune;         /* 1: measure and keep the fastest scan shape   */
+  int absolute;         /* 1: IPLS smooths each linearisation in the
+                           printed absolute coordinates (c = z_bar - F m)
+                           instead of deviations from the nominal
+                           trajectory (default 0)                        */
 } sqsm_options;
 
 typedef struct sqsm_ctx sqsm_ctx;
@@ -194,8 +198,9 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
  * ms / loglik and SQSM_ERR_NONFINITE in the status word.
  *   P0  [batch][nx][nx]: prior covariances (full, symmetric).
  *   Ps  output covariances P^s_k (full, symmetric), state layout.
- * Cubature only (SQSM_ERR_UNSUPPORTED otherwise); scan levels fold 4 items
- * per thread; no graph capture. */
+ * Cubature or extended SLR; the context's `absolute` option selects the
+ * printed absolute coordinates; scan levels fold 4 items per thread; no
+ * graph capture. */
 int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                          const double* theta, int linearization, int M,
                          int64_t batch, const int64_t* offsets, const void* y,

@@ -37,7 +37,8 @@ _int = ctypes.c_int
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int), ("autotune", _int)]
+    _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int), ("autotune", _int),
+                ("absolute", _int)]
 
 
 class Model(ctypes.Structure):
@@ -132,12 +133,14 @@ def _stream():
 class Context:
     """Owns an sqsm_ctx (workspaces, plans, graphs) on one device."""
 
-    def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True, autotune=False):
+    def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True, autotune=False,
+                 absolute=False):
         if device is None:
             device = torch.cuda.current_device()
         self.device = int(device)
         h = _p()
-        opt = Options(leaf_chunk, radix, 1 if use_graph else 0, 1 if autotune else 0)
+        opt = Options(leaf_chunk, radix, 1 if use_graph else 0, 1 if autotune else 0,
+                      1 if absolute else 0)
         rc = lib.sqsm_create(ctypes.byref(h), self.device, ctypes.byref(opt))
         if rc != OK:
             raise SqsmError(rc, "sqsm_create failed")
@@ -298,9 +301,10 @@ def sqsm_ipls_smooth_tol(ctx, theta, y, offsets, m0, N0, max_iters, tol, lineari
     return ms, Ns, loglik, iters
 
 
-def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, dt=0.01, sensors=None):
-    """Call sqsm_ipls_smooth_std (standard covariance form, cubature).
-    P0 [batch, 5, 5] prior covariances.  Returns (ms, Ps, loglik)."""
+def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, linearization=CUBATURE, dt=0.01,
+                         sensors=None):
+    """Call sqsm_ipls_smooth_std (standard covariance form).  P0 [batch, 5, 5]
+    prior covariances.  Returns (ms, Ps, loglik)."""
     import numpy as np
     dtp = y.dtype
     code = _dtype_code(dtp)
@@ -314,7 +318,8 @@ def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, dt=0.01, sensors=Non
     loglik = torch.empty(batch, dtype=torch.float64, device=dev)
     th = (ctypes.c_double * 3)(*[float(v) for v in theta])
     mdl = _model(dt, np.asarray(sensors))
-    rc = lib.sqsm_ipls_smooth_std(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), batch,
+    rc = lib.sqsm_ipls_smooth_std(ctx.h, code, ctypes.byref(mdl), th, int(linearization), int(M),
+                                  batch,
                                   off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
                                   _ptr(P0, dtp, "P0"), _ptr(ms, dtp, "ms"), _ptr(Ps, dtp, "Ps"),
                                   _ptr(loglik, torch.float64, "loglik"), _stream())

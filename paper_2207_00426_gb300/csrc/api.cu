@@ -562,6 +562,16 @@ IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* mod
   return a;
 }
 
+IplsArgs ctx_ipls_args(const sqsm_ctx* ctx, const Plan* p, const Workspace* w,
+                        const sqsm_model* model, const double* theta, int lin, int M,
+                        const void* y, const void* m0, const void* N0, const void* init_ms,
+                        const void* init_Ns, void* ms, void* Ns, double* loglik) {
+  IplsArgs a = make_ipls_args(p, w, model, theta, lin, M, y, m0, N0, init_ms, init_Ns, ms, Ns,
+                              loglik);
+  a.centered = ctx->opt.absolute ? 0 : 1;
+  return a;
+}
+
 void enqueue_ipls(sqsm_ctx* ctx, int dtype, const Plan* p, const Workspace* w, const IplsArgs& a,
                   cudaStream_t st) {
   const DevSeqs sq = seqs_of(p);
@@ -625,7 +635,7 @@ int choose_ipls_shape(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
       if (!existed) drop_plan(ctx, p);
       continue;
     }
-    const IplsArgs a = make_ipls_args(p, w, model, theta, lin, 1, y, m0, N0, init_ms, init_Ns,
+    const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, lin, 1, y, m0, N0, init_ms, init_Ns,
                                       ms, Ns, nullptr);
     if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
     float t = INFINITY;
@@ -714,7 +724,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
                               ms, Ns, loglik);
   // theta -> model constants, outside any graph so that theta is not baked in
   if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
@@ -808,7 +818,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  const IplsArgs a = make_ipls_args(p, w, model, theta, linearization, max_iters, y, m0, N0,
+  const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, max_iters, y, m0, N0,
                                     init_ms, init_Ns, ms, Ns, loglik);
   int* iters = w->tol_words;
   int* go = w->tol_words + 1;
@@ -926,8 +936,8 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization != SQSM_CUBATURE)
-    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the standard form is implemented for cubature SLR");
+  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
   if (M < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "M must be >= 1");
   if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
   if (!valid_offsets(offsets, batch))
@@ -946,7 +956,7 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   // a.N0 carries the prior covariances, a.Ns the covariance output
-  const IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, P0, nullptr,
+  const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, P0, nullptr,
                                     nullptr, ms, Ps, loglik);
   const DevSeqs sq = seqs_of(p);
   if (dtype == SQSM_F32) {
@@ -999,7 +1009,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a = make_ipls_args(p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
                               ms, Ns, nullptr);
   AdjArgs adj = w->adj;
   adj.iters = adj_iters;

@@ -39,6 +39,7 @@ struct IplsArgs {
   void *mf, *Nf, *F, *c, *SQ, *H, *d, *SR, *params, *dm0;
   void *frows, *nrows;   // packed filter output and nominal trajectory (RowsPacked)
   Prof* prof;   // optional per-kernel events
+  int centered = 1;   // 1: deviation coordinates, 0: printed absolute coordinates
 };
 
 // Everything of Alg. 3 after the parameter kernel; capturable.

@@ -62,20 +62,22 @@ void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, co
   // dx_k = x_k - m_k about its own nominal trajectory m (the previous
   // smoothing means): the SLR writes c~, d~ of that form, the prior becomes
   // m0 - m_0, and the smoother adds m back when it writes the new nominal.
+  // (With a.centered = 0 the printed absolute form is smoothed instead.)
   {
     ProfScope ps(a.prof, K_SLR, s);
     ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 1, nom,
+        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, a.centered, nom,
         (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
   }
-  {
+  if (a.centered) {
     ProfScope ps(a.prof, K_INIT, s);
     center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
                                                                    (T*)a.dm0);
   }
-  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
-                            partial, status, s, a.prof);
-  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, dmax);
+  enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y,
+                            (const T*)(a.centered ? a.dm0 : a.m0), (const T*)a.N0, fr, partial,
+                            status, s, a.prof);
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax);
 }
 
 // M iterations of Alg. 3.

@@ -284,7 +284,8 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
 // add_nominal the scan runs on deviations from a nominal trajectory held in
 // `out_rows` itself, and the written mean is nominal + deviation (each row is
 // read, then written, by the same thread); with dmax set, the largest
-// |deviation| over all rows is max-reduced into *dmax (float bits).
+// change of a mean from the one held in `out_rows` (the deviation, with
+// add_nominal) is max-reduced over all rows into *dmax (float bits).
 template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
 __global__ void __launch_bounds__(kBlock)
 smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ carry,
@@ -327,15 +328,21 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
 #pragma unroll
       for (int i = 0; i < NX; ++i) out[i] += gm[i];
       out_rows.store(e, out, Dm);
+      if (dmax) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) change = fmaxf(change, fabsf((float)gm[i]));
+      }
     } else {
+      if (dmax) {   // the change from the previous mean held in out_rows
+        T old[NX];
+        out_rows.load_mean(e, old);
+#pragma unroll
+        for (int i = 0; i < NX; ++i) change = fmaxf(change, fabsf((float)(gm[i] - old[i])));
+      }
       out_rows.store(e, gm, Dm);
     }
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);
-    if (dmax) {
-#pragma unroll
-      for (int i = 0; i < NX; ++i) change = fmaxf(change, fabsf((float)gm[i]));
-    }
   }
   if (!ok) flag_status(status, 8);
   if (dmax) {

@@ -544,11 +544,13 @@ SQSM_DEV void cubature_regress_std(const T* m, const T* N, const T* P, const T* 
 }
 
 // One thread per step: the covariance-form linearisation of step s about
-// the nominal rows (m, P) (deviation form, as ct_slr_kernel centred).
+// the nominal rows (m, P), cubature (linearization 0: Sec. 4.1 with sigma
+// points) or Taylor (1: Jacobians, Lambda = Q, Omega = R); centered as in
+// ct_slr_kernel (1: deviation form, 0: the printed absolute form).
 template <typename T, typename NO>
 __global__ void __launch_bounds__(kBlock)
 std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, NO nom,
-               const T* __restrict__ y, T* __restrict__ gam) {
+               int linearization, int centered, const T* __restrict__ y, T* __restrict__ gam) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ch = tid / leaf;
   if (ch >= lv.n_chunks) return;
@@ -566,16 +568,34 @@ std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
 #pragma unroll
     for (int i = 0; i < NX * NX; ++i) N[i] = Pc[i];
     chol_inplace<T, NX>(N);
-    nom.load_mean(rk, mk);
-    ct_f_minus_x(P, m, fm);
+    if (centered) {
+      nom.load_mean(rk, mk);
+      ct_f_minus_x(P, m, fm);
 #pragma unroll
-    for (int r = 0; r < NX; ++r) fm[r] += m[r] - mk[r];
+      for (int r = 0; r < NX; ++r) fm[r] += m[r] - mk[r];
+    } else {
+      ct_f(P, m, fm);
+    }
     T Qc[NX * NX];
     mmt<T, NX, NX, NX>(P.SQ, P.SQ, Qc);   // Q = S_Q S_Q^T
-    const Turn<T> tm = turn(m[4], P.dt);
-    cubature_regress_std<T, NX, true>(
-        m, N, Pc, fm, Qc, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
-        out.F, out.c, out.SQ);
+    if (linearization == 0) {
+      const Turn<T> tm = turn(m[4], P.dt);
+      cubature_regress_std<T, NX, true>(
+          m, N, Pc, fm, Qc, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
+          out.F, out.c, out.SQ);
+    } else {
+      ct_jac_f(P, m, out.F);
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) out.SQ[i] = Qc[i];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) out.c[r] = fm[r];
+    }
+    if (!centered) {   // c = z_bar - F m
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) out.c[r] -= out.F[r * NX + k] * m[k];
+    }
     out.store_transition(GammaPacked<T>{gam}, s);
   }
   {
@@ -588,9 +608,23 @@ std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
     const T Rc[NY * NY] = {P.sigma * P.sigma, T(0), T(0), P.sigma * P.sigma};
-    cubature_regress_std<T, NY, false>(
-        m, N, Pc, hm, Rc, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
-        out.H, out.d, out.SR);
+    if (linearization == 0) {
+      cubature_regress_std<T, NY, false>(
+          m, N, Pc, hm, Rc, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
+          out.H, out.d, out.SR);
+    } else {
+      ct_jac_h(P, m, out.H);
+#pragma unroll
+      for (int i = 0; i < NY * NY; ++i) out.SR[i] = Rc[i];
+#pragma unroll
+      for (int r = 0; r < NY; ++r) out.d[r] = hm[r];
+    }
+    if (!centered) {   // d = z_bar - H m
+#pragma unroll
+      for (int r = 0; r < NY; ++r)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) out.d[r] -= out.H[r * NX + k] * m[k];
+    }
 #pragma unroll
     for (int r = 0; r < NY; ++r) out.d[r] += branch_shift(ys[r], hm[r]);
     out.store_observation(GammaPacked<T>{gam}, s);
@@ -805,12 +839,12 @@ std_smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict_
 }
 
 // Leaf down-sweep: covariance RTS steps from the chunk's carry; writes the
-// new nominal (previous nominal + deviation) into `nom`.
+// new nominal into `nom` (previous nominal + deviation with add_nominal).
 template <typename T, int NX, int NY>
 __global__ void __launch_bounds__(kBlock)
 std_smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaPacked<T> gv, RowsSym<T, NX> fo,
                        const T* __restrict__ carry, const int* __restrict__ flag,
-                       RowsSym<T, NX> nom, int* status) {
+                       RowsSym<T, NX> nom, int* status, bool add_nominal) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
@@ -841,9 +875,13 @@ std_smoother_leaf_down(DevLevel lv, DevSeqs sq, GammaPacked<T> gv, RowsSym<T, NX
       std_smoother_apply<T, NX>(el, g, L);
     }
     T out[NX];
-    nom.load_mean(e, out);
+    if (add_nominal) {
+      nom.load_mean(e, out);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) out[i] += g[i];
+      for (int i = 0; i < NX; ++i) out[i] += g[i];
+    } else {
+      copy<T, NX>(g, out);
+    }
     nom.store(e, out, L);
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(g[i]);
@@ -879,14 +917,17 @@ void std_ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
       Ls.lv[0], (const T*)a.m0, P0, nom);
   for (int it = 0; it < a.M; ++it) {
     std_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, nom, (const T*)a.y, (T*)a.F);
-    center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
-                                                                   (T*)a.dm0);
+        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, nom, a.linearization, a.centered,
+        (const T*)a.y, (T*)a.F);
+    if (a.centered)
+      center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
+                                                                     (T*)a.dm0);
+    const T* prior = (const T*)(a.centered ? a.dm0 : a.m0);
     // filter
     const int Lc = (int)Lf.lv.size();
     if (Lc > 1) {
       std_filter_leaf_up<T, NX, NY><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-          Lf.lv[0], sq, gv, (const T*)a.y, (const T*)a.dm0, P0, (T*)Wf.items[1]);
+          Lf.lv[0], sq, gv, (const T*)a.y, prior, P0, (T*)Wf.items[1]);
       for (int l = 1; l < Lc; ++l)
         std_filter_up<T, NX><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
             Lf.lv[l], (const T*)Wf.items[l], (T*)Wf.items[l + 1]);
@@ -897,8 +938,8 @@ void std_ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
           Lf.lv[l], (const T*)Wf.items[l], (const T*)Wf.carry[l + 1], Wf.flag[l + 1],
           (T*)Wf.carry[l], Wf.flag[l]);
     std_filter_leaf_down<T, NX, NY><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-        Lf.lv[0], sq, gv, (const T*)a.y, (const T*)a.dm0, P0, (const T*)Wf.carry[1], Wf.flag[1],
-        fr, partial, status);
+        Lf.lv[0], sq, gv, (const T*)a.y, prior, P0, (const T*)Wf.carry[1], Wf.flag[1], fr, partial,
+        status);
     // smoother
     const int Sc = (int)Ls.lv.size();
     if (Sc > 1) {
@@ -914,7 +955,7 @@ void std_ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
           Ls.lv[l], (const T*)Ws.items[l], (const T*)Ws.carry[l + 1], Ws.flag[l + 1],
           (T*)Ws.carry[l], Ws.flag[l]);
     std_smoother_leaf_down<T, NX, NY><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
-        Ls.lv[0], sq, gv, fr, (const T*)Ws.carry[1], Ws.flag[1], nom, status);
+        Ls.lv[0], sq, gv, fr, (const T*)Ws.carry[1], Ws.flag[1], nom, status, a.centered != 0);
   }
   const RowsSplitSym<T, NX> user{(T*)a.ms, (T*)a.Ns};
   rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, user);

@@ -87,17 +87,38 @@ def test_std_f32_short_sequence_matches_f64(B, ctx):
     assert abs(l32[0] - l64[0]) <= 1e-4 * abs(l64[0])
 
 
-def test_std_rejects_extended(B, ctx):
-    import ctypes
-    d = W.ct_batch(lengths=[10], seed=1)
-    f32 = torch.float32
-    y, m0, P0 = _dev(d["y"], f32), _dev(d["m0"], f32), _dev(_P0(d), f32)
-    ms = torch.empty((11, 5), device="cuda:0")
-    Ps = torch.empty((11, 5, 5), device="cuda:0")
-    mdl = B._model(d["dt"], np.array([[-1.5, 0.5], [1.0, 1.0]]))
-    off = (ctypes.c_int64 * 2)(0, 10)
-    th = (ctypes.c_double * 3)(*[float(v) for v in d["theta"]])
-    rc = B.lib.sqsm_ipls_smooth_std(ctx.h, B.F32, ctypes.byref(mdl), th, B.EXTENDED, 2, 1, off,
-                                    y.data_ptr(), m0.data_ptr(), P0.data_ptr(), ms.data_ptr(),
-                                    Ps.data_ptr(), None, None)
-    assert rc == B.ERR_UNSUPPORTED
+@pytest.mark.parametrize("method", ["cubature", "extended"])
+def test_absolute_coordinates(B, method):
+    """The printed absolute form (context option) is the same smoother:
+    FP64 square-root and standard forms against the oracle (which smooths in
+    absolute coordinates), and the square-root form against its deviation
+    form."""
+    lin = {"cubature": 0, "extended": 1}[method]
+    d = W.ct_batch(lengths=[50, 23], seed=64)
+    f64 = torch.float64
+    y, m0 = _dev(d["y"], f64), _dev(d["m0"], f64)
+    M = 5
+    cabs = B.Context(0, absolute=True)
+    cdev = B.Context(0)
+    ms_a, Ns_a, ll_a = B.sqsm_ipls_smooth(cabs, d["theta"], y, d["offsets"], m0,
+                                          _dev(d["N0"], f64), M, lin, dt=d["dt"])
+    ms_d, _, ll_d = B.sqsm_ipls_smooth(cdev, d["theta"], y, d["offsets"], m0, _dev(d["N0"], f64),
+                                       M, lin, dt=d["dt"])
+    ms_s, Ps_s, ll_s = B.sqsm_ipls_smooth_std(cabs, d["theta"], y, d["offsets"], m0,
+                                              _dev(_P0(d), f64), M, lin, dt=d["dt"])
+    torch.cuda.synchronize()
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    off = d["offsets"]
+    for b in range(2):
+        yb = d["y"][off[b]:off[b + 1]]
+        rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, method)
+        rows = slice(off[b] + b, off[b + 1] + b + 1)
+        for ms in (ms_a, ms_d, ms_s):
+            assert rel_mean_err(ms[rows].cpu().numpy(), rms) < 1e-9
+        assert _rel_cov(Ps_s[rows].cpu().numpy(), rNs @ np.swapaxes(rNs, 1, 2)) < 1e-9
+        for ll in (ll_a, ll_d, ll_s):
+            assert abs(ll[b].item() - rll) <= 1e-9 * abs(rll)
+    cabs.close()
+    cdev.close()
+
+
