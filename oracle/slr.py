@@ -26,13 +26,53 @@ def cubature_points(m, N):
     return np.array(X), w
 
 
-def _gslr_sigma(m, N, Zs, w, S_cond):
+# Further positive-weight sigma-point rules (Sec. 4.3 admits any rule with
+# positive weights; readings: the unscented transform with alpha = 1,
+# beta = 0, kappa = 1, and the three-point Gauss-Hermite rule per dimension).
+UT_KAPPA = 1.0
+
+
+def unscented_points(m, N, kappa=UT_KAPPA):
+    """2 n_x + 1 points m, m +- sqrt(n_x + lambda) N e_i with lambda = kappa
+    (alpha = 1) and weights lambda / (n_x + lambda), 1 / (2 (n_x + lambda));
+    with beta = 0 the mean and covariance weights coincide."""
+    nx = m.shape[0]
+    lam = kappa
+    s = np.sqrt(nx + lam)
+    X = [m] + [m + s * N[:, i] for i in range(nx)] + [m - s * N[:, i] for i in range(nx)]
+    w = np.array([lam / (nx + lam)] + [0.5 / (nx + lam)] * (2 * nx))
+    return np.array(X), w
+
+
+def gauss_hermite_points(m, N):
+    """The tensor product of the three-point Gauss-Hermite rule for N(0, 1)
+    (nodes 0, +-sqrt(3), weights 2/3, 1/6, 1/6): 3^n_x points m + N xi,
+    weight prod_k w(xi_k)."""
+    nx = m.shape[0]
+    nodes = np.array([0.0, np.sqrt(3.0), -np.sqrt(3.0)])
+    w1 = np.array([2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0])
+    X, w = [], []
+    for p in range(3 ** nx):
+        digits = [(p // 3 ** k) % 3 for k in range(nx)]
+        xi = nodes[digits]
+        X.append(m + N @ xi)
+        w.append(np.prod(w1[digits]))
+    return np.array(X), np.array(w)
+
+
+SIGMA_RULES = {"cubature": cubature_points, "unscented": unscented_points,
+               "gauss-hermite": gauss_hermite_points}
+
+
+def _gslr_sigma(m, N, Zs, w, S_cond, X=None):
     """Sec. 4.3: z_bar (eq. z-bar), the regression matrix
     sum_i w_i (Z_i - z_bar)(X_i - m)^T (N N^T)^{-1}, the offset
     z_bar - G m, and the noise factor
     DownDate(Tria(sqrt(w_1) S_1, ..., sqrt(w_s) S_s, Z), G N)
-    (eqs. lambda-prime and sqr-lambda-sigma-point)."""
-    X, _ = cubature_points(m, N)
+    (eqs. lambda-prime and sqr-lambda-sigma-point).  X: the points (default:
+    the cubature rule's)."""
+    if X is None:
+        X, _ = cubature_points(m, N)
     zbar = np.sum(w[:, None] * Zs, axis=0)
     Cross = sum(w[i] * np.outer(Zs[i] - zbar, X[i] - m) for i in range(len(w)))
     # G = Cross (N N^T)^{-1} = ((N N^T)^{-1} Cross^T)^T via two triangular solves
@@ -76,6 +116,23 @@ def observation_cubature(model, m, N, y):
     return H, d, S
 
 
+def transition_sigma(model, m, N, rule):
+    """(F, c, S_Lambda) with the named sigma-point rule."""
+    X, w = SIGMA_RULES[rule](m, N)
+    Zs = np.array([model.f(x) for x in X])
+    return _gslr_sigma(m, N, Zs, w, model.SQ(), X)
+
+
+def observation_sigma(model, m, N, y, rule):
+    """(H, d, S_Omega) with the named sigma-point rule, bearings on the
+    branch nearest h(m) as in observation_cubature."""
+    X, w = SIGMA_RULES[rule](m, N)
+    ref = model.h(m)
+    Zs = np.array([model.branch(model.h(x), ref) for x in X])
+    H, d, S = _gslr_sigma(m, N, Zs, w, model.SR(), X)
+    return H, d + (y - model.branch(y, ref)), S
+
+
 def transition_taylor(model, m):
     """Sec. 4.2: F = grad f(m^s_{k-1}), c = f(m) - F m, S_Lambda = S_Q."""
     F = model.jac_f(m)
@@ -105,6 +162,9 @@ def linearize(model, ms, Ns, y, method):
         elif method == "extended":
             F[t], c[t], SQ[t] = transition_taylor(model, ms[t])
             H[t], d[t], SR[t] = observation_taylor(model, ms[t + 1], y[t])
+        elif method in SIGMA_RULES:
+            F[t], c[t], SQ[t] = transition_sigma(model, ms[t], Ns[t], method)
+            H[t], d[t], SR[t] = observation_sigma(model, ms[t + 1], Ns[t + 1], y[t], method)
         else:
             raise ValueError(method)
     return F, c, SQ, H, d, SR

@@ -160,3 +160,77 @@ def test_bearing_branch_across_the_cut():
         r = y - H @ m - d
         np.testing.assert_allclose(r, models.wrap_angle(y - ct.h(m)), atol=5e-3)
         assert np.all(np.abs(r) < 0.1)
+
+
+# ----- further sigma-point rules (unscented, Gauss-Hermite) ---------------
+from paper_2207_00426_gb300 import workloads as W
+
+
+def _mn(seed):
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal(5) * 0.5
+    N = np.tril(0.2 * rng.standard_normal((5, 5))) + np.diag(rng.uniform(0.2, 0.5, 5))
+    return m, N
+
+
+@pytest.mark.parametrize("rule", ["cubature", "unscented", "gauss-hermite"])
+def test_sigma_rules_match_the_first_two_moments(rule):
+    m, N = _mn(1)
+    X, w = slr.SIGMA_RULES[rule](m, N)
+    assert np.all(w > 0) and abs(w.sum() - 1) < 1e-14
+    np.testing.assert_allclose((w[:, None] * X).sum(0), m, atol=1e-14)
+    C = sum(w[i] * np.outer(X[i] - m, X[i] - m) for i in range(len(w)))
+    np.testing.assert_allclose(C, N @ N.T, atol=1e-14)
+
+
+def test_gauss_hermite_is_exact_to_degree_five():
+    # E over N(m, P) of x_1^4 and x_1^4 x_2 in closed form
+    m, N = _mn(2)
+    P = N @ N.T
+    X, w = slr.gauss_hermite_points(m, N)
+    e4 = 3 * P[0, 0] ** 2 + 6 * P[0, 0] * m[0] ** 2 + m[0] ** 4
+    assert abs((w * X[:, 0] ** 4).sum() - e4) < 1e-13
+    # x1^4 x2: E = m2 E[x1^4] + 4 P12 E[x1^3 centered moments] via Stein's lemma:
+    # E[x1^4 x2] = m2 E[x1^4] + P12 E[4 x1^3] and E[x1^3] = m1^3 + 3 m1 P11
+    e = m[1] * e4 + P[0, 1] * 4 * (m[0] ** 3 + 3 * m[0] * P[0, 0])
+    assert abs((w * X[:, 0] ** 4 * X[:, 1]).sum() - e) < 1e-13
+    # the third-degree rules are not exact for x^4
+    Xc, wc = slr.cubature_points(m, N)
+    assert abs((wc * Xc[:, 0] ** 4).sum() - e4) > 1e-3
+
+
+@pytest.mark.parametrize("rule", ["unscented", "gauss-hermite"])
+def test_sigma_rules_exact_on_linear_functions(rule):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((5, 5))
+    u = rng.standard_normal(5)
+    SQ = np.tril(rng.standard_normal((5, 5))) * 0.1 + np.eye(5) * 0.3
+
+    class Lin:
+        def f(self, x):
+            return A @ x + u
+
+        def SQ(self):
+            return SQ
+
+    m, N = _mn(4)
+    F, c, S = slr.transition_sigma(Lin(), m, N, rule)
+    np.testing.assert_allclose(F, A, atol=1e-12)
+    np.testing.assert_allclose(c, u, atol=1e-12)
+    np.testing.assert_allclose(S @ S.T, SQ @ SQ.T, atol=1e-12)
+
+
+@pytest.mark.parametrize("rule", ["unscented", "gauss-hermite"])
+def test_sigma_rules_ct_downdate_equals_residual_form(rule):
+    d = W.ct_sequence(n=3, seed=5)
+    ct = models.CTBearings(d["theta"], dt=d["dt"])
+    m, N = _mn(6)
+    m = d["x"][1] + 0.05 * m
+    F, c, S = slr.transition_sigma(ct, m, N, rule)
+    X, w = slr.SIGMA_RULES[rule](m, N)
+    Zs = np.array([ct.f(x) for x in X])
+    zbar = (w[:, None] * Zs).sum(0)
+    Lam = ct.SQ() @ ct.SQ().T + sum(w[i] * np.outer(Zs[i] - zbar - F @ (X[i] - m),
+                                                    Zs[i] - zbar - F @ (X[i] - m))
+                                    for i in range(len(w)))
+    np.testing.assert_allclose(S @ S.T, Lam, atol=1e-12)
