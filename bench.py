@@ -403,6 +403,18 @@ def gpu_arm(args, rank, world, local):
                / tb / 1e12}
     del yb, msb, Nsb
 
+    # ---- the same solve with each SLR rule (FP32, n = 1e5, M = 10)
+    rules = {}
+    for name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED),
+                      ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
+        def rstep(lin=lin):
+            B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, lin, dt=d["dt"],
+                               ms=ms, Ns=Ns, loglik=ll)
+        rstep()
+        torch.cuda.synchronize()
+        tr = timed(rstep, 3)
+        rules[name] = {"value": n * M / tr, "ms_per_step": 1e3 * tr}
+
     # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
     #      for cubature and extended SLR in FP32 and cubature in FP64, and
     #      the whole-step fraction of the FP32 peak (cubature FP32)
@@ -520,6 +532,7 @@ def gpu_arm(args, rank, world, local):
                 "roofline": roofline, "whole_step": whole, "kernels": kernels,
                 "nll_grad": grads, "batched": batched,
                 "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
+                "slr_rules": {"unit": UNIT, "n": n, "M": M, "by_rule": rules},
                 "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},

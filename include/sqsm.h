@@ -63,7 +63,11 @@ typedef enum { SQSM_F32 = 0, SQSM_F64 = 1 } sqsm_dtype;
 /* Linearisation rule of the SLR step (Sec. 4.2 / 4.3). */
 typedef enum {
   SQSM_CUBATURE = 0,   /* third-degree spherical-radial rule, 2 nx points */
-  SQSM_EXTENDED = 1    /* first-order Taylor expansion at the mean         */
+  SQSM_EXTENDED = 1,   /* first-order Taylor expansion at the mean         */
+  SQSM_UNSCENTED = 2,  /* unscented transform, alpha = 1, beta = 0,
+                          kappa = 1: 2 nx + 1 points, positive weights     */
+  SQSM_GAUSS_HERMITE = 3   /* three-point Gauss-Hermite rule per dimension,
+                              3^nx points (243 at nx = 5), two passes     */
 } sqsm_linearization;
 
 /* Compiled-in model families (a C ABI cannot carry device functions). */

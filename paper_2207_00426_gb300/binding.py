@@ -22,7 +22,7 @@ ERR_CUDA = 16
 ERR_NO_MEMORY = 32
 ERR_TOO_LARGE = 64
 F32, F64 = 0, 1
-CUBATURE, EXTENDED = 0, 1
+CUBATURE, EXTENDED, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
 MODEL_CT_BEARINGS = 1
 
 if not os.path.exists(LIB_PATH):

@@ -29,9 +29,9 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
   const RowsSplit<T, NX> nom{(T*)g.nom_m, (T*)g.nom_N}, fo{(T*)a.mf, (T*)a.Nf},
       so{(T*)g.ms2, (T*)g.Ns2};
-  ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, 0, 0, nom, (const T*)a.y, (T*)a.F,
-      nullptr, nullptr, nullptr, nullptr, nullptr);
+  launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, 0, Lf.lv[0], a.leaf, sq,
+                         (const CTParams<T>*)a.params, 0, nom, (const T*)a.y, (T*)a.F, (T*)nullptr,
+                         (T*)nullptr, (T*)nullptr, (T*)nullptr, (T*)nullptr);
   const GammaPacked<T> gv{(T*)a.F};
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0, fo,
                             partial, status, s);

@@ -701,7 +701,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
   if (M < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "M must be >= 1");
   if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
@@ -793,7 +793,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
   if (max_iters < 1) return fail(ctx, SQSM_ERR_INVALID_ARG, "max_iters must be >= 1");
   if (!(tol >= 0.0) || !std::isfinite(tol))
@@ -1072,7 +1072,7 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
   if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
   if (!valid_offsets(offsets, batch))

@@ -274,11 +274,21 @@ SQSM_DEV T branch_shift(T y, T ref) {
 // the difference at m + dl; with ADD_I it returns that difference minus dl
 // (the regression of x itself is exactly I, and the pair means and
 // residuals are unchanged because the +-dl of a pair cancel).
-template <typename T, int NO, bool ADD_I, typename DG>
+// Sigma-point rules with the pair structure m, m +- s N e_i: the cubature
+// rule (s^2 = n_x, no centre point) and the unscented transform with
+// alpha = 1, beta = 0, kappa = 1 (s^2 = n_x + 1, centre weight
+// 1 / (n_x + 1), pair weights 1 / (2 (n_x + 1))).
+enum SigmaRule { kCubature = 0, kUnscented = 1 };
+constexpr double kUtKappa = 1.0;
+
+template <typename T, int NO, bool ADD_I, typename DG, int RULE = kCubature>
 SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtract_Gm,
                                const T* Sc, DG dg, T* G, T* off, T* Sout) {
   constexpr int NX = 5;
-  const T sq = sq_sqrt(T(NX));
+  // pair scale s, pair weight w = 1 / (2 s^2), centre weight w0
+  constexpr double s2 = RULE == kUnscented ? NX + kUtKappa : NX;
+  constexpr double w0 = RULE == kUnscented ? kUtKappa / (NX + kUtKappa) : 0.0;
+  const T sq = sq_sqrt(T(s2));
   T D[NO * NX], Hs[NO * NX], dsum[NO];
 #pragma unroll
   for (int r = 0; r < NO; ++r) dsum[r] = T(0);
@@ -299,9 +309,10 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
       dsum[r] += zp[r] + zn[r];
     }
   }
+  // z_bar - g(m): the centre point's difference is 0
   T dbar[NO];
 #pragma unroll
-  for (int r = 0; r < NO; ++r) dbar[r] = dsum[r] / T(2 * NX);
+  for (int r = 0; r < NO; ++r) dbar[r] = dsum[r] / T(2 * s2);
   rsolve<T, NO, NX>(D, N);           // G = D N^{-1}
   if constexpr (ADD_I) {
     static_assert(NO == NX, "identity split needs a square regression");
@@ -319,7 +330,9 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 #pragma unroll
     for (int k = 0; k < NX; ++k) G[r * NX + k] = D[r * NX + k];
   }
-  constexpr int C = NO + NX;
+  // residual columns sqrt(2 w) ((Z_i^+ + Z_i^-) / 2 - z_bar) (both points of
+  // pair i have the same residual), and sqrt(w0) (Z_0 - z_bar) for a centre
+  constexpr int C = NO + NX + (w0 > 0.0 ? 1 : 0);
   T B[NO * C];
 #pragma unroll
   for (int r = 0; r < NO; ++r) {
@@ -327,9 +340,117 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
     for (int j = 0; j < NO; ++j) B[r * C + j] = Sc[r * NO + j];
 #pragma unroll
     for (int i = 0; i < NX; ++i) B[r * C + NO + i] = (Hs[r * NX + i] - dbar[r]) / sq;
+    if constexpr (w0 > 0.0) B[r * C + NO + NX] = -T(sqrt(w0)) * dbar[r];
   }
   tria<T, NO, C>(B);
   take_lower<T, NO, C>(B, Sout);
+}
+
+// The same regression with the tensor-product three-point Gauss-Hermite
+// rule (3^n_x points m + N xi, xi_k in {0, +sqrt 3, -sqrt 3}, weights
+// prod 2/3, 1/6, 1/6), in two passes over the points because the residuals
+// need z_bar and G first: pass 1 accumulates z_bar - g(m) and
+// D = sum w (Z - z_bar) xi^T (= the regression times N, as sum w xi xi^T = I);
+// pass 2 evaluates the points again and folds the residual columns
+// sqrt(w) (Z - z_bar - D xi) into the noise factor K at a time,
+// L <- Tria([L, columns]).
+template <typename T, int NO, bool ADD_I, typename DG>
+SQSM_DEV void gauss_hermite_regress(const T* m, const T* N, const T* gm, bool subtract_Gm,
+                                    const T* Sc, DG dg, T* G, T* off, T* Sout) {
+  constexpr int NX = 5, NP = 243, K = 5;
+  const T r3 = sq_sqrt(T(3));
+  auto node = [&](int digit) { return digit == 0 ? T(0) : (digit == 1 ? r3 : -r3); };
+  auto weight = [&](int digit) { return digit == 0 ? T(2.0 / 3.0) : T(1.0 / 6.0); };
+  T D[NO * NX], dbar[NO];
+#pragma unroll
+  for (int i = 0; i < NO * NX; ++i) D[i] = T(0);
+#pragma unroll
+  for (int r = 0; r < NO; ++r) dbar[r] = T(0);
+  // the point: xi from the base-3 digits of p, delta = N xi, its weight
+  auto point = [&](int p, T* xi, T* dl) -> T {
+    T w = T(1);
+    int q = p;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      const int dgt = q % 3;
+      q /= 3;
+      xi[k] = node(dgt);
+      w *= weight(dgt);
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = T(0);
+#pragma unroll
+      for (int k = 0; k <= r; ++k) a += N[r * NX + k] * xi[k];
+      dl[r] = a;
+    }
+    return w;
+  };
+#pragma unroll 1
+  for (int p = 0; p < NP; ++p) {
+    T xi[NX], dl[NX], z[NO];
+    const T w = point(p, xi, dl);
+    dg(m, dl, z);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      dbar[r] += w * z[r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) D[r * NX + k] += w * z[r] * xi[k];
+    }
+  }
+  // G = D N^{-1} (+ I); the offset as in cubature_regress
+#pragma unroll
+  for (int i = 0; i < NO * NX; ++i) G[i] = D[i];
+  rsolve<T, NO, NX>(G, N);
+  if constexpr (ADD_I) {
+    static_assert(NO == NX, "identity split needs a square regression");
+#pragma unroll
+    for (int r = 0; r < NO; ++r) G[r * NX + r] += T(1);
+  }
+#pragma unroll
+  for (int r = 0; r < NO; ++r) {
+    T a = gm[r] + dbar[r];
+    if (subtract_Gm) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) a -= G[r * NX + k] * m[k];
+    }
+    off[r] = a;
+  }
+  // pass 2: residual columns folded into L, K points at a time
+  T L[NO * NO];
+#pragma unroll
+  for (int i = 0; i < NO * NO; ++i) L[i] = Sc[i];
+  constexpr int C = NO + K;
+#pragma unroll 1
+  for (int p0 = 0; p0 < NP; p0 += K) {
+    T B[NO * C];
+#pragma unroll
+    for (int r = 0; r < NO; ++r)
+#pragma unroll
+      for (int j = 0; j < NO; ++j) B[r * C + j] = L[r * NO + j];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      T xi[NX], dl[NX], z[NO];
+      const bool valid = p0 + q < NP;   // the last group is partial: zero columns
+      const T w = point(valid ? p0 + q : 0, xi, dl);
+      dg(m, dl, z);
+      const T sw = valid ? sq_sqrt(w) : T(0);
+#pragma unroll
+      for (int r = 0; r < NO; ++r) {
+        T res = z[r] - dbar[r];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) res -= D[r * NX + k] * xi[k];
+        B[r * C + NO + q] = sw * res;
+      }
+    }
+    tria<T, NO, C>(B);
+#pragma unroll
+    for (int r = 0; r < NO; ++r)
+#pragma unroll
+      for (int j = 0; j < NO; ++j) L[r * NO + j] = j <= r ? B[r * C + j] : T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < NO * NO; ++i) Sout[i] = L[i];
 }
 
 // One thread per step s: the transition is linearised at state row s + b
@@ -348,10 +469,10 @@ SQSM_DEV void cubature_regress(const T* m, const T* N, const T* gm, bool subtrac
 // Steps are independent: one thread per step, addressed as (leaf chunk,
 // position in chunk) so that the chunk table gives the sequence; launch
 // n_chunks * leaf threads.
-template <typename T, bool PACKED, typename NO>
+template <typename T, bool PACKED, typename NO, int LIN>
 __global__ void __launch_bounds__(kBlock)
-ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
-              int linearization, int centered, NO nom, const T* __restrict__ y, T* __restrict__ F,
+ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
+              int centered, NO nom, const T* __restrict__ y, T* __restrict__ F,
               T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d,
               T* __restrict__ SRo) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -362,6 +483,7 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
   constexpr int NX = 5, NY = 2;
   const CTParams<T> P = *Pp;
   const int b = lv.seq[ch];
+  constexpr int linearization = LIN;
   {
     const int64_t s = lv.first[ch] + j;
     const int64_t rp = s + b, rk = s + b + 1;
@@ -379,11 +501,15 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
     } else {
       ct_f(P, m, fm);
     }
-    if (linearization == 0) {
-      const Turn<T> tm = turn(m[4], P.dt);
-      cubature_regress<T, NX, true>(
-          m, N, fm, !centered, P.SQ,
-          [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); }, Fm, cm, Sl);
+    const Turn<T> tm = turn(m[4], P.dt);
+    auto gd = [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); };
+    if constexpr (LIN == 0) {
+      cubature_regress<T, NX, true>(m, N, fm, !centered, P.SQ, gd, Fm, cm, Sl);
+    } else if constexpr (LIN == 2) {
+      cubature_regress<T, NX, true, decltype(gd), kUnscented>(m, N, fm, !centered, P.SQ, gd, Fm,
+                                                               cm, Sl);
+    } else if constexpr (LIN == 3) {
+      gauss_hermite_regress<T, NX, true>(m, N, fm, !centered, P.SQ, gd, Fm, cm, Sl);
     } else {
       ct_jac_f(P, m, Fm);
 #pragma unroll
@@ -414,11 +540,15 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
     T hm[NY], Hm[NY * NX], dm[NY], So[NY * NY], ys[NY];
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
-    if (linearization == 0) {
-      const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
-      cubature_regress<T, NY, false>(m, N, hm, !centered, Sr,
-                              [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
-                              Hm, dm, So);
+    const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
+    auto hd = [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); };
+    if constexpr (LIN == 0) {
+      cubature_regress<T, NY, false>(m, N, hm, !centered, Sr, hd, Hm, dm, So);
+    } else if constexpr (LIN == 2) {
+      cubature_regress<T, NY, false, decltype(hd), kUnscented>(m, N, hm, !centered, Sr, hd, Hm, dm,
+                                                                So);
+    } else if constexpr (LIN == 3) {
+      gauss_hermite_regress<T, NY, false>(m, N, hm, !centered, Sr, hd, Hm, dm, So);
     } else {
       ct_jac_h(P, m, Hm);
 #pragma unroll
@@ -445,6 +575,33 @@ ct_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__
       store<T, NY>(d + s * NY, dm);
       store_lower<T, NY>(SRo + s * NY * NY, So);
     }
+  }
+}
+
+// ct_slr_kernel_lin for a run-time linearisation (0 cubature, 1 Taylor,
+// 2 unscented, 3 Gauss-Hermite): one instantiation per rule, so that each
+// keeps its own register budget.
+template <typename T, bool PACKED, typename NO>
+void launch_ct_slr(unsigned grid, cudaStream_t s, int linearization, DevLevel lv, int leaf,
+                   DevSeqs sq, const CTParams<T>* Pp, int centered, NO nom, const T* y, T* F,
+                   T* c, T* SQo, T* H, T* d, T* SRo) {
+  switch (linearization) {
+    case 0:
+      ct_slr_kernel_lin<T, PACKED, NO, 0><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered, nom,
+                                                                   y, F, c, SQo, H, d, SRo);
+      break;
+    case 2:
+      ct_slr_kernel_lin<T, PACKED, NO, 2><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered, nom,
+                                                                   y, F, c, SQo, H, d, SRo);
+      break;
+    case 3:
+      ct_slr_kernel_lin<T, PACKED, NO, 3><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered, nom,
+                                                                   y, F, c, SQo, H, d, SRo);
+      break;
+    default:
+      ct_slr_kernel_lin<T, PACKED, NO, 1><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered, nom,
+                                                                   y, F, c, SQo, H, d, SRo);
+      break;
   }
 }
 

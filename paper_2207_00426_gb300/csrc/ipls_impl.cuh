@@ -21,9 +21,9 @@ void ipls_params(const IplsArgs& a, cudaStream_t s) {
 template <typename T>
 void ct_linearize(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_t s) {
   const RowsSplit<T, 5> nom{(T*)a.ms, (T*)a.Ns};
-  ct_slr_kernel<T, false><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-      Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, 0, nom,
-      (const T*)a.y, (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
+  launch_ct_slr<T, false>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, a.linearization, Lf.lv[0],
+                          a.leaf, sq, (const CTParams<T>*)a.params, 0, nom, (const T*)a.y,
+                          (T*)a.F, (T*)a.c, (T*)a.SQ, (T*)a.H, (T*)a.d, (T*)a.SR);
 }
 
 // One phase of Alg. 3 (IPLS_PRE: initial nominal trajectory; IPLS_ITER: one
@@ -65,9 +65,10 @@ void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, co
   // (With a.centered = 0 the printed absolute form is smoothed instead.)
   {
     ProfScope ps(a.prof, K_SLR, s);
-    ct_slr_kernel<T, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, a.linearization, a.centered, nom,
-        (const T*)a.y, (T*)a.F, nullptr, nullptr, nullptr, nullptr, nullptr);
+    launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, a.linearization, Lf.lv[0],
+                           a.leaf, sq, (const CTParams<T>*)a.params, a.centered, nom,
+                           (const T*)a.y, (T*)a.F, (T*)nullptr, (T*)nullptr, (T*)nullptr,
+                           (T*)nullptr, (T*)nullptr);
   }
   if (a.centered) {
     ProfScope ps(a.prof, K_INIT, s);

@@ -11,7 +11,7 @@ from oracle.kalman import sqrt_filter_smoother
 from paper_2207_00426_gb300 import workloads as W
 from gpu_util import rel_mean_err, rel_cov_err, TOL
 
-LIN = {"cubature": 0, "extended": 1}
+LIN = {"cubature": 0, "extended": 1, "unscented": 2, "gauss-hermite": 3}
 
 
 @pytest.fixture(scope="module")
@@ -30,7 +30,7 @@ def _dev(a, dtype):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("method", ["cubature", "extended"])
+@pytest.mark.parametrize("method", ["cubature", "extended", "unscented", "gauss-hermite"])
 def test_linearize_matches_oracle(B, ctx, prec, method):
     d = W.ct_sequence(n=40, seed=11)
     rng = np.random.default_rng(3)
@@ -58,7 +58,7 @@ def test_linearize_matches_oracle(B, ctx, prec, method):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("method", ["cubature", "extended"])
+@pytest.mark.parametrize("method", ["cubature", "extended", "unscented", "gauss-hermite"])
 def test_ipls_single_sequence(B, ctx, prec, method):
     d = W.ct_sequence(n=97, seed=12)
     dt = torch.float64 if prec == "f64" else torch.float32
