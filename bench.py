@@ -415,6 +415,29 @@ def gpu_arm(args, rank, world, local):
         tr = timed(rstep, 3)
         rules[name] = {"value": n * M / tr, "ms_per_step": 1e3 * tr}
 
+    # ---- the paper's sequential-vs-parallel comparison on the GPU: the
+    #      sequential smoother is the same library with one leaf chunk per
+    #      sequence (one thread runs the whole filter and smoother; the SLR
+    #      stays one thread per step), M = 10, FP32, each rule
+    seqpar = {}
+    for ns in (100, 1000, 4000):
+        dq = W.ct_sequence(n=ns, seed=7 + ns)
+        yq = torch.tensor(dq["y"], dtype=f32, device=dev)
+        m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
+        N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
+        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
+        row = {}
+        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE),
+                          ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
+            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
+                def qstep(cq=cq, lin=lin):
+                    B.sqsm_ipls_smooth(cq, dq["theta"], yq, [0, ns], m0q, N0q, M, lin, dt=dq["dt"])
+                qstep()
+                torch.cuda.synchronize()
+                row[f"{name}_{mode}_ms"] = 1e3 * timed(qstep, 2)
+        cseq.close()
+        seqpar[str(ns)] = row
+
     # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
     #      for cubature and extended SLR in FP32 and cubature in FP64, and
     #      the whole-step fraction of the FP32 peak (cubature FP32)
@@ -533,6 +556,7 @@ def gpu_arm(args, rank, world, local):
                 "nll_grad": grads, "batched": batched,
                 "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
                 "slr_rules": {"unit": UNIT, "n": n, "M": M, "by_rule": rules},
+                "sequential_vs_parallel": {"M": M, "dtype": "f32", "by_n": seqpar},
                 "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
