@@ -160,3 +160,46 @@ class LinearCV:
         R = self.sigma ** 2 * I2
         SR = self.sigma * I2
         return F, Q, SQ, H, R, SR
+
+
+class RickerPoisson:
+    """Stochastic Ricker population model with Poisson counts (Sec. 6.1):
+        x_k = log a + x_{k-1} - exp(x_{k-1}) + q_k,  q_k ~ N(0, Q),
+        y_k | x_k ~ Poisson(b exp(x_k)),  x_0 = log c (a point mass).
+    The observation noise is not additive: its conditional mean and variance
+    are both b exp(x), so the SLR takes the per-point conditional factor
+    sqrt(b exp(X_i)) (Sec. 4.3, general GSLR).  Parameters theta =
+    (log a, log b, log Q); the paper's values a = 44.7, b = 10, Q = 0.3^2,
+    c = 7."""
+    nx = 1
+    ny = 1
+
+    def __init__(self, theta):
+        self.a, self.b, self.q = (float(np.exp(t)) for t in theta)
+
+    def f(self, x):
+        return np.log(self.a) + x - np.exp(x)
+
+    def jac_f(self, x):
+        return np.array([[1.0 - np.exp(x[0])]])
+
+    def SQ(self):
+        return np.array([[np.sqrt(self.q)]])
+
+    def h(self, x):
+        """Conditional mean E[y | x]."""
+        return self.b * np.exp(x)
+
+    def jac_h(self, x):
+        return np.array([[self.b * np.exp(x[0])]])
+
+    def cond_SR(self, x):
+        """Lower factor of the conditional covariance Var[y | x]."""
+        return np.array([[np.sqrt(self.b * np.exp(x[0]))]])
+
+    def SR(self):
+        raise TypeError("the observation noise of this model depends on the state: use cond_SR")
+
+    def branch(self, z, ref):
+        return z
+

@@ -79,7 +79,9 @@ def _gslr_sigma(m, N, Zs, w, S_cond, X=None):
     G = solve_upper(N.T, solve_lower(N, Cross.T)).T
     off = zbar - G @ m
     Zdev = np.array([np.sqrt(w[i]) * (Zs[i] - zbar) for i in range(len(w))]).T
-    blocks = [np.sqrt(w[i]) * S_cond for i in range(len(w))] + [Zdev]
+    # S_cond: one conditional factor for every point, or a list of them
+    S_i = S_cond if isinstance(S_cond, list) else [S_cond] * len(w)
+    blocks = [np.sqrt(w[i]) * S_i[i] for i in range(len(w))] + [Zdev]
     S_prime = tria(np.hstack(blocks))
     S = downdate(S_prime, G @ N)
     return G, off, S
@@ -98,26 +100,47 @@ def residual_noise_factor(m, N, Zs, w, S_cond, G):
     return tria(np.hstack(cols))
 
 
+def _point_mass(N):
+    """A zero factor (a point-mass marginal, e.g. a known initial state):
+    every sigma point is m and the regression is undefined; its limit as
+    N -> 0 is the Taylor linearisation (Sec. 4.2), which is taken instead."""
+    return np.min(np.abs(np.diag(N))) < 1e-300
+
+
 def transition_cubature(model, m, N):
     """(F_{k-1}, c_{k-1}, S_Lambda_{k-1}) from (m^s_{k-1}, N^s_{k-1})."""
+    if _point_mass(N):
+        return transition_taylor(model, m)
     X, w = cubature_points(m, N)
     Zs = np.array([model.f(x) for x in X])
     return _gslr_sigma(m, N, Zs, w, model.SQ())
 
 
+def _cond_factors(model, X):
+    """Per-point conditional observation factors for a model whose noise
+    depends on the state, else the constant S_R."""
+    if hasattr(model, "cond_SR"):
+        return [model.cond_SR(x) for x in X]
+    return model.SR()
+
+
 def observation_cubature(model, m, N, y):
     """(H_k, d_k, S_Omega_k) from (m^s_k, N^s_k); bearings on the branch
     nearest h(m), d absorbing the 2 pi shift of y."""
+    if _point_mass(N):
+        return observation_taylor(model, m, y)
     X, w = cubature_points(m, N)
     ref = model.h(m)
     Zs = np.array([model.branch(model.h(x), ref) for x in X])
-    H, d, S = _gslr_sigma(m, N, Zs, w, model.SR())
+    H, d, S = _gslr_sigma(m, N, Zs, w, _cond_factors(model, X))
     d = d + (y - model.branch(y, ref))
     return H, d, S
 
 
 def transition_sigma(model, m, N, rule):
     """(F, c, S_Lambda) with the named sigma-point rule."""
+    if _point_mass(N):
+        return transition_taylor(model, m)
     X, w = SIGMA_RULES[rule](m, N)
     Zs = np.array([model.f(x) for x in X])
     return _gslr_sigma(m, N, Zs, w, model.SQ(), X)
@@ -126,10 +149,12 @@ def transition_sigma(model, m, N, rule):
 def observation_sigma(model, m, N, y, rule):
     """(H, d, S_Omega) with the named sigma-point rule, bearings on the
     branch nearest h(m) as in observation_cubature."""
+    if _point_mass(N):
+        return observation_taylor(model, m, y)
     X, w = SIGMA_RULES[rule](m, N)
     ref = model.h(m)
     Zs = np.array([model.branch(model.h(x), ref) for x in X])
-    H, d, S = _gslr_sigma(m, N, Zs, w, model.SR(), X)
+    H, d, S = _gslr_sigma(m, N, Zs, w, _cond_factors(model, X), X)
     return H, d + (y - model.branch(y, ref)), S
 
 
@@ -141,11 +166,12 @@ def transition_taylor(model, m):
 
 def observation_taylor(model, m, y):
     """Sec. 4.2: H = grad h(m^s_k), d = h(m) - H m (+ branch shift of y),
-    S_Omega = S_R."""
+    S_Omega = S_R (the conditional factor at m for a state-dependent noise)."""
     H = model.jac_h(m)
     ref = model.h(m)
     d = ref - H @ m + (y - model.branch(y, ref))
-    return H, d, model.SR()
+    SR = model.cond_SR(m) if hasattr(model, "cond_SR") else model.SR()
+    return H, d, SR
 
 
 def linearize(model, ms, Ns, y, method):

@@ -173,3 +173,37 @@ def ct_batch(batch=4096, lo=100, hi=5000, seed=3, dt=CT_DT, theta=CT_THETA_TRUE,
     return dict(y=y, offsets=offsets, m0=m0, N0=N0,
                 theta=np.array(theta, dtype=np.float64), dt=dt,
                 sensors=np.array(sensors, dtype=np.float64))
+
+
+# Stochastic Ricker population model with Poisson counts: a = 44.7, b = 10,
+# Q = 0.3^2, known initial state x_0 = log 7.
+RICKER_THETA_TRUE = np.log(np.array([44.7, 10.0, 0.09]))   # (a, b, Q)
+RICKER_X0 = float(np.log(7.0))
+
+
+def ricker_batch(lengths, seed=0, theta=RICKER_THETA_TRUE, x0=RICKER_X0):
+    """Independent Ricker sequences (vectorised over the batch):
+    x_k = log a + x_{k-1} - exp(x_{k-1}) + q_k, y_k ~ Poisson(b exp(x_k)),
+    x_0 = x0.  Returns y [sum n, 1], offsets, x (states, state layout),
+    m0 [B, 1] = x0, N0 [B, 1, 1] = 0 (a point mass), theta."""
+    rng = np.random.default_rng(seed)
+    a, b, q = np.exp(theta)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    B = len(lengths)
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    x = np.full(B, x0)
+    xs = np.zeros((int(offsets[-1]) + B, 1))
+    y = np.zeros((int(offsets[-1]), 1))
+    for bb in range(B):
+        xs[offsets[bb] + bb, 0] = x0
+    for t in range(int(lengths.max())):
+        x = np.log(a) + x - np.exp(x) + np.sqrt(q) * rng.standard_normal(B)
+        counts = rng.poisson(b * np.exp(x))
+        for bb in range(B):
+            if t < lengths[bb]:
+                y[offsets[bb] + t, 0] = counts[bb]
+                xs[offsets[bb] + bb + t + 1, 0] = x[bb]
+    return {"y": y, "offsets": offsets, "x": xs, "m0": np.full((B, 1), x0),
+            "N0": np.zeros((B, 1, 1)), "theta": np.asarray(theta, dtype=np.float64)}
+

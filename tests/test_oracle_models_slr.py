@@ -234,3 +234,67 @@ def test_sigma_rules_ct_downdate_equals_residual_form(rule):
                                                     Zs[i] - zbar - F @ (X[i] - m))
                                     for i in range(len(w)))
     np.testing.assert_allclose(S @ S.T, Lam, atol=1e-12)
+
+
+# ----- Ricker / Poisson model: state-dependent observation noise ----------
+
+def test_ricker_jacobians_match_central_differences():
+    mdl = models.RickerPoisson(W.RICKER_THETA_TRUE)
+    for x0 in (-1.0, 0.5, 2.0):
+        x = np.array([x0])
+        h = 1e-6
+        df = (mdl.f(x + h) - mdl.f(x - h)) / (2 * h)
+        dh = (mdl.h(x + h) - mdl.h(x - h)) / (2 * h)
+        np.testing.assert_allclose(mdl.jac_f(x)[0, 0], df[0], rtol=1e-8)
+        np.testing.assert_allclose(mdl.jac_h(x)[0, 0], dh[0], rtol=1e-8)
+
+
+class _QuadraticObs:
+    """y | x with E[y|x] = x^2 and Var[y|x] = x^2 + 1 (n_x = n_y = 1)."""
+    nx = ny = 1
+
+    def h(self, x):
+        return x ** 2
+
+    def cond_SR(self, x):
+        return np.array([[np.sqrt(x[0] ** 2 + 1.0)]])
+
+    def branch(self, z, ref):
+        return z
+
+
+def test_per_point_conditional_covariance_closed_form():
+    # x ~ N(m, P): H = 2m, d = P - m^2, and Omega = E[Var(y|x)] + Var(E[y|x])
+    # - H P H = m^2 + P + 1 + 2 P^2; Gauss-Hermite is exact to degree five
+    m, P = 0.7, 0.3
+    H, d, S = slr.observation_sigma(_QuadraticObs(), np.array([m]), np.array([[np.sqrt(P)]]),
+                                    np.array([0.0]), "gauss-hermite")
+    np.testing.assert_allclose(H[0, 0], 2 * m, rtol=1e-13)
+    np.testing.assert_allclose(d[0], P - m * m, atol=1e-13)
+    np.testing.assert_allclose(S[0, 0] ** 2, m * m + P + 1 + 2 * P * P, rtol=1e-13)
+
+
+def test_per_point_factor_list_equals_constant_factor():
+    m, N = _mn(7)
+    d = W.ct_sequence(n=3, seed=8)
+    ct = models.CTBearings(d["theta"], dt=d["dt"])
+    X, w = slr.cubature_points(m, N)
+    Zs = np.array([ct.f(x) for x in X])
+    a = slr._gslr_sigma(m, N, Zs, w, ct.SQ())
+    b = slr._gslr_sigma(m, N, Zs, w, [ct.SQ()] * len(w))
+    for u, v in zip(a, b):
+        np.testing.assert_allclose(u, v, atol=1e-15)
+
+
+def test_point_mass_limit_is_taylor():
+    mdl = models.RickerPoisson(W.RICKER_THETA_TRUE)
+    m = np.array([1.2])
+    for N, tol in ((np.zeros((1, 1)), 0.0), (np.array([[1e-6]]), 1e-9)):
+        F, c, SQ = slr.transition_cubature(mdl, m, N)
+        Ft, ct_, SQt = slr.transition_taylor(mdl, m)
+        np.testing.assert_allclose(F, Ft, atol=tol, rtol=tol)
+        np.testing.assert_allclose(c, ct_, atol=tol * 10)
+        H, dd, SR = slr.observation_cubature(mdl, m, N, np.array([3.0]))
+        Ht, dt_, SRt = slr.observation_taylor(mdl, m, np.array([3.0]))
+        np.testing.assert_allclose(H, Ht, rtol=max(tol, 1e-15))
+        np.testing.assert_allclose(SR, SRt, rtol=max(tol, 1e-15))
