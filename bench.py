@@ -438,6 +438,28 @@ def gpu_arm(args, rank, world, local):
         cseq.close()
         seqpar[str(ns)] = row
 
+    # ---- the paper's population-model timing (Ricker dynamics, Poisson
+    #      counts, n_x = n_y = 1): M = 100 iterations, Taylor and cubature,
+    #      parallel against sequential (one leaf chunk per sequence), FP32
+    population = {}
+    for ns in (100, 1000, 10000):
+        dp = W.ricker_batch([ns], seed=11 + ns)
+        yp = torch.tensor(dp["y"], dtype=f32, device=dev)
+        m0p = torch.tensor(dp["m0"], dtype=f32, device=dev)
+        N0p = torch.tensor(dp["N0"], dtype=f32, device=dev)
+        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
+        row = {}
+        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE)):
+            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
+                def pstep(cq=cq, lin=lin):
+                    B.sqsm_ipls_smooth_population(cq, dp["theta"], yp, dp["offsets"], m0p, N0p,
+                                                  100, lin)
+                pstep()
+                torch.cuda.synchronize()
+                row[f"{name}_{mode}_ms"] = 1e3 * timed(pstep, 2)
+        cseq.close()
+        population[str(ns)] = row
+
     # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
     #      for cubature and extended SLR in FP32 and cubature in FP64, and
     #      the whole-step fraction of the FP32 peak (cubature FP32)
@@ -557,6 +579,7 @@ def gpu_arm(args, rank, world, local):
                 "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
                 "slr_rules": {"unit": UNIT, "n": n, "M": M, "by_rule": rules},
                 "sequential_vs_parallel": {"M": M, "dtype": "f32", "by_n": seqpar},
+                "population_model": {"M": 100, "dtype": "f32", "by_n": population},
                 "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},

@@ -72,7 +72,15 @@ typedef enum {
 
 /* Compiled-in model families (a C ABI cannot carry device functions). */
 typedef enum {
-  SQSM_MODEL_CT_BEARINGS = 1   /* coordinated turn, two bearing sensors */
+  SQSM_MODEL_CT_BEARINGS = 1,  /* coordinated turn, two bearing sensors:
+                                  nx = 5, ny = 2, theta = (log sigma,
+                                  log q_c, log q_omega)                   */
+  SQSM_MODEL_POPULATION = 2    /* stochastic Ricker model, Poisson counts
+                                  (state-dependent observation noise):
+                                  nx = ny = 1, theta = (log a, log b,
+                                  log Q); dt and sensors unused; cubature
+                                  or extended SLR; sqsm_ipls_smooth and
+                                  sqsm_ipls_smooth_tol only               */
 } sqsm_model_kind;
 
 /* Coordinated-turn bearings-only model (Sec. 6.2): state

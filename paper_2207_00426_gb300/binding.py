@@ -24,6 +24,7 @@ ERR_TOO_LARGE = 64
 F32, F64 = 0, 1
 CUBATURE, EXTENDED, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
 MODEL_CT_BEARINGS = 1
+MODEL_POPULATION = 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -325,6 +326,36 @@ def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, linearization=CUBATU
                                   _ptr(loglik, torch.float64, "loglik"), _stream())
     ctx.check(rc)
     return ms, Ps, loglik
+
+
+def sqsm_ipls_smooth_population(ctx, theta, y, offsets, m0, N0, M, linearization=CUBATURE,
+                                tol=None, max_iters=None):
+    """Alg. 3 on the Ricker population model (n_x = n_y = 1), theta =
+    (log a, log b, log Q); y [sum n, 1] counts, m0 [B, 1], N0 [B, 1, 1] (0 for
+    a known initial state).  With tol set, iterate until convergence (at
+    most max_iters, default M).  Returns (ms, Ns, loglik) or, with tol,
+    (ms, Ns, loglik, iters_done)."""
+    dtp = y.dtype
+    code = _dtype_code(dtp)
+    off, batch = _offsets(offsets)
+    rows = int(off[batch]) + batch
+    dev = y.device
+    ms = torch.empty((rows, 1), dtype=dtp, device=dev)
+    Ns = torch.empty((rows, 1, 1), dtype=dtp, device=dev)
+    loglik = torch.empty(batch, dtype=torch.float64, device=dev)
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    mdl = Model(MODEL_POPULATION, 1.0, (ctypes.c_double * 4)())
+    args = (batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"), None, None,
+            _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"), _ptr(loglik, torch.float64, "loglik"))
+    if tol is None:
+        ctx.check(lib.sqsm_ipls_smooth(ctx.h, code, ctypes.byref(mdl), th, int(linearization),
+                                       int(M), *args, _stream()))
+        return ms, Ns, loglik
+    iters = torch.zeros(1, dtype=torch.int32, device=dev)
+    ctx.check(lib.sqsm_ipls_smooth_tol(ctx.h, code, ctypes.byref(mdl), th, int(linearization),
+                                       int(max_iters or M), float(tol), *args,
+                                       _ptr(iters, torch.int32, "iters_done"), _stream()))
+    return ms, Ns, loglik, iters
 
 
 def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt=0.01,

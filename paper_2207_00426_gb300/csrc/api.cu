@@ -68,10 +68,12 @@ struct GraphKey {
   const void *y, *m0, *N0, *ims, *iNs, *ms, *Ns, *ll;
   double tol = -1.0;                // tolerance mode (M = iteration cap), else -1
   const void* iters = nullptr;
+  int kind = SQSM_MODEL_CT_BEARINGS;
   bool operator<(const GraphKey& o) const {
-    return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll, tol, iters) <
+    return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll, tol, iters,
+                    kind) <
            std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.adj, o.y, o.m0, o.N0, o.ims, o.iNs,
-                    o.ms, o.Ns, o.ll, o.tol, o.iters);
+                    o.ms, o.Ns, o.ll, o.tol, o.iters, o.kind);
   }
 };
 
@@ -330,16 +332,15 @@ Workspace* get_ws(Plan* p, int dtype, int nx) {
   return r;
 }
 
-bool ensure_ipls(Workspace* w, const Plan* p, int dtype) {
+bool ensure_ipls(Workspace* w, const Plan* p, int dtype, int nx = 5, int ny = 2) {
   if (w->ipls_ready) return true;
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
   const int64_t n = p->filt.n_items[0];
-  const int nx = 5;
   // the linearised model of every step as packed records
-  w->gamma = w->mem.get(es * PRec<5, 2>::size * n);
+  w->gamma = w->mem.get(es * prec_size(nx, ny) * n);
   const int64_t rows = p->smth.n_items[0];
-  w->frows = w->mem.get(es * XRow<5>::size * rows);
-  w->nrows = w->mem.get(es * XRow<5>::size * rows);
+  w->frows = w->mem.get(es * xrow_size(nx) * rows);
+  w->nrows = w->mem.get(es * xrow_size(nx) * rows);
   if (!w->gamma || !w->frows || !w->nrows) return false;
   w->params = w->mem.get(512);
   w->dm0 = w->mem.get(es * nx * p->B);
@@ -581,6 +582,33 @@ void enqueue_ipls(sqsm_ctx* ctx, int dtype, const Plan* p, const Workspace* w, c
     ipls_enqueue_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st);
 }
 
+// The population model's params kernel and M-iteration enqueue.
+void pop_params(int dtype, const IplsArgs& a, cudaStream_t s) {
+  if (dtype == SQSM_F32) pop_params_f32(a, s); else pop_params_f64(a, s);
+}
+
+void pop_phase(int dtype, sqsm_ctx* ctx, const Plan* p, const Workspace* w, const IplsArgs& a,
+               cudaStream_t st, int phase, unsigned* dmax) {
+  const DevSeqs sq = seqs_of(p);
+  if (dtype == SQSM_F32)
+    pop_phase_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, phase,
+                  dmax);
+  else
+    pop_phase_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, phase,
+                  dmax);
+}
+
+void enqueue_pop(sqsm_ctx* ctx, int dtype, const Plan* p, const Workspace* w, const IplsArgs& a,
+                 cudaStream_t st) {
+  pop_phase(dtype, ctx, p, w, a, st, IPLS_PRE, nullptr);
+  for (int it = 0; it < a.M; ++it) pop_phase(dtype, ctx, p, w, a, st, IPLS_ITER, nullptr);
+  pop_phase(dtype, ctx, p, w, a, st, IPLS_POST, nullptr);
+}
+
+bool known_model(const sqsm_model* model) {
+  return model && (model->kind == SQSM_MODEL_CT_BEARINGS || model->kind == SQSM_MODEL_POPULATION);
+}
+
 int floor_log2(int64_t v) {
   int l = 0;
   while (v > 1) {
@@ -697,9 +725,11 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  const bool pop = model->kind == SQSM_MODEL_POPULATION;
+  if (!pop && !(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (pop && linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the population model takes cubature or extended SLR");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
   if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
@@ -717,18 +747,29 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   int L0 = 0, R = 0;
-  const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
-                                    m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
-  if (trc != SQSM_OK) return trc;
+  if (pop) {
+    default_shape(ctx, offsets, batch, &L0, &R);
+  } else {
+    const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
+                                      m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
+    if (trc != SQSM_OK) return trc;
+  }
   Plan* p = get_plan(ctx, offsets, batch, L0, R);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
-  Workspace* w = get_ws(p, dtype, 5);
-  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
+  Workspace* w = get_ws(p, dtype, nx);
+  if (!w || !ensure_ipls(w, p, dtype, nx, ny))
+    return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
                               ms, Ns, loglik);
   // theta -> model constants, outside any graph so that theta is not baked in
-  if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
-  auto enqueue = [&](cudaStream_t st) { enqueue_ipls(ctx, dtype, p, w, a, st); };
+  if (pop) pop_params(dtype, a, s);
+  else if (dtype == SQSM_F32) ipls_params_f32(a, s);
+  else ipls_params_f64(a, s);
+  auto enqueue = [&](cudaStream_t st) {
+    if (pop) enqueue_pop(ctx, dtype, p, w, a, st);
+    else enqueue_ipls(ctx, dtype, p, w, a, st);
+  };
   if (!ctx->opt.use_graph) {
     if (ctx->prof_on) {
       ctx->call_prof.clear();
@@ -739,6 +780,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   } else {
     GraphKey key{p, dtype, linearization, M, ctx->prof_on ? 1 : 0, 0, y, m0, N0, init_ms, init_Ns,
                  ms, Ns, loglik};
+    key.kind = model->kind;
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
@@ -789,9 +831,11 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  const bool pop = model->kind == SQSM_MODEL_POPULATION;
+  if (!pop && !(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (pop && linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the population model takes cubature or extended SLR");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
   if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
@@ -811,13 +855,19 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
   int L0 = 0, R = 0;
-  const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
-                                    m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
-  if (trc != SQSM_OK) return trc;
+  if (pop) {
+    default_shape(ctx, offsets, batch, &L0, &R);
+  } else {
+    const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
+                                      m0, N0, init_ms, init_Ns, ms, Ns, s, &L0, &R);
+    if (trc != SQSM_OK) return trc;
+  }
   Plan* p = get_plan(ctx, offsets, batch, L0, R);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
-  Workspace* w = get_ws(p, dtype, 5);
-  if (!w || !ensure_ipls(w, p, dtype)) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
+  Workspace* w = get_ws(p, dtype, nx);
+  if (!w || !ensure_ipls(w, p, dtype, nx, ny))
+    return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, max_iters, y, m0, N0,
                                     init_ms, init_Ns, ms, Ns, loglik);
   int* iters = w->tol_words;
@@ -825,14 +875,18 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   unsigned* dmax = (unsigned*)(w->tol_words + 2);
   const DevSeqs sq = seqs_of(p);
   auto phase = [&](int ph, cudaStream_t st) {
-    if (dtype == SQSM_F32)
+    if (pop)
+      pop_phase(dtype, ctx, p, w, a, st, ph, ph == IPLS_ITER ? dmax : nullptr);
+    else if (dtype == SQSM_F32)
       ipls_phase_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, ph,
                      ph == IPLS_ITER ? dmax : nullptr);
     else
       ipls_phase_f64(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial, ctx->d_status, st, ph,
                      ph == IPLS_ITER ? dmax : nullptr);
   };
-  if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
+  if (pop) pop_params(dtype, a, s);
+  else if (dtype == SQSM_F32) ipls_params_f32(a, s);
+  else ipls_params_f64(a, s);
   if (!ctx->opt.use_graph) {
     // host-driven loop: one device-to-host read of the continue flag per iteration
     phase(IPLS_PRE, s);
@@ -856,6 +910,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
                  ms, Ns, loglik};
     key.tol = tol;
     key.iters = iters_done;
+    key.kind = model->kind;
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
@@ -932,8 +987,9 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
   if (linearization != SQSM_CUBATURE && linearization != SQSM_EXTENDED)
@@ -979,8 +1035,9 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
   if (linearization != SQSM_CUBATURE)
@@ -1068,8 +1125,9 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!model || model->kind != SQSM_MODEL_CT_BEARINGS)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
   if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)

@@ -66,6 +66,16 @@ void ipls_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf
 void ipls_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                     const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                     int* status, cudaStream_t s, int phase, unsigned* dmax);
+// The Ricker population model (n_x = n_y = 1): parameters and phases.
+void pop_params_f32(const IplsArgs& a, cudaStream_t s);
+void pop_params_f64(const IplsArgs& a, cudaStream_t s);
+void pop_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                   const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                   int* status, cudaStream_t s, int phase, unsigned* dmax);
+void pop_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                   const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                   int* status, cudaStream_t s, int phase, unsigned* dmax);
+
 // After one iteration of the tolerance mode: counts it in *iters, compares
 // the largest change *dmax (float bits) with tol, clears *dmax, and sets
 // whether the loop continues (change >= tol and fewer than max_iters

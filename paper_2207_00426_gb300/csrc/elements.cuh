@@ -194,6 +194,12 @@ template <int NX> struct SRec {
 };
 inline int frec_size(int nx) { return (3 * nx * nx + 2 * nx + 3) / 4 * 4; }
 inline int srec_size(int nx) { return (2 * nx * nx + nx + 3) / 4 * 4; }
+// Run-time sizes of PRec<nx, ny> and XRow<nx> (same formulas).
+inline int prec_size(int nx, int ny) {
+  const int h = (nx * nx + nx + nx * (nx + 1) / 2 + 3) / 4 * 4;
+  return (h + ny * nx + ny + ny * (ny + 1) / 2 + 3) / 4 * 4;
+}
+inline int xrow_size(int nx) { return (nx + nx * (nx + 1) / 2 + 3) / 4 * 4; }
 
 // Clear the padding words of a record after its fields are written.
 template <typename T, int USED, int SIZE>

@@ -6,9 +6,15 @@
 #pragma once
 
 #include "ct_model.cuh"
+#include "pop_model.cuh"
 #include "dispatch.h"
 
 namespace sqsm {
+
+template <typename T>
+void pop_params(const IplsArgs& a, cudaStream_t s) {
+  pop_params_kernel<T><<<1, 1, 0, s>>>(a.theta[0], a.theta[1], a.theta[2], (PopParams<T>*)a.params);
+}
 
 template <typename T>
 void ipls_params(const IplsArgs& a, cudaStream_t s) {
@@ -29,11 +35,12 @@ void ct_linearize(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStream_
 // One phase of Alg. 3 (IPLS_PRE: initial nominal trajectory; IPLS_ITER: one
 // iteration, with dmax set also the largest change of the nominal means;
 // IPLS_POST: the result into the caller's arrays and the log-likelihood).
-template <typename T>
-void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, const LevelSet& Ls,
-                const ScanBuffers& Ws, DevSeqs sq, double* partial, int* status, cudaStream_t s,
-                int phase, unsigned* dmax) {
-  constexpr int NX = 5, NY = 2;
+// NX, NY: the model's dimensions; slr(nom, s) launches the model's SLR of
+// every step about the nominal rows.
+template <typename T, int NX, int NY, typename SLR>
+void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                      const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                      int* status, cudaStream_t s, int phase, unsigned* dmax, SLR slr) {
   const int64_t rows = Ls.n_items[0];
   const RowsPacked<T, NX> nom{(T*)a.nrows}, fr{(T*)a.frows};
   if (phase == IPLS_PRE) {
@@ -65,10 +72,7 @@ void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, co
   // (With a.centered = 0 the printed absolute form is smoothed instead.)
   {
     ProfScope ps(a.prof, K_SLR, s);
-    launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, a.linearization, Lf.lv[0],
-                           a.leaf, sq, (const CTParams<T>*)a.params, a.centered, nom,
-                           (const T*)a.y, (T*)a.F, (T*)nullptr, (T*)nullptr, (T*)nullptr,
-                           (T*)nullptr, (T*)nullptr);
+    slr(nom, s);
   }
   if (a.centered) {
     ProfScope ps(a.prof, K_INIT, s);
@@ -79,6 +83,33 @@ void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, co
                             (const T*)(a.centered ? a.dm0 : a.m0), (const T*)a.N0, fr, partial,
                             status, s, a.prof);
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax);
+}
+
+// The CT bearings model's phase.
+template <typename T>
+void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, const LevelSet& Ls,
+                const ScanBuffers& Ws, DevSeqs sq, double* partial, int* status, cudaStream_t s,
+                int phase, unsigned* dmax) {
+  auto slr = [&](RowsPacked<T, 5> nom, cudaStream_t st) {
+    launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), st, a.linearization, Lf.lv[0],
+                           a.leaf, sq, (const CTParams<T>*)a.params, a.centered, nom,
+                           (const T*)a.y, (T*)a.F, (T*)nullptr, (T*)nullptr, (T*)nullptr,
+                           (T*)nullptr, (T*)nullptr);
+  };
+  ipls_phase_model<T, 5, 2>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax, slr);
+}
+
+// The Ricker population model's phase.
+template <typename T>
+void pop_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, const LevelSet& Ls,
+               const ScanBuffers& Ws, DevSeqs sq, double* partial, int* status, cudaStream_t s,
+               int phase, unsigned* dmax) {
+  auto slr = [&](RowsPacked<T, 1> nom, cudaStream_t st) {
+    launch_pop_slr<T>(grid_for(Lf.lv[0].n_chunks * a.leaf), st, a.linearization, Lf.lv[0],
+                      a.leaf, sq, (const PopParams<T>*)a.params, a.centered, nom, (const T*)a.y,
+                      (T*)a.F);
+  };
+  ipls_phase_model<T, 1, 1>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax, slr);
 }
 
 // M iterations of Alg. 3.

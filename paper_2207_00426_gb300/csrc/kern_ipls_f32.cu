@@ -15,6 +15,14 @@ void ipls_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf
   ipls_phase<float>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax);
 }
 
+void pop_params_f32(const IplsArgs& a, cudaStream_t s) { pop_params<float>(a, s); }
+
+void pop_phase_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                   const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                   int* status, cudaStream_t s, int phase, unsigned* dmax) {
+  pop_phase<float>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax);
+}
+
 void ipls_enqueue_f32(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                       const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                       int* status, cudaStream_t s) {

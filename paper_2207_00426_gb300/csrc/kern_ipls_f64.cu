@@ -15,6 +15,14 @@ void ipls_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf
   ipls_phase<double>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax);
 }
 
+void pop_params_f64(const IplsArgs& a, cudaStream_t s) { pop_params<double>(a, s); }
+
+void pop_phase_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
+                   const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
+                   int* status, cudaStream_t s, int phase, unsigned* dmax) {
+  pop_phase<double>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax);
+}
+
 void ipls_enqueue_f64(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf,
                       const LevelSet& Ls, const ScanBuffers& Ws, DevSeqs sq, double* partial,
                       int* status, cudaStream_t s) {
