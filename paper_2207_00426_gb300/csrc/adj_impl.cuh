@@ -2,6 +2,8 @@
 // pass at the final trajectory, and the fixed-point adjoint iterations).
 #pragma once
 
+#include <algorithm>
+
 #include "adjoint_kernels.cuh"
 #include "dispatch.h"
 
@@ -100,8 +102,14 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
     // SLR adjoint -> next cotangent of the nominal trajectory, theta partials
     adj_slr_kernel<T><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
         Ls.lv[0], sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
-    if (it + 1 == g.iters && g.change)
-      adj_change_reduce<T><<<1, 256, 0, s>>>(X * rows, lam_b, lam_a, g.change);
+    if (it + 1 == g.iters && g.change) {
+      unsigned* words = (unsigned*)g.change_words;
+      cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), s);
+      const int64_t n = X * rows;
+      const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4 * 152);
+      adj_change_partial<T><<<blocks, 256, 0, s>>>(n, lam_b, lam_a, words);
+      adj_change_final<<<1, 1, 0, s>>>(words, g.change);
+    }
     T* t = lam_a;
     lam_a = lam_b;
     lam_b = t;

@@ -393,27 +393,33 @@ static __global__ void adj_theta_reduce(int64_t n, const double* __restrict__ pa
     for (int j = 0; j < 3; ++j) out[j] = sign * buf[j][0];
 }
 
-// Relative max-norm change between two cotangent iterates (one block).
+// Relative max-norm change between two cotangent iterates, in two kernels:
+// every block max-reduces |a - b| and |a| over a grid-stride slice and folds
+// them into words[0], words[1] (bits of non-negative floats, ordered like
+// the values; the caller clears them), then one thread forms the ratio.
 template <typename T>
-static __global__ void adj_change_reduce(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
-                                  double* __restrict__ out) {
-  __shared__ double s1[256], s2[256];
-  double d = 0.0, m = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    d = fmax(d, fabs((double)a[i] - (double)b[i]));
-    m = fmax(m, fabs((double)a[i]));
+static __global__ void __launch_bounds__(256)
+adj_change_partial(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
+                   unsigned* __restrict__ words) {
+  float d = 0.f, m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    d = fmaxf(d, fabsf((float)(a[i] - b[i])));
+    m = fmaxf(m, fabsf((float)a[i]));
   }
-  s1[threadIdx.x] = d;
-  s2[threadIdx.x] = m;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + w]);
-      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
-    }
-    __syncthreads();
+  unsigned bd = __float_as_uint(d), bm = __float_as_uint(m);
+  bd = __reduce_max_sync(0xffffffffu, bd);
+  bm = __reduce_max_sync(0xffffffffu, bm);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(words, bd);
+    atomicMax(words + 1, bm);
   }
-  if (threadIdx.x == 0) out[0] = s2[0] > 0.0 ? s1[0] / s2[0] : s1[0];
+}
+
+static __global__ void adj_change_final(const unsigned* __restrict__ words,
+                                        double* __restrict__ out) {
+  const double d = __uint_as_float(words[0]), m = __uint_as_float(words[1]);
+  out[0] = m > 0.0 ? d / m : d;
 }
 
 // Sum of the per-sequence log-likelihoods times sign (one thread, fixed order).

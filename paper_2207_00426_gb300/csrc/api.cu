@@ -368,6 +368,8 @@ bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
   g.gbar = w->mem.get(es * grec * steps);
   g.th_partial = (double*)w->mem.get(sizeof(double) * 3 * p->smth.lv[0].n_chunks);
   g.ll = (double*)w->mem.get(sizeof(double) * p->B);
+  g.change_words = w->mem.get(2 * sizeof(unsigned));
+  if (!g.change_words) return false;
   if (!g.nom_m || !g.nom_N || !g.ms2 || !g.Ns2 || !g.dir || !g.dfilt || !g.lam_a || !g.lam_b ||
       !g.gbar || !g.th_partial || !g.ll)
     return false;

@@ -95,6 +95,7 @@ struct AdjArgs {
   void *nom_m, *nom_N, *ms2, *Ns2;    // linearisation point, its smoother output
   void *dir, *dfilt, *gbar, *lam_a, *lam_b;
   double *th_partial, *ll, *nll, *grad, *change;
+  void* change_words;                 // two words for the change reduction
 };
 void adj_enqueue_f32(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf,
                      const ScanBuffers& Wf, const LevelSet& Ls, const ScanBuffers& Ws,
