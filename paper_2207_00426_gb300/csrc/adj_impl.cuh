@@ -9,6 +9,36 @@
 
 namespace sqsm {
 
+// Upper levels 1 .. Lk-1 of an adjoint scan (items[1] already written by
+// the leaf up-sweep), then the Kogge-Stone top over the items of level Lk.
+template <typename T, bool FWD>
+void adj_scan_up(const LevelSet& L, const ScanBuffers& W, int Lk, cudaStream_t s) {
+  constexpr int KS = KsMax<T, MapRec<5>::size>::value;
+  for (int l = 1; l < Lk; ++l)
+    if (L.chunk_scan(l))
+      adj_up_cs<T, FWD><<<(unsigned)L.lv[l].n_chunks, kChunkScan, 0, s>>>(
+          L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
+    else
+      adj_up<T, FWD><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(L.lv[l], (const T*)W.items[l],
+                                                                   (T*)W.items[l + 1]);
+  adj_top_ks<T, FWD><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk], (const T*)W.items[Lk],
+                                         (T*)W.carry[Lk], W.flag[Lk]);
+}
+
+// Down-sweep of an adjoint scan from the carries of level `top` to level 1.
+template <typename T, bool FWD>
+void adj_scan_down(const LevelSet& L, const ScanBuffers& W, int top, cudaStream_t s) {
+  for (int l = top - 1; l >= 1; --l)
+    if (L.chunk_scan(l))
+      adj_down_cs<T, FWD><<<cs_down_grid(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
+          W.flag[l]);
+    else
+      adj_down<T, FWD><<<grid_for(L.lv[l].n_chunks), kBlock, 0, s>>>(
+          L.lv[l], (const T*)W.items[l], (const T*)W.carry[l + 1], W.flag[l + 1], (T*)W.carry[l],
+          W.flag[l]);
+}
+
 template <typename T>
 void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const ScanBuffers& Wf,
                  const LevelSet& Ls, const ScanBuffers& Ws, const ScanBuffers& Wa, DevSeqs sq,
@@ -40,68 +70,47 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fo, so, status, s);
   enqueue_loglik_reduce(sq, partial, g.ll, status, s);
   adj_nll_kernel<<<1, 1, 0, s>>>(sq.B, g.ll, -1.0, g.nll);
-  // 3. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)
+  // 3. per-step tables of that linearisation (fixed over the iterations)
   AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F,
-             g.dir, g.dfilt, g.gbar};
+             g.dir, g.dfilt, g.gbar, g.ktab, g.rtab, g.stab};
+  adj_tables_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+      Lf.lv[0], a.leaf, (const CTParams<T>*)a.params, ab);
+  // 4. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)
   const T lbar = T(-1);
   T* lam_a = (T*)g.lam_a;
   T* lam_b = (T*)g.lam_b;
   cudaMemsetAsync(lam_a, 0, sizeof(T) * X * rows, s);
+  cudaMemsetAsync(g.dir, 0, sizeof(T) * X * rows, s);   // step 1 of lam = 0
   const int Lc = (int)Lf.lv.size();
+  const int Lk = Lf.ks_level(KsMax<T, MREC>::value);
+  const unsigned slr_blocks = grid_for(Ls.lv[0].n_chunks * a.leaf);
   for (int it = 0; it < g.iters; ++it) {
-    adj_direct_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, (const T*)g.Ns2, lam_a,
-                                                               (T*)g.dir);
     // smoother adjoint: forward-in-time scan of maps
     if (Lc > 1) {
       adj_smoother_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab,
                                                                              (T*)Wa.items[1]);
-      for (int l = 1; l < Lc; ++l)
-        if (Lf.chunk_scan(l))
-          adj_up_cs<T, true><<<(unsigned)Lf.lv[l].n_chunks, kChunkScan, 0, s>>>(
-              Lf.lv[l], (T*)Wa.items[l], (T*)Wa.items[l + 1]);
-        else
-          adj_up<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-              Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+      adj_scan_up<T, true>(Lf, Wa, Lk, s);
+    } else {
+      cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     }
-    cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
-    for (int l = Lc - 1; l >= 1; --l)
-      if (Lf.chunk_scan(l))
-        adj_down_cs<T, true><<<cs_down_grid(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-            (T*)Wa.carry[l], Wa.flag[l]);
-      else
-        adj_down<T, true><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-            (T*)Wa.carry[l], Wa.flag[l]);
-    adj_smoother_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-        Lf.lv[0], sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
+    adj_scan_down<T, true>(Lf, Wa, Lc > 1 ? Lk : Lc, s);
+    adj_smoother_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+        Lf.lv[0], a.leaf, sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
     // filter adjoint: backward-in-time scan of maps
     if (Lc > 1) {
       adj_filter_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab, lbar,
                                                                            (T*)Wa.items[1]);
-      for (int l = 1; l < Lc; ++l)
-        if (Lf.chunk_scan(l))
-          adj_up_cs<T, false><<<(unsigned)Lf.lv[l].n_chunks, kChunkScan, 0, s>>>(
-              Lf.lv[l], (T*)Wa.items[l], (T*)Wa.items[l + 1]);
-        else
-          adj_up<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-              Lf.lv[l], (const T*)Wa.items[l], (T*)Wa.items[l + 1]);
+      adj_scan_up<T, false>(Lf, Wa, Lk, s);
+    } else {
+      cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     }
-    cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
-    for (int l = Lc - 1; l >= 1; --l)
-      if (Lf.chunk_scan(l))
-        adj_down_cs<T, false><<<cs_down_grid(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-            (T*)Wa.carry[l], Wa.flag[l]);
-      else
-        adj_down<T, false><<<grid_for(Lf.lv[l].n_chunks), kBlock, 0, s>>>(
-            Lf.lv[l], (const T*)Wa.items[l], (const T*)Wa.carry[l + 1], Wa.flag[l + 1],
-            (T*)Wa.carry[l], Wa.flag[l]);
-    adj_filter_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(
-        Lf.lv[0], sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
-    // SLR adjoint -> next cotangent of the nominal trajectory, theta partials
-    adj_slr_kernel<T><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
-        Ls.lv[0], sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
+    adj_scan_down<T, false>(Lf, Wa, Lc > 1 ? Lk : Lc, s);
+    adj_filter_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+        Lf.lv[0], a.leaf, sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
+    // SLR adjoint -> next cotangent of the nominal trajectory (and its direct
+    // cotangents for the next iteration), theta partials
+    adj_slr_kernel<T><<<slr_blocks, kBlock, 0, s>>>(
+        Ls.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
     if (it + 1 == g.iters && g.change) {
       unsigned* words = (unsigned*)g.change_words;
       cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), s);
@@ -114,9 +123,8 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
     lam_a = lam_b;
     lam_b = t;
   }
-  if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(Ls.lv[0].n_chunks, g.th_partial, 1.0, g.grad);
+  if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(slr_blocks, g.th_partial, 1.0, g.grad);
   else cudaMemsetAsync(g.grad, 0, 3 * sizeof(double), s);
-  (void)MREC;
 }
 
 }  // namespace sqsm

@@ -27,6 +27,7 @@
 // holds them independent of its carry.
 #pragma once
 
+#include "adj_tables.h"
 #include "ct_model.cuh"
 
 namespace sqsm {
@@ -155,67 +156,126 @@ SQSM_DEV void predict_factor(const T* F, const T* N, const T* SQ, T* Nm) {
   take_lower<T, NX, 2 * NX>(P, Nm);
 }
 
-// Covariance quantities of the Kalman step k (t = k-1) from the filter
-// output at k-1: m^- = F m + c, P^- = N^- N^-^T, S = H P^- H^T + Omega,
-// W = S^{-1}, U = P^- H^T, K = U W, v = y - H m^- - d.
+// The Kalman-step quantities the VJP reads, loaded from a KfTab record.
 template <typename T, int NX, int NY>
 struct KfQ {
   T mp[NX], Pp[NX * NX], W[NY * NY], U[NX * NY], K[NX * NY], v[NY], Pprev[NX * NX];
-
-  SQSM_DEV void compute(const Gamma<T, NX, NY>& g, const T* y, const T* mprev, const T* Nprev) {
-    mv<T, NX, NX>(g.F, mprev, mp);
+  SQSM_DEV void load(const T* t) {
+    using KT = KfTab<NX, NY>;
 #pragma unroll
-    for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
-    gram_lower<T, NX>(Nprev, Pprev);
-    T Nm[NX * NX];
-    predict_factor<T, NX>(g.F, Nprev, g.SQ, Nm);
-    gram_lower<T, NX>(Nm, Pp);
-    mmt<T, NX, NX, NY>(Pp, g.H, U);                  // P^- H^T
-    T S[NY * NY];
-    mm<T, NY, NX, NY>(g.H, U, S);                    // H P^- H^T
-    T R[NY * NY];
-    gram_lower<T, NY>(g.SR, R);
+    for (int i = 0; i < NX; ++i) mp[i] = t[KT::mp + i];
 #pragma unroll
-    for (int i = 0; i < NY * NY; ++i) S[i] += R[i];
-    // W = S^{-1} through its Cholesky factor
-    T Ls[NY * NY];
-#pragma unroll
-    for (int i = 0; i < NY * NY; ++i) Ls[i] = S[i];
-    chol_inplace<NY>(Ls);
-    T Li[NY * NY];
-    inv_lower<T, NY>(Ls, Li);
-    mtm<T, NY, NY, NY>(Li, Li, W);
-    mm<T, NX, NY, NY>(U, W, K);
-#pragma unroll
-    for (int i = 0; i < NY; ++i) {
-      T s = y[i] - g.d[i];
-#pragma unroll
-      for (int k = 0; k < NX; ++k) s -= g.H[i * NX + k] * mp[k];
-      v[i] = s;
+    for (int i = 0; i < NX * NX; ++i) {
+      Pp[i] = t[KT::Pp + i];
+      Pprev[i] = t[KT::Pprev + i];
     }
-  }
-
-  template <int N>
-  SQSM_DEV static void chol_inplace(T* A) {
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T s = A[j * N + j];
+    for (int i = 0; i < NY * NY; ++i) W[i] = t[KT::W + i];
 #pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[j * N + k] * A[j * N + k];
-      const T d = sq_sqrt(s);
-      A[j * N + j] = d;
-#pragma unroll
-      for (int i = j + 1; i < N; ++i) {
-        T t = A[i * N + j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) t -= A[i * N + k] * A[j * N + k];
-        A[i * N + j] = t / d;
-      }
-#pragma unroll
-      for (int i = 0; i < j; ++i) A[i * N + j] = T(0);
+    for (int i = 0; i < NX * NY; ++i) {
+      U[i] = t[KT::U + i];
+      K[i] = t[KT::K + i];
     }
+#pragma unroll
+    for (int i = 0; i < NY; ++i) v[i] = t[KT::v + i];
   }
 };
+
+// Both tables of one step from its linearised model g, observation y, the
+// filter output (mf, Nf) at row e and the smoother output (msn, Nsn) at row
+// e + 1.  The prediction (m^-, N^-) is shared by the Kalman and RTS steps.
+template <typename T, int NX, int NY>
+SQSM_DEV void adj_step_tables(const Gamma<T, NX, NY>& g, const T* y, const T* mf, const T* Nf,
+                              const T* msn, const T* Nsn, T* kt, T* rt) {
+  using KT = KfTab<NX, NY>;
+  using RT = RtsTab<NX>;
+  T mp[NX];
+  mv<T, NX, NX>(g.F, mf, mp);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
+  T Nm[NX * NX], Pp[NX * NX], Pf[NX * NX];
+  predict_factor<T, NX>(g.F, Nf, g.SQ, Nm);
+  gram_lower<T, NX>(Nm, Pp);
+  gram_lower<T, NX>(Nf, Pf);
+  // Kalman step
+  T U[NX * NY], S[NY * NY], R[NY * NY];
+  mmt<T, NX, NX, NY>(Pp, g.H, U);                  // P^- H^T
+  mm<T, NY, NX, NY>(g.H, U, S);                    // H P^- H^T
+  gram_lower<T, NY>(g.SR, R);
+#pragma unroll
+  for (int i = 0; i < NY * NY; ++i) S[i] += R[i];
+  chol_inplace<T, NY>(S);                          // W = S^{-1} from its factor
+  T Si[NY * NY], W[NY * NY], K[NX * NY], v[NY];
+  inv_lower<T, NY>(S, Si);
+  mtm<T, NY, NY, NY>(Si, Si, W);
+  mm<T, NX, NY, NY>(U, W, K);
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    T a = y[i] - g.d[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) a -= g.H[i * NX + k] * mp[k];
+    v[i] = a;
+  }
+  // fixed parts of the backward map
+  T KH[NX * NX];
+  mm<T, NX, NY, NX>(K, g.H, KH);
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) KH[i] = ((i / NX) == (i % NX) ? T(1) : T(0)) - KH[i];
+  mm<T, NX, NX, NX>(KH, g.F, kt + KT::A);
+  T HF[NY * NX], al[NY], WHF[NY * NX];
+  mm<T, NY, NX, NX>(g.H, g.F, HF);
+  mv<T, NY, NY>(W, v, al);
+  mtv<T, NY, NX>(HF, al, kt + KT::w);
+  mm<T, NY, NY, NX>(W, HF, WHF);
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T a = T(0);
+#pragma unroll
+      for (int k = 0; k < NY; ++k) a += HF[k * NX + i] * WHF[k * NX + j];
+      kt[KT::C + i * NX + j] = a - kt[KT::w + i] * kt[KT::w + j];
+    }
+#pragma unroll
+  for (int i = KT::C + NX * NX; i < KT::head; ++i) kt[i] = T(0);
+#pragma unroll
+  for (int i = 0; i < NY * NY; ++i) kt[KT::W + i] = W[i];
+#pragma unroll
+  for (int i = 0; i < NY; ++i) kt[KT::v + i] = v[i];
+#pragma unroll
+  for (int i = 0; i < NX * NY; ++i) {
+    kt[KT::K + i] = K[i];
+    kt[KT::U + i] = U[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NX; ++i) kt[KT::mp + i] = mp[i];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) {
+    kt[KT::Pp + i] = Pp[i];
+    kt[KT::Pprev + i] = Pf[i];
+  }
+#pragma unroll
+  for (int i = KT::Pprev + NX * NX; i < KT::size; ++i) kt[i] = T(0);
+  // RTS step
+  T Li[NX * NX], PFt[NX * NX];
+  inv_lower<T, NX>(Nm, Li);
+  mtm<T, NX, NX, NX>(Li, Li, rt + RT::Wp);
+  mmt<T, NX, NX, NX>(Pf, g.F, PFt);
+  mm<T, NX, NX, NX>(PFt, rt + RT::Wp, rt + RT::G);
+#pragma unroll
+  for (int i = RT::G + NX * NX; i < RT::head; ++i) rt[i] = T(0);
+  T Ps1[NX * NX];
+  gram_lower<T, NX>(Nsn, Ps1);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) rt[RT::dm + i] = msn[i] - mp[i];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) {
+    rt[RT::Pf + i] = Pf[i];
+    rt[RT::D + i] = Ps1[i] - Pp[i];
+  }
+#pragma unroll
+  for (int i = RT::D + NX * NX; i < RT::size; ++i) rt[i] = T(0);
+}
 
 // Linearised-model cotangent record of one step: F | c | Lambda | H | d | Omega.
 template <int NX, int NY> struct GRec {
@@ -225,18 +285,16 @@ template <int NX, int NY> struct GRec {
 };
 
 // ---------------------------------------------------------------------------
-// Step 1: direct cotangents of the smoother output, per state row.
+// Step 1: direct cotangents of the smoother output of one state row from
+// its factor L = N^s and the cotangent lam = (m-bar, lower N-bar).
 // ---------------------------------------------------------------------------
 template <typename T, int NX>
-__global__ void __launch_bounds__(kBlock)
-adj_direct_kernel(int64_t rows, const T* __restrict__ Ns, const T* __restrict__ lam,
-                  T* __restrict__ dir) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= rows) return;
-  constexpr int X = XRec<NX>::size;
-  T L[NX * NX], Lb[NX * NX];
-  load_lower<T, NX>(Ns + e * NX * NX, L);
-  load_lower<T, NX>(lam + e * X + NX, Lb);
+SQSM_DEV void direct_row(const T* L, const T* lam, T* __restrict__ o) {
+  T Lb[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Lb[i * NX + j] = j <= i ? lam[NX + i * NX + j] : T(0);
   T M[NX * NX];
   mtm<T, NX, NX, NX>(L, Lb, M);                    // L^T Lbar
 #pragma unroll
@@ -248,9 +306,8 @@ adj_direct_kernel(int64_t rows, const T* __restrict__ Ns, const T* __restrict__ 
   T A[NX * NX], P[NX * NX];
   mtm<T, NX, NX, NX>(Li, M, A);                    // L^{-T} Phi
   mm<T, NX, NX, NX>(A, Li, P);                     // ... L^{-1}
-  T* o = dir + e * X;
 #pragma unroll
-  for (int i = 0; i < NX; ++i) o[i] = lam[e * X + i];
+  for (int i = 0; i < NX; ++i) o[i] = lam[i];
 #pragma unroll
   for (int i = 0; i < NX; ++i)
 #pragma unroll
@@ -258,43 +315,18 @@ adj_direct_kernel(int64_t rows, const T* __restrict__ Ns, const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Map builders (one per time step s of sequence b; state rows e = s + b
-// (k - 1) and e + 1 (k)).
+// Maps of one time step from its tables (state rows e = s + b (k - 1) and
+// e + 1 (k) of step s in sequence b).
 // ---------------------------------------------------------------------------
-struct AdjCtx {
-  int64_t gF, gc, gL, gH, gd, gO;   // unused placeholder for layout clarity
-};
-
-// Smoother gain G_k = P^f_k F^T (P^-_{k+1})^{-1} and the intermediate
-// quantities of the RTS step, from the filter output at row e.
-template <typename T, int NX, int NY>
-struct RtsQ {
-  T Pf[NX * NX], mp[NX], Pp[NX * NX], Wp[NX * NX], G[NX * NX];
-  SQSM_DEV void compute(const Gamma<T, NX, NY>& g, const T* mf, const T* Nf) {
-    gram_lower<T, NX>(Nf, Pf);
-    mv<T, NX, NX>(g.F, mf, mp);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) mp[i] += g.c[i];
-    T Nm[NX * NX];
-    predict_factor<T, NX>(g.F, Nf, g.SQ, Nm);
-    gram_lower<T, NX>(Nm, Pp);
-    T Li[NX * NX];
-    inv_lower<T, NX>(Nm, Li);
-    mtm<T, NX, NX, NX>(Li, Li, Wp);
-    T PFt[NX * NX];
-    mmt<T, NX, NX, NX>(Pf, g.F, PFt);
-    mm<T, NX, NX, NX>(PFt, Wp, G);
-  }
-};
 
 // Forward-recurrence map of step s: x(row e) -> x(row e + 1),
 // B = G_{k-1}, r = 0, s = direct_m(e+1), S = direct_P(e+1).
-template <typename T, int NX, int NY>
-SQSM_DEV void smoother_adj_map(const RtsQ<T, NX, NY>& q, const T* dnext, T* mp) {
+template <typename T, int NX>
+SQSM_DEV void smoother_adj_map(const T* G, const T* dnext, T* mp) {
   using R = MapRec<NX>;
 #pragma unroll
   for (int i = 0; i < NX * NX; ++i) {
-    mp[R::B + i] = q.G[i];
+    mp[R::B + i] = G[i];
     mp[R::S + i] = dnext[NX + i];
   }
 #pragma unroll
@@ -305,35 +337,21 @@ SQSM_DEV void smoother_adj_map(const RtsQ<T, NX, NY>& q, const T* dnext, T* mp) 
 }
 
 // Backward-recurrence map of Kalman step k: x(row e + 1) -> x(row e),
-// B = A = (I - K H) F, r = w = F^T H^T W v,
-// s = lbar w + dfilt_m(e), S = -lbar/2 (F^T H^T W H F - w w^T) + dfilt_P(e).
+// B = A, r = w, s = lbar w + dfilt_m(e), S = -lbar/2 C + dfilt_P(e), from
+// the head of the step's KfTab record.
 template <typename T, int NX, int NY>
-SQSM_DEV void filter_adj_map(const KfQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, T lbar,
-                             const T* dprev, T* mp) {
+SQSM_DEV void filter_adj_map(const T* kt, T lbar, const T* dprev, T* mp) {
   using R = MapRec<NX>;
-  T KH[NX * NX];
-  mm<T, NX, NY, NX>(q.K, g.H, KH);
+  using KT = KfTab<NX, NY>;
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) KH[i] = ((i / NX) == (i % NX) ? T(1) : T(0)) - KH[i];
-  mm<T, NX, NX, NX>(KH, g.F, mp + R::B);
-  T HF[NY * NX], al[NY];
-  mm<T, NY, NX, NX>(g.H, g.F, HF);
-  mv<T, NY, NY>(q.W, q.v, al);
-  T w[NX];
-  mtv<T, NY, NX>(HF, al, w);
-  T WHF[NY * NX];
-  mm<T, NY, NY, NX>(q.W, HF, WHF);
+  for (int i = 0; i < NX * NX; ++i) {
+    mp[R::B + i] = kt[KT::A + i];
+    mp[R::S + i] = T(-0.5) * lbar * kt[KT::C + i] + dprev[NX + i];
+  }
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
-    mp[R::r + i] = w[i];
-    mp[R::s + i] = lbar * w[i] + dprev[i];
-#pragma unroll
-    for (int j = 0; j < NX; ++j) {
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < NY; ++k) s += HF[k * NX + i] * WHF[k * NX + j];
-      mp[R::S + i * NX + j] = T(-0.5) * lbar * (s - w[i] * w[j]) + dprev[NX + i * NX + j];
-    }
+    mp[R::r + i] = kt[KT::w + i];
+    mp[R::s + i] = lbar * kt[KT::w + i] + dprev[i];
   }
 }
 
@@ -341,25 +359,24 @@ SQSM_DEV void filter_adj_map(const KfQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g,
 // Local VJPs
 // ---------------------------------------------------------------------------
 
-// RTS step at row e (k < n) with total cotangent x = (mt, Pt): writes the
+// RTS step at row e (k < n) with total cotangent x = (mt, Pt), its RtsTab
+// record rt, transition matrix F and filter mean mf of row e: writes the
 // direct filter cotangents of row e and the smoother part of the
 // linearised-model cotangents of step t (F, c, Lambda).
 template <typename T, int NX, int NY>
-SQSM_DEV void rts_vjp(const RtsQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const T* mf,
-                      const T* msn, const T* Nsn, const T* x, T* dfilt, T* gbar) {
+SQSM_DEV void rts_vjp(const T* rt, const T* F, const T* mf, const T* x, T* dfilt, T* gbar) {
   using GR = GRec<NX, NY>;
+  using RT = RtsTab<NX>;
   const T* mt = x;
   const T* Pt = x + NX;
-  T Ps1[NX * NX];
-  gram_lower<T, NX>(Nsn, Ps1);
-  T dm_[NX], D[NX * NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) dm_[i] = msn[i] - q.mp[i];
-#pragma unroll
-  for (int i = 0; i < NX * NX; ++i) D[i] = Ps1[i] - q.Pp[i];
+  const T* G = rt + RT::G;
+  const T* Wp = rt + RT::Wp;
+  const T* Pf = rt + RT::Pf;
+  const T* dm_ = rt + RT::dm;
+  const T* D = rt + RT::D;
   // Gb = mt dm^T + 2 Pt G D
   T PtG[NX * NX], Gb[NX * NX], tmp[NX * NX];
-  mm<T, NX, NX, NX>(Pt, q.G, PtG);
+  mm<T, NX, NX, NX>(Pt, G, PtG);
   mm<T, NX, NX, NX>(PtG, D, tmp);
 #pragma unroll
   for (int i = 0; i < NX; ++i)
@@ -367,13 +384,13 @@ SQSM_DEV void rts_vjp(const RtsQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const
     for (int j = 0; j < NX; ++j) Gb[i * NX + j] = mt[i] * dm_[j] + T(2) * tmp[i * NX + j];
   // dmp = -G^T mt ; dPp = -G^T Pt G - sym(G^T Gb Wp)
   T dmp[NX];
-  mtv<T, NX, NX>(q.G, mt, dmp);
+  mtv<T, NX, NX>(G, mt, dmp);
 #pragma unroll
   for (int i = 0; i < NX; ++i) dmp[i] = -dmp[i];
   T dPp[NX * NX], GtPtG[NX * NX], GtGb[NX * NX], GtGbW[NX * NX];
-  mtm<T, NX, NX, NX>(q.G, PtG, GtPtG);
-  mtm<T, NX, NX, NX>(q.G, Gb, GtGb);
-  mm<T, NX, NX, NX>(GtGb, q.Wp, GtGbW);
+  mtm<T, NX, NX, NX>(G, PtG, GtPtG);
+  mtm<T, NX, NX, NX>(G, Gb, GtGb);
+  mm<T, NX, NX, NX>(GtGb, Wp, GtGbW);
 #pragma unroll
   for (int i = 0; i < NX; ++i)
 #pragma unroll
@@ -381,12 +398,12 @@ SQSM_DEV void rts_vjp(const RtsQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const
       dPp[i * NX + j] = -GtPtG[i * NX + j] - T(0.5) * (GtGbW[i * NX + j] + GtGbW[j * NX + i]);
   // direct filter cotangents: dmf = mt + F^T dmp ; dPf = Pt + sym(Gb Wp F) + F^T dPp F
   T Ftd[NX];
-  mtv<T, NX, NX>(g.F, dmp, Ftd);
+  mtv<T, NX, NX>(F, dmp, Ftd);
   T GbW[NX * NX], GbWF[NX * NX], FtdPp[NX * NX], FtdPpF[NX * NX];
-  mm<T, NX, NX, NX>(Gb, q.Wp, GbW);
-  mm<T, NX, NX, NX>(GbW, g.F, GbWF);
-  mtm<T, NX, NX, NX>(g.F, dPp, FtdPp);
-  mm<T, NX, NX, NX>(FtdPp, g.F, FtdPpF);
+  mm<T, NX, NX, NX>(Gb, Wp, GbW);
+  mm<T, NX, NX, NX>(GbW, F, GbWF);
+  mtm<T, NX, NX, NX>(F, dPp, FtdPp);
+  mm<T, NX, NX, NX>(FtdPp, F, FtdPpF);
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
     dfilt[i] = mt[i] + Ftd[i];
@@ -397,9 +414,9 @@ SQSM_DEV void rts_vjp(const RtsQ<T, NX, NY>& q, const Gamma<T, NX, NY>& g, const
   }
   // gF = Wp Gb^T Pf + dmp mf^T + 2 dPp F Pf ; gc = dmp ; gL = dPp
   T WGbt[NX * NX], A1[NX * NX], FPf[NX * NX], A2[NX * NX];
-  mmt<T, NX, NX, NX>(q.Wp, Gb, WGbt);
-  mm<T, NX, NX, NX>(WGbt, q.Pf, A1);
-  mm<T, NX, NX, NX>(g.F, q.Pf, FPf);
+  mmt<T, NX, NX, NX>(Wp, Gb, WGbt);
+  mm<T, NX, NX, NX>(WGbt, Pf, A1);
+  mm<T, NX, NX, NX>(F, Pf, FPf);
   mm<T, NX, NX, NX>(dPp, FPf, A2);
 #pragma unroll
   for (int i = 0; i < NX; ++i) {

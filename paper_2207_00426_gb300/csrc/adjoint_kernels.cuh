@@ -8,7 +8,9 @@
 //   dir      direct cotangents (m, P) of the smoother output,
 //   dfilt    direct cotangents (m, P) of the filter output (from the RTS VJP),
 //   gbar     cotangents of the linearised model (GRec, per step),
-//   lam      cotangent of the nominal trajectory (m, lower N).
+//   lam      cotangent of the nominal trajectory (m, lower N),
+//   ktab, rtab, stab  per-step KfTab / RtsTab / SlrTab records (written
+//            once per evaluation).
 #pragma once
 
 #include "adjoint.cuh"
@@ -19,6 +21,7 @@ struct AdjBufs {
   const void *mf, *Nf, *ms, *Ns, *nom_m, *nom_N, *y;
   const void* gam;   // linearised model, PRec records
   void *dir, *dfilt, *gbar;
+  void *ktab, *rtab, *stab;
 };
 
 template <typename T>
@@ -26,19 +29,69 @@ SQSM_DEV GammaPacked<T> gview(const AdjBufs& a) {
   return GammaPacked<T>{(T*)a.gam};
 }
 
+// --------------------------- per-step tables --------------------------------
+
+// One thread per time step (leaf chunks of `leaf` steps): the KfTab, RtsTab
+// and SlrTab records of the step from the final linearisation, its filter
+// and smoother output, and the nominal trajectory.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_tables_kernel(DevLevel lv, int leaf, const CTParams<T>* __restrict__ Pp, AdjBufs a) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ch = tid / leaf;
+  if (ch >= lv.n_chunks) return;
+  const int j = (int)(tid - ch * leaf);
+  if (j >= lv.count[ch]) return;
+  constexpr int NX = 5, NY = 2;
+  using KT = KfTab<NX, NY>;
+  using RT = RtsTab<NX>;
+  using ST = SlrTab<NX, NY>;
+  const int64_t s = lv.first[ch] + j, e = s + lv.seq[ch];
+  {
+    Gamma<T, NX, NY> g;
+    g.load_all(gview<T>(a), s);
+    T ys[NY], mf[NX], Nf[NX * NX], msn[NX], Nsn[NX * NX];
+    load<T, NY>((const T*)a.y + s * NY, ys);
+    load<T, NX>((const T*)a.mf + e * NX, mf);
+    load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nf);
+    load<T, NX>((const T*)a.ms + (e + 1) * NX, msn);
+    load_lower<T, NX>((const T*)a.Ns + (e + 1) * NX * NX, Nsn);
+    T kt[KT::size], rt[RT::size];
+    adj_step_tables<T, NX, NY>(g, ys, mf, Nf, msn, Nsn, kt, rt);
+    vstore<T, KT::size>((T*)a.ktab + s * KT::size, kt);
+    vstore<T, RT::size>((T*)a.rtab + s * RT::size, rt);
+  }
+  const CTParams<T> P = *Pp;
+  T st[ST::size];
+#pragma unroll
+  for (int i = 0; i < ST::size; ++i) st[i] = T(0);
+  {
+    T m[NX], N[NX * NX];
+    load<T, NX>((const T*)a.nom_m + e * NX, m);
+    load_lower<T, NX>((const T*)a.nom_N + e * NX * NX, N);
+    const Turn<T> tm = turn(m[4], P.dt);
+    cubature_fwd<T, NX, true>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
+                              st + ST::Gf, st + ST::sf);
+  }
+  {
+    T m[NX], N[NX * NX];
+    load<T, NX>((const T*)a.nom_m + (e + 1) * NX, m);
+    load_lower<T, NX>((const T*)a.nom_N + (e + 1) * NX * NX, N);
+    cubature_fwd<T, NY, false>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
+                               st + ST::Gh, st + ST::sh);
+  }
+  vstore<T, ST::size>((T*)a.stab + s * ST::size, st);
+}
+
 // --------------------------- smoother adjoint (forward in time) -----------
 
 template <typename T>
 SQSM_DEV void build_smoother_map(const AdjBufs& a, int64_t s, int64_t e, bool first, T* mp) {
-  constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
-  Gamma<T, NX, NY> g;
-  g.load_transition(gview<T>(a), s);
-  T mf[NX], Nf[NX * NX];
-  load<T, NX>((const T*)a.mf + e * NX, mf);
-  load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nf);
-  RtsQ<T, NX, NY> q;
-  q.compute(g, mf, Nf);
-  smoother_adj_map<T, NX, NY>(q, (const T*)a.dir + (e + 1) * X, mp);
+  constexpr int NX = 5, X = XRec<NX>::size;
+  using RT = RtsTab<NX>;
+  T G[RT::head];
+  vload<T, RT::head>((const T*)a.rtab + s * RT::size, G);
+  smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
   if (first) {
     T x0[X];
     load<T, X>((const T*)a.dir + e * X, x0);
@@ -57,55 +110,68 @@ adj_smoother_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T* __restrict__ items) 
   const int cnt = lv.count[c];
   const int64_t off = sq.offsets[b];
   T agg[REC], mp[REC], tmp[REC];
-  for (int j = 0; j < cnt; ++j) {
+  build_smoother_map<T>(a, s0, s0 + b, s0 == off, agg);
+  for (int j = 1; j < cnt; ++j) {
     const int64_t s = s0 + j;
-    build_smoother_map<T>(a, s, s + b, s == off, j == 0 ? agg : mp);
-    if (j > 0) {
-      map_compose<T, 5>(agg, mp, tmp);
-      copy<T, REC>(tmp, agg);
-    }
+    build_smoother_map<T>(a, s, s + b, false, mp);
+    map_compose<T, 5>(agg, mp, tmp);
+    copy<T, REC>(tmp, agg);
   }
   vstore<T, REC>(items + c * REC, agg);
 }
 
+// One thread per time step (leaf chunks of `leaf` steps): the cotangent
+// entering step j of a chunk is the chunk's carry (or the sequence's first
+// direct cotangent) pushed through the maps of steps 0 .. j-1 of the chunk;
+// then the RTS VJP of the step.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-adj_smoother_leaf_down(DevLevel lv, DevSeqs sq, AdjBufs a, const T* __restrict__ carry,
+adj_smoother_leaf_down(DevLevel lv, int leaf, DevSeqs sq, AdjBufs a, const T* __restrict__ carry,
                        const int* __restrict__ flag) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = tid / leaf;
   if (c >= lv.n_chunks) return;
+  const int jj = (int)(tid - c * leaf);
+  if (jj >= lv.count[c]) return;
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
+  using RT = RtsTab<NX>;
   const int b = lv.seq[c];
   const int64_t s0 = lv.first[c];
-  const int cnt = lv.count[c];
-  const int64_t last = sq.offsets[b + 1] - 1;
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
-  for (int j = 0; j < cnt; ++j) {
-    const int64_t s = s0 + j, e = s + b;
-    Gamma<T, NX, NY> g;
-    g.load_transition(gview<T>(a), s);
-    T mf[NX], Nf[NX * NX], msn[NX], Nsn[NX * NX];
-    load<T, NX>((const T*)a.mf + e * NX, mf);
-    load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nf);
-    load<T, NX>((const T*)a.ms + (e + 1) * NX, msn);
-    load_lower<T, NX>((const T*)a.Ns + (e + 1) * NX * NX, Nsn);
-    RtsQ<T, NX, NY> q;
-    q.compute(g, mf, Nf);
-    T df[X], gb[GR::size];
-    rts_vjp<T, NX, NY>(q, g, mf, msn, Nsn, x, df, gb);
-    store<T, X>((T*)a.dfilt + e * X, df);
-    T* go = (T*)a.gbar + s * GR::size;
-    store<T, NX * NX>(go + GR::F, gb + GR::F);
-    store<T, NX>(go + GR::c, gb + GR::c);
-    store<T, NX * NX>(go + GR::L, gb + GR::L);
-    T mp[REC], xn[X];
-    smoother_adj_map<T, NX, NY>(q, (const T*)a.dir + (e + 1) * X, mp);
+  for (int j = 0; j < jj; ++j) {
+    const int64_t e = s0 + j + b;
+    T G[RT::head], mp[REC], xn[X];
+    vload<T, RT::head>((const T*)a.rtab + (s0 + j) * RT::size, G);
+    smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
     map_apply<T, NX>(mp, x, xn);
     copy<T, X>(xn, x);
-    if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
+  }
+  const int64_t s = s0 + jj, e = s + b;
+  Gamma<T, NX, NY> g;
+  g.load_transition(gview<T>(a), s);
+  T mf[NX];
+  load<T, NX>((const T*)a.mf + e * NX, mf);
+  T df[X], gb[GR::size];
+  // FP32 holds the record in registers; FP64 reads it where it is used
+  // (twice the registers per value would spill).
+  const T* rtg = (const T*)a.rtab + s * RT::size;
+  T rtr[sizeof(T) == 4 ? RT::size : 4];
+  if constexpr (sizeof(T) == 4) vload<T, RT::size>(rtg, rtr);
+  const T* rt = sizeof(T) == 4 ? rtr : rtg;
+  rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
+  store<T, X>((T*)a.dfilt + e * X, df);
+  T* go = (T*)a.gbar + s * GR::size;
+  store<T, NX * NX>(go + GR::F, gb + GR::F);
+  store<T, NX>(go + GR::c, gb + GR::c);
+  store<T, NX * NX>(go + GR::L, gb + GR::L);
+  if (s == sq.offsets[b + 1] - 1) {   // k = n: dmf_n = x_n
+    T mp[REC], xn[X];
+    smoother_adj_map<T, NX>(rt + RT::G, (const T*)a.dir + (e + 1) * X, mp);
+    map_apply<T, NX>(mp, x, xn);
+    store<T, X>((T*)a.dfilt + (e + 1) * X, xn);
   }
 }
 
@@ -114,15 +180,10 @@ adj_smoother_leaf_down(DevLevel lv, DevSeqs sq, AdjBufs a, const T* __restrict__
 template <typename T>
 SQSM_DEV void build_filter_map(const AdjBufs& a, int64_t s, int64_t e, bool lastb, T lbar, T* mp) {
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
-  Gamma<T, NX, NY> g;
-  g.load_all(gview<T>(a), s);
-  T ys[NY], mprev[NX], Nprev[NX * NX];
-  load<T, NY>((const T*)a.y + s * NY, ys);
-  load<T, NX>((const T*)a.mf + e * NX, mprev);
-  load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nprev);
-  KfQ<T, NX, NY> q;
-  q.compute(g, ys, mprev, Nprev);
-  filter_adj_map<T, NX, NY>(q, g, lbar, (const T*)a.dfilt + e * X, mp);
+  using KT = KfTab<NX, NY>;
+  T h[KT::head];
+  vload<T, KT::head>((const T*)a.ktab + s * KT::size, h);
+  filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
   if (lastb) {
     T xn[X];
     load<T, X>((const T*)a.dfilt + (e + 1) * X, xn);
@@ -141,51 +202,59 @@ adj_filter_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, T* __restrict__ i
   const int cnt = lv.count[c];
   const int64_t last = sq.offsets[b + 1] - 1;
   T agg[REC], mp[REC], tmp[REC];
-  for (int j = cnt - 1; j >= 0; --j) {
+  build_filter_map<T>(a, s0 + cnt - 1, s0 + cnt - 1 + b, s0 + cnt - 1 == last, lbar, agg);
+  for (int j = cnt - 2; j >= 0; --j) {
     const int64_t s = s0 + j;
-    build_filter_map<T>(a, s, s + b, s == last, lbar, j == cnt - 1 ? agg : mp);
-    if (j < cnt - 1) {
-      map_compose<T, 5>(agg, mp, tmp);
-      copy<T, REC>(tmp, agg);
-    }
+    build_filter_map<T>(a, s, s + b, false, lbar, mp);
+    map_compose<T, 5>(agg, mp, tmp);
+    copy<T, REC>(tmp, agg);
   }
   vstore<T, REC>(items + c * REC, agg);
 }
 
+// One thread per time step: the cotangent entering step j of a chunk (of
+// its output row) is the chunk's carry (or the sequence's last filter
+// cotangent) pushed back through the maps of steps cnt-1 .. j+1; then the
+// Kalman-step VJP of the step.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-adj_filter_leaf_down(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, const T* __restrict__ carry,
-                     const int* __restrict__ flag) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+adj_filter_leaf_down(DevLevel lv, int leaf, DevSeqs sq, AdjBufs a, T lbar,
+                     const T* __restrict__ carry, const int* __restrict__ flag) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = tid / leaf;
   if (c >= lv.n_chunks) return;
+  const int jj = (int)(tid - c * leaf);
+  const int cnt = lv.count[c];
+  if (jj >= cnt) return;
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
+  using KT = KfTab<NX, NY>;
   const int b = lv.seq[c];
   const int64_t s0 = lv.first[c];
-  const int cnt = lv.count[c];
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
-  for (int j = cnt - 1; j >= 0; --j) {
-    const int64_t s = s0 + j, e = s + b;
-    Gamma<T, NX, NY> g;
-    g.load_all(gview<T>(a), s);
-    T ys[NY], mprev[NX], Nprev[NX * NX];
-    load<T, NY>((const T*)a.y + s * NY, ys);
-    load<T, NX>((const T*)a.mf + e * NX, mprev);
-    load_lower<T, NX>((const T*)a.Nf + e * NX * NX, Nprev);
-    KfQ<T, NX, NY> q;
-    q.compute(g, ys, mprev, Nprev);
-    T gb[GR::size];
-    T* go = (T*)a.gbar + s * GR::size;
-    load<T, GR::size>(go, gb);
-    kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
-    store<T, GR::size>(go, gb);
-    T mp[REC], xn[X];
-    filter_adj_map<T, NX, NY>(q, g, lbar, (const T*)a.dfilt + e * X, mp);
+  for (int j = cnt - 1; j > jj; --j) {
+    const int64_t e = s0 + j + b;
+    T h[KT::head], mp[REC], xn[X];
+    vload<T, KT::head>((const T*)a.ktab + (s0 + j) * KT::size, h);
+    filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
     map_apply<T, NX>(mp, x, xn);
     copy<T, X>(xn, x);
   }
+  const int64_t s = s0 + jj, e = s + b;
+  Gamma<T, NX, NY> g;
+  g.load_all(gview<T>(a), s);
+  T kt[KT::size], mprev[NX];
+  vload<T, KT::size>((const T*)a.ktab + s * KT::size, kt);
+  load<T, NX>((const T*)a.mf + e * NX, mprev);
+  KfQ<T, NX, NY> q;
+  q.load(kt);
+  T gb[GR::size];
+  T* go = (T*)a.gbar + s * GR::size;
+  load<T, GR::size>(go, gb);
+  kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
+  store<T, GR::size>(go, gb);
 }
 
 // --------------------------- upper levels (both directions) ---------------
@@ -301,78 +370,159 @@ adj_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
   fout[i] = head ? flag : 1;
 }
 
+// Top of an adjoint scan: one block per sequence scans the sequence's items
+// of the level (at most KS of them, in scan order) with Kogge-Stone in
+// shared memory.  The first item in scan order holds the constant boundary
+// map (flag 0), so every prefix is a constant map and the cotangent
+// entering item t is the constant part (s, S) of the composition of the
+// items before it.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__((KsMax<T, MapRec<5>::size>::value))
+adj_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
+           T* __restrict__ carry_out, int* __restrict__ flag_out) {
+  constexpr int REC = MapRec<5>::size, KS = KsMax<T, REC>::value, X = XRec<5>::size;
+  using R = MapRec<5>;
+  __shared__ __align__(16) T S[KS * REC];
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int64_t i0 = seq_item_off[b];
+  const int c = (int)(seq_item_off[b + 1] - i0);
+  const int64_t i = i0 + (FWD ? t : c - 1 - t);
+  T mine[REC], tmp[REC];
+  if (t < c) vload<T, REC>(items + i * REC, mine);
+  for (int d = 1; d < c; d <<= 1) {
+    if (t < c) vstore<T, REC>(S + t * REC, mine);
+    __syncthreads();
+    if (t < c && t >= d) {
+      map_compose<T, 5>(S + (t - d) * REC, mine, tmp);
+      copy<T, REC>(tmp, mine);
+    }
+    __syncthreads();
+  }
+  if (t < c) vstore<T, REC>(S + t * REC, mine);
+  __syncthreads();
+  if (t < c) {
+    if (t > 0) {
+      const T* p = S + (t - 1) * REC;
+      T* co = carry_out + i * X;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) co[k] = p[R::s + k];
+#pragma unroll
+      for (int k = 0; k < 25; ++k) co[5 + k] = p[R::S + k];
+    }
+    flag_out[i] = t > 0 ? 1 : 0;
+  }
+}
+
 // --------------------------- SLR VJP and reductions ------------------------
 
-// One thread per smoother leaf chunk (state rows): nominal-trajectory
-// cotangent of row k from the transition regression of step k (k < n) and
-// the observation regression of step k - 1 (k >= 1); theta partial sums.
+// Nominal-trajectory cotangent lam of state row e of sequence b from the
+// transition regression of step k (k < n) and the observation regression of
+// step k - 1 (k >= 1), the row's theta partials added to th, and the direct
+// cotangents of the row that the next iteration starts from (step 1 applied
+// to lam); the regressions' forward quantities come from the SlrTab records.
 template <typename T>
-__global__ void __launch_bounds__(kBlock)
-adj_slr_kernel(DevLevel lv, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
-               T* __restrict__ lam_out, double* __restrict__ th_partial) {
-  const int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (ch >= lv.n_chunks) return;
+SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>* __restrict__ Pp,
+                          const AdjBufs& a, T* __restrict__ lam_out, double* th) {
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
   using GR = GRec<NX, NY>;
+  using ST = SlrTab<NX, NY>;
   const CTParams<T> P = *Pp;
-  const int b = lv.seq[ch];
-  const int64_t so = sq.offsets[b] + b;
+  const int64_t k = e - (sq.offsets[b] + b);
   const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
-  T Q[NX * NX];
-  gram_lower<T, NX>(P.SQ, Q);
-  double th[3] = {0.0, 0.0, 0.0};
-  for (int j = 0; j < lv.count[ch]; ++j) {
-    const int64_t e = lv.first[ch] + j;
-    const int64_t k = e - so;
-    T m[NX], N[NX * NX], mb[NX], Nb[NX * NX];
-    load<T, NX>((const T*)a.nom_m + e * NX, m);
-    load_lower<T, NX>((const T*)a.nom_N + e * NX * NX, N);
+  T m[NX], N[NX * NX], mb[NX], Nb[NX * NX];
+  load<T, NX>((const T*)a.nom_m + e * NX, m);
+  load_lower<T, NX>((const T*)a.nom_N + e * NX * NX, N);
 #pragma unroll
-    for (int i = 0; i < NX; ++i) mb[i] = T(0);
+  for (int i = 0; i < NX; ++i) mb[i] = T(0);
 #pragma unroll
-    for (int i = 0; i < NX * NX; ++i) Nb[i] = T(0);
-    if (k < nb) {
-      const T* gb = (const T*)a.gbar + (sq.offsets[b] + k) * GR::size;
-      T G[NX * NX], sres[NX * NX], Lb[NX * NX];
-      const Turn<T> tm = turn(m[4], P.dt);
-      cubature_fwd<T, NX, true>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
-                                G, sres);
+  for (int i = 0; i < NX * NX; ++i) Nb[i] = T(0);
+  if (k < nb) {
+    const int64_t s = sq.offsets[b] + k;
+    const T* gb = (const T*)a.gbar + s * GR::size;
+    T t[ST::obs];
+    vload<T, ST::obs>((const T*)a.stab + s * ST::size, t);
+    T Lb[NX * NX];
 #pragma unroll
-      for (int i = 0; i < NX; ++i)
+    for (int i = 0; i < NX; ++i)
 #pragma unroll
-        for (int q = 0; q < NX; ++q) Lb[i * NX + q] = T(0.5) * (gb[GR::L + i * NX + q] + gb[GR::L + q * NX + i]);
-      cubature_vjp<T, NX>(m, N, G, sres, gb + GR::F, gb + GR::c, Lb,
-                          [&](const T* xx, T* J) { ct_jac_f(P, xx, J); }, mb, Nb);
-      double tq = 0.0;
+      for (int q = 0; q < NX; ++q) Lb[i * NX + q] = T(0.5) * (gb[GR::L + i * NX + q] + gb[GR::L + q * NX + i]);
+    cubature_vjp<T, NX>(m, N, t + ST::Gf, t + ST::sf, gb + GR::F, gb + GR::c, Lb,
+                        [&](const T* xx, T* J) { ct_jac_f(P, xx, J); }, mb, Nb);
+    T Q[NX * NX];
+    gram_lower<T, NX>(P.SQ, Q);
+    double tq = 0.0;
 #pragma unroll
-      for (int i = 0; i < NX * NX; ++i) tq += (double)Lb[i] * (double)Q[i];
-      const double t44 = (double)Lb[24] * (double)Q[24];
-      th[1] += tq - t44;
-      th[2] += t44;
-    }
-    if (k >= 1) {
-      const T* gb = (const T*)a.gbar + (sq.offsets[b] + k - 1) * GR::size;
-      T G[NY * NX], sres[NY * NX], Lb[NY * NY];
-      cubature_fwd<T, NY, false>(m, N, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
-                                 G, sres);
-#pragma unroll
-      for (int i = 0; i < NY; ++i)
-#pragma unroll
-        for (int q = 0; q < NY; ++q) Lb[i * NY + q] = T(0.5) * (gb[GR::O + i * NY + q] + gb[GR::O + q * NY + i]);
-      cubature_vjp<T, NY>(m, N, G, sres, gb + GR::H, gb + GR::d, Lb,
-                          [&](const T* xx, T* J) { ct_jac_h(P, xx, J); }, mb, Nb);
-      th[0] += 2.0 * (double)P.sigma * (double)P.sigma * ((double)Lb[0] + (double)Lb[3]);
-    }
-    T* o = lam_out + e * X;
-    store<T, NX>(o, mb);
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = 0; q < NX; ++q) o[NX + r * NX + q] = q <= r ? Nb[r * NX + q] : T(0);
+    for (int i = 0; i < NX * NX; ++i) tq += (double)Lb[i] * (double)Q[i];
+    const double t44 = (double)Lb[24] * (double)Q[24];
+    th[1] += tq - t44;
+    th[2] += t44;
   }
-  th_partial[ch * 3 + 0] = th[0];
-  th_partial[ch * 3 + 1] = th[1];
-  th_partial[ch * 3 + 2] = th[2];
+  if (k >= 1) {
+    const int64_t s = sq.offsets[b] + k - 1;
+    const T* gb = (const T*)a.gbar + s * GR::size;
+    T t[ST::size - ST::obs];
+    vload<T, ST::size - ST::obs>((const T*)a.stab + s * ST::size + ST::obs, t);
+    T Lb[NY * NY];
+#pragma unroll
+    for (int i = 0; i < NY; ++i)
+#pragma unroll
+      for (int q = 0; q < NY; ++q) Lb[i * NY + q] = T(0.5) * (gb[GR::O + i * NY + q] + gb[GR::O + q * NY + i]);
+    cubature_vjp<T, NY>(m, N, t + ST::Gh - ST::obs, t + ST::sh - ST::obs, gb + GR::H, gb + GR::d, Lb,
+                        [&](const T* xx, T* J) { ct_jac_h(P, xx, J); }, mb, Nb);
+    th[0] += 2.0 * (double)P.sigma * (double)P.sigma * ((double)Lb[0] + (double)Lb[3]);
+  }
+  T o[X];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) o[i] = mb[i];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = 0; q < NX; ++q) o[NX + r * NX + q] = q <= r ? Nb[r * NX + q] : T(0);
+  store<T, X>(lam_out + e * X, o);
+  // the next iteration's direct cotangents of this row (step 1)
+  T L[NX * NX], d[X];
+  load_lower<T, NX>((const T*)a.Ns + e * NX * NX, L);
+  direct_row<T, NX>(L, o, d);
+  store<T, X>((T*)a.dir + e * X, d);
+}
+
+// Sum of three values over the block (kBlock threads) in a fixed order,
+// written by thread 0 to out[0..2].
+SQSM_DEV void block_sum3(double* v, double* __restrict__ out) {
+  __shared__ double part[kBlock / 32][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) part[w][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < kBlock / 32; ++q) t += part[q][j];
+      out[j] = t;
+    }
+}
+
+// One thread per state row (smoother leaf chunks of `leaf` rows); every
+// thread of the block takes part in the block's theta sum (rows past the
+// end add zero), written to th_partial[3 * block].
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
+               T* __restrict__ lam_out, double* __restrict__ th_partial) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ch = tid / leaf;
+  const int jr = (int)(tid - ch * leaf);
+  double th[3] = {0.0, 0.0, 0.0};
+  if (ch < lv.n_chunks && jr < lv.count[ch])
+    adj_slr_row<T>(lv.first[ch] + jr, lv.seq[ch], sq, Pp, a, lam_out, th);
+  block_sum3(th, th_partial + 3 * blockIdx.x);
 }
 
 // Fixed-order sums of the theta partials (one block): out[j] = sign * sum.

@@ -366,12 +366,17 @@ bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
   g.lam_a = w->mem.get(es * X * rows);
   g.lam_b = w->mem.get(es * X * rows);
   g.gbar = w->mem.get(es * grec * steps);
-  g.th_partial = (double*)w->mem.get(sizeof(double) * 3 * p->smth.lv[0].n_chunks);
+  g.ktab = w->mem.get(es * KfTab<5, 2>::size * steps);
+  g.rtab = w->mem.get(es * RtsTab<5>::size * steps);
+  g.stab = w->mem.get(es * SlrTab<5, 2>::size * steps);
+  // theta partial sums, one triple per block of the SLR VJP kernel
+  g.th_partial = (double*)w->mem.get(
+      sizeof(double) * 3 * std::max<int64_t>(1, grid_for(p->smth.lv[0].n_chunks * p->L0)));
   g.ll = (double*)w->mem.get(sizeof(double) * p->B);
   g.change_words = w->mem.get(2 * sizeof(unsigned));
   if (!g.change_words) return false;
   if (!g.nom_m || !g.nom_N || !g.ms2 || !g.Ns2 || !g.dir || !g.dfilt || !g.lam_a || !g.lam_b ||
-      !g.gbar || !g.th_partial || !g.ll)
+      !g.gbar || !g.ktab || !g.rtab || !g.stab || !g.th_partial || !g.ll)
     return false;
   if (!alloc_scan(w->mem, p->filt, w->adj_scan, es * (2 * nx * nx + 2 * nx), es * X)) return false;
   w->adj_ready = true;

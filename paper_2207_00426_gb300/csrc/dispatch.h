@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "adj_tables.h"
 #include "engine.cuh"
 
 namespace sqsm {
@@ -94,6 +95,7 @@ struct AdjArgs {
   int iters;                          // adjoint fixed-point iterations
   void *nom_m, *nom_N, *ms2, *Ns2;    // linearisation point, its smoother output
   void *dir, *dfilt, *gbar, *lam_a, *lam_b;
+  void *ktab, *rtab, *stab;           // per-step KfTab / RtsTab / SlrTab records
   double *th_partial, *ll, *nll, *grad, *change;
   void* change_words;                 // two words for the change reduction
 };

@@ -165,6 +165,30 @@ SQSM_DEV void mtv(const T* A, const T* x, T* y) {
   }
 }
 
+// Lower Cholesky factor in place (upper part cleared).  A non-positive pivot
+// gives NaN, as the standard form does when a covariance loses definiteness.
+template <typename T, int N>
+SQSM_DEV void chol_inplace(T* A) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T s = A[j * N + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= A[j * N + k] * A[j * N + k];
+    const T d = sq_sqrt(s);
+    const T inv = T(1) / d;
+    A[j * N + j] = d;
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      T t = A[i * N + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= A[i * N + k] * A[j * N + k];
+      A[i * N + j] = t * inv;
+    }
+#pragma unroll
+    for (int i = 0; i < j; ++i) A[i * N + j] = T(0);
+  }
+}
+
 // Triangular solves divide once per diagonal entry and multiply by the
 // reciprocal elsewhere.
 
