@@ -16,7 +16,10 @@ taken here are:
   omega, whose lower Cholesky factor is written in closed form;
 * bearings h_i(x) = atan2(p_y - s_y^i, p_x - s_x^i) from sensors
   (-1.5, 0.5) and (1, 1), noise sigma^2 I2;
-* parameters theta = (log sigma, log q_c, log q_w).
+* parameters theta = (log sigma, log q_c, log q_w), or, with one noise
+  level per sensor as in the sqrt(R_11) estimation of Sec. 6.4,
+  theta = (log sqrt(R_11), log q_c, log q_w, log sqrt(R_22)) and noise
+  diag(R_11, R_22).
 """
 import numpy as np
 
@@ -63,7 +66,10 @@ class CTBearings:
         self.theta = np.asarray(theta, dtype=np.float64)
         self.dt = float(dt)
         self.sensors = np.asarray(sensors, dtype=np.float64)
+        if self.theta.size not in (3, 4):
+            raise ValueError("theta has 3 or 4 entries")
         self.sigma = np.exp(self.theta[0])
+        self.sigma2 = np.exp(self.theta[3]) if self.theta.size == 4 else self.sigma
         self.qc = np.exp(self.theta[1])
         self.qw = np.exp(self.theta[2])
 
@@ -133,7 +139,7 @@ class CTBearings:
         return ref + wrap_angle(z - ref)
 
     def SR(self):
-        return self.sigma * np.eye(2)
+        return np.diag([self.sigma, self.sigma2])
 
 
 class LinearCV:

@@ -132,3 +132,39 @@ def test_fd_gradient_ct_step_consistency():
     g2 = ipls.nll_grad_fd(models.CTBearings, THETA, d["y"], d["m0"], d["N0"], "cubature",
                           h=2e-4, tol=1e-13, **kw)
     np.testing.assert_allclose(g1, g2, rtol=1e-5, atol=1e-6 * np.abs(g1).max())
+
+
+def test_ct_per_sensor_noise_reduces_to_shared():
+    """theta = (log s1, log q_c, log q_w, log s2) at s1 = s2 is the model with
+    one noise level: same nll, and by the chain rule the shared-sigma
+    derivative is the sum of the two per-sensor ones."""
+    d = workloads.ct_sequence(n=20, seed=23)
+    kw = dict(dt=d["dt"])
+    th4 = np.r_[THETA, THETA[0]]
+    n3 = ipls.nll(models.CTBearings, THETA, d["y"], d["m0"], d["N0"], "cubature", tol=1e-13, **kw)
+    n4 = ipls.nll(models.CTBearings, th4, d["y"], d["m0"], d["N0"], "cubature", tol=1e-13, **kw)
+    assert n3 == n4
+    g3 = ipls.nll_grad_fd(models.CTBearings, THETA, d["y"], d["m0"], d["N0"], "cubature",
+                          h=1e-4, tol=1e-13, **kw)
+    g4 = ipls.nll_grad_fd(models.CTBearings, th4, d["y"], d["m0"], d["N0"], "cubature",
+                          h=1e-4, tol=1e-13, **kw)
+    np.testing.assert_allclose([g4[0] + g4[3], g4[1], g4[2]], g3, rtol=1e-6,
+                               atol=1e-7 * np.abs(g3).max())
+
+
+def test_ct_per_sensor_noise_follows_its_sensor():
+    """Relabelling the two sensors, with their noise levels and observation
+    columns, leaves the nll unchanged; keeping the noise levels in place
+    does not (sqrt(R_11) belongs to the first sensor)."""
+    d = workloads.ct_sequence(n=20, seed=29)
+    th = np.r_[np.log(0.03), THETA[1:], np.log(0.08)]
+    S = models.SENSORS
+    kw = dict(dt=d["dt"])
+    base = ipls.nll(models.CTBearings, th, d["y"], d["m0"], d["N0"], "cubature", tol=1e-13,
+                    sensors=S, **kw)
+    swapped = ipls.nll(models.CTBearings, th[[3, 1, 2, 0]], d["y"][:, ::-1], d["m0"], d["N0"],
+                       "cubature", tol=1e-13, sensors=S[::-1], **kw)
+    wrong = ipls.nll(models.CTBearings, th, d["y"][:, ::-1], d["m0"], d["N0"], "cubature",
+                     tol=1e-13, sensors=S[::-1], **kw)
+    assert abs(swapped - base) <= 1e-10 * abs(base)
+    assert abs(wrong - base) > 1e-3 * abs(base)
