@@ -75,12 +75,20 @@ typedef enum {
   SQSM_MODEL_CT_BEARINGS = 1,  /* coordinated turn, two bearing sensors:
                                   nx = 5, ny = 2, theta = (log sigma,
                                   log q_c, log q_omega)                   */
-  SQSM_MODEL_POPULATION = 2    /* stochastic Ricker model, Poisson counts
+  SQSM_MODEL_POPULATION = 2,   /* stochastic Ricker model, Poisson counts
                                   (state-dependent observation noise):
                                   nx = ny = 1, theta = (log a, log b,
                                   log Q); dt and sensors unused; cubature
                                   or extended SLR; sqsm_ipls_smooth and
                                   sqsm_ipls_smooth_tol only               */
+  SQSM_MODEL_CT_BEARINGS_R = 3 /* the coordinated-turn bearings model with
+                                  one noise standard deviation per sensor
+                                  (Sec. 6.4 estimates the first one,
+                                  sqrt(R_11)): theta = (log sqrt(R_11),
+                                  log q_c, log q_omega, log sqrt(R_22)),
+                                  host double[4]; gradients double[4].
+                                  Accepted wherever SQSM_MODEL_CT_BEARINGS
+                                  is, which is the case R_11 = R_22       */
 } sqsm_model_kind;
 
 /* Coordinated-turn bearings-only model (Sec. 6.2): state
@@ -88,7 +96,9 @@ typedef enum {
  * p_x - s_x), ny = 2; additive process noise with covariance
  * q_c [[dt^3/3 I, dt^2/2 I], [dt^2/2 I, dt I]] on (p, v) and q_omega dt on
  * omega; bearing noise sigma^2 I.  theta = (log sigma, log q_c,
- * log q_omega) is passed separately (host double[3]). */
+ * log q_omega) is passed separately (host double[3]); with
+ * SQSM_MODEL_CT_BEARINGS_R the noise is diag(R_11, R_22) and theta has
+ * four entries (see there). */
 typedef struct {
   int kind;             /* sqsm_model_kind                          */
   double dt;            /* time step                                */
@@ -175,7 +185,8 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n,
 /* Iterated posterior linearisation smoother (Alg. 3) on `batch`
  * independent sequences of a compiled-in model, in one set of launches.
  *
- *   model, theta   model description and host double[3] parameters.
+ *   model, theta   model description and host parameters (double[3];
+ *                  double[4] for SQSM_MODEL_CT_BEARINGS_R).
  *   linearization  sqsm_linearization.
  *   M              number of iterations (>= 1).
  *   batch          number of sequences (>= 1).
@@ -255,7 +266,8 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
  *
  *   ms, Ns      outputs: the trajectory n* (state layout), as
  *               sqsm_ipls_smooth with the same M.
- *   nll         device double[1]; grad device double[3] (theta order).
+ *   nll         device double[1]; grad device double[3] (double[4] for
+ *               SQSM_MODEL_CT_BEARINGS_R), theta order.
  *   adj_change  device double[1] or NULL: max-norm change of lambda in the
  *               last adjoint iteration relative to its max-norm (a
  *               convergence measure; the gradient assumes n* is a fixed

@@ -25,6 +25,7 @@ F32, F64 = 0, 1
 CUBATURE, EXTENDED, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
 MODEL_CT_BEARINGS = 1
 MODEL_POPULATION = 2
+MODEL_CT_BEARINGS_R = 3
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -232,9 +233,18 @@ def sqsm_lgssm_smooth(ctx, F, c, SQ, H, d, SR, m0, N0, y, mf=None, Nf=None, ms=N
     return mf, Nf, ms, Ns, loglik
 
 
-def _model(dt, sensors):
-    s = (ctypes.c_double * 4)(*[float(v) for v in sensors.reshape(-1)])
-    return Model(MODEL_CT_BEARINGS, float(dt), s)
+def _ct_model(theta, dt, sensors):
+    """Model struct and host theta array of the CT bearings model: three
+    parameters (log sigma, log q_c, log q_omega) give both sensors one noise
+    level (MODEL_CT_BEARINGS); four (log sqrt(R_11), log q_c, log q_omega,
+    log sqrt(R_22)) give one per sensor (MODEL_CT_BEARINGS_R)."""
+    import numpy as np
+    th = [float(v) for v in np.asarray(theta, dtype=np.float64).reshape(-1)]
+    if len(th) not in (3, 4):
+        raise ValueError("CT theta has 3 or 4 entries")
+    s = (ctypes.c_double * 4)(*[float(v) for v in np.asarray(sensors).reshape(-1)])
+    kind = MODEL_CT_BEARINGS if len(th) == 3 else MODEL_CT_BEARINGS_R
+    return Model(kind, float(dt), s), (ctypes.c_double * len(th))(*th)
 
 
 def _offsets(offsets):
@@ -260,8 +270,7 @@ def sqsm_ipls_smooth(ctx, theta, y, offsets, m0, N0, M, linearization=CUBATURE, 
         Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
     if loglik is None:
         loglik = torch.empty(batch, dtype=torch.float64, device=dev)
-    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
-    mdl = _model(dt, np.asarray(sensors))
+    mdl, th = _ct_model(theta, dt, sensors)
     rc = lib.sqsm_ipls_smooth(ctx.h, code, ctypes.byref(mdl), th, int(linearization), int(M),
                               batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
                               _ptr(N0, dtp, "N0"), _ptr(init_ms, dtp, "init_ms"),
@@ -289,8 +298,7 @@ def sqsm_ipls_smooth_tol(ctx, theta, y, offsets, m0, N0, max_iters, tol, lineari
     Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
     loglik = torch.empty(batch, dtype=torch.float64, device=dev)
     iters = torch.zeros(1, dtype=torch.int32, device=dev)
-    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
-    mdl = _model(dt, np.asarray(sensors))
+    mdl, th = _ct_model(theta, dt, sensors)
     rc = lib.sqsm_ipls_smooth_tol(ctx.h, code, ctypes.byref(mdl), th, int(linearization),
                                   int(max_iters), float(tol), batch, off, _ptr(y, dtp, "y"),
                                   _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"),
@@ -317,8 +325,7 @@ def sqsm_ipls_smooth_std(ctx, theta, y, offsets, m0, P0, M, linearization=CUBATU
     ms = torch.empty((rows, 5), dtype=dtp, device=dev)
     Ps = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
     loglik = torch.empty(batch, dtype=torch.float64, device=dev)
-    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
-    mdl = _model(dt, np.asarray(sensors))
+    mdl, th = _ct_model(theta, dt, sensors)
     rc = lib.sqsm_ipls_smooth_std(ctx.h, code, ctypes.byref(mdl), th, int(linearization), int(M),
                                   batch,
                                   off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
@@ -372,8 +379,7 @@ def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt
     dev = y.device
     out = [torch.empty(s, dtype=dtp, device=dev) for s in
            ((n, 5, 5), (n, 5), (n, 5, 5), (n, 2, 5), (n, 2), (n, 2, 2))]
-    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
-    mdl = _model(dt, np.asarray(sensors))
+    mdl, th = _ct_model(theta, dt, sensors)
     rc = lib.sqsm_ct_linearize(ctx.h, code, ctypes.byref(mdl), th, int(linearization), batch, off,
                                _ptr(y, dtp, "y"), _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"),
                                *[_ptr(o, dtp) for o in out], _stream())
@@ -385,7 +391,7 @@ def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, se
                        init_ms=None, init_Ns=None, ms=None, Ns=None, nll=None, grad=None,
                        change=None):
     """Call sqsm_ipls_nll_grad (cubature).  Returns (nll, grad, change, ms,
-    Ns) as device tensors (nll [1], grad [3], change [1] float64)."""
+    Ns) as device tensors (nll [1], grad [len(theta)], change [1] float64)."""
     import numpy as np
     dtp = y.dtype
     code = _dtype_code(dtp)
@@ -400,10 +406,9 @@ def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, se
         Ns = torch.empty((rows, 5, 5), dtype=dtp, device=dev)
     f64 = torch.float64
     nll = torch.empty(1, dtype=f64, device=dev) if nll is None else nll
-    grad = torch.empty(3, dtype=f64, device=dev) if grad is None else grad
     change = torch.empty(1, dtype=f64, device=dev) if change is None else change
-    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
-    mdl = _model(dt, np.asarray(sensors))
+    mdl, th = _ct_model(theta, dt, sensors)
+    grad = torch.empty(len(th), dtype=f64, device=dev) if grad is None else grad
     rc = lib.sqsm_ipls_nll_grad(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), int(adj_iters),
                                 batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"),
                                 _ptr(init_ms, dtp, "init_ms"), _ptr(init_Ns, dtp, "init_Ns"),

@@ -9,6 +9,8 @@
 
 namespace sqsm {
 
+constexpr int kAdjPerStepMaxLeaf = 8;
+
 // Upper levels 1 .. Lk-1 of an adjoint scan (items[1] already written by
 // the leaf up-sweep), then the Kogge-Stone top over the items of level Lk.
 template <typename T, bool FWD>
@@ -84,6 +86,10 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   const int Lc = (int)Lf.lv.size();
   const int Lk = Lf.ks_level(KsMax<T, MREC>::value);
   const unsigned slr_blocks = grid_for(Ls.lv[0].n_chunks * a.leaf);
+  // leaf down-sweeps: one thread per step for short leaf chunks (each replays
+  // at most kAdjPerStepMaxLeaf - 1 maps), one per chunk for long ones
+  const bool per_step = a.leaf <= kAdjPerStepMaxLeaf;
+  const unsigned down_grid = grid_for(Lf.lv[0].n_chunks * (per_step ? a.leaf : 1));
   for (int it = 0; it < g.iters; ++it) {
     // smoother adjoint: forward-in-time scan of maps
     if (Lc > 1) {
@@ -94,8 +100,8 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
       cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     }
     adj_scan_down<T, true>(Lf, Wa, Lc > 1 ? Lk : Lc, s);
-    adj_smoother_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
+    adj_smoother_leaf_down<T><<<down_grid, kBlock, 0, s>>>(
+        Lf.lv[0], a.leaf, per_step, sq, ab, (const T*)Wa.carry[1], Wa.flag[1]);
     // filter adjoint: backward-in-time scan of maps
     if (Lc > 1) {
       adj_filter_leaf_up<T><<<grid_for(Lf.lv[0].n_chunks), kBlock, 0, s>>>(Lf.lv[0], sq, ab, lbar,
@@ -105,8 +111,8 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
       cudaMemsetAsync(Wa.flag[Lc], 0, sizeof(int) * Lf.n_items[Lc], s);
     }
     adj_scan_down<T, false>(Lf, Wa, Lc > 1 ? Lk : Lc, s);
-    adj_filter_leaf_down<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
+    adj_filter_leaf_down<T><<<down_grid, kBlock, 0, s>>>(
+        Lf.lv[0], a.leaf, per_step, sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
     // SLR adjoint -> next cotangent of the nominal trajectory (and its direct
     // cotangents for the next iteration), theta partials
     adj_slr_kernel<T><<<slr_blocks, kBlock, 0, s>>>(
@@ -123,8 +129,8 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
     lam_a = lam_b;
     lam_b = t;
   }
-  if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(slr_blocks, g.th_partial, 1.0, g.grad);
-  else cudaMemsetAsync(g.grad, 0, 3 * sizeof(double), s);
+  if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(slr_blocks, g.th_partial, 1.0, g.n_theta, g.grad);
+  else cudaMemsetAsync(g.grad, 0, g.n_theta * sizeof(double), s);
 }
 
 }  // namespace sqsm

@@ -120,58 +120,61 @@ adj_smoother_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T* __restrict__ items) 
   vstore<T, REC>(items + c * REC, agg);
 }
 
-// One thread per time step (leaf chunks of `leaf` steps): the cotangent
-// entering step j of a chunk is the chunk's carry (or the sequence's first
-// direct cotangent) pushed through the maps of steps 0 .. j-1 of the chunk;
-// then the RTS VJP of the step.
+// Leaf chunks of `leaf` steps.  per_step: one thread per time step; the
+// cotangent entering step j of a chunk is the chunk's carry (or the
+// sequence's first direct cotangent) pushed through the maps of steps
+// 0 .. j-1 of the chunk, then the RTS VJP of the step (short chunks: the
+// replayed maps are cheap next to the VJP).  Otherwise one thread per chunk
+// walks its steps in order (long chunks, e.g. one per sequence).
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-adj_smoother_leaf_down(DevLevel lv, int leaf, DevSeqs sq, AdjBufs a, const T* __restrict__ carry,
-                       const int* __restrict__ flag) {
+adj_smoother_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a,
+                       const T* __restrict__ carry, const int* __restrict__ flag) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t c = tid / leaf;
+  const int64_t c = per_step ? tid / leaf : tid;
   if (c >= lv.n_chunks) return;
-  const int jj = (int)(tid - c * leaf);
-  if (jj >= lv.count[c]) return;
+  const int cnt = lv.count[c];
+  const int jj = per_step ? (int)(tid - c * leaf) : 0;
+  if (jj >= cnt) return;
+  const int j1 = per_step ? jj + 1 : cnt;   // steps [jj0, j1) take their VJP
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
   using RT = RtsTab<NX>;
   const int b = lv.seq[c];
   const int64_t s0 = lv.first[c];
+  const int64_t last = sq.offsets[b + 1] - 1;
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
-  for (int j = 0; j < jj; ++j) {
-    const int64_t e = s0 + j + b;
-    T G[RT::head], mp[REC], xn[X];
-    vload<T, RT::head>((const T*)a.rtab + (s0 + j) * RT::size, G);
-    smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
-    map_apply<T, NX>(mp, x, xn);
-    copy<T, X>(xn, x);
-  }
-  const int64_t s = s0 + jj, e = s + b;
-  Gamma<T, NX, NY> g;
-  g.load_transition(gview<T>(a), s);
-  T mf[NX];
-  load<T, NX>((const T*)a.mf + e * NX, mf);
-  T df[X], gb[GR::size];
-  // FP32 holds the record in registers; FP64 reads it where it is used
-  // (twice the registers per value would spill).
-  const T* rtg = (const T*)a.rtab + s * RT::size;
-  T rtr[sizeof(T) == 4 ? RT::size : 4];
-  if constexpr (sizeof(T) == 4) vload<T, RT::size>(rtg, rtr);
-  const T* rt = sizeof(T) == 4 ? rtr : rtg;
-  rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
-  store<T, X>((T*)a.dfilt + e * X, df);
-  T* go = (T*)a.gbar + s * GR::size;
-  store<T, NX * NX>(go + GR::F, gb + GR::F);
-  store<T, NX>(go + GR::c, gb + GR::c);
-  store<T, NX * NX>(go + GR::L, gb + GR::L);
-  if (s == sq.offsets[b + 1] - 1) {   // k = n: dmf_n = x_n
-    T mp[REC], xn[X];
-    smoother_adj_map<T, NX>(rt + RT::G, (const T*)a.dir + (e + 1) * X, mp);
-    map_apply<T, NX>(mp, x, xn);
-    store<T, X>((T*)a.dfilt + (e + 1) * X, xn);
+  for (int j = 0; j < j1; ++j) {
+    const int64_t s = s0 + j, e = s + b;
+    const T* rtg = (const T*)a.rtab + s * RT::size;
+    if (j >= jj) {
+      Gamma<T, NX, NY> g;
+      g.load_transition(gview<T>(a), s);
+      T mf[NX];
+      load<T, NX>((const T*)a.mf + e * NX, mf);
+      T df[X], gb[GR::size];
+      // FP32 holds the record in registers; FP64 reads it where it is used
+      // (twice the registers per value would spill).
+      T rtr[sizeof(T) == 4 ? RT::size : 4];
+      if constexpr (sizeof(T) == 4) vload<T, RT::size>(rtg, rtr);
+      const T* rt = sizeof(T) == 4 ? rtr : rtg;
+      rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
+      store<T, X>((T*)a.dfilt + e * X, df);
+      T* go = (T*)a.gbar + s * GR::size;
+      store<T, NX * NX>(go + GR::F, gb + GR::F);
+      store<T, NX>(go + GR::c, gb + GR::c);
+      store<T, NX * NX>(go + GR::L, gb + GR::L);
+    }
+    if (j + 1 < j1 || s == last) {
+      T G[RT::head], mp[REC], xn[X];
+      vload<T, RT::head>(rtg, G);
+      smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
+      map_apply<T, NX>(mp, x, xn);
+      copy<T, X>(xn, x);
+      if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
+    }
   }
 }
 
@@ -212,20 +215,23 @@ adj_filter_leaf_up(DevLevel lv, DevSeqs sq, AdjBufs a, T lbar, T* __restrict__ i
   vstore<T, REC>(items + c * REC, agg);
 }
 
-// One thread per time step: the cotangent entering step j of a chunk (of
-// its output row) is the chunk's carry (or the sequence's last filter
-// cotangent) pushed back through the maps of steps cnt-1 .. j+1; then the
-// Kalman-step VJP of the step.
+// Leaf chunks of `leaf` steps, walked backward in time.  per_step: one
+// thread per time step; the cotangent entering step j of a chunk (of its
+// output row) is the chunk's carry (or the sequence's last filter
+// cotangent) pushed back through the maps of steps cnt-1 .. j+1, then the
+// Kalman-step VJP of the step.  Otherwise one thread per chunk walks its
+// steps from the last.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-adj_filter_leaf_down(DevLevel lv, int leaf, DevSeqs sq, AdjBufs a, T lbar,
+adj_filter_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a, T lbar,
                      const T* __restrict__ carry, const int* __restrict__ flag) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t c = tid / leaf;
+  const int64_t c = per_step ? tid / leaf : tid;
   if (c >= lv.n_chunks) return;
-  const int jj = (int)(tid - c * leaf);
   const int cnt = lv.count[c];
+  const int jj = per_step ? (int)(tid - c * leaf) : 0;
   if (jj >= cnt) return;
+  const int j1 = per_step ? jj : 0;   // steps cnt-1 .. j1 are walked
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
   using KT = KfTab<NX, NY>;
@@ -234,27 +240,30 @@ adj_filter_leaf_down(DevLevel lv, int leaf, DevSeqs sq, AdjBufs a, T lbar,
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
-  for (int j = cnt - 1; j > jj; --j) {
-    const int64_t e = s0 + j + b;
-    T h[KT::head], mp[REC], xn[X];
-    vload<T, KT::head>((const T*)a.ktab + (s0 + j) * KT::size, h);
-    filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
-    map_apply<T, NX>(mp, x, xn);
-    copy<T, X>(xn, x);
+  for (int j = cnt - 1; j >= j1; --j) {
+    const int64_t s = s0 + j, e = s + b;
+    if (!per_step || j == jj) {
+      Gamma<T, NX, NY> g;
+      g.load_all(gview<T>(a), s);
+      T kt[KT::size], mprev[NX];
+      vload<T, KT::size>((const T*)a.ktab + s * KT::size, kt);
+      load<T, NX>((const T*)a.mf + e * NX, mprev);
+      KfQ<T, NX, NY> q;
+      q.load(kt);
+      T gb[GR::size];
+      T* go = (T*)a.gbar + s * GR::size;
+      load<T, GR::size>(go, gb);
+      kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
+      store<T, GR::size>(go, gb);
+    }
+    if (j > j1) {
+      T h[KT::head], mp[REC], xn[X];
+      vload<T, KT::head>((const T*)a.ktab + s * KT::size, h);
+      filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
+      map_apply<T, NX>(mp, x, xn);
+      copy<T, X>(xn, x);
+    }
   }
-  const int64_t s = s0 + jj, e = s + b;
-  Gamma<T, NX, NY> g;
-  g.load_all(gview<T>(a), s);
-  T kt[KT::size], mprev[NX];
-  vload<T, KT::size>((const T*)a.ktab + s * KT::size, kt);
-  load<T, NX>((const T*)a.mf + e * NX, mprev);
-  KfQ<T, NX, NY> q;
-  q.load(kt);
-  T gb[GR::size];
-  T* go = (T*)a.gbar + s * GR::size;
-  load<T, GR::size>(go, gb);
-  kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
-  store<T, GR::size>(go, gb);
 }
 
 // --------------------------- upper levels (both directions) ---------------
@@ -469,7 +478,9 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
       for (int q = 0; q < NY; ++q) Lb[i * NY + q] = T(0.5) * (gb[GR::O + i * NY + q] + gb[GR::O + q * NY + i]);
     cubature_vjp<T, NY>(m, N, t + ST::Gh - ST::obs, t + ST::sh - ST::obs, gb + GR::H, gb + GR::d, Lb,
                         [&](const T* xx, T* J) { ct_jac_h(P, xx, J); }, mb, Nb);
-    th[0] += 2.0 * (double)P.sigma * (double)P.sigma * ((double)Lb[0] + (double)Lb[3]);
+    // Omega = diag(sigma_1^2, sigma_2^2): d/d log sigma_i = 2 sigma_i^2 Omega-bar_ii
+    th[0] += 2.0 * (double)P.sigma[0] * (double)P.sigma[0] * (double)Lb[0];
+    th[3] += 2.0 * (double)P.sigma[1] * (double)P.sigma[1] * (double)Lb[3];
   }
   T o[X];
 #pragma unroll
@@ -486,22 +497,22 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
   store<T, X>((T*)a.dir + e * X, d);
 }
 
-// Sum of three values over the block (kBlock threads) in a fixed order,
-// written by thread 0 to out[0..2].
-SQSM_DEV void block_sum3(double* v, double* __restrict__ out) {
-  __shared__ double part[kBlock / 32][3];
+// Sum of four values over the block (kBlock threads) in a fixed order,
+// written by thread 0 to out[0..3].
+SQSM_DEV void block_sum4(double* v, double* __restrict__ out) {
+  __shared__ double part[kBlock / 32][4];
 #pragma unroll
-  for (int j = 0; j < 3; ++j)
+  for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) part[w][j] = v[j];
+    for (int j = 0; j < 4; ++j) part[w][j] = v[j];
   __syncthreads();
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < 4; ++j) {
       double t = 0.0;
 #pragma unroll
       for (int q = 0; q < kBlock / 32; ++q) t += part[q][j];
@@ -510,8 +521,9 @@ SQSM_DEV void block_sum3(double* v, double* __restrict__ out) {
 }
 
 // One thread per state row (smoother leaf chunks of `leaf` rows); every
-// thread of the block takes part in the block's theta sum (rows past the
-// end add zero), written to th_partial[3 * block].
+// thread of the block takes part in the block's theta sums (rows past the
+// end add zero), written to th_partial[4 * block]: log sigma_1, log q_c,
+// log q_w, log sigma_2.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
@@ -519,28 +531,37 @@ adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ch = tid / leaf;
   const int jr = (int)(tid - ch * leaf);
-  double th[3] = {0.0, 0.0, 0.0};
+  double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (ch < lv.n_chunks && jr < lv.count[ch])
     adj_slr_row<T>(lv.first[ch] + jr, lv.seq[ch], sq, Pp, a, lam_out, th);
-  block_sum3(th, th_partial + 3 * blockIdx.x);
+  block_sum4(th, th_partial + 4 * blockIdx.x);
 }
 
-// Fixed-order sums of the theta partials (one block): out[j] = sign * sum.
+// Fixed-order sums of the theta partials (one block over n four-entry
+// partials): with n_theta = 4, out[j] = sign * sum of entry j; with 3 (one
+// noise level for both sensors), out[0] sums entries 0 and 3.
 static __global__ void adj_theta_reduce(int64_t n, const double* __restrict__ part, double sign,
-                                        double* __restrict__ out) {
-  __shared__ double buf[3][256];
-  double acc[3] = {0.0, 0.0, 0.0};
+                                        int n_theta, double* __restrict__ out) {
+  __shared__ double buf[4][256];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-    for (int j = 0; j < 3; ++j) acc[j] += part[i * 3 + j];
-  for (int j = 0; j < 3; ++j) buf[j][threadIdx.x] = acc[j];
+    for (int j = 0; j < 4; ++j) acc[j] += part[i * 4 + j];
+  for (int j = 0; j < 4; ++j) buf[j][threadIdx.x] = acc[j];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
-      for (int j = 0; j < 3; ++j) buf[j][threadIdx.x] += buf[j][threadIdx.x + w];
+      for (int j = 0; j < 4; ++j) buf[j][threadIdx.x] += buf[j][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0)
-    for (int j = 0; j < 3; ++j) out[j] = sign * buf[j][0];
+  if (threadIdx.x == 0) {
+    if (n_theta == 4) {
+      for (int j = 0; j < 4; ++j) out[j] = sign * buf[j][0];
+    } else {
+      out[0] = sign * (buf[0][0] + buf[3][0]);
+      out[1] = sign * buf[1][0];
+      out[2] = sign * buf[2][0];
+    }
+  }
 }
 
 // Relative max-norm change between two cotangent iterates, in two kernels:

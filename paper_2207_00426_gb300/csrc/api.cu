@@ -69,11 +69,12 @@ struct GraphKey {
   double tol = -1.0;                // tolerance mode (M = iteration cap), else -1
   const void* iters = nullptr;
   int kind = SQSM_MODEL_CT_BEARINGS;
+  const void *grad = nullptr, *change = nullptr;   // NLL + gradient outputs
   bool operator<(const GraphKey& o) const {
     return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll, tol, iters,
-                    kind) <
+                    kind, grad, change) <
            std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.adj, o.y, o.m0, o.N0, o.ims, o.iNs,
-                    o.ms, o.Ns, o.ll, o.tol, o.iters, o.kind);
+                    o.ms, o.Ns, o.ll, o.tol, o.iters, o.kind, o.grad, o.change);
   }
 };
 
@@ -371,7 +372,7 @@ bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
   g.stab = w->mem.get(es * SlrTab<5, 2>::size * steps);
   // theta partial sums, one triple per block of the SLR VJP kernel
   g.th_partial = (double*)w->mem.get(
-      sizeof(double) * 3 * std::max<int64_t>(1, grid_for(p->smth.lv[0].n_chunks * p->L0)));
+      sizeof(double) * 4 * std::max<int64_t>(1, grid_for(p->smth.lv[0].n_chunks * p->L0)));
   g.ll = (double*)w->mem.get(sizeof(double) * p->B);
   g.change_words = w->mem.get(2 * sizeof(unsigned));
   if (!g.change_words) return false;
@@ -547,6 +548,15 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const
 
 namespace {
 
+// theta into IplsArgs::theta[4]: the CT model with one noise level per
+// sensor passes log sigma of the second sensor as its fourth entry; with one
+// noise level for both sensors (and for the other models) entry 3 repeats
+// entry 0.
+void copy_theta(double* dst, const sqsm_model* model, const double* theta) {
+  for (int i = 0; i < 3; ++i) dst[i] = theta[i];
+  dst[3] = model->kind == SQSM_MODEL_CT_BEARINGS_R ? theta[3] : theta[0];
+}
+
 // Arguments of one IPLS enqueue on plan p's workspace w.
 IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* model,
                         const double* theta, int lin, int M, const void* y, const void* m0,
@@ -556,7 +566,7 @@ IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* mod
   a.linearization = lin;
   a.leaf = p->L0;
   a.M = M;
-  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  copy_theta(a.theta, model, theta);
   a.dt = model->dt;
   for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
   a.y = y; a.m0 = m0; a.N0 = N0; a.init_ms = init_ms; a.init_Ns = init_Ns;
@@ -613,7 +623,21 @@ void enqueue_pop(sqsm_ctx* ctx, int dtype, const Plan* p, const Workspace* w, co
 }
 
 bool known_model(const sqsm_model* model) {
-  return model && (model->kind == SQSM_MODEL_CT_BEARINGS || model->kind == SQSM_MODEL_POPULATION);
+  return model && (model->kind == SQSM_MODEL_CT_BEARINGS || model->kind == SQSM_MODEL_POPULATION ||
+                   model->kind == SQSM_MODEL_CT_BEARINGS_R);
+}
+
+bool is_ct(const sqsm_model* model) {
+  return model->kind == SQSM_MODEL_CT_BEARINGS || model->kind == SQSM_MODEL_CT_BEARINGS_R;
+}
+
+// Number of theta entries the caller passes (and of gradient entries).
+int n_theta(const sqsm_model* model) { return model->kind == SQSM_MODEL_CT_BEARINGS_R ? 4 : 3; }
+
+bool theta_finite(const sqsm_model* model, const double* theta) {
+  for (int i = 0; i < n_theta(model); ++i)
+    if (!std::isfinite(theta[i])) return false;
+  return true;
 }
 
 int floor_log2(int64_t v) {
@@ -748,8 +772,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -856,8 +879,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -995,7 +1017,7 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
   if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+  if (!is_ct(model))
     return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
@@ -1007,8 +1029,7 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
     return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
   if (!y || !m0 || !P0 || !ms || !Ps)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -1043,7 +1064,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
   if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+  if (!is_ct(model))
     return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
@@ -1059,8 +1080,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -1077,6 +1097,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
                               ms, Ns, nullptr);
   AdjArgs adj = w->adj;
   adj.iters = adj_iters;
+  adj.n_theta = n_theta(model);
   adj.nll = nll;
   adj.grad = grad;
   adj.change = adj_change;
@@ -1095,9 +1116,12 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   } else {
     GraphKey key{p, dtype, linearization, M, 0, adj_iters + 1, y, m0, N0, init_ms, init_Ns,
                  ms, Ns, nll};
+    key.kind = model->kind;
+    key.grad = grad;          // every pointer the captured kernels write is
+    key.change = adj_change;  // part of the key
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
-    if (it != ctx->graphs.end() && it->first.adj == adj_iters + 1 && key.ll == nll) {
+    if (it != ctx->graphs.end()) {
       exec = it->second.exec;
     } else {
       cudaGraph_t graph = nullptr;
@@ -1133,7 +1157,7 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
   if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (model->kind != SQSM_MODEL_CT_BEARINGS)
+  if (!is_ct(model))
     return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
@@ -1144,8 +1168,7 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
     return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
   if (!y || !ms || !Ns || !F || !c || !SQ || !H || !d || !SR)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null pointer");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(theta[i])) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
   DeviceGuard g(ctx->device);
   Plan* p = get_plan(ctx, offsets, batch);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
@@ -1154,7 +1177,7 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
   IplsArgs a{};
   a.linearization = linearization;
   a.leaf = p->L0;
-  for (int i = 0; i < 3; ++i) a.theta[i] = theta[i];
+  copy_theta(a.theta, model, theta);
   a.dt = model->dt;
   for (int i = 0; i < 4; ++i) a.sensors[i] = model->sensors[i];
   a.y = y;

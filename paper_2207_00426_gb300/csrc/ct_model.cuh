@@ -35,7 +35,7 @@ template <typename T>
 struct CTParams {
   T dt;
   T sx[2], sy[2];
-  T sigma;
+  T sigma[2];    // bearing noise standard deviation of each sensor
   T SQ[25];      // lower Cholesky factor of the process noise
 };
 
@@ -46,17 +46,19 @@ SQSM_DEV double sq_atan2(double y, double x) { return atan2(y, x); }
 SQSM_DEV float sq_floor(float x) { return floorf(x); }
 SQSM_DEV double sq_floor(double x) { return floor(x); }
 
-// Parameters from theta = (log sigma, log q_c, log q_w) (closed-form factor
-// of q_c [[dt^3/3, dt^2/2], [dt^2/2, dt]] per axis and q_w dt).
+// Parameters from theta = (log sigma_1, log q_c, log q_w, log sigma_2)
+// (bearing noise standard deviation of each sensor; closed-form factor of
+// q_c [[dt^3/3, dt^2/2], [dt^2/2, dt]] per axis and q_w dt).
 template <typename T>
-__global__ void ct_params_kernel(double th0, double th1, double th2, double dt, double s1x,
-                                 double s1y, double s2x, double s2y, CTParams<T>* P) {
+__global__ void ct_params_kernel(double th0, double th1, double th2, double th3, double dt,
+                                 double s1x, double s1y, double s2x, double s2y, CTParams<T>* P) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double sigma = exp(th0), qc = exp(th1), qw = exp(th2);
+  const double qc = exp(th1), qw = exp(th2);
   CTParams<T> p;
   p.dt = (T)dt;
   p.sx[0] = (T)s1x; p.sy[0] = (T)s1y; p.sx[1] = (T)s2x; p.sy[1] = (T)s2y;
-  p.sigma = (T)sigma;
+  p.sigma[0] = (T)exp(th0);
+  p.sigma[1] = (T)exp(th3);
   for (int i = 0; i < 25; ++i) p.SQ[i] = T(0);
   const double a = sqrt(qc * dt * dt * dt / 3.0);
   const double b = sqrt(qc) * sqrt(3.0 * dt) / 2.0;
@@ -540,7 +542,7 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
     T hm[NY], Hm[NY * NX], dm[NY], So[NY * NY], ys[NY];
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
-    const T Sr[NY * NY] = {P.sigma, T(0), T(0), P.sigma};
+    const T Sr[NY * NY] = {P.sigma[0], T(0), T(0), P.sigma[1]};
     auto hd = [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); };
     if constexpr (LIN == 0) {
       cubature_regress<T, NY, false>(m, N, hm, !centered, Sr, hd, Hm, dm, So);
@@ -560,7 +562,7 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
         }
         dm[r] = sacc;
       }
-      So[0] = P.sigma; So[1] = T(0); So[2] = T(0); So[3] = P.sigma;
+      So[0] = P.sigma[0]; So[1] = T(0); So[2] = T(0); So[3] = P.sigma[1];
     }
 #pragma unroll
     for (int r = 0; r < NY; ++r) dm[r] += branch_shift(ys[r], hm[r]);

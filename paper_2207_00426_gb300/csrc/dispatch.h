@@ -32,7 +32,7 @@ bool lgssm_shape_supported(int nx, int ny);
 struct IplsArgs {
   int linearization, M;
   int leaf;            // leaf chunk length of the plan
-  double theta[3], dt, sensors[4];
+  double theta[4], dt, sensors[4];   // theta[3]: CT second sensor log sigma
   const void *y, *m0, *N0, *init_ms, *init_Ns;
   void *ms, *Ns;
   double* loglik;
@@ -93,6 +93,7 @@ void ipls_params_f64(const IplsArgs& a, cudaStream_t s);
 // Buffers of the NLL + gradient evaluation (all device).
 struct AdjArgs {
   int iters;                          // adjoint fixed-point iterations
+  int n_theta;                        // 3: one CT noise level, 4: one per sensor
   void *nom_m, *nom_N, *ms2, *Ns2;    // linearisation point, its smoother output
   void *dir, *dfilt, *gbar, *lam_a, *lam_b;
   void *ktab, *rtab, *stab;           // per-step KfTab / RtsTab / SlrTab records

@@ -18,7 +18,8 @@ void pop_params(const IplsArgs& a, cudaStream_t s) {
 
 template <typename T>
 void ipls_params(const IplsArgs& a, cudaStream_t s) {
-  ct_params_kernel<T><<<1, 1, 0, s>>>(a.theta[0], a.theta[1], a.theta[2], a.dt, a.sensors[0],
+  ct_params_kernel<T><<<1, 1, 0, s>>>(a.theta[0], a.theta[1], a.theta[2], a.theta[3], a.dt,
+                                      a.sensors[0],
                                       a.sensors[1], a.sensors[2], a.sensors[3],
                                       (CTParams<T>*)a.params);
 }

@@ -583,7 +583,7 @@ std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
     T hm[NY], ys[NY];
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
-    const T Rc[NY * NY] = {P.sigma * P.sigma, T(0), T(0), P.sigma * P.sigma};
+    const T Rc[NY * NY] = {P.sigma[0] * P.sigma[0], T(0), T(0), P.sigma[1] * P.sigma[1]};
     if (linearization == 0) {
       cubature_regress_std<T, NY, false>(
           m, N, Pc, hm, Rc, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },

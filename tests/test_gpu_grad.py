@@ -54,10 +54,12 @@ def test_gradient_matches_oracle_fd(B, ctx, prec, tol, n):
     assert change.item() < (1e-8 if prec == "f64" else 1e-3)
 
 
-@pytest.mark.parametrize("leaf,radix", [(4, 4), (2, 3)])
+@pytest.mark.parametrize("leaf,radix", [(4, 4), (2, 3), (12, 4), (200, 4)])
 def test_gradient_fold_levels(B, leaf, radix):
     """The adjoint's map scans with every upper level folded (explicit radix)
-    instead of warp-scanned."""
+    instead of warp-scanned; leaf chunks of 12 take the one-thread-per-chunk
+    leaf down-sweeps, and 200 > n puts the whole sequence in one chunk (no
+    upper levels: the sequential smoother's shape)."""
     c2 = B.Context(0, leaf_chunk=leaf, radix=radix)
     n = 131
     d = W.ct_sequence(n=n, seed=31 + n)
@@ -106,11 +108,86 @@ def test_extended_is_rejected(B, ctx):
     d = W.ct_sequence(n=10, seed=44)
     dt = torch.float64
     import ctypes
-    th = (ctypes.c_double * 3)(*THETA)
-    mdl = B._model(d["dt"], d["sensors"])
+    mdl, th = B._ct_model(THETA, d["dt"], d["sensors"])
     off, batch = B._offsets([0, 10])
     z = torch.zeros(64, dtype=dt, device="cuda:0")
     p = z.data_ptr()
     rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, B.EXTENDED, 5, 5, batch, off,
                                   p, p, p, None, None, p, p, p, p, None, None)
     assert rc == B.ERR_UNSUPPORTED
+
+
+THETA_R = np.r_[np.log(0.03), THETA[1:], np.log(0.08)]
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-6), ("f32", 1e-3)])
+def test_gradient_per_sensor_noise(B, ctx, prec, tol):
+    """The model with one noise level per sensor (theta = (log sqrt(R_11),
+    log q_c, log q_w, log sqrt(R_22)), Sec. 6.4): nll and the four-entry
+    gradient against the oracle's central differences."""
+    n = 131
+    d = W.ct_sequence(n=n, seed=37)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    nll, grad, change, _, _ = B.sqsm_ipls_nll_grad(ctx, THETA_R, _dev(d["y"], dt), [0, n],
+                                                   _dev(d["m0"][None], dt),
+                                                   _dev(d["N0"][None], dt), M=40, adj_iters=40,
+                                                   dt=d["dt"])
+    torch.cuda.synchronize()
+    rnll, rg = _oracle(d, THETA_R)
+    g = grad.cpu().numpy()
+    assert g.shape == (4,)
+    assert abs(nll.item() - rnll) <= (1e-9 if prec == "f64" else 1e-5) * abs(rnll)
+    assert np.linalg.norm(g - rg) <= tol * np.linalg.norm(rg), (g, rg)
+    assert change.item() < (1e-8 if prec == "f64" else 1e-3)
+
+
+@pytest.mark.parametrize("method", ["cubature", "extended"])
+def test_smoother_per_sensor_noise(B, ctx, method):
+    """sqsm_ipls_smooth with the per-sensor model against the oracle (FP64),
+    and the shared-noise model is its case sqrt(R_11) = sqrt(R_22)."""
+    d = W.ct_sequence(n=97, seed=13)
+    f64 = torch.float64
+    lin = {"cubature": 0, "extended": 1}[method]
+    args = (_dev(d["y"], f64), [0, 97], _dev(d["m0"][None], f64), _dev(d["N0"][None], f64), 6, lin)
+    ms, Ns, ll = B.sqsm_ipls_smooth(ctx, THETA_R, *args, dt=d["dt"])
+    torch.cuda.synchronize()
+    rms, rNs, rll, _ = O.ipls(OM.CTBearings(THETA_R, dt=d["dt"]), d["y"], d["m0"], d["N0"], 6,
+                              method)
+    P = Ns.cpu().numpy() @ np.swapaxes(Ns.cpu().numpy(), -1, -2)
+    Pr = rNs @ np.swapaxes(rNs, -1, -2)
+    assert np.linalg.norm(ms.cpu().numpy() - rms, axis=-1).max() <= 1e-9 * np.linalg.norm(rms, axis=-1).max()
+    assert np.abs(P - Pr).max() <= 1e-9 * np.abs(Pr).max()
+    assert abs(ll.item() - rll) <= 1e-10 * abs(rll)
+    th4 = np.r_[THETA, THETA[0]]
+    a3 = B.sqsm_ipls_smooth(ctx, THETA, *args, dt=d["dt"])
+    a4 = B.sqsm_ipls_smooth(ctx, th4, *args, dt=d["dt"])
+    torch.cuda.synchronize()
+    for u, v in zip(a3, a4):
+        assert torch.equal(u, v)
+
+
+def test_graph_cache_keys_every_output(B):
+    """A second call that keeps ms, Ns and nll but hands new grad / change
+    tensors must write those (the captured graph is keyed on every output
+    pointer), and give the same values as the first call."""
+    c2 = B.Context(0, use_graph=True)
+    n = 60
+    d = W.ct_sequence(n=n, seed=47)
+    f64 = torch.float64
+    y, m0, N0 = _dev(d["y"], f64), _dev(d["m0"][None], f64), _dev(d["N0"][None], f64)
+    ms = torch.empty((n + 1, 5), dtype=f64, device="cuda:0")
+    Ns = torch.empty((n + 1, 5, 5), dtype=f64, device="cuda:0")
+    nll = torch.empty(1, dtype=f64, device="cuda:0")
+    outs = []
+    for _ in range(2):
+        g = torch.full((3,), float("nan"), dtype=f64, device="cuda:0")
+        ch = torch.full((1,), float("nan"), dtype=f64, device="cuda:0")
+        B.sqsm_ipls_nll_grad(c2, THETA, y, [0, n], m0, N0, 30, 30, dt=d["dt"], ms=ms, Ns=Ns,
+                             nll=nll, grad=g, change=ch)
+        torch.cuda.synchronize()
+        outs.append((g.cpu().numpy(), ch.item()))
+    c2.close()
+    (g1, c1), (g2, c2v) = outs
+    assert np.all(np.isfinite(g1)) and np.all(np.isfinite(g2))
+    np.testing.assert_array_equal(g1, g2)
+    assert c1 == c2v
