@@ -166,6 +166,93 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+R11_TRUE = 0.05
+R11_START = 0.1
+# L-BFGS-B's first step runs to a bound; below 0.01 (a fifth of the true
+# value) the FP32 evaluation of the far-off first point is not reliable
+R11_BOUNDS = (0.01, 1.0)
+
+
+def r11_study(B, ctx, local, dev):
+    """Maximum-likelihood estimate of the first sensor's noise standard
+    deviation sqrt(R_11) (Sec. 6.4) on ten simulated trajectories, each
+    calibrated on its first n observations: L-BFGS-B on phi = log sqrt(R_11)
+    from sqrt(R_11) = 0.1 within [0.01, 1], the other parameters at their
+    true values, with
+    the negative pseudo log-likelihood and its derivative from
+    sqsm_ipls_nll_grad (per-sensor noise model, cubature, M = 20 IPLS and 20
+    adjoint iterations, FP32).  Wall time of each whole fit (GPU evaluations
+    and host optimiser), parallel scan against the sequential smoother (one
+    leaf chunk per sequence).  The sequential fits take minutes at the
+    larger n, so that arm fits fewer trajectories there and, at n = 4000,
+    is timed per evaluation only."""
+    import torch
+    from scipy.optimize import minimize
+    from paper_2207_00426_gb300 import workloads as W
+    f32 = torch.float32
+    M, ADJ = 20, 20
+    trajs = [W.ct_sequence(n=4000, seed=100 + i) for i in range(10)]
+    out = {"M": M, "adjoint_iterations": ADJ, "dtype": "f32", "true": R11_TRUE,
+           "start": R11_START, "bounds": list(R11_BOUNDS), "linearization": "cubature",
+           "by_n": {}}
+    for ns in (100, 1000, 4000):
+        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
+        row = {}
+        for mode, cq, nfit in (("parallel", ctx, 10),
+                               ("sequential", cseq, {100: 10, 1000: 2, 4000: 0}[ns])):
+            def make(dq):
+                yq = torch.tensor(dq["y"][:ns], dtype=f32, device=dev)
+                m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
+                N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
+                th = np.asarray(dq["theta"], dtype=np.float64)
+                last = {}
+
+                def fg(phi):
+                    t4 = np.array([phi[0], th[1], th[2], th[0]])
+                    nll, g, ch, _, _ = B.sqsm_ipls_nll_grad(cq, t4, yq, [0, ns], m0q, N0q, M, ADJ,
+                                                            dt=dq["dt"])
+                    last["change"] = ch.item()
+                    f, g0 = nll.item(), g[0].item()
+                    if not (np.isfinite(f) and np.isfinite(g0)):
+                        last["nonfinite"] = last.get("nonfinite", 0) + 1
+                    return f, np.array([g0])
+                return fg, last
+            fits = []
+            for dq in trajs[:nfit]:
+                fg, last = make(dq)
+                fg([np.log(R11_START)])   # plan, workspace and graph
+                t0 = time.perf_counter()
+                res = minimize(fg, [np.log(R11_START)], jac=True, method="L-BFGS-B",
+                               bounds=[(np.log(R11_BOUNDS[0]), np.log(R11_BOUNDS[1]))],
+                               options={"maxiter": 50})
+                fits.append({"estimate": float(np.exp(res.x[0])), "evaluations": int(res.nfev),
+                             "seconds": time.perf_counter() - t0, "status": int(res.status),
+                             "adjoint_last_rel_change": last["change"],
+                             "nonfinite_evaluations": last.get("nonfinite", 0)})
+            fg, _ = make(trajs[0])
+            fg([np.log(R11_START)])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(2):
+                fg([np.log(R11_START)])
+            per_eval = (time.perf_counter() - t0) / 2
+            ent = {"ms_per_evaluation": 1e3 * per_eval, "fits": len(fits)}
+            if fits:
+                est = np.array([f["estimate"] for f in fits])
+                ent.update({"estimate_mean": float(est.mean()), "estimate_std": float(est.std()),
+                            "seconds_per_fit_mean": float(np.mean([f["seconds"] for f in fits])),
+                            "evaluations_mean": float(np.mean([f["evaluations"] for f in fits])),
+                            "status": [f["status"] for f in fits],
+                            "max_adjoint_rel_change": max(f["adjoint_last_rel_change"]
+                                                          for f in fits),
+                            "nonfinite_evaluations": sum(f["nonfinite_evaluations"]
+                                                         for f in fits)})
+            row[mode] = ent
+        cseq.close()
+        out["by_n"][str(ns)] = row
+    return out
+
+
 def gpu_arm(args, rank, world, local):
     import torch
     from paper_2207_00426_gb300 import binding as B
@@ -460,6 +547,9 @@ def gpu_arm(args, rank, world, local):
         cseq.close()
         population[str(ns)] = row
 
+    # ---- sqrt(R_11) maximum-likelihood estimation (Sec. 6.4)
+    r11 = r11_study(B, ctx, local, dev)
+
     # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
     #      for cubature and extended SLR in FP32 and cubature in FP64, and
     #      the whole-step fraction of the FP32 peak (cubature FP32)
@@ -580,6 +670,7 @@ def gpu_arm(args, rank, world, local):
                 "slr_rules": {"unit": UNIT, "n": n, "M": M, "by_rule": rules},
                 "sequential_vs_parallel": {"M": M, "dtype": "f32", "by_n": seqpar},
                 "population_model": {"M": 100, "dtype": "f32", "by_n": population},
+                "sqrt_r11_estimation": r11,
                 "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
