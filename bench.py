@@ -428,6 +428,27 @@ def gpu_arm(args, rank, world, local):
 
     grads["f32"] = nll_grad_rate(torch.float32, max(2, min(args.steps, 5)))
     grads["f64"] = nll_grad_rate(torch.float64, 2)
+    # the parameter-estimation batch: 256 sequences of n = 2000, FP32
+    try:
+        dg = W.ct_batch(lengths=[2000] * 256, seed=4)
+        yg = torch.tensor(dg["y"], dtype=torch.float32, device=dev)
+        m0g = torch.tensor(dg["m0"], dtype=torch.float32, device=dev)
+        N0g = torch.tensor(dg["N0"], dtype=torch.float32, device=dev)
+        offg = [int(v) for v in dg["offsets"]]
+        outg = {}
+
+        def evg():
+            outg["r"] = B.sqsm_ipls_nll_grad(ctx, dg["theta"], yg, offg, m0g, N0g, M, ADJ,
+                                             dt=dg["dt"])
+        evg()
+        torch.cuda.synchronize()
+        tg = timed(evg, 3)
+        grads["batch_256x2000_f32"] = {"evals_per_s": 1.0 / tg, "ms_per_eval": 1e3 * tg,
+                                       "steps_per_eval": int(offg[-1]),
+                                       "adjoint_iterations": ADJ,
+                                       "adjoint_last_rel_change": outg["r"][2].item()}
+    except Exception as e:   # reported, not fatal to the main metric
+        grads["batch_256x2000_f32"] = {"error": repr(e)[:300]}
     # how far the M-iteration trajectory is from a fixed point: max-norm
     # change of m^s from iteration M to M + 1 (FP32)
     ms_next = torch.empty_like(ms)
