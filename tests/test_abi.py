@@ -45,3 +45,31 @@ def test_null_context_is_rejected(lib):
 def test_supported_shapes(lib):
     assert lib.supported_shape(5, 2) and lib.supported_shape(4, 2)
     assert not lib.supported_shape(7, 7)
+
+
+def test_enum_values_match_the_header(lib):
+    """Every enum constant of include/sqsm.h that the binding mirrors has the
+    header's value."""
+    src = open(os.path.join(ROOT, "include", "sqsm.h")).read()
+    values = {k: int(v) for k, v in re.findall(r"\bSQSM_([A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    assert {"OK", "CUBATURE", "MODEL_CT_BEARINGS_R"} <= set(values)
+    mirrored = [k for k in values if hasattr(lib, k)]
+    assert len(mirrored) >= 15
+    for k in mirrored:
+        assert getattr(lib, k) == values[k], k
+
+
+def test_ct_model_from_theta_length(lib):
+    """Three CT parameters select the shared-noise model, four the model with
+    one noise level per sensor; other lengths are refused on the host."""
+    import numpy as np
+    sensors = np.array([[-1.5, 0.5], [1.0, 1.0]])
+    m3, t3 = lib._ct_model(np.log([0.05, 0.01, 0.1]), 0.01, sensors)
+    m4, t4 = lib._ct_model(np.log([0.03, 0.01, 0.1, 0.08]), 0.01, sensors)
+    assert m3.kind == lib.MODEL_CT_BEARINGS and len(t3) == 3
+    assert m4.kind == lib.MODEL_CT_BEARINGS_R and len(t4) == 4
+    assert abs(t4[3] - np.log(0.08)) == 0.0 and m4.dt == 0.01
+    assert list(m4.sensors) == [-1.5, 0.5, 1.0, 1.0]
+    for bad in ([0.0, 0.0], [0.0] * 5):
+        with pytest.raises(ValueError):
+            lib._ct_model(bad, 0.01, sensors)
