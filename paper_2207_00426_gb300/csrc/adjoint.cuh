@@ -24,7 +24,12 @@
 // reduce-then-scan as the forward filter and smoother (no thread waits on
 // another).  The first map of the forward recurrence and the last of the
 // backward one absorb their boundary value (B = 0), which makes a chunk that
-// holds them independent of its carry.
+// holds them independent of its carry.  Every iteration of Alg. 4 runs on
+// the same linearisation, so what steps 2-5 need of it (the Kalman and RTS
+// quantities, the fixed parts of both maps, the cubature regressions' G and
+// residual columns) is computed once per evaluation into per-step tables
+// (adj_tables.h); an iteration then does only the work that depends on
+// lambda.
 #pragma once
 
 #include "adj_tables.h"
