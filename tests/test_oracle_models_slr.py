@@ -298,3 +298,33 @@ def test_point_mass_limit_is_taylor():
         Ht, dt_, SRt = slr.observation_taylor(mdl, m, np.array([3.0]))
         np.testing.assert_allclose(H, Ht, rtol=max(tol, 1e-15))
         np.testing.assert_allclose(SR, SRt, rtol=max(tol, 1e-15))
+
+
+@pytest.mark.parametrize("m", [-0.5, 0.3, 1.2])
+@pytest.mark.parametrize("P", [1e-3, 1e-2])
+def test_ricker_gauss_hermite_slr_against_lognormal_moments(m, P):
+    """x ~ N(m, P): the Poisson count y | x ~ Poisson(b e^x) has E[y] =
+    b e^{m+P/2}, Cov(x, y) = P E[y] (Stein's lemma), Var(y) = E[y] +
+    b^2 e^{2m+P}(e^P - 1), so H = E[y] and the residual Omega - E[y] =
+    b^2 e^{2m+P}(e^P - 1 - P); the transition log a + x - e^x has F = 1 -
+    e^{m+P/2} and Lambda - Q = e^{2m+P}(e^P - 1 - P).  The three-point
+    Gauss-Hermite rule is exact to degree five and gives E[z^6] = 9 instead
+    of 15, which fixes its leading errors: -P^2/20 (relative) in the
+    regression slope, -5P/6 (relative) in the residual variances, -P^3/120
+    (relative) in E[e^x]."""
+    mdl = models.RickerPoisson(W.RICKER_THETA_TRUE)
+    a, b, q = mdl.a, mdl.b, mdl.q
+    N = np.array([[np.sqrt(P)]])
+    H, d, S = slr.observation_sigma(mdl, np.array([m]), N, np.array([3.0]), "gauss-hermite")
+    Ey = b * np.exp(m + P / 2)
+    resid = np.exp(2 * m + P) * (np.exp(P) - 1 - P)
+    assert abs(H[0, 0] / Ey - 1 + P * P / 20) <= P ** 3
+    assert abs((d[0] + H[0, 0] * m) / Ey - 1) <= P ** 3
+    # Omega = E[Var(y|x)] + residual of E[y|x]; the rule's E[b e^x] is
+    # E[y] (1 - P^3/120), its residual b^2 resid (1 - 5P/6)
+    assert abs((S[0, 0] ** 2 - Ey * (1 - P ** 3 / 120)) / (b * b * resid) - 1 + 5 * P / 6) <= 2 * P * P
+    F, c, SQ = slr.transition_sigma(mdl, np.array([m]), N, "gauss-hermite")
+    e = np.exp(m + P / 2)
+    assert abs(F[0, 0] - (1 - e) - e * P * P / 20) <= e * P ** 3
+    assert abs(c[0] + F[0, 0] * m - (np.log(a) + m - e)) <= e * P ** 3
+    assert abs((SQ[0, 0] ** 2 - q) / resid - 1 + 5 * P / 6) <= 2 * P * P
