@@ -328,3 +328,19 @@ def test_ricker_gauss_hermite_slr_against_lognormal_moments(m, P):
     assert abs(F[0, 0] - (1 - e) - e * P * P / 20) <= e * P ** 3
     assert abs(c[0] + F[0, 0] * m - (np.log(a) + m - e)) <= e * P ** 3
     assert abs((SQ[0, 0] ** 2 - q) / resid - 1 + 5 * P / 6) <= 2 * P * P
+
+
+@pytest.mark.parametrize("rule,z4", [("cubature", 1.0), ("unscented", 2.0)])
+@pytest.mark.parametrize("m,P", [(1.2, 1e-2), (0.3, 1e-2), (-0.5, 1e-3)])
+def test_degree_three_rules_against_lognormal_moments(rule, z4, m, P):
+    """At n_x = 1 the cubature points m +- N (weights 1/2) and the unscented
+    points m, m +- sqrt(2) N (weights 1/2, 1/4, kappa = 1) are exact to
+    degree three and give E[z^4] = 1 and 2 instead of 3, so on the Poisson
+    count of the Ricker model (E[y] = b e^{m+P/2} = H) the slope is off by
+    (E[z^4] - 3) P/6 and the mean by (E[z^4] - 3) P^2/24 (relative)."""
+    mdl = models.RickerPoisson(W.RICKER_THETA_TRUE)
+    H, d, _ = slr.observation_sigma(mdl, np.array([m]), np.array([[np.sqrt(P)]]),
+                                    np.array([3.0]), rule)
+    Ey = mdl.b * np.exp(m + P / 2)
+    assert abs(H[0, 0] / Ey - 1 - (z4 - 3) * P / 6) <= P * P
+    assert abs((d[0] + H[0, 0] * m) / Ey - 1 - (z4 - 3) * P * P / 24) <= P ** 3
