@@ -511,13 +511,16 @@ def gpu_arm(args, rank, world, local):
                / tb / 1e12}
     del yb, msb, Nsb
 
-    # ---- the same solve with each SLR rule (FP32, n = 1e5, M = 10)
+    # ---- the same solve with each SLR rule (FP32, n = 1e5, M = 10), into
+    #      buffers of its own (ms, Ns, ll keep the cubature solve compared
+    #      with FP64 below)
     rules = {}
+    msr, Nsr, llr = torch.empty_like(ms), torch.empty_like(Ns), torch.empty_like(ll)
     for name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED),
                       ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
         def rstep(lin=lin):
             B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, lin, dt=d["dt"],
-                               ms=ms, Ns=Ns, loglik=ll)
+                               ms=msr, Ns=Nsr, loglik=llr)
         rstep()
         torch.cuda.synchronize()
         tr = timed(rstep, 3)
