@@ -51,7 +51,10 @@ typedef enum {
   SQSM_OK = 0,
   SQSM_ERR_INVALID_ARG = 1,      /* null pointer, bad size/stride/enum      */
   SQSM_ERR_UNSUPPORTED = 2,      /* (nx, ny) pair not compiled in            */
-  SQSM_ERR_NOT_PD = 4,           /* device: zero pivot in a triangular solve */
+  SQSM_ERR_NOT_PD = 4,           /* reserved: no kernel raises it; a zero
+                                    pivot in a triangular solve or a lost
+                                    definiteness surfaces as a non-finite
+                                    output (SQSM_ERR_NONFINITE)             */
   SQSM_ERR_NONFINITE = 8,        /* device: NaN/Inf in an output             */
   SQSM_ERR_CUDA = 16,            /* a CUDA runtime call failed               */
   SQSM_ERR_NO_MEMORY = 32,       /* workspace allocation failed              */
@@ -151,9 +154,9 @@ int sqsm_destroy(sqsm_ctx* ctx);
  * valid until the next call on ctx. */
 const char* sqsm_last_error(const sqsm_ctx* ctx);
 
-/* Synchronise ctx's device, read and clear the device status word: 0 or an
- * OR of SQSM_ERR_NONFINITE / SQSM_ERR_NOT_PD raised by kernels since the
- * last read.  *status is host memory. */
+/* Synchronise ctx's device, read and clear the device status word: 0 or
+ * SQSM_ERR_NONFINITE if a kernel produced a non-finite filtered or smoothed
+ * mean or log-likelihood since the last read.  *status is host memory. */
 int sqsm_get_status(sqsm_ctx* ctx, int* status);
 
 /* Parallel square-root Kalman filter and RTS smoother on one linear-Gaussian
