@@ -1,11 +1,13 @@
 """torch.autograd.Function for the negative pseudo log-likelihood of the CT
-bearings model as a function of theta = (log sigma, log q_c, log q_omega).
+bearings model as a function of theta = (log sigma, log q_c, log q_omega),
+or of theta = (log sqrt(R_11), log q_c, log q_omega, log sqrt(R_22)) with
+one noise level per sensor (Sec. 6.4).
 
 forward() calls sqsm_ipls_nll_grad (IPLS to the trajectory n*, the
 pseudo log-likelihood of Sec. 5.1 and its gradient by the hand-written
 adjoint of Sec. 5.2) and keeps the gradient; backward() scales it by the
-incoming gradient.  theta is a CPU float64 tensor of shape (3,) (the C ABI
-takes the parameters on the host); the data live on the GPU.
+incoming gradient.  theta is a CPU float64 tensor of shape (3,) or (4,)
+(the C ABI takes the parameters on the host); the data live on the GPU.
 """
 import torch
 
