@@ -457,6 +457,8 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
       for (int q = 0; q < NX; ++q) Lb[i * NX + q] = T(0.5) * (gb[GR::L + i * NX + q] + gb[GR::L + q * NX + i]);
     cubature_vjp<T, NX>(m, N, t + ST::Gf, t + ST::sf, gb + GR::F, gb + GR::c, Lb,
                         [&](const T* xx, T* J) { ct_jac_f(P, xx, J); }, mb, Nb);
+    // Q = q_c Q_c + q_w Q_w (Q_w only at (4, 4)): d/d log q_c = Lambda-bar :
+    // (Q - Q_44 e_4 e_4^T), d/d log q_w = Lambda-bar_44 Q_44
     T Q[NX * NX];
     gram_lower<T, NX>(P.SQ, Q);
     double tq = 0.0;
