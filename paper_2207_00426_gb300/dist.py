@@ -3,7 +3,7 @@
 Sequences are independent (each has its own prior and observations), so a
 batch is sharded by sequence and every rank smooths its own shard with no
 collective on the data path.  The only exchange is a sum over ranks of the
-per-rank negative log-likelihood and gradient (3 values) when a summed
+per-rank negative log-likelihood and gradient (1 + len(theta) values) when a summed
 objective is wanted, and a max over ranks of timings.
 
 shard_sequences   longest-processing-time assignment of sequences to ranks
