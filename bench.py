@@ -6,20 +6,28 @@ log-likelihood, parallel square-root smoother scan -- over one synthetic
 coordinated-turn sequence of n = 100000 observations (n_x = 5, n_y = 2),
 FP32 arithmetic with FP64 log-likelihood accumulation.
 
-Metric: smoothed steps/s = (time steps x IPLS iterations) per second.
+Metric: smoothed steps/s = (time steps x IPLS iterations) per second; the
+same line carries the NLL + gradient evaluations/s (Sec. 5.2) at the same
+size and the FP64 build's rate and error (``nll_grad``, ``f64``).
 Timing: CUDA events around each step on the launch stream, L2 flushed (a
 256 MiB write) between steps outside the events, max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--studies [--studies-out PATH]]
 
 With torchrun (N > 1) every rank smooths its own sequence (weak scaling, no
 data-path collective; a gloo group only aligns the timed region and takes the
 max over ranks).  --impl reference times the FP64 CPU oracle instead (rank 0
-only) on a bounded sample of the same workload.
+only) on a bounded sample of the same workload.  --studies also runs the
+paper's further experiments (length sweep, SLR rules, sequential against
+parallel, population model, sqrt(R_11) estimation, FP32 robustness) and
+writes them to a JSON file; the last stdout line is always the short
+benchmark line.
 """
 import os
 
-# the oracle legs run single-threaded: pin BLAS threads before numpy loads
+# the oracle legs run single-threaded per process: pin BLAS threads before
+# numpy loads (the batched CPU baselines use one process per core)
 for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, "1")
 
@@ -35,13 +43,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "smoothed steps/sec (CT bearings-only IPLS, n=1e5, nx=5)"
+METRIC = "smoothed steps/sec and NLL+grad evals/sec at n=1e5, nx=5, FP32 vs FP64"
 UNIT = "smoothed steps/s"
 N_STEPS = 100_000
 M_ITERS = 10
+ADJ_ITERS = 10
 SEED = 1
 CPU_SAMPLE_STEPS = 1000          # oracle sample for the CPU baseline leg
 REF_SAMPLE_STEPS = 400           # oracle sample per --impl reference step
+BATCH_CPU_PREFIX = 250           # observations of each sampled sequence of the 4096
+GRAD_CPU_PREFIX = 100            # ... and of the 256 x 2000 batch (host baselines)
+
+# DRAM bytes per launch of a kernel family at the benchmark workload
+# (n = 1e5, FP32, default scan shape), from one ncu capture of the current
+# kernels: dram__bytes_read.sum + dram__bytes_write.sum.  A family whose
+# kernels changed since their capture has no entry (traffic null).
+NCU_TRAFFIC = {("filter_up", 100_000): 4.12e6}
 
 
 def parse():
@@ -53,6 +70,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N_STEPS)
     ap.add_argument("--M", type=int, default=M_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--studies", action="store_true",
+                    help="also run the paper's further experiments (minutes)")
+    ap.add_argument("--studies-out", default=os.path.join("gpurun_out", "bench_studies.json"))
     return ap.parse_args()
 
 
@@ -63,13 +83,11 @@ def dist_env():
     return rank, world, local
 
 
-def config(args, world):
-    from paper_2207_00426_gb300.costmodel import default_leaf
+def config(args, world, leaf=None):
     return {"workload": f"coordinated-turn bearings-only tracking, cubature IPLS, "
                         f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
             "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
-            "sequences_total": world, "leaf_chunk": default_leaf(args.n),
-            "upper_levels": "folds of 4 above 160000 items, 32-item warp scans below",
+            "sequences_total": world, "leaf_chunk": leaf,
             "l2": "flushed between timed steps (256 MiB write outside the events)",
             "parallelism": f"independent sequences, {world} GPU(s)"}
 
@@ -79,7 +97,7 @@ def config(args, world):
 # ---------------------------------------------------------------------------
 def oracle_rate(n_sample, M, reps=1):
     """Time the FP64 oracle's IPLS on the first n_sample observations of the
-    workload (single thread).  Returns (steps/s, seconds, sample text)."""
+    workload (single thread).  Returns (steps/s, seconds)."""
     from oracle import ipls as O, models as OM
     from paper_2207_00426_gb300 import workloads as W
     d = W.ct_sequence(n=n_sample, seed=SEED)
@@ -89,6 +107,78 @@ def oracle_rate(n_sample, M, reps=1):
         O.ipls(ct, d["y"], d["m0"], d["N0"], M, "cubature")
     dt = time.perf_counter() - t0
     return n_sample * M * reps / dt, dt
+
+
+def _oracle_ipls_job(job):
+    """One oracle IPLS solve (a worker of the batched CPU baseline)."""
+    from oracle import ipls as O, models as OM
+    theta, dt, y, m0, N0, M = job
+    O.ipls(OM.CTBearings(theta, dt=dt), y, m0, N0, M, "cubature")
+    return len(y)
+
+
+def _oracle_grad_job(job):
+    """One oracle NLL + gradient evaluation by central differences at fixed
+    M (a worker of the batched CPU baseline of the parameter-estimation
+    batch)."""
+    from oracle import ipls as O, models as OM
+    theta, dt, y, m0, N0, M = job
+    h = 1e-4
+    th = np.asarray(theta, dtype=np.float64)
+
+    def nll(t):
+        return -O.ipls(OM.CTBearings(t, dt=dt), y, m0, N0, M, "cubature")[2]
+    nll(th)
+    for i in range(len(th)):
+        e = np.zeros_like(th)
+        e[i] = h
+        nll(th + e)
+        nll(th - e)
+    return len(y)
+
+
+def batched_cpu_baselines(M):
+    """The oracle on samples of the two batched workloads, one process per
+    host core (spawned): the 4096-sequence batch (IPLS, smoothed steps/s;
+    two sequences per core, each on its first BATCH_CPU_PREFIX observations)
+    and the 256 x 2000 parameter-estimation batch (NLL + gradient by central
+    differences at fixed M; one sequence per core on its first
+    GRAD_CPU_PREFIX observations, the rate scaled to the whole batch)."""
+    import multiprocessing as mp
+    from paper_2207_00426_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    out = {}
+    ctx = mp.get_context("spawn")
+    db = W.ct_batch(batch=4096, lo=100, hi=5000, seed=3)
+    off = db["offsets"]
+    pick = np.random.default_rng(0).choice(4096, 2 * cores, replace=False)
+    jobs = [(db["theta"], db["dt"], db["y"][off[b]:min(off[b + 1], off[b] + BATCH_CPU_PREFIX)],
+             db["m0"][b], db["N0"][b], M) for b in pick]
+    dg = W.ct_batch(lengths=[2000] * 256, seed=4)
+    og = dg["offsets"]
+    gjobs = [(dg["theta"], dg["dt"], dg["y"][og[b]:og[b] + GRAD_CPU_PREFIX], dg["m0"][b],
+              dg["N0"][b], M) for b in range(min(cores, 256))]
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_ipls_job, [(db["theta"], db["dt"], db["y"][:20], db["m0"][0],
+                                     db["N0"][0], 1)] * cores)   # workers up, imports done
+        t0 = time.perf_counter()
+        steps = sum(pool.map(_oracle_ipls_job, jobs, chunksize=1))
+        t_b = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        gsteps = sum(pool.map(_oracle_grad_job, gjobs, chunksize=1))
+        t_g = time.perf_counter() - t0
+    out["batch_4096"] = {
+        "value": steps * M / t_b, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": f"{len(jobs)} sequences drawn from the 4096 (seed 0), first "
+                  f"{BATCH_CPU_PREFIX} observations of each ({steps} steps), M={M}, "
+                  f"one process per core ({t_b:.1f} s)"}
+    out["batch_256x2000_nll_grad"] = {
+        "value": gsteps / t_g / (256 * 2000), "unit": "NLL+grad evals/s", "cores": cores,
+        "kind": "oracle",
+        "sample": f"first {GRAD_CPU_PREFIX} observations of {len(gjobs)} of the 256 "
+                  f"sequences, M={M}, gradient by central differences (7 IPLS solves), "
+                  f"one process per core ({t_g:.1f} s); rate scaled to 256 x 2000 steps"}
+    return out
 
 
 def reference_arm(args, rank):
@@ -104,11 +194,12 @@ def reference_arm(args, rank):
     value = REF_SAMPLE_STEPS * args.M * args.steps / tot
     sample = (f"first {REF_SAMPLE_STEPS} observations of the n={args.n} sequence, "
               f"M={args.M}, per step")
+    from paper_2207_00426_gb300.costmodel import default_leaf
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args, 1),
+            "config": config(args, 1, default_leaf(args.n)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -164,6 +255,450 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def fp32_peak(B, torch, dev, stream, sm_count):
+    """Measured FP32 roof: the library's FMA-only probe kernel, 8 blocks of
+    256 threads per SM, timed with CUDA events on the launch stream (best of
+    five after a warm-up).  Returns (TFLOP/s, basis text)."""
+    blocks, threads, iters = 8 * sm_count, 256, 20000
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    B.fp32_fma_probe(iters, blocks, threads, out)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fl = B.fp32_fma_probe(iters, blocks, threads, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        best = t if best is None else min(best, t)
+    return fl / best / 1e12, (f"FMA-only probe kernel, {blocks} x {threads} threads, "
+                              f"{fl:.3g} flops, CUDA events, best of 5")
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+    from paper_2207_00426_gb300 import binding as B
+    from paper_2207_00426_gb300 import costmodel as CM
+    from paper_2207_00426_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        from paper_2207_00426_gb300 import dist as D
+        return D.allreduce_max(x)
+
+    n, M = args.n, args.M
+    d = W.ct_sequence(n=n, seed=SEED + rank)
+    f32 = torch.float32
+    y = torch.tensor(d["y"], dtype=f32, device=dev)
+    m0 = torch.tensor(d["m0"][None], dtype=f32, device=dev)
+    N0 = torch.tensor(d["N0"][None], dtype=f32, device=dev)
+    ms = torch.empty((n + 1, 5), dtype=f32, device=dev)
+    Ns = torch.empty((n + 1, 5, 5), dtype=f32, device=dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    ctx = B.Context(local, use_graph=True)
+    leaf = ctx.scan_shape([0, n])[0]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, B.CUBATURE, dt=d["dt"],
+                           ms=ms, Ns=Ns, loglik=ll)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert ctx.status() == 0 and np.isfinite(ll.item())
+
+    # ---- timed region: K steps, device time per step, L2 flushed between
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    barrier()
+    t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    t_max = max_over_ranks(t_dev)
+    value = n * M * args.steps * world / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    hy = torch.tensor(d["y"], dtype=f32).pin_memory()
+    hm0 = torch.tensor(d["m0"][None], dtype=f32).pin_memory()
+    hN0 = torch.tensor(d["N0"][None], dtype=f32).pin_memory()
+    hms = torch.empty((n + 1, 5), dtype=f32).pin_memory()
+    hNs = torch.empty((n + 1, 5, 5), dtype=f32).pin_memory()
+    hll = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        y.copy_(hy, non_blocking=True)
+        m0.copy_(hm0, non_blocking=True)
+        N0.copy_(hN0, non_blocking=True)
+        step()
+        hms.copy_(ms, non_blocking=True)
+        hNs.copy_(Ns, non_blocking=True)
+        hll.copy_(ll, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    eevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    barrier()
+    for a, b in eevs:
+        flush.fill_(1)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(sum(a.elapsed_time(b) for a, b in eevs) / 1e3)
+    h2d = hy.numel() * 4 + hm0.numel() * 4 + hN0.numel() * 4
+    d2h = hms.numel() * 4 + hNs.numel() * 4 + 8
+
+    # ---- per-kernel event timing (instrumented replay of the same step)
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    acc = {}
+    nprof = max(3, min(args.steps, 10))
+    for _ in range(nprof):
+        flush.fill_(1)
+        step()
+        for k, (t, c) in ctx.profile_read().items():
+            a0 = acc.setdefault(k, [0.0, 0])
+            a0[0] += t
+            a0[1] += c
+    ctx.profile(False)
+    launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
+    flops = CM.ipls_kernel_flops([n], leaf=leaf)
+    total_ms = sum(t for t, _ in acc.values())
+    top = max(acc, key=lambda k: acc[k][0])
+    # algorithmic flops of the family per step, spread over its launches
+    fam_flops = flops[top][0] * flops[top][1] * M
+    f_launch = fam_flops / (acc[top][1] / nprof)
+    t_launch = acc[top][0] / acc[top][1] / 1e3
+    peak, peak_basis = fp32_peak(B, torch, dev, stream, sm_count)
+    derived = sm_count * 128 * 2 * 2070e6 / 1e12
+    achieved = f_launch / t_launch / 1e12
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((top, n)), "traffic_unit": "bytes per launch",
+                "flops_per_launch": f_launch, "share_of_step": acc[top][0] / total_ms,
+                "peak_note": "measured (" + peak_basis + ")",
+                "peak_derived": derived,
+                "peak_derived_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    it_flops = CM.ipls_iteration_flops([n], leaf=leaf)
+    whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
+    whole["frac"] = whole["achieved_tflops"] / peak
+    shares = {k: round(t / total_ms, 4) for k, (t, _) in acc.items()}
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / k
+
+    # ---- NLL + gradient (Sec. 5.2) at the same size: M IPLS iterations, the
+    #      final linearisation pass and ADJ adjoint fixed-point iterations
+    grads = {}
+
+    def nll_grad_rate(dtype, k):
+        yy, mm0, NN0 = y.to(dtype), m0.to(dtype), N0.to(dtype)
+        out = {}
+
+        def ev():
+            out["r"] = B.sqsm_ipls_nll_grad(ctx, d["theta"], yy, [0, n], mm0, NN0, M, ADJ_ITERS,
+                                            dt=d["dt"])
+        ev()
+        torch.cuda.synchronize()
+        t = timed(ev, k)
+        ch = out["r"][2].item()
+        # the gradient is the derivative at the fixed point of Alg. 3; this
+        # trajectory after M iterations is not one (see ipls_change_after_M)
+        return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t,
+                "adjoint_last_rel_change": ch,
+                "fixed_point_reached": bool(np.isfinite(ch) and ch < 1e-3)}
+
+    grads["f32"] = nll_grad_rate(torch.float32, max(2, min(args.steps, 5)))
+    grads["f64"] = nll_grad_rate(torch.float64, 2)
+    grads["M"], grads["adjoint_iterations"] = M, ADJ_ITERS
+    # the parameter-estimation batch: 256 sequences of n = 2000, FP32
+    dg = W.ct_batch(lengths=[2000] * 256, seed=4)
+    yg = torch.tensor(dg["y"], dtype=torch.float32, device=dev)
+    m0g = torch.tensor(dg["m0"], dtype=torch.float32, device=dev)
+    N0g = torch.tensor(dg["N0"], dtype=torch.float32, device=dev)
+    offg = [int(v) for v in dg["offsets"]]
+
+    def evg():
+        B.sqsm_ipls_nll_grad(ctx, dg["theta"], yg, offg, m0g, N0g, M, ADJ_ITERS, dt=dg["dt"])
+    evg()
+    torch.cuda.synchronize()
+    tg = timed(evg, 3)
+    grads["batch_256x2000_f32"] = {"evals_per_s": 1.0 / tg, "ms_per_eval": 1e3 * tg}
+    del yg, m0g, N0g
+    # how far the M-iteration trajectory is from a fixed point: max-norm
+    # change of m^s from iteration M to M + 1 (FP32)
+    ms_next = torch.empty_like(ms)
+    B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M + 1, B.CUBATURE, dt=d["dt"],
+                       ms=ms_next, Ns=torch.empty_like(Ns), loglik=torch.empty_like(ll))
+    step()
+    torch.cuda.synchronize()
+    grads["ipls_change_after_M"] = (ms_next - ms).abs().max().item()
+    del ms_next
+
+    # ---- batched: 4096 independent sequences, lengths U{100..5000} (ragged),
+    #      scan shape chosen by the library's autotuner (first call, untimed)
+    db = W.ct_batch(batch=4096, lo=100, hi=5000, seed=3)
+    yb = torch.tensor(db["y"], dtype=f32, device=dev)
+    m0b = torch.tensor(db["m0"], dtype=f32, device=dev)
+    N0b = torch.tensor(db["N0"], dtype=f32, device=dev)
+    nb_tot = int(db["offsets"][-1])
+    rows_b = nb_tot + 4096
+    msb = torch.empty((rows_b, 5), dtype=f32, device=dev)
+    Nsb = torch.empty((rows_b, 5, 5), dtype=f32, device=dev)
+    llb = torch.empty(4096, dtype=torch.float64, device=dev)
+    tctx = B.Context(local, use_graph=True, autotune=True)
+
+    def bstep():
+        B.sqsm_ipls_smooth(tctx, db["theta"], yb, db["offsets"], m0b, N0b, M, B.CUBATURE,
+                           dt=db["dt"], ms=msb, Ns=Nsb, loglik=llb)
+    bstep()
+    torch.cuda.synchronize()
+    tb = timed(bstep, 3)
+    bshape = tctx.scan_shape(db["offsets"])
+    tctx.close()
+    bwhole = CM.ipls_iteration_flops(list(np.diff(db["offsets"])), leaf=bshape[0],
+                                     radix=bshape[1]) * M / tb / 1e12
+    batched = {"workload": "4096 CT sequences, lengths U{100..5000}, cubature IPLS, M=10",
+               "steps_total": nb_tot, "value": nb_tot * M / tb, "unit": UNIT,
+               "ms_per_step": 1e3 * tb, "scan_shape": list(bshape),
+               "whole_step_tflops": bwhole, "whole_step_frac": bwhole / peak}
+    del yb, msb, Nsb
+
+    # ---- FP64 variant of the same step (comparator), few steps
+    f64 = torch.float64
+    y64, m064, N064 = y.double(), m0.double(), N0.double()
+    ms64 = torch.empty((n + 1, 5), dtype=f64, device=dev)
+    Ns64 = torch.empty((n + 1, 5, 5), dtype=f64, device=dev)
+    ll64 = torch.empty(1, dtype=f64, device=dev)
+
+    def step64():
+        B.sqsm_ipls_smooth(ctx, d["theta"], y64, [0, n], m064, N064, M, B.CUBATURE, dt=d["dt"],
+                           ms=ms64, Ns=Ns64, loglik=ll64)
+    step64()
+    torch.cuda.synchronize()
+    t64 = timed(step64, 3)
+    step()
+    torch.cuda.synchronize()
+    err_f32 = float((ms.double() - ms64).norm(dim=1).max() / ms64.norm(dim=1).max())
+    ll_rel = abs(ll.item() - ll64.item()) / abs(ll64.item())
+
+    studies = None
+    if args.studies:
+        studies = run_studies(B, torch, ctx, local, dev, M, peak, timed)
+        os.makedirs(os.path.dirname(os.path.abspath(args.studies_out)), exist_ok=True)
+        with open(args.studies_out, "w") as f:
+            json.dump(studies, f, indent=1)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": config(args, world, leaf),
+                "wall_s_timed_region": wall,
+                "e2e": {"value": n * M * args.steps * world / t_e2e, "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "clocks": clk.summary(), "roofline": roofline, "whole_step": whole,
+                "shares": shares,
+                "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
+                        "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
+                "nll_grad": grads, "batched": batched, "loglik": ll.item(),
+                "studies": args.studies_out if studies is not None else None}
+    ctx.close()
+    return line
+
+
+def run_studies(B, torch, ctx, local, dev, M, peak, timed):
+    """The paper's further experiments on the GPU (returned as one dict):
+    the SLR rules at n = 1e5, sequential against parallel, the population
+    model, the sqrt(R_11) study, the length sweep and the FP32 robustness
+    experiment."""
+    from paper_2207_00426_gb300 import costmodel as CM
+    from paper_2207_00426_gb300 import workloads as W
+    f32 = torch.float32
+    out = {}
+    n = N_STEPS
+    d = W.ct_sequence(n=n, seed=SEED)
+    y = torch.tensor(d["y"], dtype=f32, device=dev)
+    m0 = torch.tensor(d["m0"][None], dtype=f32, device=dev)
+    N0 = torch.tensor(d["N0"][None], dtype=f32, device=dev)
+
+    # ---- the same solve with each SLR rule (FP32, n = 1e5, M = 10)
+    rules = {}
+    for name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED),
+                      ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
+        def rstep(lin=lin):
+            B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, lin, dt=d["dt"])
+        rstep()
+        torch.cuda.synchronize()
+        tr = timed(rstep, 3)
+        rules[name] = {"value": n * M / tr, "ms_per_step": 1e3 * tr}
+    out["slr_rules"] = {"unit": UNIT, "n": n, "M": M, "by_rule": rules}
+
+    # ---- the paper's sequential-vs-parallel comparison on the GPU: the
+    #      sequential smoother is the same library with one leaf chunk per
+    #      sequence (one thread runs the whole filter and smoother; the SLR
+    #      stays one thread per step), M = 10, FP32, each rule
+    seqpar = {}
+    for ns in (100, 1000, 4000):
+        dq = W.ct_sequence(n=ns, seed=7 + ns)
+        yq = torch.tensor(dq["y"], dtype=f32, device=dev)
+        m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
+        N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
+        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
+        row = {}
+        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE),
+                          ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
+            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
+                def qstep(cq=cq, lin=lin):
+                    B.sqsm_ipls_smooth(cq, dq["theta"], yq, [0, ns], m0q, N0q, M, lin, dt=dq["dt"])
+                qstep()
+                torch.cuda.synchronize()
+                row[f"{name}_{mode}_ms"] = 1e3 * timed(qstep, 2)
+        cseq.close()
+        seqpar[str(ns)] = row
+    out["sequential_vs_parallel"] = {"M": M, "dtype": "f32", "by_n": seqpar}
+
+    # ---- the paper's population-model timing (Ricker dynamics, Poisson
+    #      counts, n_x = n_y = 1): M = 100 iterations, Taylor and cubature,
+    #      parallel against sequential (one leaf chunk per sequence), FP32
+    population = {}
+    for ns in (100, 1000, 10000):
+        dp = W.ricker_batch([ns], seed=11 + ns)
+        yp = torch.tensor(dp["y"], dtype=f32, device=dev)
+        m0p = torch.tensor(dp["m0"], dtype=f32, device=dev)
+        N0p = torch.tensor(dp["N0"], dtype=f32, device=dev)
+        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
+        row = {}
+        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE)):
+            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
+                def pstep(cq=cq, lin=lin):
+                    B.sqsm_ipls_smooth_population(cq, dp["theta"], yp, dp["offsets"], m0p, N0p,
+                                                  100, lin)
+                pstep()
+                torch.cuda.synchronize()
+                row[f"{name}_{mode}_ms"] = 1e3 * timed(pstep, 2)
+        cseq.close()
+        population[str(ns)] = row
+    out["population_model"] = {"M": 100, "dtype": "f32", "by_n": population}
+
+    # ---- sqrt(R_11) maximum-likelihood estimation (Sec. 6.4)
+    out["sqrt_r11_estimation"] = r11_study(B, ctx, local, dev)
+
+    # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
+    #      for cubature and extended SLR in FP32 and cubature in FP64, and
+    #      the whole-step fraction of the FP32 peak (cubature FP32)
+    sweep = {}
+    for lg in range(10, 21, 2):
+        ns = 1 << lg
+        ds = W.ct_sequence(n=ns, seed=2 + lg)
+        row = {}
+        for name, dtp, lin in (("f32_cubature", torch.float32, B.CUBATURE),
+                               ("f32_extended", torch.float32, B.EXTENDED),
+                               ("f64_cubature", torch.float64, B.CUBATURE)):
+            ys = torch.tensor(ds["y"], dtype=dtp, device=dev)
+            m0s = torch.tensor(ds["m0"][None], dtype=dtp, device=dev)
+            N0s = torch.tensor(ds["N0"][None], dtype=dtp, device=dev)
+
+            def sstep():
+                B.sqsm_ipls_smooth(ctx, ds["theta"], ys, [0, ns], m0s, N0s, M, lin, dt=ds["dt"])
+            sstep()
+            torch.cuda.synchronize()
+            ts = timed(sstep, 3 if dtp == torch.float32 else 1)
+            row[name] = ns * M / ts
+            if name == "f32_cubature":
+                row["f32_cubature_frac_of_fp32_peak"] = (CM.ipls_iteration_flops([ns]) * M / ts
+                                                         / 1e12 / peak)
+        sweep[str(ns)] = row
+    out["sweep"] = {"unit": UNIT, "M": M, "by_n": sweep}
+
+    # ---- FP32 stability of the square-root form against the standard
+    #      (covariance) form, as in the paper's robustness experiment: 15
+    #      sequences per length, M = 20, cubature and extended SLR, share of
+    #      sequences whose log-likelihood is not finite; both in the printed
+    #      absolute coordinates and in the deviation coordinates used here,
+    #      with the means' error against the FP64 square-root run (finite runs)
+    cabs = B.Context(local, use_graph=True, absolute=True)
+    stability = {}
+    noise_sets = {"q_c=0.01,q_w=0.1": W.CT_THETA_TRUE,
+                  "q_c=0.1,q_w=0.1": (W.CT_THETA_TRUE[0], float(np.log(0.1)), float(np.log(0.1)))}
+    for ns, (noise, theta_s) in [(ns, kv) for kv in noise_sets.items()
+                                 for ns in (100, 500, 1000, 2000, 4000, 8000)]:
+        dsb = W.ct_batch(lengths=[ns] * 15, seed=1000 + ns, theta=theta_s)
+        offs = [int(v) for v in dsb["offsets"]]
+        P0s = dsb["N0"] @ np.swapaxes(dsb["N0"], 1, 2)
+        t64 = {k: torch.tensor(dsb[k], dtype=torch.float64, device=dev) for k in ("y", "m0", "N0")}
+        t32 = {k: torch.tensor(dsb[k], dtype=f32, device=dev) for k in ("y", "m0", "N0")}
+        P032 = torch.tensor(P0s, dtype=f32, device=dev)
+        res = {}
+        for lin_name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED)):
+            ms64, _, _ = B.sqsm_ipls_smooth(ctx, dsb["theta"], t64["y"], offs, t64["m0"],
+                                            t64["N0"], 20, lin, dt=dsb["dt"])
+            for coords, c in (("absolute", cabs), ("deviation", ctx)):
+                for form in ("sqrt", "standard"):
+                    if form == "sqrt":
+                        msf, _, llf = B.sqsm_ipls_smooth(c, dsb["theta"], t32["y"], offs,
+                                                         t32["m0"], t32["N0"], 20, lin,
+                                                         dt=dsb["dt"])
+                    else:
+                        msf, _, llf = B.sqsm_ipls_smooth_std(c, dsb["theta"], t32["y"], offs,
+                                                             t32["m0"], P032, 20, lin,
+                                                             dt=dsb["dt"])
+                    torch.cuda.synchronize()
+                    c.status()   # clears the non-finite flag a diverged run raises
+                    llf = llf.cpu().numpy()
+                    fin = np.isfinite(llf)
+                    errs = []
+                    for b in np.nonzero(fin)[0]:
+                        rows = slice(offs[b] + b, offs[b + 1] + b + 1)
+                        ref = ms64[rows].cpu().numpy()
+                        errs.append(float(np.abs(msf[rows].double().cpu().numpy() - ref).max()
+                                          / np.abs(ref).max()))
+                    res[f"{form}_{lin_name}_{coords}"] = {
+                        "divergence_rate": float(1.0 - fin.mean()),
+                        "median_mean_rel_err_vs_f64": float(np.median(errs)) if errs else None}
+        stability.setdefault(noise, {})[str(ns)] = res
+    cabs.close()
+    out["stability_f32"] = {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability}
+    return out
 
 
 R11_TRUE = 0.05
@@ -253,456 +788,6 @@ def r11_study(B, ctx, local, dev):
     return out
 
 
-def gpu_arm(args, rank, world, local):
-    import torch
-    from paper_2207_00426_gb300 import binding as B
-    from paper_2207_00426_gb300 import costmodel as CM
-    from paper_2207_00426_gb300 import workloads as W
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        pg = dist
-
-    def barrier():
-        if pg:
-            pg.barrier()
-
-    def max_over_ranks(x):
-        from paper_2207_00426_gb300 import dist as D
-        return D.allreduce_max(x)
-
-    n, M = args.n, args.M
-    d = W.ct_sequence(n=n, seed=SEED + rank)
-    f32 = torch.float32
-    y = torch.tensor(d["y"], dtype=f32, device=dev)
-    m0 = torch.tensor(d["m0"][None], dtype=f32, device=dev)
-    N0 = torch.tensor(d["N0"][None], dtype=f32, device=dev)
-    ms = torch.empty((n + 1, 5), dtype=f32, device=dev)
-    Ns = torch.empty((n + 1, 5, 5), dtype=f32, device=dev)
-    ll = torch.empty(1, dtype=torch.float64, device=dev)
-    ctx = B.Context(local, use_graph=True)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    def step():
-        B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, B.CUBATURE, dt=d["dt"],
-                           ms=ms, Ns=Ns, loglik=ll)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    assert ctx.status() == 0 and np.isfinite(ll.item())
-
-    # ---- timed region: K steps, device time per step, L2 flushed between
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        w0 = time.perf_counter()
-        for a, b in evs:
-            flush.fill_(1)
-            a.record(stream)
-            step()
-            b.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
-    barrier()
-    t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-    t_max = max_over_ranks(t_dev)
-    value = n * M * args.steps * world / t_max
-    ms_per_step = 1e3 * t_max / args.steps
-
-    # ---- end to end through the C ABI with host buffers (pinned)
-    hy = torch.tensor(d["y"], dtype=f32).pin_memory()
-    hm0 = torch.tensor(d["m0"][None], dtype=f32).pin_memory()
-    hN0 = torch.tensor(d["N0"][None], dtype=f32).pin_memory()
-    hms = torch.empty((n + 1, 5), dtype=f32).pin_memory()
-    hNs = torch.empty((n + 1, 5, 5), dtype=f32).pin_memory()
-    hll = torch.empty(1, dtype=torch.float64).pin_memory()
-
-    def e2e_step():
-        y.copy_(hy, non_blocking=True)
-        m0.copy_(hm0, non_blocking=True)
-        N0.copy_(hN0, non_blocking=True)
-        step()
-        hms.copy_(ms, non_blocking=True)
-        hNs.copy_(Ns, non_blocking=True)
-        hll.copy_(ll, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    eevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in range(args.steps)]
-    barrier()
-    for a, b in eevs:
-        flush.fill_(1)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-    torch.cuda.synchronize()
-    t_e2e = max_over_ranks(sum(a.elapsed_time(b) for a, b in eevs) / 1e3)
-    h2d = hy.numel() * 4 + hm0.numel() * 4 + hN0.numel() * 4
-    d2h = hms.numel() * 4 + hNs.numel() * 4 + 8
-
-    # ---- per-kernel event timing (instrumented replay of the same step)
-    ctx.profile(True)
-    step()
-    torch.cuda.synchronize()
-    acc = {}
-    nprof = max(3, min(args.steps, 10))
-    for _ in range(nprof):
-        flush.fill_(1)
-        step()
-        for k, (t, c) in ctx.profile_read().items():
-            a0 = acc.setdefault(k, [0.0, 0])
-            a0[0] += t
-            a0[1] += c
-    ctx.profile(False)
-    launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
-    flops = CM.ipls_kernel_flops([n])
-    total_ms = sum(t for t, _ in acc.values())
-    kernels = {k: {"ms_per_launch": t / c, "launches_per_step": c / nprof,
-                   "share": t / total_ms} for k, (t, c) in acc.items()}
-    top = max(acc, key=lambda k: acc[k][0])
-    # algorithmic flops of the family per step, spread over its launches
-    fam_flops = flops[top][0] * flops[top][1] * M
-    f_launch = fam_flops / (acc[top][1] / nprof)
-    t_launch = acc[top][0] / acc[top][1] / 1e3
-    peak = 152 * 128 * 2 * 2070e6 / 1e12        # FP32 FMA lanes x 2 x max SM clock
-    achieved = f_launch / t_launch / 1e12
-    # DRAM bytes per launch of the filter scan's upper family at this
-    # workload (n = 1e5, FP32, default scan shape), from an ncu capture of the
-    # same kernels (dram__bytes_read.sum + dram__bytes_write.sum, 12.35 MB
-    # per iteration over its three launches); other workloads: not measured
-    traffic = 4.12e6 if (top == "filter_up" and n == N_STEPS) else None
-    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
-                "peak_note": "derived",
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_unit": "bytes per launch",
-                "flops_per_launch": f_launch, "peak_basis":
-                "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)"}
-    it_flops = CM.ipls_iteration_flops([n])
-    whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
-    whole["frac_of_fp32_peak"] = whole["achieved_tflops"] / peak
-
-    def timed(fn, k):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(k)]
-        for a, b in evs:
-            flush.fill_(1)
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / k
-
-    # ---- NLL + gradient (Sec. 5.2) at the same size: M IPLS iterations, the
-    #      final linearisation pass and ADJ adjoint fixed-point iterations
-    ADJ = 10
-    grads = {}
-
-    def nll_grad_rate(dtype, k):
-        yy, mm0, NN0 = y.to(dtype), m0.to(dtype), N0.to(dtype)
-        out = {}
-
-        def ev():
-            out["r"] = B.sqsm_ipls_nll_grad(ctx, d["theta"], yy, [0, n], mm0, NN0, M, ADJ, dt=d["dt"])
-        ev()
-        torch.cuda.synchronize()
-        t = timed(ev, k)
-        nll_, g_, ch_, _, _ = out["r"]
-        ch = ch_.item()
-        # the gradient is the derivative at the fixed point of Alg. 3; when
-        # the adjoint iteration has not settled (the trajectory after M
-        # iterations is not a fixed point) its value is not reported
-        settled = bool(np.isfinite(ch) and ch < 1e-3)
-        return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "nll": nll_.item(),
-                "grad": g_.cpu().tolist() if settled else None,
-                "adjoint_iterations": ADJ, "adjoint_last_rel_change": ch,
-                "fixed_point_reached": settled}
-
-    grads["f32"] = nll_grad_rate(torch.float32, max(2, min(args.steps, 5)))
-    grads["f64"] = nll_grad_rate(torch.float64, 2)
-    # the parameter-estimation batch: 256 sequences of n = 2000, FP32
-    try:
-        dg = W.ct_batch(lengths=[2000] * 256, seed=4)
-        yg = torch.tensor(dg["y"], dtype=torch.float32, device=dev)
-        m0g = torch.tensor(dg["m0"], dtype=torch.float32, device=dev)
-        N0g = torch.tensor(dg["N0"], dtype=torch.float32, device=dev)
-        offg = [int(v) for v in dg["offsets"]]
-        outg = {}
-
-        def evg():
-            outg["r"] = B.sqsm_ipls_nll_grad(ctx, dg["theta"], yg, offg, m0g, N0g, M, ADJ,
-                                             dt=dg["dt"])
-        evg()
-        torch.cuda.synchronize()
-        tg = timed(evg, 3)
-        grads["batch_256x2000_f32"] = {"evals_per_s": 1.0 / tg, "ms_per_eval": 1e3 * tg,
-                                       "steps_per_eval": int(offg[-1]),
-                                       "adjoint_iterations": ADJ,
-                                       "adjoint_last_rel_change": outg["r"][2].item()}
-    except Exception as e:   # reported, not fatal to the main metric
-        grads["batch_256x2000_f32"] = {"error": repr(e)[:300]}
-    # how far the M-iteration trajectory is from a fixed point: max-norm
-    # change of m^s from iteration M to M + 1 (FP32)
-    ms_next = torch.empty_like(ms)
-    B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M + 1, B.CUBATURE, dt=d["dt"],
-                       ms=ms_next, Ns=torch.empty_like(Ns), loglik=torch.empty_like(ll))
-    step()
-    torch.cuda.synchronize()
-    grads["ipls_max_change_after_M"] = (ms_next - ms).abs().max().item()
-
-    # ---- batched: 4096 independent sequences, lengths U{100..5000} (ragged)
-    db = W.ct_batch(batch=4096, lo=100, hi=5000, seed=3)
-    yb = torch.tensor(db["y"], dtype=f32, device=dev)
-    m0b = torch.tensor(db["m0"], dtype=f32, device=dev)
-    N0b = torch.tensor(db["N0"], dtype=f32, device=dev)
-    nb_tot = int(db["offsets"][-1])
-    rows_b = nb_tot + 4096
-    msb = torch.empty((rows_b, 5), dtype=f32, device=dev)
-    Nsb = torch.empty((rows_b, 5, 5), dtype=f32, device=dev)
-    llb = torch.empty(4096, dtype=torch.float64, device=dev)
-
-    # the scan shape of this workload is chosen by the library's autotuner
-    # (first call measures the candidates, outside the timed runs)
-    tctx = B.Context(local, use_graph=True, autotune=True)
-
-    def bstep(c=tctx):
-        B.sqsm_ipls_smooth(c, db["theta"], yb, db["offsets"], m0b, N0b, M, B.CUBATURE, dt=db["dt"],
-                           ms=msb, Ns=Nsb, loglik=llb)
-    bstep()
-    torch.cuda.synchronize()
-    tb = timed(bstep, 3)
-    bshape = tctx.scan_shape(db["offsets"])
-    bstep(ctx)
-    torch.cuda.synchronize()
-    tb_default = timed(lambda: bstep(ctx), 3)
-    tctx.profile(True)
-    bstep()
-    torch.cuda.synchronize()
-    bacc = {}
-    for _ in range(2):
-        bstep()
-        for k, (t, c) in tctx.profile_read().items():
-            a0 = bacc.setdefault(k, [0.0, 0])
-            a0[0] += t
-            a0[1] += c
-    tctx.profile(False)
-    tctx.close()
-    bflops = CM.ipls_kernel_flops(list(np.diff(db["offsets"])), leaf=bshape[0], radix=bshape[1])
-    btot = sum(t for t, _ in bacc.values())
-    btop = max(bacc, key=lambda k: bacc[k][0])
-    bach = bflops[btop][0] * bflops[btop][1] * M / (bacc[btop][0] / 2 / 1e3) / 1e12
-    batched = {"workload": "4096 CT sequences, lengths U{100..5000}, cubature IPLS, M=10",
-               "steps_total": nb_tot, "value": nb_tot * M / tb, "unit": UNIT,
-               "ms_per_step": 1e3 * tb,
-               "scan_shape": {"leaf_chunk": bshape[0], "radix": bshape[1], "chosen_by": "autotune"},
-               "ms_per_step_default_shape": 1e3 * tb_default,
-               "roofline": {"bound": "alu", "kernel": btop, "achieved": bach, "peak": peak,
-                            "unit": "TFLOP/s", "frac": bach / peak},
-               "shares": {k: t / btot for k, (t, _) in bacc.items()},
-               "whole_step_tflops": CM.ipls_iteration_flops(list(np.diff(db["offsets"]))) * M
-               / tb / 1e12}
-    del yb, msb, Nsb
-
-    # ---- the same solve with each SLR rule (FP32, n = 1e5, M = 10), into
-    #      buffers of its own (ms, Ns, ll keep the cubature solve compared
-    #      with FP64 below)
-    rules = {}
-    msr, Nsr, llr = torch.empty_like(ms), torch.empty_like(Ns), torch.empty_like(ll)
-    for name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED),
-                      ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
-        def rstep(lin=lin):
-            B.sqsm_ipls_smooth(ctx, d["theta"], y, [0, n], m0, N0, M, lin, dt=d["dt"],
-                               ms=msr, Ns=Nsr, loglik=llr)
-        rstep()
-        torch.cuda.synchronize()
-        tr = timed(rstep, 3)
-        rules[name] = {"value": n * M / tr, "ms_per_step": 1e3 * tr}
-
-    # ---- the paper's sequential-vs-parallel comparison on the GPU: the
-    #      sequential smoother is the same library with one leaf chunk per
-    #      sequence (one thread runs the whole filter and smoother; the SLR
-    #      stays one thread per step), M = 10, FP32, each rule
-    seqpar = {}
-    for ns in (100, 1000, 4000):
-        dq = W.ct_sequence(n=ns, seed=7 + ns)
-        yq = torch.tensor(dq["y"], dtype=f32, device=dev)
-        m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
-        N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
-        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
-        row = {}
-        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE),
-                          ("unscented", B.UNSCENTED), ("gauss_hermite", B.GAUSS_HERMITE)):
-            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
-                def qstep(cq=cq, lin=lin):
-                    B.sqsm_ipls_smooth(cq, dq["theta"], yq, [0, ns], m0q, N0q, M, lin, dt=dq["dt"])
-                qstep()
-                torch.cuda.synchronize()
-                row[f"{name}_{mode}_ms"] = 1e3 * timed(qstep, 2)
-        cseq.close()
-        seqpar[str(ns)] = row
-
-    # ---- the paper's population-model timing (Ricker dynamics, Poisson
-    #      counts, n_x = n_y = 1): M = 100 iterations, Taylor and cubature,
-    #      parallel against sequential (one leaf chunk per sequence), FP32
-    population = {}
-    for ns in (100, 1000, 10000):
-        dp = W.ricker_batch([ns], seed=11 + ns)
-        yp = torch.tensor(dp["y"], dtype=f32, device=dev)
-        m0p = torch.tensor(dp["m0"], dtype=f32, device=dev)
-        N0p = torch.tensor(dp["N0"], dtype=f32, device=dev)
-        cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
-        row = {}
-        for name, lin in (("extended", B.EXTENDED), ("cubature", B.CUBATURE)):
-            for mode, cq in (("parallel", ctx), ("sequential", cseq)):
-                def pstep(cq=cq, lin=lin):
-                    B.sqsm_ipls_smooth_population(cq, dp["theta"], yp, dp["offsets"], m0p, N0p,
-                                                  100, lin)
-                pstep()
-                torch.cuda.synchronize()
-                row[f"{name}_{mode}_ms"] = 1e3 * timed(pstep, 2)
-        cseq.close()
-        population[str(ns)] = row
-
-    # ---- sqrt(R_11) maximum-likelihood estimation (Sec. 6.4)
-    r11 = r11_study(B, ctx, local, dev)
-
-    # ---- length sweep n = 2^10 .. 2^20 (every other power): smoothed steps/s
-    #      for cubature and extended SLR in FP32 and cubature in FP64, and
-    #      the whole-step fraction of the FP32 peak (cubature FP32)
-    sweep = {}
-    for lg in range(10, 21, 2):
-        ns = 1 << lg
-        ds = W.ct_sequence(n=ns, seed=2 + lg)
-        row = {}
-        for name, dtp, lin in (("f32_cubature", torch.float32, B.CUBATURE),
-                               ("f32_extended", torch.float32, B.EXTENDED),
-                               ("f64_cubature", torch.float64, B.CUBATURE)):
-            ys = torch.tensor(ds["y"], dtype=dtp, device=dev)
-            m0s = torch.tensor(ds["m0"][None], dtype=dtp, device=dev)
-            N0s = torch.tensor(ds["N0"][None], dtype=dtp, device=dev)
-            mss = torch.empty((ns + 1, 5), dtype=dtp, device=dev)
-            Nss = torch.empty((ns + 1, 5, 5), dtype=dtp, device=dev)
-            lls = torch.empty(1, dtype=torch.float64, device=dev)
-
-            def sstep():
-                B.sqsm_ipls_smooth(ctx, ds["theta"], ys, [0, ns], m0s, N0s, M, lin, dt=ds["dt"],
-                                   ms=mss, Ns=Nss, loglik=lls)
-            sstep()
-            torch.cuda.synchronize()
-            ts = timed(sstep, 3 if dtp == torch.float32 else 1)
-            row[name] = ns * M / ts
-            if name == "f32_cubature":
-                row["f32_cubature_frac_of_fp32_peak"] = (CM.ipls_iteration_flops([ns]) * M / ts
-                                                         / 1e12 / peak)
-        sweep[str(ns)] = row
-
-    # ---- FP32 stability of the square-root form against the standard
-    #      (covariance) form, as in the paper's robustness experiment: 15
-    #      sequences per length, M = 20, cubature and extended SLR, share of
-    #      sequences whose log-likelihood is not finite; both in the printed
-    #      absolute coordinates and in the deviation coordinates used here,
-    #      with the means' error against the FP64 square-root run (finite runs)
-    cabs = B.Context(local, use_graph=True, absolute=True)
-    stability = {}
-    noise_sets = {"q_c=0.01,q_w=0.1": W.CT_THETA_TRUE,
-                  "q_c=0.1,q_w=0.1": (W.CT_THETA_TRUE[0], float(np.log(0.1)), float(np.log(0.1)))}
-    for ns, (noise, theta_s) in [(ns, kv) for kv in noise_sets.items()
-                                 for ns in (100, 500, 1000, 2000, 4000, 8000)]:
-        dsb = W.ct_batch(lengths=[ns] * 15, seed=1000 + ns, theta=theta_s)
-        offs = [int(v) for v in dsb["offsets"]]
-        P0s = dsb["N0"] @ np.swapaxes(dsb["N0"], 1, 2)
-        t64 = {k: torch.tensor(dsb[k], dtype=torch.float64, device=dev) for k in ("y", "m0", "N0")}
-        t32 = {k: torch.tensor(dsb[k], dtype=f32, device=dev) for k in ("y", "m0", "N0")}
-        P032 = torch.tensor(P0s, dtype=f32, device=dev)
-        res = {}
-        for lin_name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED)):
-            ms64, _, _ = B.sqsm_ipls_smooth(ctx, dsb["theta"], t64["y"], offs, t64["m0"],
-                                            t64["N0"], 20, lin, dt=dsb["dt"])
-            for coords, c in (("absolute", cabs), ("deviation", ctx)):
-                for form in ("sqrt", "standard"):
-                    if form == "sqrt":
-                        msf, _, llf = B.sqsm_ipls_smooth(c, dsb["theta"], t32["y"], offs,
-                                                         t32["m0"], t32["N0"], 20, lin,
-                                                         dt=dsb["dt"])
-                    else:
-                        msf, _, llf = B.sqsm_ipls_smooth_std(c, dsb["theta"], t32["y"], offs,
-                                                             t32["m0"], P032, 20, lin,
-                                                             dt=dsb["dt"])
-                    torch.cuda.synchronize()
-                    c.status()   # clears the non-finite flag a diverged run raises
-                    llf = llf.cpu().numpy()
-                    fin = np.isfinite(llf)
-                    errs = []
-                    for b in np.nonzero(fin)[0]:
-                        rows = slice(offs[b] + b, offs[b + 1] + b + 1)
-                        ref = ms64[rows].cpu().numpy()
-                        errs.append(float(np.abs(msf[rows].double().cpu().numpy() - ref).max()
-                                          / np.abs(ref).max()))
-                    res[f"{form}_{lin_name}_{coords}"] = {
-                        "divergence_rate": float(1.0 - fin.mean()),
-                        "median_mean_rel_err_vs_f64": float(np.median(errs)) if errs else None}
-        stability.setdefault(noise, {})[str(ns)] = res
-    cabs.close()
-
-    # ---- FP64 variant of the same step (comparator), few steps
-    f64 = torch.float64
-    y64, m064, N064 = y.double(), m0.double(), N0.double()
-    ms64 = torch.empty((n + 1, 5), dtype=f64, device=dev)
-    Ns64 = torch.empty((n + 1, 5, 5), dtype=f64, device=dev)
-    ll64 = torch.empty(1, dtype=f64, device=dev)
-
-    def step64():
-        B.sqsm_ipls_smooth(ctx, d["theta"], y64, [0, n], m064, N064, M, B.CUBATURE, dt=d["dt"],
-                           ms=ms64, Ns=Ns64, loglik=ll64)
-
-    step64()
-    torch.cuda.synchronize()
-    e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(3)]
-    for a, b in e64:
-        flush.fill_(1)
-        a.record(stream)
-        step64()
-        b.record(stream)
-    torch.cuda.synchronize()
-    t64 = sum(a.elapsed_time(b) for a, b in e64) / 1e3 / 3
-    err_f32 = float((ms.double() - ms64).norm(dim=1).max() / ms64.norm(dim=1).max())
-    ll_rel = abs(ll.item() - ll64.item()) / abs(ll64.item())
-
-    line = None
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic", "config": config(args, world),
-                "wall_s_timed_region": wall,
-                "e2e": {"value": n * M * args.steps * world / t_e2e, "unit": UNIT,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(round(launches_per_step * args.steps)),
-                "clocks": clk.summary(),
-                "roofline": roofline, "whole_step": whole, "kernels": kernels,
-                "nll_grad": grads, "batched": batched,
-                "sweep": {"unit": UNIT, "M": M, "by_n": sweep},
-                "slr_rules": {"unit": UNIT, "n": n, "M": M, "by_rule": rules},
-                "sequential_vs_parallel": {"M": M, "dtype": "f32", "by_n": seqpar},
-                "population_model": {"M": 100, "dtype": "f32", "by_n": population},
-                "sqrt_r11_estimation": r11,
-                "stability_f32": {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability},
-                "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
-                        "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
-                "loglik": ll.item()}
-    ctx.close()
-    return line
-
-
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -717,6 +802,13 @@ def main():
                 "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"FP64 oracle IPLS on the first {CPU_SAMPLE_STEPS} observations "
                           f"of the workload, M={args.M}, one thread ({dt:.1f} s)"}
+            line["batched"]["cpu_baseline"] = None
+            try:
+                bl = batched_cpu_baselines(args.M)
+                line["batched"]["cpu_baseline"] = bl["batch_4096"]
+                line["nll_grad"]["batch_256x2000_cpu_baseline"] = bl["batch_256x2000_nll_grad"]
+            except Exception as e:   # reported, not fatal to the main metric
+                line["batched"]["cpu_baseline"] = {"error": repr(e)[:200]}
         print(json.dumps(line), flush=True)
 
 

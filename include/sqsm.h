@@ -319,6 +319,19 @@ int sqsm_profile_read(sqsm_ctx* ctx, int nkinds, double* ms, int* launches,
 /* Name of kernel family k ("" if out of range). */
 const char* sqsm_kernel_name(int k);
 
+/* Measurement aid, not part of the method (the paper has no counterpart):
+ * enqueues on `stream` one kernel of `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 1024) whose only work is independent chains of
+ * FP32 fused multiply-adds, `iters` loop trips of 128 FMAs per thread, and
+ * writes one float per thread to the device buffer `out` (blocks * threads
+ * floats, caller-owned).  *flops (host) receives the floating-point
+ * operations it performs (an FMA counts 2).  Timing it with CUDA events on
+ * `stream` gives the FP32 pipe's measured peak, the roof of the ALU-bound
+ * scan and SLR kernels.  Returns SQSM_ERR_INVALID_ARG for bad sizes or null
+ * pointers, SQSM_ERR_CUDA if the launch fails. */
+int sqsm_fp32_fma_probe(int iters, int blocks, int threads, void* out, double* flops,
+                        void* stream);
+
 /* The linear smoother of sqsm_lgssm_smooth for callers that cannot
  * allocate device memory.  The paper has no counterpart of this call; it
  * exists for code running where cudaMalloc is unavailable or forbidden (an
@@ -329,20 +342,32 @@ const char* sqsm_kernel_name(int k);
  * buffers live in one fixed array of 32 MiB per device, part of the loaded
  * library, held until the process exits.
  *
- * Arguments and results are those of sqsm_lgssm_smooth (same scan shape,
- * so the same results), except that mf and Nf must not be NULL and there is
- * no device status word.  The current CUDA device is used; `stream` must
- * belong to it.
+ * Arguments and results are those of sqsm_lgssm_smooth, except:
+ * - mf and Nf must not be NULL.
+ * - Scan shape: leaf chunks of 4 steps and radix-4 folds on every upper
+ *   level, the shape of a context created with leaf_chunk = 4 and radix = 4;
+ *   on such a context sqsm_lgssm_smooth gives bit-identical results.  A
+ *   context with the default shape brackets the scan differently, so its
+ *   results agree with this call's to rounding only.
+ * - There is no device status word: a non-finite result (a diverging
+ *   filter) is not reported and the call still returns SQSM_OK; callers who
+ *   need to know check the outputs (for example isfinite(*loglik)).
+ * - The current CUDA device is used; `stream` must belong to it.
  * - Limit: n is bounded by the scratch size (about 280 bytes per step at
  *   FP32 and nx = 5, i.e. n up to roughly 1.2e5; half that at FP64).
  *   Larger problems return SQSM_ERR_TOO_LARGE before any GPU work.
- * - The first call on a device looks up the scratch array's device address
- *   (this loads the library's device code on that device); make that first
- *   call before any stream capture.
+ * - Set-up: the first call on a device (and the first after the device's
+ *   context was reset, e.g. by cudaDeviceReset) initialises the device's
+ *   primary context if needed and looks up the scratch array's device
+ *   address, which loads the library's device code on that device; make
+ *   that first call before any stream capture.
  * - All calls on a device share the scratch and its contents persist
  *   between calls; each call rewrites or clears what it reads.  Calls whose
  *   GPU work overlaps (different streams, different host threads) race on
  *   the scratch and must be serialised by the caller.
+ * - If the calling thread has a CUDA error pending (cudaPeekAtLastError),
+ *   the call enqueues nothing, leaves that error in place and returns
+ *   SQSM_ERR_CUDA.
  * Returns SQSM_ERR_INVALID_ARG / SQSM_ERR_UNSUPPORTED as sqsm_lgssm_smooth,
  * SQSM_ERR_TOO_LARGE, or SQSM_ERR_CUDA. */
 int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n,

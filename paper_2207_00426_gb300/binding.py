@@ -92,12 +92,15 @@ lib.sqsm_kernel_name.restype = ctypes.c_char_p
 lib.sqsm_scan_shape.argtypes = [_p, _int, _int, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_int),
                                 ctypes.POINTER(_int)]
 lib.sqsm_scan_shape.restype = _int
+lib.sqsm_fp32_fma_probe.argtypes = [_int, _int, _int, _p, ctypes.POINTER(ctypes.c_double), _p]
+lib.sqsm_fp32_fma_probe.restype = _int
 
 EXPORTED = ["sqsm_create", "sqsm_destroy", "sqsm_last_error", "sqsm_get_status",
             "sqsm_supported_shape", "sqsm_lgssm_smooth", "sqsm_ipls_smooth",
             "sqsm_ct_linearize", "sqsm_profile_enable", "sqsm_profile_read",
             "sqsm_kernel_name", "sqsm_lgssm_smooth_noalloc", "sqsm_ipls_nll_grad",
-            "sqsm_scan_shape", "sqsm_ipls_smooth_tol", "sqsm_ipls_smooth_std"]
+            "sqsm_scan_shape", "sqsm_ipls_smooth_tol", "sqsm_ipls_smooth_std",
+            "sqsm_fp32_fma_probe"]
 
 
 class SqsmError(RuntimeError):
@@ -416,3 +419,17 @@ def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, se
                                 _ptr(grad, f64, "grad"), _ptr(change, f64, "change"), _stream())
     ctx.check(rc)
     return nll, grad, change, ms, Ns
+
+
+def fp32_fma_probe(iters, blocks, threads, out):
+    """Enqueue the FP32 FMA-pipe probe on the current stream; out is a
+    float32 CUDA tensor of blocks * threads elements.  Returns the probe's
+    floating-point operation count."""
+    if out.numel() < blocks * threads:
+        raise ValueError("out holds fewer than blocks * threads floats")
+    fl = ctypes.c_double(0.0)
+    rc = lib.sqsm_fp32_fma_probe(int(iters), int(blocks), int(threads),
+                                 _ptr(out, torch.float32, "out"), ctypes.byref(fl), _stream())
+    if rc != OK:
+        raise SqsmError(rc, "sqsm_fp32_fma_probe failed")
+    return fl.value

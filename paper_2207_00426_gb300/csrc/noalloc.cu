@@ -13,11 +13,20 @@
 // library image (kNoAllocScratchBytes per device, held until the process
 // exits).
 //
+// Scan shape: leaf chunks of 4 steps and radix-4 folds at every upper level
+// below the Kogge-Stone top block -- the shape of a context created with
+// leaf_chunk = 4, radix = 4, whose results it reproduces bit for bit.  The
+// default shape of a context (leaf 3 or 4, 32-item warp chunk scans on small
+// levels) brackets the combines differently, so against a default context
+// the results agree to rounding only.
+//
 // The scratch is shared by every call on a device and keeps the previous
 // call's contents; everything a call reads is written (or cleared) by that
 // same call first.  Calls whose GPU work overlaps -- on different streams or
 // from different host threads -- race on the scratch and must be serialised
 // by the caller.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/sqsm.h"
@@ -33,21 +42,63 @@ constexpr int kMaxLevels = 40;   // per scan; n <= 2^31 needs at most 17 at radi
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 
-// Device address of g_scratch for each device, looked up once with that
-// device current (a host-side reference to g_scratch is only a stand-in
-// symbol, not a device address).
-void* g_scratch_addr[kMaxDevices] = {};
+// Device address of g_scratch per device, looked up once with that device
+// current (in host code g_scratch names a host-side stand-in, not a device
+// address).  The address belongs to the CUDA context the library's device
+// code was loaded into; if the caller resets the device (cudaDeviceReset)
+// a new primary context loads the code again, possibly at another address.
+// So each entry remembers the unique id of its context, and a call made
+// under a different context repeats the look-up.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  void* ptr = nullptr;
+};
+ScratchSlot g_slots[kMaxDevices];
 std::mutex g_setup_mutex;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current CUDA context (made current by the
+// runtime call before); 0 and false if it cannot be read.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) !=
+            cudaSuccess ||
+        q0 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess)
+      return false;
+    get_current = (CtxGetCurrentFn)f0;
+    get_id = (CtxGetIdFn)f1;
+  }
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return SQSM_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  // cudaSetDevice on the current device initialises its primary context
+  // and makes it current, so that its id can be read
+  if (cudaSetDevice(dev) != cudaSuccess) return SQSM_ERR_CUDA;
+  unsigned long long id = 0;
+  if (!current_context_id(&id)) return SQSM_ERR_CUDA;
+  ScratchSlot& slot = g_slots[dev];
+  if (!slot.ptr || slot.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SQSM_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+    slot.ptr = p;
+    slot.ctx_id = id;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.ptr;
   return SQSM_OK;
 }
 
@@ -170,7 +221,11 @@ extern "C" int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n, c
   if (!F || !c || !SQ || !H || !d || !SR || !m0 || !N0 || !y || !mf || !Nf || !ms || !Ns)
     return SQSM_ERR_INVALID_ARG;
   if (sF < 0 || sc < 0 || sSQ < 0 || sH < 0 || sd < 0 || sSR < 0) return SQSM_ERR_INVALID_ARG;
-  const int L0 = 4, R = 4;   // the default scan shape of sqsm_lgssm_smooth
+  // an error the caller has pending stays theirs: run nothing, clear nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return SQSM_ERR_CUDA;
+  // leaf chunks of 4 steps, radix-4 folds: the scan shape of a context with
+  // leaf_chunk = 4, radix = 4
+  const int L0 = 4, R = 4;
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
   const size_t frec = frec_size(nx), srec = srec_size(nx), crec = nx + nx * nx;
 
@@ -197,7 +252,6 @@ extern "C" int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n, c
     if (pass == 0) continue;
 
     cudaStream_t s = (cudaStream_t)stream;
-    cudaGetLastError();
     td.n = n;
     td.leaf_chunks = Lf.lv[0].n_chunks;
     Lf.leaf_chunk_off = td.leaf_chunk_off;
