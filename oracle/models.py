@@ -141,6 +141,29 @@ class CTBearings:
     def SR(self):
         return np.diag([self.sigma, self.sigma2])
 
+    # parameter derivatives (forward-mode gradient) ---------------------------
+    def dSQ_dtheta(self):
+        """d SQ / d theta_j, trailing axis j: SQ scales with sqrt(q_c) on the
+        (p, v) block and with sqrt(q_omega) on omega, so the derivatives in
+        log q_c and log q_omega are half of those parts; sigma does not
+        enter."""
+        L = self.SQ()
+        D = np.zeros((5, 5, self.theta.size))
+        D[:4, :4, 1] = 0.5 * L[:4, :4]
+        D[4, 4, 2] = 0.5 * L[4, 4]
+        return D
+
+    def dSR_dtheta(self):
+        """d SR / d theta_j: SR = diag(sigma, sigma_2) with sigma = e^theta_0
+        (and sigma_2 = e^theta_3 when theta has four entries, else sigma)."""
+        D = np.zeros((2, 2, self.theta.size))
+        if self.theta.size == 4:
+            D[0, 0, 0] = self.sigma
+            D[1, 1, 3] = self.sigma2
+        else:
+            D[:, :, 0] = self.SR()
+        return D
+
 
 class LinearCV:
     """Linear constant-velocity model of the 2-D tracking example:
