@@ -88,7 +88,7 @@ def config(args, world, leaf=None):
                         f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
             "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
             "sequences_total": world, "leaf_chunk": leaf,
-            "l2": "flushed between timed steps (256 MiB write outside the events)",
+            "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"independent sequences, {world} GPU(s)"}
 
 
@@ -169,15 +169,13 @@ def batched_cpu_baselines(M):
         t_g = time.perf_counter() - t0
     out["batch_4096"] = {
         "value": steps * M / t_b, "unit": UNIT, "cores": cores, "kind": "oracle",
-        "sample": f"{len(jobs)} sequences drawn from the 4096 (seed 0), first "
-                  f"{BATCH_CPU_PREFIX} observations of each ({steps} steps), M={M}, "
-                  f"one process per core ({t_b:.1f} s)"}
+        "sample": f"{len(jobs)} of the 4096 sequences, first {BATCH_CPU_PREFIX} steps each, "
+                  f"M={M}, 1 process/core, {t_b:.1f} s"}
     out["batch_256x2000_nll_grad"] = {
         "value": gsteps / t_g / (256 * 2000), "unit": "NLL+grad evals/s", "cores": cores,
         "kind": "oracle",
-        "sample": f"first {GRAD_CPU_PREFIX} observations of {len(gjobs)} of the 256 "
-                  f"sequences, M={M}, gradient by central differences (7 IPLS solves), "
-                  f"one process per core ({t_g:.1f} s); rate scaled to 256 x 2000 steps"}
+        "sample": f"{len(gjobs)} of the 256 sequences, first {GRAD_CPU_PREFIX} steps each, M={M}, "
+                  f"central differences, 1 process/core, {t_g:.1f} s, scaled to 256x2000"}
     return out
 
 
@@ -274,8 +272,7 @@ def fp32_peak(B, torch, dev, stream, sm_count):
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 1e3
         best = t if best is None else min(best, t)
-    return fl / best / 1e12, (f"FMA-only probe kernel, {blocks} x {threads} threads, "
-                              f"{fl:.3g} flops, CUDA events, best of 5")
+    return fl / best / 1e12, f"FMA-only probe kernel, {blocks}x{threads} threads, best of 5"
 
 
 def gpu_arm(args, rank, world, local):
@@ -403,15 +400,12 @@ def gpu_arm(args, rank, world, local):
     achieved = f_launch / t_launch / 1e12
     roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((top, n)), "traffic_unit": "bytes per launch",
-                "flops_per_launch": f_launch, "share_of_step": acc[top][0] / total_ms,
-                "peak_note": "measured (" + peak_basis + ")",
-                "peak_derived": derived,
-                "peak_derived_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+                "traffic": NCU_TRAFFIC.get((top, n)), "flops_per_launch": f_launch,
+                "share_of_step": acc[top][0] / total_ms, "peak_note": "measured: " + peak_basis,
+                "peak_derived": derived}
     it_flops = CM.ipls_iteration_flops([n], leaf=leaf)
     whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
     whole["frac"] = whole["achieved_tflops"] / peak
-    shares = {k: round(t / total_ms, 4) for k, (t, _) in acc.items()}
 
     def timed(fn, k):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -462,6 +456,7 @@ def gpu_arm(args, rank, world, local):
     tg = timed(evg, 3)
     grads["batch_256x2000_f32"] = {"evals_per_s": 1.0 / tg, "ms_per_eval": 1e3 * tg}
     del yg, m0g, N0g
+    grads["converged_50x2000_f32"] = converged_nll_grad(B, torch, ctx, dev, timed)
     # how far the M-iteration trajectory is from a fixed point: max-norm
     # change of m^s from iteration M to M + 1 (FP32)
     ms_next = torch.empty_like(ms)
@@ -495,7 +490,7 @@ def gpu_arm(args, rank, world, local):
     tctx.close()
     bwhole = CM.ipls_iteration_flops(list(np.diff(db["offsets"])), leaf=bshape[0],
                                      radix=bshape[1]) * M / tb / 1e12
-    batched = {"workload": "4096 CT sequences, lengths U{100..5000}, cubature IPLS, M=10",
+    batched = {"workload": "4096 CT sequences, n~U{100..5000}, cubature, M=10",
                "steps_total": nb_tot, "value": nb_tot * M / tb, "unit": UNIT,
                "ms_per_step": 1e3 * tb, "scan_shape": list(bshape),
                "whole_step_tflops": bwhole, "whole_step_frac": bwhole / peak}
@@ -537,13 +532,55 @@ def gpu_arm(args, rank, world, local):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "clocks": clk.summary(), "roofline": roofline, "whole_step": whole,
-                "shares": shares,
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
                 "nll_grad": grads, "batched": batched, "loglik": ll.item(),
                 "studies": args.studies_out if studies is not None else None}
     ctx.close()
     return line
+
+
+def converged_nll_grad(B, torch, ctx, dev, timed):
+    """NLL + gradient at a fixed point, at the benchmark's size in total:
+    50 coordinated-turn sequences of 2000 steps (1e5 steps) whose Alg. 3
+    iteration settles -- the first 50 of 128 (seed 5) that one more FP64
+    iteration after 40 moves by less than 1e-9 -- evaluated in FP32 with
+    M = 30 IPLS and 30 adjoint iterations and the library's fixed-point
+    check at tol = 1e-4 (SQSM_ERR_NOT_CONVERGED clear = both fixed points
+    settled)."""
+    from paper_2207_00426_gb300 import workloads as W
+    f64 = torch.float64
+    L, cand = 2000, 128
+    dc = W.ct_batch(lengths=[L] * cand, seed=5)
+    off = [int(v) for v in dc["offsets"]]
+    T = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    y, m0, N0 = T(dc["y"], f64), T(dc["m0"], f64), T(dc["N0"], f64)
+    ms, Ns, _ = B.sqsm_ipls_smooth(ctx, dc["theta"], y, off, m0, N0, 40, dt=dc["dt"])
+    ms1, _, _ = B.sqsm_ipls_smooth(ctx, dc["theta"], y, off, m0, N0, 1, dt=dc["dt"], init_ms=ms,
+                                   init_Ns=Ns)
+    torch.cuda.synchronize()
+    ch = (ms1 - ms).abs().max(dim=1).values.cpu().numpy()
+    keep = [b for b in range(cand) if ch[off[b] + b:off[b + 1] + b + 1].max() < 1e-9][:50]
+    if len(keep) < 50:
+        return {"error": f"only {len(keep)} of {cand} sequences settled"}
+    yk = np.concatenate([dc["y"][off[b]:off[b + 1]] for b in keep])
+    f32 = torch.float32
+    yk, m0k, N0k = T(yk, f32), T(dc["m0"][keep], f32), T(dc["N0"][keep], f32)
+    offk = [L * i for i in range(51)]
+    out = {}
+
+    def ev():
+        out["r"] = B.sqsm_ipls_nll_grad(ctx, dc["theta"], yk, offk, m0k, N0k, 30, 30, dt=dc["dt"],
+                                        tol=1e-4)
+    ev()
+    torch.cuda.synchronize()
+    settled = ctx.status() == 0
+    t = timed(ev, 3)
+    torch.cuda.synchronize()
+    settled = settled and ctx.status() == 0
+    return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "M": 30, "adjoint_iterations": 30,
+            "fixed_point_reached": bool(settled), "grad": out["r"][1].cpu().tolist(),
+            "adjoint_last_rel_change": out["r"][2].item()}
 
 
 def run_studies(B, torch, ctx, local, dev, M, peak, timed):
@@ -788,6 +825,18 @@ def r11_study(B, ctx, local, dev):
     return out
 
 
+def _round(x, digits=6):
+    """Floats of a JSON-able value to `digits` significant digits (keeps the
+    final line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if np.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: _round(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_round(v, digits) for v in x]
+    return x
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -800,8 +849,8 @@ def main():
             rate, dt = oracle_rate(CPU_SAMPLE_STEPS, args.M)
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"FP64 oracle IPLS on the first {CPU_SAMPLE_STEPS} observations "
-                          f"of the workload, M={args.M}, one thread ({dt:.1f} s)"}
+                "sample": f"FP64 oracle IPLS, first {CPU_SAMPLE_STEPS} steps of the sequence, "
+                          f"M={args.M}, 1 thread, {dt:.1f} s"}
             line["batched"]["cpu_baseline"] = None
             try:
                 bl = batched_cpu_baselines(args.M)
@@ -809,7 +858,7 @@ def main():
                 line["nll_grad"]["batch_256x2000_cpu_baseline"] = bl["batch_256x2000_nll_grad"]
             except Exception as e:   # reported, not fatal to the main metric
                 line["batched"]["cpu_baseline"] = {"error": repr(e)[:200]}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_round(line), separators=(",", ":")), flush=True)
 
 
 if __name__ == "__main__":

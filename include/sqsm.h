@@ -31,9 +31,13 @@
  *   frees or retains caller memory beyond the call, and never synchronises
  *   the stream except where stated.  Work is enqueued on `stream`
  *   (a cudaStream_t passed as void*; NULL = legacy default stream).
+ * - Alignment: every array pointer must be a multiple of its element size
+ *   (4 bytes for float, 8 for double and for the double outputs, 4 for
+ *   int); a misaligned pointer is an argument error.
  * - Errors: every call returns an sqsm_status.  Argument errors are detected
- *   on the host before anything is enqueued.  Numerical failures detected
- *   on the device (a non-finite output) are OR-ed into a device status word
+ *   on the host before anything is enqueued.  Conditions detected on the
+ *   device (a non-finite output, a prior covariance that is not positive
+ *   definite, an unsettled fixed point) are OR-ed into a device status word
  *   that sqsm_get_status() reads.  sqsm_last_error() gives the text of the
  *   last host-side error of a context.
  * - A context is not thread-safe; use one context per host thread.
@@ -49,16 +53,20 @@ extern "C" {
 
 typedef enum {
   SQSM_OK = 0,
-  SQSM_ERR_INVALID_ARG = 1,      /* null pointer, bad size/stride/enum      */
+  SQSM_ERR_INVALID_ARG = 1,      /* null or misaligned pointer, bad
+                                    size/stride/offsets/enum              */
   SQSM_ERR_UNSUPPORTED = 2,      /* (nx, ny) pair not compiled in            */
-  SQSM_ERR_NOT_PD = 4,           /* reserved: no kernel raises it; a zero
-                                    pivot in a triangular solve or a lost
-                                    definiteness surfaces as a non-finite
-                                    output (SQSM_ERR_NONFINITE)             */
+  SQSM_ERR_NOT_PD = 4,           /* device: a prior covariance given with
+                                    sqsm_options.prior_covariance is not
+                                    positive definite (its FP64 Cholesky
+                                    met a non-positive pivot; the factor and
+                                    the outputs it feeds are NaN)          */
   SQSM_ERR_NONFINITE = 8,        /* device: NaN/Inf in an output             */
   SQSM_ERR_CUDA = 16,            /* a CUDA runtime call failed               */
   SQSM_ERR_NO_MEMORY = 32,       /* workspace allocation failed              */
-  SQSM_ERR_TOO_LARGE = 64        /* problem exceeds a fixed-size buffer      */
+  SQSM_ERR_TOO_LARGE = 64,       /* problem exceeds a fixed-size buffer      */
+  SQSM_ERR_NOT_CONVERGED = 128   /* device: sqsm_ipls_nll_grad's trajectory or
+                                    adjoint had not settled to its tol      */
 } sqsm_status;
 
 typedef enum { SQSM_F32 = 0, SQSM_F64 = 1 } sqsm_dtype;
@@ -129,6 +137,29 @@ typedef struct {
                            printed absolute coordinates (c = z_bar - F m)
                            instead of deviations from the nominal
                            trajectory (default 0)                        */
+  int prior_covariance; /* 1: the N0 argument of sqsm_lgssm_smooth,
+                           sqsm_ipls_smooth, sqsm_ipls_smooth_tol and
+                           sqsm_ipls_nll_grad holds prior covariances P0
+                           (full nx x nx per sequence, lower triangle
+                           read) instead of lower factors; each call
+                           factors them on the GPU with an FP64 Cholesky
+                           (N0 = chol(P0), written in the call's dtype)
+                           before its scans.  A P0 that is not positive
+                           definite sets SQSM_ERR_NOT_PD in the device
+                           status word.  Default 0.                     */
+  int refine;           /* mixed-precision refinement passes (0..2) of
+                           every IPLS iteration's linear smoother: after
+                           the smoother, the residual model about its
+                           result is formed in FP64 (its offsets
+                           c' = F dx + c - dx_k, d' = d + H dx_k, rounded
+                           once) and smoothed again in the call's dtype,
+                           the correction added to the trajectory.  Each
+                           pass costs one more filter and smoother scan;
+                           it removes most of the FP32 error of the linear
+                           solve, which a non-converging Alg. 3 amplifies
+                           from iteration to iteration.  Deviation
+                           coordinates only (ignored with absolute).
+                           Default 0.                                    */
 } sqsm_options;
 
 typedef struct sqsm_ctx sqsm_ctx;
@@ -154,9 +185,12 @@ int sqsm_destroy(sqsm_ctx* ctx);
  * valid until the next call on ctx. */
 const char* sqsm_last_error(const sqsm_ctx* ctx);
 
-/* Synchronise ctx's device, read and clear the device status word: 0 or
- * SQSM_ERR_NONFINITE if a kernel produced a non-finite filtered or smoothed
- * mean or log-likelihood since the last read.  *status is host memory. */
+/* Synchronise ctx's device, read and clear the device status word: the OR
+ * of the device-detected conditions since the last read -- SQSM_ERR_NONFINITE
+ * (a kernel produced a non-finite filtered or smoothed mean or
+ * log-likelihood), SQSM_ERR_NOT_PD (a prior covariance was not positive
+ * definite), SQSM_ERR_NOT_CONVERGED (sqsm_ipls_nll_grad's fixed points had
+ * not settled) -- or 0.  *status is host memory. */
 int sqsm_get_status(sqsm_ctx* ctx, int* status);
 
 /* Parallel square-root Kalman filter and RTS smoother on one linear-Gaussian
@@ -267,21 +301,37 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
  * adjoint of the cubature regression.  Only SQSM_CUBATURE is supported
  * (SQSM_ERR_UNSUPPORTED otherwise).
  *
+ *   adj_iters   adjoint iterations (>= 0); always all of them (a fixed
+ *               amount of work per evaluation, replayable as one graph).
+ *               Iteration i takes the trajectory cotangent lambda of
+ *               iteration i - 1 (0 in the first), so adj_iters = 1 gives
+ *               the partial derivative of nll with respect to theta at the
+ *               fixed trajectory n* (with M = 0: at init_ms/init_Ns);
+ *               adj_iters = 0 computes nll only and writes grad = 0.
+ *   tol         fixed-point tolerance (relative, max-norm): when > 0 the
+ *               call sets SQSM_ERR_NOT_CONVERGED in the device status word
+ *               if ipls_change >= tol or adj_change >= tol (or either is
+ *               not finite), i.e. if n* is not a fixed point of Alg. 3 or
+ *               lambda has not converged, so that grad is not the
+ *               derivative Sec. 5.2 defines.  tol <= 0: no check.
  *   ms, Ns      outputs: the trajectory n* (state layout), as
  *               sqsm_ipls_smooth with the same M.
  *   nll         device double[1]; grad device double[3] (double[4] for
  *               SQSM_MODEL_CT_BEARINGS_R), theta order.
  *   adj_change  device double[1] or NULL: max-norm change of lambda in the
- *               last adjoint iteration relative to its max-norm (a
- *               convergence measure; the gradient assumes n* is a fixed
- *               point and lambda converged).
+ *               last adjoint iteration relative to its max-norm (0 when
+ *               adj_iters = 0).
+ *   ipls_change device double[1] or NULL: max-norm change of the smoothing
+ *               means from n* to the smoother of its linearisation (one
+ *               more iteration of Alg. 3), relative to their max-norm.
  * Other arguments as sqsm_ipls_smooth. */
 int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                        const double* theta, int linearization, int M,
-                       int adj_iters, int64_t batch, const int64_t* offsets,
-                       const void* y, const void* m0, const void* N0,
-                       const void* init_ms, const void* init_Ns, void* ms,
-                       void* Ns, double* nll, double* grad, double* adj_change,
+                       int adj_iters, double tol, int64_t batch,
+                       const int64_t* offsets, const void* y, const void* m0,
+                       const void* N0, const void* init_ms,
+                       const void* init_Ns, void* ms, void* Ns, double* nll,
+                       double* grad, double* adj_change, double* ipls_change,
                        void* stream);
 
 /* Statistical linear regression of a compiled-in model about a nominal

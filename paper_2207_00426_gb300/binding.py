@@ -21,6 +21,7 @@ ERR_NONFINITE = 8
 ERR_CUDA = 16
 ERR_NO_MEMORY = 32
 ERR_TOO_LARGE = 64
+ERR_NOT_CONVERGED = 128
 F32, F64 = 0, 1
 CUBATURE, EXTENDED, UNSCENTED, GAUSS_HERMITE = 0, 1, 2, 3
 MODEL_CT_BEARINGS = 1
@@ -40,7 +41,7 @@ _int = ctypes.c_int
 
 class Options(ctypes.Structure):
     _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int), ("autotune", _int),
-                ("absolute", _int)]
+                ("absolute", _int), ("prior_covariance", _int), ("refine", _int)]
 
 
 class Model(ctypes.Structure):
@@ -77,7 +78,8 @@ lib.sqsm_ct_linearize.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTE
 lib.sqsm_ct_linearize.restype = _int
 
 lib.sqsm_ipls_nll_grad.argtypes = [_p, _int, ctypes.POINTER(Model), ctypes.POINTER(ctypes.c_double),
-                                   _int, _int, _int, _i64, ctypes.POINTER(_i64)] + [_p] * 10 + [_p]
+                                   _int, _int, _int, ctypes.c_double, _i64,
+                                   ctypes.POINTER(_i64)] + [_p] * 11 + [_p]
 lib.sqsm_ipls_nll_grad.restype = _int
 lib.sqsm_lgssm_smooth_noalloc.argtypes = ([_int, _int, _int, _i64] + [_p, _i64] * 6
                                           + [_p] * 3 + [_p] * 4 + [_p, _p])
@@ -139,13 +141,13 @@ class Context:
     """Owns an sqsm_ctx (workspaces, plans, graphs) on one device."""
 
     def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True, autotune=False,
-                 absolute=False):
+                 absolute=False, prior_covariance=False, refine=0):
         if device is None:
             device = torch.cuda.current_device()
         self.device = int(device)
         h = _p()
         opt = Options(leaf_chunk, radix, 1 if use_graph else 0, 1 if autotune else 0,
-                      1 if absolute else 0)
+                      1 if absolute else 0, 1 if prior_covariance else 0, int(refine))
         rc = lib.sqsm_create(ctypes.byref(h), self.device, ctypes.byref(opt))
         if rc != OK:
             raise SqsmError(rc, "sqsm_create failed")
@@ -392,9 +394,12 @@ def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt
 
 def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, sensors=None,
                        init_ms=None, init_Ns=None, ms=None, Ns=None, nll=None, grad=None,
-                       change=None):
+                       change=None, tol=0.0, ipls_change=None):
     """Call sqsm_ipls_nll_grad (cubature).  Returns (nll, grad, change, ms,
-    Ns) as device tensors (nll [1], grad [len(theta)], change [1] float64)."""
+    Ns) as device tensors (nll [1], grad [len(theta)], change [1] float64).
+    tol > 0 sets ERR_NOT_CONVERGED in the status word when a fixed point has
+    not settled; ipls_change (float64 [1], optional) receives the relative
+    change of the trajectory in one more iteration of Alg. 3."""
     import numpy as np
     dtp = y.dtype
     code = _dtype_code(dtp)
@@ -413,10 +418,12 @@ def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, se
     mdl, th = _ct_model(theta, dt, sensors)
     grad = torch.empty(len(th), dtype=f64, device=dev) if grad is None else grad
     rc = lib.sqsm_ipls_nll_grad(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), int(adj_iters),
-                                batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"), _ptr(N0, dtp, "N0"),
-                                _ptr(init_ms, dtp, "init_ms"), _ptr(init_Ns, dtp, "init_Ns"),
-                                _ptr(ms, dtp, "ms"), _ptr(Ns, dtp, "Ns"), _ptr(nll, f64, "nll"),
-                                _ptr(grad, f64, "grad"), _ptr(change, f64, "change"), _stream())
+                                float(tol), batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
+                                _ptr(N0, dtp, "N0"), _ptr(init_ms, dtp, "init_ms"),
+                                _ptr(init_Ns, dtp, "init_Ns"), _ptr(ms, dtp, "ms"),
+                                _ptr(Ns, dtp, "Ns"), _ptr(nll, f64, "nll"), _ptr(grad, f64, "grad"),
+                                _ptr(change, f64, "change"), _ptr(ipls_change, f64, "ipls_change"),
+                                _stream())
     ctx.check(rc)
     return nll, grad, change, ms, Ns
 

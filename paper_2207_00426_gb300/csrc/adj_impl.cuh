@@ -72,6 +72,14 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fo, so, status, s);
   enqueue_loglik_reduce(sq, partial, g.ll, status, s);
   adj_nll_kernel<<<1, 1, 0, s>>>(sq.B, g.ll, -1.0, g.nll);
+  // how far n* is from a fixed point of Alg. 3: the relative change of the
+  // smoothing means in that one more iteration (words 2, 3)
+  unsigned* words = (unsigned*)g.change_words;
+  const unsigned change_blocks =
+      (unsigned)std::min<int64_t>((X * rows + 255) / 256, 4 * 152);
+  cudaMemsetAsync(words, 0, 4 * sizeof(unsigned), s);
+  adj_change_partial<T><<<change_blocks, 256, 0, s>>>(NX * rows, (const T*)g.ms2,
+                                                     (const T*)g.nom_m, words + 2);
   // 3. per-step tables of that linearisation (fixed over the iterations)
   AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F,
              g.dir, g.dfilt, g.gbar, g.ktab, g.rtab, g.stab};
@@ -117,20 +125,15 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
     // cotangents for the next iteration), theta partials
     adj_slr_kernel<T><<<slr_blocks, kBlock, 0, s>>>(
         Ls.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
-    if (it + 1 == g.iters && g.change) {
-      unsigned* words = (unsigned*)g.change_words;
-      cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), s);
-      const int64_t n = X * rows;
-      const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4 * 152);
-      adj_change_partial<T><<<blocks, 256, 0, s>>>(n, lam_b, lam_a, words);
-      adj_change_final<<<1, 1, 0, s>>>(words, g.change);
-    }
+    if (it + 1 == g.iters)   // the last iteration's change of lambda (words 0, 1)
+      adj_change_partial<T><<<change_blocks, 256, 0, s>>>(X * rows, lam_b, lam_a, words);
     T* t = lam_a;
     lam_a = lam_b;
     lam_b = t;
   }
   if (g.iters > 0) adj_theta_reduce<<<1, 256, 0, s>>>(slr_blocks, g.th_partial, 1.0, g.n_theta, g.grad);
   else cudaMemsetAsync(g.grad, 0, g.n_theta * sizeof(double), s);
+  adj_settle_check<<<1, 1, 0, s>>>(words, g.iters > 0 ? 1 : 0, g.tol, g.change, g.ichange, status);
 }
 
 }  // namespace sqsm

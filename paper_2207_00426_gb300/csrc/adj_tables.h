@@ -39,9 +39,12 @@ template <int NX, int NY> struct SlrTab {
                        sh = Gh + NY * NX, size = (sh + NY * NX + 3) / 4 * 4;
 };
 
-// The kernels move whole blocks with 16-byte vector accesses from 256-byte
-// aligned buffers: every block offset and record size is a multiple of four
-// elements (16 bytes in FP32, 32 in FP64).
+// The kernels move records with 16-byte vector accesses from 256-byte
+// aligned buffers, but only from three kinds of offset: the start of a
+// record, its head (KfTab/RtsTab::head, SlrTab::obs) and the record size.
+// Those are multiples of four elements (16 bytes in FP32, 32 in FP64); the
+// inner block offsets (KfTab K, mp, ...; RtsTab Pf, ...) are not, and those
+// blocks are read element by element.
 static_assert(KfTab<5, 2>::head % 4 == 0 && KfTab<5, 2>::size % 4 == 0, "KfTab alignment");
 static_assert(RtsTab<5>::head % 4 == 0 && RtsTab<5>::size % 4 == 0, "RtsTab alignment");
 static_assert(SlrTab<5, 2>::obs % 4 == 0 && SlrTab<5, 2>::size % 4 == 0, "SlrTab alignment");

@@ -577,8 +577,10 @@ adj_change_partial(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
   float d = 0.f, m = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    d = fmaxf(d, fabsf((float)(a[i] - b[i])));
-    m = fmaxf(m, fabsf((float)a[i]));
+    // a NaN counts as an infinite change (fmaxf alone would drop it)
+    const float di = fabsf((float)(a[i] - b[i])), mi = fabsf((float)a[i]);
+    d = di == di ? fmaxf(d, di) : INFINITY;
+    m = mi == mi ? fmaxf(m, mi) : INFINITY;
   }
   unsigned bd = __float_as_uint(d), bm = __float_as_uint(m);
   bd = __reduce_max_sync(0xffffffffu, bd);
@@ -589,10 +591,19 @@ adj_change_partial(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
   }
 }
 
-static __global__ void adj_change_final(const unsigned* __restrict__ words,
-                                        double* __restrict__ out) {
-  const double d = __uint_as_float(words[0]), m = __uint_as_float(words[1]);
-  out[0] = m > 0.0 ? d / m : d;
+// Relative changes of lambda (words 0, 1; 0 without adjoint iterations) and
+// of the trajectory (words 2, 3) into the optional outputs; with tol > 0 a
+// change >= tol or not finite sets SQSM_ERR_NOT_CONVERGED (128).
+static __global__ void adj_settle_check(const unsigned* __restrict__ words, int have_adj,
+                                        double tol, double* __restrict__ adj_change,
+                                        double* __restrict__ ipls_change, int* status) {
+  const double da = __uint_as_float(words[0]), ma = __uint_as_float(words[1]);
+  const double di = __uint_as_float(words[2]), mi = __uint_as_float(words[3]);
+  const double ra = have_adj ? (ma > 0.0 ? da / ma : da) : 0.0;
+  const double ri = mi > 0.0 ? di / mi : di;
+  if (adj_change) adj_change[0] = ra;
+  if (ipls_change) ipls_change[0] = ri;
+  if (tol > 0.0 && status && !(ra < tol && ri < tol)) atomicOr(status, 128);
 }
 
 // Sum of the per-sequence log-likelihoods times sign (one thread, fixed order).

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <string>
@@ -45,6 +47,9 @@ struct Workspace {
                              // [2] largest change of the nominal means (float bits)
   void* params = nullptr;    // IPLS model constants
   void* dm0 = nullptr;       // IPLS prior mean in deviation coordinates
+  void* n0fac = nullptr;     // prior factors chol(P0) when N0 arguments are covariances
+  void* prevrows = nullptr;  // refinement: nominal rows before the last smoother pass
+  double* partial2 = nullptr;   // refinement passes' log-likelihood partials
   bool ipls_ready = false;
   // NLL + gradient
   AdjArgs adj{};
@@ -70,11 +75,14 @@ struct GraphKey {
   const void* iters = nullptr;
   int kind = SQSM_MODEL_CT_BEARINGS;
   const void *grad = nullptr, *change = nullptr;   // NLL + gradient outputs
+  const void* ichange = nullptr;
+  int prior_cov = 0;                // N0 holds prior covariances
   bool operator<(const GraphKey& o) const {
     return std::tie(plan, dtype, lin, M, prof, adj, y, m0, N0, ims, iNs, ms, Ns, ll, tol, iters,
-                    kind, grad, change) <
+                    kind, grad, change, ichange, prior_cov) <
            std::tie(o.plan, o.dtype, o.lin, o.M, o.prof, o.adj, o.y, o.m0, o.N0, o.ims, o.iNs,
-                    o.ms, o.Ns, o.ll, o.tol, o.iters, o.kind, o.grad, o.change);
+                    o.ms, o.Ns, o.ll, o.tol, o.iters, o.kind, o.grad, o.change, o.ichange,
+                    o.prior_cov);
   }
 };
 
@@ -346,7 +354,9 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype, int nx = 5, int ny = 2)
   w->params = w->mem.get(512);
   w->dm0 = w->mem.get(es * nx * p->B);
   w->tol_words = (int*)w->mem.get(4 * sizeof(int));
-  if (!w->params || !w->dm0 || !w->tol_words) return false;
+  w->prevrows = w->mem.get(es * xrow_size(nx) * rows);
+  w->partial2 = (double*)w->mem.get(sizeof(double) * p->filt.lv[0].n_chunks);
+  if (!w->params || !w->dm0 || !w->tol_words || !w->prevrows || !w->partial2) return false;
   w->ipls_ready = true;
   return true;
 }
@@ -374,7 +384,7 @@ bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
   g.th_partial = (double*)w->mem.get(
       sizeof(double) * 4 * std::max<int64_t>(1, grid_for(p->smth.lv[0].n_chunks * p->L0)));
   g.ll = (double*)w->mem.get(sizeof(double) * p->B);
-  g.change_words = w->mem.get(2 * sizeof(unsigned));
+  g.change_words = w->mem.get(4 * sizeof(unsigned));
   if (!g.change_words) return false;
   if (!g.nom_m || !g.nom_N || !g.ms2 || !g.Ns2 || !g.dir || !g.dfilt || !g.lam_a || !g.lam_b ||
       !g.gbar || !g.ktab || !g.rtab || !g.stab || !g.th_partial || !g.ll)
@@ -399,6 +409,33 @@ bool valid_offsets(const int64_t* off, int64_t batch) {
   return true;
 }
 
+// Every non-null pointer is a multiple of `bytes` (the kernels access caller
+// arrays element by element, so an element must not straddle its boundary).
+bool aligned(size_t bytes, std::initializer_list<const void*> ptrs) {
+  for (const void* q : ptrs)
+    if (q && reinterpret_cast<uintptr_t>(q) % bytes != 0) return false;
+  return true;
+}
+
+size_t elem_bytes(int dtype) { return dtype == SQSM_F64 ? 8 : 4; }
+
+// With the prior_covariance option the N0 argument of a call holds prior
+// covariances P0: the scans then read the FP64 Cholesky factors that
+// enqueue_prior writes into the workspace (returned here; null if that
+// buffer cannot be allocated), else the caller's N0 itself.
+const void* prior_input(const sqsm_ctx* ctx, Workspace* w, const Plan* p, int dtype, int nx,
+                        const void* N0) {
+  if (!ctx->opt.prior_covariance) return N0;
+  if (!w->n0fac) w->n0fac = w->mem.get(elem_bytes(dtype) * nx * nx * p->B);
+  return w->n0fac;
+}
+
+void enqueue_prior(const sqsm_ctx* ctx, const Plan* p, const Workspace* w, int dtype, int nx,
+                   const void* P0, cudaStream_t s) {
+  if (ctx->opt.prior_covariance)
+    enqueue_prior_cholesky(dtype == SQSM_F64, p->B, nx, P0, w->n0fac, ctx->d_status, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -406,6 +443,7 @@ extern "C" {
 int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
   if (!out) return SQSM_ERR_INVALID_ARG;
   *out = nullptr;
+  if (opt && (opt->refine < 0 || opt->refine > 2)) return SQSM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return SQSM_ERR_CUDA;
@@ -517,22 +555,28 @@ int sqsm_lgssm_smooth(sqsm_ctx* ctx, int dtype, int nx, int ny, int64_t n, const
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or smoother output pointer");
   if (sF < 0 || sc < 0 || sSQ < 0 || sH < 0 || sd < 0 || sSR < 0)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "negative stride");
+  if (!aligned(elem_bytes(dtype), {F, c, SQ, H, d, SR, m0, N0, y, mf, Nf, ms, Ns}) ||
+      !aligned(8, {loglik}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   const int64_t offsets[2] = {0, n};
   Plan* p = get_plan(ctx, offsets, 1);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, nx);
   if (!w) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace allocation failed");
+  const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
+  if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace allocation failed");
   Prof* prof = nullptr;
   if (ctx->prof_on) {
     ctx->call_prof.clear();
     prof = &ctx->call_prof;
     ctx->last_prof = prof;
   }
-  LgssmArgs a{nx, ny, F, c, SQ, H, d, SR, sF, sc, sSQ, sH, sd, sSR, m0, N0, y,
+  LgssmArgs a{nx, ny, F, c, SQ, H, d, SR, sF, sc, sSQ, sH, sd, sSR, m0, n0, y,
               mf ? mf : w->mf, Nf ? Nf : w->Nf, ms, Ns, prof};
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
+  enqueue_prior(ctx, p, w, dtype, nx, N0, s);
   const DevSeqs sq = seqs_of(p);
   int rc = dtype == SQSM_F32
                ? lgssm_enqueue_f32(a, p->filt, w->filt, p->smth, w->smth, sq, w->partial,
@@ -577,6 +621,8 @@ IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* mod
   a.nrows = w->nrows;
   a.params = w->params;
   a.dm0 = w->dm0;
+  a.prevrows = w->prevrows;
+  a.partial2 = w->partial2;
   return a;
 }
 
@@ -587,6 +633,7 @@ IplsArgs ctx_ipls_args(const sqsm_ctx* ctx, const Plan* p, const Workspace* w,
   IplsArgs a = make_ipls_args(p, w, model, theta, lin, M, y, m0, N0, init_ms, init_Ns, ms, Ns,
                               loglik);
   a.centered = ctx->opt.absolute ? 0 : 1;
+  a.refine = ctx->opt.refine;
   return a;
 }
 
@@ -690,12 +737,14 @@ int choose_ipls_shape(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
     Plan* p = get_plan(ctx, offsets, batch, c[0], c[1]);
     if (!p) continue;
     Workspace* w = get_ws(p, dtype, 5);
-    if (!w || !ensure_ipls(w, p, dtype)) {
+    const void* n0 = w && ensure_ipls(w, p, dtype) ? prior_input(ctx, w, p, dtype, 5, N0) : nullptr;
+    if (!n0) {
       if (!existed) drop_plan(ctx, p);
       continue;
     }
-    const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, lin, 1, y, m0, N0, init_ms, init_Ns,
+    const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, lin, 1, y, m0, n0, init_ms, init_Ns,
                                       ms, Ns, nullptr);
+    enqueue_prior(ctx, p, w, dtype, 5, N0, s);
     if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
     float t = INFINITY;
     for (int rep = 0; rep < 3; ++rep) {
@@ -773,6 +822,8 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
   if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, m0, N0, init_ms, init_Ns, ms, Ns}) || !aligned(8, {loglik}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -790,13 +841,16 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   Workspace* w = get_ws(p, dtype, nx);
   if (!w || !ensure_ipls(w, p, dtype, nx, ny))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+  const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
+  if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, n0, init_ms, init_Ns,
                               ms, Ns, loglik);
   // theta -> model constants, outside any graph so that theta is not baked in
   if (pop) pop_params(dtype, a, s);
   else if (dtype == SQSM_F32) ipls_params_f32(a, s);
   else ipls_params_f64(a, s);
   auto enqueue = [&](cudaStream_t st) {
+    enqueue_prior(ctx, p, w, dtype, nx, N0, st);
     if (pop) enqueue_pop(ctx, dtype, p, w, a, st);
     else enqueue_ipls(ctx, dtype, p, w, a, st);
   };
@@ -811,6 +865,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
     GraphKey key{p, dtype, linearization, M, ctx->prof_on ? 1 : 0, 0, y, m0, N0, init_ms, init_Ns,
                  ms, Ns, loglik};
     key.kind = model->kind;
+    key.prior_cov = ctx->opt.prior_covariance;
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
@@ -880,6 +935,9 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
   if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, m0, N0, init_ms, init_Ns, ms, Ns}) ||
+      !aligned(8, {loglik}) || !aligned(4, {iters_done}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -897,7 +955,9 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   Workspace* w = get_ws(p, dtype, nx);
   if (!w || !ensure_ipls(w, p, dtype, nx, ny))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, max_iters, y, m0, N0,
+  const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
+  if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  const IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, max_iters, y, m0, n0,
                                     init_ms, init_Ns, ms, Ns, loglik);
   int* iters = w->tol_words;
   int* go = w->tol_words + 1;
@@ -918,6 +978,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   else ipls_params_f64(a, s);
   if (!ctx->opt.use_graph) {
     // host-driven loop: one device-to-host read of the continue flag per iteration
+    enqueue_prior(ctx, p, w, dtype, nx, N0, s);
     phase(IPLS_PRE, s);
     cudaMemsetAsync(w->tol_words, 0, 4 * sizeof(int), s);
     for (int it = 0; it < max_iters; ++it) {
@@ -940,6 +1001,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
     key.tol = tol;
     key.iters = iters_done;
     key.kind = model->kind;
+    key.prior_cov = ctx->opt.prior_covariance;
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
@@ -948,6 +1010,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
       cudaStream_t cs = ctx->capture_stream;
       cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+      enqueue_prior(ctx, p, w, dtype, nx, N0, cs);
       phase(IPLS_PRE, cs);
       cudaMemsetAsync(w->tol_words, 0, 4 * sizeof(int), cs);
       cudaStreamCaptureStatus cst;
@@ -1030,6 +1093,8 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (!y || !m0 || !P0 || !ms || !Ps)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
   if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, m0, P0, ms, Ps}) || !aligned(8, {loglik}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -1056,10 +1121,11 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
 }
 
 int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
-                       int linearization, int M, int adj_iters, int64_t batch,
+                       int linearization, int M, int adj_iters, double tol, int64_t batch,
                        const int64_t* offsets, const void* y, const void* m0, const void* N0,
                        const void* init_ms, const void* init_Ns, void* ms, void* Ns,
-                       double* nll, double* grad, double* adj_change, void* stream) {
+                       double* nll, double* grad, double* adj_change, double* ipls_change,
+                       void* stream) {
   if (!ctx) return SQSM_ERR_INVALID_ARG;
   if (dtype != SQSM_F32 && dtype != SQSM_F64)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
@@ -1071,6 +1137,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   if (linearization != SQSM_CUBATURE)
     return fail(ctx, SQSM_ERR_UNSUPPORTED, "the gradient is implemented for cubature SLR only");
   if (M < 0 || adj_iters < 0) return fail(ctx, SQSM_ERR_INVALID_ARG, "M, adj_iters must be >= 0");
+  if (std::isnan(tol)) return fail(ctx, SQSM_ERR_INVALID_ARG, "tol is NaN");
   if (M == 0 && (!init_ms || !init_Ns))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "M = 0 needs an initial trajectory");
   if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
@@ -1081,6 +1148,9 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   if ((init_ms == nullptr) != (init_Ns == nullptr))
     return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
   if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, m0, N0, init_ms, init_Ns, ms, Ns}) ||
+      !aligned(8, {nll, grad, adj_change, ipls_change}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaGetLastError();
@@ -1093,7 +1163,9 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
-  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, N0, init_ms, init_Ns,
+  const void* n0 = prior_input(ctx, w, p, dtype, 5, N0);
+  if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
+  IplsArgs a = ctx_ipls_args(ctx, p, w, model, theta, linearization, M, y, m0, n0, init_ms, init_Ns,
                               ms, Ns, nullptr);
   AdjArgs adj = w->adj;
   adj.iters = adj_iters;
@@ -1101,9 +1173,12 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   adj.nll = nll;
   adj.grad = grad;
   adj.change = adj_change;
+  adj.ichange = ipls_change;
+  adj.tol = tol;
   const DevSeqs sq = seqs_of(p);
   if (dtype == SQSM_F32) ipls_params_f32(a, s); else ipls_params_f64(a, s);
   auto enqueue = [&](cudaStream_t st) {
+    enqueue_prior(ctx, p, w, dtype, 5, N0, st);
     if (dtype == SQSM_F32)
       adj_enqueue_f32(a, adj, p->filt, w->filt, p->smth, w->smth, w->adj_scan, sq, w->partial,
                       ctx->d_status, st);
@@ -1118,7 +1193,10 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
                  ms, Ns, nll};
     key.kind = model->kind;
     key.grad = grad;          // every pointer the captured kernels write is
-    key.change = adj_change;  // part of the key
+    key.change = adj_change;  // part of the key, and the tolerance the
+    key.ichange = ipls_change;   // check kernel is given
+    key.tol = tol;
+    key.prior_cov = ctx->opt.prior_covariance;
     auto it = ctx->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it != ctx->graphs.end()) {
@@ -1169,6 +1247,8 @@ int sqsm_ct_linearize(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
   if (!y || !ms || !Ns || !F || !c || !SQ || !H || !d || !SR)
     return fail(ctx, SQSM_ERR_INVALID_ARG, "null pointer");
   if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, ms, Ns, F, c, SQ, H, d, SR}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
   DeviceGuard g(ctx->device);
   Plan* p = get_plan(ctx, offsets, batch);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");

@@ -633,6 +633,57 @@ __global__ void __launch_bounds__(kBlock) rows_copy_kernel(int64_t rows, RI in, 
   out.store(e, m, N);
 }
 
+// Residual model of one refinement pass of the linear smoother (mixed
+// precision iterative refinement).  The smoother of the linearised model in
+// deviation coordinates about m (the iteration's nominal means, rows
+// prev) returned n1 = m + dx; the correction delta = x - n1 solves the same
+// linear-Gaussian model about n1, whose offsets are, with dx = n1 - m,
+//   c' = F dx_{k-1} + c~ - dx_k,   d' = d~ + H dx_k
+// (x_k = F x_{k-1} + c~ + q and y_k = H x_k + d~ + r written for x - dx);
+// the prior's is dm0 - dx_0 (center_prior_kernel on n1).  dx and the
+// offsets are formed in FP64 from the stored values -- dx exactly, the
+// products and sums with FP64 rounding -- and rounded once when written
+// back into the PRec records in place.  One thread per step.
+template <typename T, int NX, int NY, typename RI>
+__global__ void __launch_bounds__(kBlock)
+refine_residual_kernel(DevLevel lv, int leaf, RI prev, RI now, T* __restrict__ rec) {
+  using P = PRec<NX, NY>;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ch = tid / leaf;
+  if (ch >= lv.n_chunks) return;
+  const int j = (int)(tid - ch * leaf);
+  if (j >= lv.count[ch]) return;
+  const int b = lv.seq[ch];
+  const int64_t s = lv.first[ch] + j;
+  const int64_t rp = s + b, rk = s + b + 1;
+  T m0v[NX], m1v[NX], k0v[NX], k1v[NX];
+  prev.load_mean(rp, m0v);
+  now.load_mean(rp, m1v);
+  prev.load_mean(rk, k0v);
+  now.load_mean(rk, k1v);
+  double dp[NX], dk[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    dp[i] = (double)m1v[i] - (double)m0v[i];
+    dk[i] = (double)k1v[i] - (double)k0v[i];
+  }
+  T* r = rec + s * P::size;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    double a = (double)r[P::c + i] - dk[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) a += (double)r[P::F + i * NX + k] * dp[k];
+    r[P::c + i] = (T)a;
+  }
+#pragma unroll
+  for (int i = 0; i < NY; ++i) {
+    double a = (double)r[P::d + i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) a += (double)r[P::H + i * NX + k] * dk[k];
+    r[P::d + i] = (T)a;
+  }
+}
+
 // Prior of the deviation model: dm0[b] = m0[b] - m_0 (nominal row 0 of b).
 template <typename T, int NX, typename RI>
 __global__ void center_prior_kernel(DevSeqs sq, const T* __restrict__ m0, RI nom,

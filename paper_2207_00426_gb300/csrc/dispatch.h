@@ -41,6 +41,12 @@ struct IplsArgs {
   void *frows, *nrows;   // packed filter output and nominal trajectory (RowsPacked)
   Prof* prof;   // optional per-kernel events
   int centered = 1;   // 1: deviation coordinates, 0: printed absolute coordinates
+  // mixed-precision refinement of each iteration's linear smoother (deviation
+  // coordinates only): passes, the nominal rows before the last smoother
+  // pass (RowsPacked) and the refinement passes' log-likelihood partials
+  int refine = 0;
+  void* prevrows = nullptr;
+  double* partial2 = nullptr;
 };
 
 // Everything of Alg. 3 after the parameter kernel; capturable.
@@ -98,7 +104,9 @@ struct AdjArgs {
   void *dir, *dfilt, *gbar, *lam_a, *lam_b;
   void *ktab, *rtab, *stab;           // per-step KfTab / RtsTab / SlrTab records
   double *th_partial, *ll, *nll, *grad, *change;
-  void* change_words;                 // two words for the change reduction
+  double* ichange;                    // relative change of the trajectory in one more iteration
+  double tol;                         // fixed-point tolerance of the status check (<= 0: none)
+  void* change_words;                 // four words: the adjoint's and the trajectory's change
 };
 void adj_enqueue_f32(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf,
                      const ScanBuffers& Wf, const LevelSet& Ls, const ScanBuffers& Ws,
@@ -115,6 +123,14 @@ void ct_linearize_f64(const IplsArgs& a, const LevelSet& Lf, DevSeqs sq, cudaStr
 
 void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, int* status,
                            cudaStream_t s, Prof* P = nullptr);
+
+// Largest state dimension of the prior Cholesky kernel.
+constexpr int kMaxPriorNx = 8;
+// N0[b] = chol(P0[b]) in FP64 for b < batch (nx x nx, row-major, element
+// type double if dtype_f64 else float); a P0 that is not positive definite
+// gives a NaN factor and sets SQSM_ERR_NOT_PD in *status.
+void enqueue_prior_cholesky(int dtype_f64, int64_t batch, int nx, const void* P0, void* N0,
+                            int* status, cudaStream_t s);
 
 }  // namespace sqsm
 

@@ -80,10 +80,36 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
     center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
                                                                    (T*)a.dm0);
   }
+  // refinement passes need the nominal rows from before each smoother pass
+  const int passes = a.centered ? a.refine : 0;
+  const RowsPacked<T, NX> prev{(T*)a.prevrows};
+  auto keep_prev = [&]() {
+    ProfScope ps(a.prof, K_INIT, s);
+    rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, prev);
+  };
+  if (passes > 0) keep_prev();
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y,
                             (const T*)(a.centered ? a.dm0 : a.m0), (const T*)a.N0, fr, partial,
                             status, s, a.prof);
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax);
+  // Mixed-precision iterative refinement: the smoother's FP32 error is that
+  // of a linear solve, so one more pass on the residual model about its own
+  // result (offsets formed in FP64) removes most of it; the factors do not
+  // change.  The change measure and the log-likelihood stay those of the
+  // first pass.
+  for (int r = 0; r < passes; ++r) {
+    {
+      ProfScope ps(a.prof, K_INIT, s);
+      refine_residual_kernel<T, NX, NY><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+          Lf.lv[0], a.leaf, prev, nom, (T*)a.F);
+      center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
+                                                                     (T*)a.dm0);
+    }
+    if (r + 1 < passes) keep_prev();
+    enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
+                              a.partial2, status, s, a.prof);
+    enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, nullptr);
+  }
 }
 
 // The CT bearings model's phase.

@@ -32,6 +32,37 @@ void enqueue_loglik_reduce(DevSeqs sq, const double* partial, double* loglik, in
 
 namespace {
 
+// N0 = chol(P0) per sequence in FP64 (one thread per sequence; the lower
+// triangle of P0 is read, the factor is written with zeros above the
+// diagonal).  A pivot that is not positive (P0 not positive definite) or not
+// finite makes the whole factor NaN and sets SQSM_ERR_NOT_PD (4).
+template <typename T>
+__global__ void prior_cholesky(int64_t batch, int nx, const T* __restrict__ P0,
+                               T* __restrict__ N0, int* status) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const T* P = P0 + b * nx * nx;
+  T* N = N0 + b * nx * nx;
+  double L[kMaxPriorNx * kMaxPriorNx];
+  bool pd = true;
+  for (int j = 0; j < nx; ++j) {
+    double d = (double)P[j * nx + j];
+    for (int k = 0; k < j; ++k) d -= L[j * kMaxPriorNx + k] * L[j * kMaxPriorNx + k];
+    if (!(d > 0.0) || !isfinite(d)) pd = false;
+    const double ljj = sqrt(d > 0.0 ? d : 1.0);
+    L[j * kMaxPriorNx + j] = ljj;
+    for (int i = j + 1; i < nx; ++i) {
+      double v = (double)P[i * nx + j];
+      for (int k = 0; k < j; ++k) v -= L[i * kMaxPriorNx + k] * L[j * kMaxPriorNx + k];
+      L[i * kMaxPriorNx + j] = v / ljj;
+    }
+  }
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < nx; ++j)
+      N[i * nx + j] = !pd ? T(NAN) : j <= i ? (T)L[i * kMaxPriorNx + j] : T(0);
+  if (!pd && status) atomicOr(status, 4);
+}
+
 __global__ void ipls_tol_check(unsigned* dmax, int* iters, int max_iters, float tol,
                                cudaGraphConditionalHandle handle, int use_handle, int* go) {
   const float d = __uint_as_float(*dmax);
@@ -44,6 +75,16 @@ __global__ void ipls_tol_check(unsigned* dmax, int* iters, int max_iters, float 
 }
 
 }  // namespace
+
+void enqueue_prior_cholesky(int dtype_f64, int64_t batch, int nx, const void* P0, void* N0,
+                            int* status, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((batch + 127) / 128);
+  if (dtype_f64)
+    prior_cholesky<double><<<blocks, 128, 0, s>>>(batch, nx, (const double*)P0, (double*)N0,
+                                                  status);
+  else
+    prior_cholesky<float><<<blocks, 128, 0, s>>>(batch, nx, (const float*)P0, (float*)N0, status);
+}
 
 void enqueue_tol_check(unsigned* dmax, int* iters, int max_iters, float tol,
                        cudaGraphConditionalHandle handle, int use_handle, int* go, cudaStream_t s) {

@@ -27,6 +27,8 @@
 // by the caller.
 #include <cuda.h>
 
+#include <cstdint>
+#include <initializer_list>
 #include <mutex>
 
 #include "../../include/sqsm.h"
@@ -221,6 +223,11 @@ extern "C" int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n, c
   if (!F || !c || !SQ || !H || !d || !SR || !m0 || !N0 || !y || !mf || !Nf || !ms || !Ns)
     return SQSM_ERR_INVALID_ARG;
   if (sF < 0 || sc < 0 || sSQ < 0 || sH < 0 || sd < 0 || sSR < 0) return SQSM_ERR_INVALID_ARG;
+  const uintptr_t es_mask = (dtype == SQSM_F64 ? 8 : 4) - 1;
+  for (const void* q : {F, c, SQ, H, d, SR, m0, N0, y, (const void*)mf, (const void*)Nf,
+                        (const void*)ms, (const void*)Ns})
+    if (reinterpret_cast<uintptr_t>(q) & es_mask) return SQSM_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(loglik) & 7) return SQSM_ERR_INVALID_ARG;
   // an error the caller has pending stays theirs: run nothing, clear nothing
   if (cudaPeekAtLastError() != cudaSuccess) return SQSM_ERR_CUDA;
   // leaf chunks of 4 steps, radix-4 folds: the scan shape of a context with

@@ -73,3 +73,36 @@ def test_ct_model_from_theta_length(lib):
     for bad in ([0.0, 0.0], [0.0] * 5):
         with pytest.raises(ValueError):
             lib._ct_model(bad, 0.01, sensors)
+
+
+def test_noalloc_argument_errors_before_any_cuda_call(lib):
+    """The no-allocation smoother validates its arguments on the host before
+    any CUDA call (so this runs without a GPU): a pointer that is not a
+    multiple of its element size, a negative stride, a null output, n < 1
+    and an unknown dtype are refused."""
+    f = lib.lib.sqsm_lgssm_smooth_noalloc
+    good = 0x10000                      # never dereferenced: validation fails first
+    ptrs = [good] * 13
+
+    def call(dtype=0, n=10, ptrs=ptrs, strides=(25, 5, 25, 10, 2, 4), ll=good):
+        args = []
+        for p, s in zip(ptrs[:6], strides):
+            args += [p, s]
+        return f(dtype, 5, 2, n, *args, *ptrs[6:9], *ptrs[9:13], ll, None)
+
+    for i in range(13):
+        bad = list(ptrs)
+        bad[i] = good + 2               # misaligned for float and double
+        assert call(ptrs=bad) == lib.ERR_INVALID_ARG, i
+        assert call(dtype=1, ptrs=bad) == lib.ERR_INVALID_ARG, i
+    bad = list(ptrs)
+    bad[0] = good + 4                   # aligned for float, not for double
+    assert call(dtype=1, ptrs=bad) == lib.ERR_INVALID_ARG
+    assert call(ll=good + 4) == lib.ERR_INVALID_ARG
+    assert call(strides=(25, 5, 25, 10, 2, -4)) == lib.ERR_INVALID_ARG
+    nul = list(ptrs)
+    nul[10] = None                      # Nf
+    assert call(ptrs=nul) == lib.ERR_INVALID_ARG
+    assert call(n=0) == lib.ERR_INVALID_ARG
+    assert call(dtype=2) == lib.ERR_INVALID_ARG
+    assert f(0, 7, 7, 10, *([good, 0] * 6), *([good] * 7), good, None) == lib.ERR_UNSUPPORTED

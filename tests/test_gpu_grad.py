@@ -112,8 +112,8 @@ def test_extended_is_rejected(B, ctx):
     off, batch = B._offsets([0, 10])
     z = torch.zeros(64, dtype=dt, device="cuda:0")
     p = z.data_ptr()
-    rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, B.EXTENDED, 5, 5, batch, off,
-                                  p, p, p, None, None, p, p, p, p, None, None)
+    rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, B.EXTENDED, 5, 5, 0.0, batch,
+                                  off, p, p, p, None, None, p, p, p, p, None, None, None)
     assert rc == B.ERR_UNSUPPORTED
 
 
