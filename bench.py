@@ -4,7 +4,11 @@ One step = one full iterated posterior linearisation solve (Alg. 3) of
 M = 10 iterations -- SLR, parallel square-root filter scan with the
 log-likelihood, parallel square-root smoother scan -- over one synthetic
 coordinated-turn sequence of n = 100000 observations (n_x = 5, n_y = 2),
-FP32 arithmetic with FP64 log-likelihood accumulation.
+FP32 arithmetic with FP64 log-likelihood accumulation, each iteration's
+linear smoother refined once (one more filter and smoother pass on the
+residual model formed in FP64), the mode in which the FP32 means meet the
+1e-4 accuracy target at this non-converging configuration.  The unrefined
+mode (half the work, 3.3e-4) is reported beside it as ``fast``.
 
 Metric: smoothed steps/s = (time steps x IPLS iterations) per second; the
 same line carries the NLL + gradient evaluations/s (Sec. 5.2) at the same
@@ -51,6 +55,7 @@ ADJ_ITERS = 10
 SEED = 1
 CPU_SAMPLE_STEPS = 1000          # oracle sample for the CPU baseline leg
 REF_SAMPLE_STEPS = 400           # oracle sample per --impl reference step
+REFINE = 1                       # refinement passes of the benchmarked mode
 BATCH_CPU_PREFIX = 250           # observations of each sampled sequence of the 4096
 GRAD_CPU_PREFIX = 100            # ... and of the 256 x 2000 batch (host baselines)
 
@@ -86,7 +91,8 @@ def dist_env():
 def config(args, world, leaf=None):
     return {"workload": f"coordinated-turn bearings-only tracking, cubature IPLS, "
                         f"n={args.n} observations, M={args.M} iterations, nx=5, ny=2",
-            "n": args.n, "M": args.M, "linearization": "cubature", "batch_per_gpu": 1,
+            "n": args.n, "M": args.M, "linearization": "cubature", "refine": REFINE,
+            "batch_per_gpu": 1,
             "sequences_total": world, "leaf_chunk": leaf,
             "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"independent sequences, {world} GPU(s)"}
@@ -307,7 +313,7 @@ def gpu_arm(args, rank, world, local):
     ms = torch.empty((n + 1, 5), dtype=f32, device=dev)
     Ns = torch.empty((n + 1, 5, 5), dtype=f32, device=dev)
     ll = torch.empty(1, dtype=torch.float64, device=dev)
-    ctx = B.Context(local, use_graph=True)
+    ctx = B.Context(local, use_graph=True, refine=REFINE)
     leaf = ctx.scan_shape([0, n])[0]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -388,7 +394,7 @@ def gpu_arm(args, rank, world, local):
             a0[1] += c
     ctx.profile(False)
     launches_per_step = sum(c for _, c in acc.values()) / nprof + 1   # + parameter kernel
-    flops = CM.ipls_kernel_flops([n], leaf=leaf)
+    flops = CM.ipls_kernel_flops([n], leaf=leaf, refine=REFINE)
     total_ms = sum(t for t, _ in acc.values())
     top = max(acc, key=lambda k: acc[k][0])
     # algorithmic flops of the family per step, spread over its launches
@@ -403,7 +409,7 @@ def gpu_arm(args, rank, world, local):
                 "traffic": NCU_TRAFFIC.get((top, n)), "flops_per_launch": f_launch,
                 "share_of_step": acc[top][0] / total_ms, "peak_note": "measured: " + peak_basis,
                 "peak_derived": derived}
-    it_flops = CM.ipls_iteration_flops([n], leaf=leaf)
+    it_flops = CM.ipls_iteration_flops([n], leaf=leaf, refine=REFINE)
     whole = {"achieved_tflops": it_flops * M / (ms_per_step / 1e3) / 1e12}
     whole["frac"] = whole["achieved_tflops"] / peak
 
@@ -420,14 +426,17 @@ def gpu_arm(args, rank, world, local):
 
     # ---- NLL + gradient (Sec. 5.2) at the same size: M IPLS iterations, the
     #      final linearisation pass and ADJ adjoint fixed-point iterations
+    #      (unrefined forward iterations: the gradient's 1e-3 target holds
+    #      without refinement, see the full-size gradient tests)
     grads = {}
+    gctx = B.Context(local, use_graph=True)
 
     def nll_grad_rate(dtype, k):
         yy, mm0, NN0 = y.to(dtype), m0.to(dtype), N0.to(dtype)
         out = {}
 
         def ev():
-            out["r"] = B.sqsm_ipls_nll_grad(ctx, d["theta"], yy, [0, n], mm0, NN0, M, ADJ_ITERS,
+            out["r"] = B.sqsm_ipls_nll_grad(gctx, d["theta"], yy, [0, n], mm0, NN0, M, ADJ_ITERS,
                                             dt=d["dt"])
         ev()
         torch.cuda.synchronize()
@@ -450,13 +459,14 @@ def gpu_arm(args, rank, world, local):
     offg = [int(v) for v in dg["offsets"]]
 
     def evg():
-        B.sqsm_ipls_nll_grad(ctx, dg["theta"], yg, offg, m0g, N0g, M, ADJ_ITERS, dt=dg["dt"])
+        B.sqsm_ipls_nll_grad(gctx, dg["theta"], yg, offg, m0g, N0g, M, ADJ_ITERS, dt=dg["dt"])
     evg()
     torch.cuda.synchronize()
     tg = timed(evg, 3)
     grads["batch_256x2000_f32"] = {"evals_per_s": 1.0 / tg, "ms_per_eval": 1e3 * tg}
     del yg, m0g, N0g
-    grads["converged_50x2000_f32"] = converged_nll_grad(B, torch, ctx, dev, timed)
+    grads["converged_50x2000_f32"] = converged_nll_grad(B, torch, gctx, dev, timed)
+    gctx.close()
     # how far the M-iteration trajectory is from a fixed point: max-norm
     # change of m^s from iteration M to M + 1 (FP32)
     ms_next = torch.empty_like(ms)
@@ -513,6 +523,21 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.synchronize()
     err_f32 = float((ms.double() - ms64).norm(dim=1).max() / ms64.norm(dim=1).max())
     ll_rel = abs(ll.item() - ll64.item()) / abs(ll64.item())
+    ll_head = ll.item()
+    # the unrefined FP32 mode: time and error against the same FP64 run
+    fctx = B.Context(local, use_graph=True, refine=0)
+
+    def fstep():
+        B.sqsm_ipls_smooth(fctx, d["theta"], y, [0, n], m0, N0, M, B.CUBATURE, dt=d["dt"],
+                           ms=ms, Ns=Ns, loglik=ll)
+    fstep()
+    torch.cuda.synchronize()
+    tf = timed(fstep, max(3, min(args.steps, 10)))
+    fast = {"value": n * M / tf, "ms_per_step": 1e3 * tf, "refine": 0,
+            "f32_vs_f64_mean_rel_err": float((ms.double() - ms64).norm(dim=1).max()
+                                             / ms64.norm(dim=1).max()),
+            "f32_vs_f64_loglik_rel_err": abs(ll.item() - ll64.item()) / abs(ll64.item())}
+    fctx.close()
 
     studies = None
     if args.studies:
@@ -534,7 +559,7 @@ def gpu_arm(args, rank, world, local):
                 "clocks": clk.summary(), "roofline": roofline, "whole_step": whole,
                 "f64": {"value": n * M / t64, "ms_per_step": 1e3 * t64,
                         "f32_vs_f64_mean_rel_err": err_f32, "f32_vs_f64_loglik_rel_err": ll_rel},
-                "nll_grad": grads, "batched": batched, "loglik": ll.item(),
+                "fast": fast, "nll_grad": grads, "batched": batched, "loglik": ll_head,
                 "studies": args.studies_out if studies is not None else None}
     ctx.close()
     return line
@@ -545,9 +570,9 @@ def converged_nll_grad(B, torch, ctx, dev, timed):
     50 coordinated-turn sequences of 2000 steps (1e5 steps) whose Alg. 3
     iteration settles -- the first 50 of 128 (seed 5) that one more FP64
     iteration after 40 moves by less than 1e-9 -- evaluated in FP32 with
-    M = 30 IPLS and 30 adjoint iterations and the library's fixed-point
-    check at tol = 1e-4 (SQSM_ERR_NOT_CONVERGED clear = both fixed points
-    settled)."""
+    M = 30 IPLS and 40 adjoint iterations and the library's fixed-point
+    check at tol = 1e-3, the gradient's accuracy target
+    (SQSM_ERR_NOT_CONVERGED clear = both fixed points settled)."""
     from paper_2207_00426_gb300 import workloads as W
     f64 = torch.float64
     L, cand = 2000, 128
@@ -570,15 +595,15 @@ def converged_nll_grad(B, torch, ctx, dev, timed):
     out = {}
 
     def ev():
-        out["r"] = B.sqsm_ipls_nll_grad(ctx, dc["theta"], yk, offk, m0k, N0k, 30, 30, dt=dc["dt"],
-                                        tol=1e-4)
+        out["r"] = B.sqsm_ipls_nll_grad(ctx, dc["theta"], yk, offk, m0k, N0k, 30, 40, dt=dc["dt"],
+                                        tol=1e-3)
     ev()
     torch.cuda.synchronize()
     settled = ctx.status() == 0
     t = timed(ev, 3)
     torch.cuda.synchronize()
     settled = settled and ctx.status() == 0
-    return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "M": 30, "adjoint_iterations": 30,
+    return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "M": 30, "adjoint_iterations": 40,
             "fixed_point_reached": bool(settled), "grad": out["r"][1].cpu().tolist(),
             "adjoint_last_rel_change": out["r"][2].item()}
 

@@ -129,9 +129,11 @@ def _levels(counts0, leaf, radix):
             return levels
 
 
-def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cubature"):
+def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cubature",
+                      refine=0):
     """Algorithmic flops per launch of each kernel family for one IPLS
-    iteration over sequences of the given lengths.  Returns
+    iteration over sequences of the given lengths; with `refine` passes the
+    filter and smoother scans run 1 + refine times per iteration.  Returns
     {family: (flops per launch, launches per iteration)}."""
     out = {}
     nsteps = sum(lengths)
@@ -160,6 +162,8 @@ def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cu
         out["smoother_up"] = (sum(ups) / len(ups), len(ups))
         out["smoother_down"] = (sum(downs) / len(downs), len(downs))
     out["smoother_leaf_down"] = ((nel - len(lengths)) * (se + sa), 1)
+    if refine:
+        out = {k: (f, n * (1 + refine) if k != "ct_slr" else n) for k, (f, n) in out.items()}
     return out
 
 

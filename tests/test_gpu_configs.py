@@ -60,7 +60,7 @@ def test_ct_n1e4_m10(B, ctx):
     Gn = [g.double().cpu().numpy() for g in G]
     ref = sqrt_filter_smoother(*Gn, d["y"], d["m0"], d["N0"])
     assert rel_mean_err(msl.double().cpu().numpy(), ref[2]) < 1e-4
-    assert rel_cov_err(Nsl.double().cpu().numpy(), ref[3]) < 1e-3
+    assert rel_cov_err(Nsl.double().cpu().numpy(), ref[3]) < 1e-4
     assert abs(lll.item() - ref[4]) < 1e-5 * abs(ref[4])
     ms32, _, ll32 = _smooth(B, ctx, d, f32, M, "cubature")
     ms64, _, ll64 = _smooth(B, ctx, d, torch.float64, M, "cubature")
@@ -79,7 +79,7 @@ def test_sweep_n1024_against_oracle(B, ctx, method, prec):
     rms, rNs, rll, _ = O.ipls(ct, d["y"], d["m0"], d["N0"], M, method)
     tol = TOL[prec]
     assert rel_mean_err(ms, rms) < tol["mean"]
-    assert rel_cov_err(Ns, rNs) < (tol["cov"] if prec == "f64" else 1e-3)
+    assert rel_cov_err(Ns, rNs) < tol["cov"]
     assert abs(ll[0] - rll) <= (1e-9 if prec == "f64" else 1e-5) * abs(rll)
 
 
@@ -91,7 +91,7 @@ def test_sweep_n2pow20_f32_against_f64(B, ctx, method):
     ms64, Ns64, ll64 = _smooth(B, ctx, d, torch.float64, M, method)
     assert np.all(np.isfinite(ms32)) and ctx.status() == 0
     assert rel_mean_err(ms32, ms64) < 1e-4
-    assert rel_cov_err(Ns32, Ns64) < 1e-3
+    assert rel_cov_err(Ns32, Ns64) < 1e-4
     assert abs(ll32[0] - ll64[0]) < 1e-5 * abs(ll64[0])
 
 
@@ -114,7 +114,7 @@ def test_batch_4096_ragged(B, ctx):
         rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
         rows = slice(off[b] + b, off[b + 1] + b + 1)
         assert rel_mean_err(ms[rows], rms) < TOL["f32"]["mean"]
-        assert rel_cov_err(Ns[rows], rNs) < 1e-3
+        assert rel_cov_err(Ns[rows], rNs) < 1e-4
         assert abs(ll[b] - rll) <= 1e-5 * abs(rll)
     f32 = torch.float32
     y = _dev(d["y"], f32)
@@ -129,8 +129,8 @@ def test_batch_4096_ragged(B, ctx):
         rows = slice(off[b] + b, off[b + 1] + b + 1)
         ref = sqrt_filter_smoother(*[g[steps] for g in Gn], d["y"][steps], d["m0"][b], d["N0"][b])
         assert rel_mean_err(ms[rows], ref[2]) < 1e-4
-        assert rel_cov_err(Ns[rows], ref[3]) < 1e-3
-        assert abs(ll[b] - ref[4]) <= 1e-5 * max(abs(ref[4]), lengths[b])
+        assert rel_cov_err(Ns[rows], ref[3]) < 1e-4
+        assert abs(ll[b] - ref[4]) <= 1e-5 * abs(ref[4])
 
 
 def _nll(B, c, th, y, off, m0, N0, M, dt):

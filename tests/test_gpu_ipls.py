@@ -70,8 +70,8 @@ def test_ipls_single_sequence(B, ctx, prec, method):
     rms, rNs, rll, _ = O.ipls(ct, d["y"], d["m0"], d["N0"], M, method)
     tol = TOL[prec]
     assert rel_mean_err(ms.cpu().numpy(), rms) < tol["mean"]
-    assert rel_cov_err(Ns.cpu().numpy(), rNs) < (tol["cov"] if prec == "f64" else 1e-3)
-    assert abs(ll.item() - rll) <= max(tol["ll"], 1e-10) * abs(rll) * (10 if prec == "f32" else 1)
+    assert rel_cov_err(Ns.cpu().numpy(), rNs) < tol["cov"]
+    assert abs(ll.item() - rll) <= tol["ll"] * abs(rll)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -91,7 +91,7 @@ def test_ipls_ragged_batch(B, ctx, prec):
         rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
         rows = slice(off[b] + b, off[b + 1] + b + 1)
         assert rel_mean_err(ms[rows], rms) < TOL[prec]["mean"]
-        assert abs(ll[b] - rll) <= (1e-9 if prec == "f64" else 1e-4) * abs(rll)
+        assert abs(ll[b] - rll) <= TOL[prec]["ll"] * abs(rll)
 
 
 def test_large_batch_folds_and_warp_scans(B, ctx):
@@ -116,8 +116,8 @@ def test_large_batch_folds_and_warp_scans(B, ctx):
         rms, rNs, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
         rows = slice(off[b] + b, off[b + 1] + b + 1)
         assert rel_mean_err(ms[rows], rms) < TOL["f32"]["mean"]
-        assert rel_cov_err(Ns[rows], rNs) < 1e-3
-        assert abs(ll[b] - rll) <= 1e-4 * abs(rll)
+        assert rel_cov_err(Ns[rows], rNs) < TOL["f32"]["cov"]
+        assert abs(ll[b] - rll) <= TOL["f32"]["ll"] * abs(rll)
 
 
 def test_graph_replay_and_theta_update(B):
@@ -171,25 +171,28 @@ def test_full_size_chain_f32(B, ctx):
     assert abs(lll.item() - ref[4]) < 1e-5 * abs(ref[4])
 
 
-def test_full_size_fp32_accuracy_against_fp64(B, ctx):
-    """n = 100000, cubature: FP32 smoothed means against the FP64 build of
-    the same kernels (itself equal to the oracle at every size the oracle can
-    run).  The workload is far from converged at M = 10 (its trajectory still
-    moves by ~100 between iterations), which amplifies any perturbation: the
-    FP64 run itself moves 3.6e-5 under 1e-7 relative noise on y.  Measured:
-    4e-6 (M = 1), 1.7e-5 (M = 2), 1.7e-4 (M = 10)."""
+def test_full_size_fp32_accuracy_against_fp64(B):
+    """n = 100000, cubature, the benchmark's mode (one refinement pass of each
+    iteration's linear smoother): FP32 smoothed means against the FP64 build
+    of the same kernels (itself equal to the oracle at every size the oracle
+    can run, and to the stored oracle run at this size) within the 1e-4 /
+    1e-5 targets at M = 1, 2 and 10.  The workload is far from converged at
+    M = 10, which amplifies any per-iteration error (the FP64 run itself
+    moves 3.6e-5 under 1e-7 relative noise on y); without refinement the
+    FP32 scans' error grows to 3.3e-4 at M = 10, with it 7.8e-5."""
     n = 100_000
     d = W.ct_sequence(n=n, seed=1)
-    res = {}
-    for M, tol in ((1, 2e-5), (2, 1e-4), (10, 5e-4)):
+    c32, c64 = B.Context(0, refine=1), B.Context(0)
+    for M in (1, 2, 10):
         out = []
-        for dt in (torch.float32, torch.float64):
-            ms, Ns, ll = B.sqsm_ipls_smooth(ctx, d["theta"], _dev(d["y"], dt), [0, n],
+        for c, dt in ((c32, torch.float32), (c64, torch.float64)):
+            ms, Ns, ll = B.sqsm_ipls_smooth(c, d["theta"], _dev(d["y"], dt), [0, n],
                                             _dev(d["m0"][None], dt), _dev(d["N0"][None], dt), M, 0,
                                             dt=d["dt"])
             torch.cuda.synchronize()
             out.append((ms.double().cpu().numpy(), ll.item()))
         err = rel_mean_err(out[0][0], out[1][0])
-        res[M] = err
-        assert err < tol, (M, err)
-        assert abs(out[0][1] - out[1][1]) < 2e-5 * abs(out[1][1])
+        assert err < 1e-4, (M, err)
+        assert abs(out[0][1] - out[1][1]) < 1e-5 * abs(out[1][1])
+    c32.close()
+    c64.close()

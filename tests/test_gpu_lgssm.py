@@ -53,10 +53,7 @@ SHAPES = [(1, 1), (1, 2), (2, 2), (3, 2), (2, 3), (4, 2), (5, 2), (6, 3)]
 def test_random_models(B, ctx, prec, nx, ny, n):
     m = W.random_lgssm(n, nx, ny, seed=n * 31 + nx * 7 + ny)
     got = _run(B, ctx, m, torch.float64 if prec == "f64" else torch.float32)
-    tol = dict(TOL[prec])
-    if prec == "f32":
-        tol["ll"] = 1e-4 if n < 10 else tol["ll"]
-    _check(got, m, tol)
+    _check(got, m, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
