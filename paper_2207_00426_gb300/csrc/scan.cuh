@@ -307,26 +307,39 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
     load<T, NX * NX>(carry + c * CREC + NX, Dm);
   }
   bool ok = true;
+  // The inputs of a step (filter row, transition record, the mean held in
+  // out_rows) do not depend on the steps after it, so each iteration issues
+  // the loads of the next step before computing its own: their latency
+  // overlaps this step's element and RTS step instead of stalling the chain
+  // (the row it writes is never one it prefetches).
+  const bool need_old = add_nominal || dmax != nullptr;
+  auto fetch = [&](int j, T* m, T* N, Gamma<T, NX, NY>& g, T* old) {
+    const int64_t e = e0 + j;
+    fo.load(e, m, N);
+    if (e - r0 != nb) g.load_transition(gv, sq.offsets[b] + (e - r0));
+    if (need_old) out_rows.load_mean(e, old);
+  };
+  T m[NX], N[NX * NX], old[NX];
+  Gamma<T, NX, NY> g;
+  fetch(cnt - 1, m, N, g, old);
   for (int j = cnt - 1; j >= 0; --j) {
     const int64_t e = e0 + j;
     const int64_t k = e - r0;
-    T m[NX], N[NX * NX];
-    fo.load(e, m, N);
+    T pm[NX], pN[NX * NX], pold[NX];
+    Gamma<T, NX, NY> pg;
+    if (j > 0) fetch(j - 1, pm, pN, pg, pold);
     if (k == nb) {
       copy<T, NX>(m, gm);
       copy<T, NX * NX>(N, Dm);
     } else {
-      Gamma<T, NX, NY> g;
-      g.load_transition(gv, sq.offsets[b] + k);
       T el[REC];
       smoother_element<T, NX, NY>(g, m, N, el);
       smoother_apply<T, NX>(el, gm, Dm);
     }
     if (add_nominal) {
       T out[NX];
-      out_rows.load_mean(e, out);
 #pragma unroll
-      for (int i = 0; i < NX; ++i) out[i] += gm[i];
+      for (int i = 0; i < NX; ++i) out[i] = old[i] + gm[i];
       out_rows.store(e, out, Dm);
       if (dmax) {
 #pragma unroll
@@ -334,8 +347,6 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
       }
     } else {
       if (dmax) {   // the change from the previous mean held in out_rows
-        T old[NX];
-        out_rows.load_mean(e, old);
 #pragma unroll
         for (int i = 0; i < NX; ++i) change = fmaxf(change, fabsf((float)(gm[i] - old[i])));
       }
@@ -343,6 +354,12 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
     }
 #pragma unroll
     for (int i = 0; i < NX; ++i) ok = ok && finite(gm[i]);
+    if (j > 0) {
+      copy<T, NX>(pm, m);
+      copy<T, NX * NX>(pN, N);
+      copy<T, NX>(pold, old);
+      g = pg;
+    }
   }
   if (!ok) flag_status(status, 8);
   if (dmax) {
