@@ -770,19 +770,23 @@ R11_START = 0.1
 R11_BOUNDS = (0.01, 1.0)
 
 
+R11_RULES = (("extended", 1), ("cubature", 0), ("unscented", 2), ("gauss-hermite", 3))
+
+
 def r11_study(B, ctx, local, dev):
     """Maximum-likelihood estimate of the first sensor's noise standard
     deviation sqrt(R_11) (Sec. 6.4) on ten simulated trajectories, each
     calibrated on its first n observations: L-BFGS-B on phi = log sqrt(R_11)
     from sqrt(R_11) = 0.1 within [0.01, 1], the other parameters at their
-    true values, with
-    the negative pseudo log-likelihood and its derivative from
-    sqsm_ipls_nll_grad (per-sensor noise model, cubature, M = 20 IPLS and 20
-    adjoint iterations, FP32).  Wall time of each whole fit (GPU evaluations
-    and host optimiser), parallel scan against the sequential smoother (one
-    leaf chunk per sequence).  The sequential fits take minutes at the
-    larger n, so that arm fits fewer trajectories there and, at n = 4000,
-    is timed per evaluation only."""
+    true values, with the negative pseudo log-likelihood and its derivative
+    from sqsm_ipls_nll_grad (per-sensor noise model, M = 20 IPLS and 20
+    adjoint iterations, FP32), for each of the four linearisations the paper
+    compares (Taylor, cubature, unscented, Gauss-Hermite).  Wall time of
+    each whole fit (GPU evaluations and host optimiser) on the parallel
+    scan, and, for each rule, the time per evaluation of the sequential
+    smoother (one leaf chunk per sequence); the sequential arm also fits the
+    cubature rule at n = 100 and 1000 (its fits at the larger n take
+    minutes)."""
     import torch
     from scipy.optimize import minimize
     from paper_2207_00426_gb300 import workloads as W
@@ -790,61 +794,67 @@ def r11_study(B, ctx, local, dev):
     M, ADJ = 20, 20
     trajs = [W.ct_sequence(n=4000, seed=100 + i) for i in range(10)]
     out = {"M": M, "adjoint_iterations": ADJ, "dtype": "f32", "true": R11_TRUE,
-           "start": R11_START, "bounds": list(R11_BOUNDS), "linearization": "cubature",
-           "by_n": {}}
+           "start": R11_START, "bounds": list(R11_BOUNDS), "by_n": {}}
     for ns in (100, 1000, 4000):
         cseq = B.Context(local, use_graph=True, leaf_chunk=ns)
         row = {}
-        for mode, cq, nfit in (("parallel", ctx, 10),
-                               ("sequential", cseq, {100: 10, 1000: 2, 4000: 0}[ns])):
-            def make(dq):
-                yq = torch.tensor(dq["y"][:ns], dtype=f32, device=dev)
-                m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
-                N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
-                th = np.asarray(dq["theta"], dtype=np.float64)
-                last = {}
+        for rule, lin in R11_RULES:
+            for mode, cq, nfit in (("parallel", ctx, 10),
+                                   ("sequential", cseq,
+                                    {100: 10, 1000: 2, 4000: 0}[ns] if lin == 0 else 0)):
+                def make(dq):
+                    yq = torch.tensor(dq["y"][:ns], dtype=f32, device=dev)
+                    m0q = torch.tensor(dq["m0"][None], dtype=f32, device=dev)
+                    N0q = torch.tensor(dq["N0"][None], dtype=f32, device=dev)
+                    th = np.asarray(dq["theta"], dtype=np.float64)
+                    last = {}
 
-                def fg(phi):
-                    t4 = np.array([phi[0], th[1], th[2], th[0]])
-                    nll, g, ch, _, _ = B.sqsm_ipls_nll_grad(cq, t4, yq, [0, ns], m0q, N0q, M, ADJ,
-                                                            dt=dq["dt"])
-                    last["change"] = ch.item()
-                    f, g0 = nll.item(), g[0].item()
-                    if not (np.isfinite(f) and np.isfinite(g0)):
-                        last["nonfinite"] = last.get("nonfinite", 0) + 1
-                    return f, np.array([g0])
-                return fg, last
-            fits = []
-            for dq in trajs[:nfit]:
-                fg, last = make(dq)
-                fg([np.log(R11_START)])   # plan, workspace and graph
-                t0 = time.perf_counter()
-                res = minimize(fg, [np.log(R11_START)], jac=True, method="L-BFGS-B",
-                               bounds=[(np.log(R11_BOUNDS[0]), np.log(R11_BOUNDS[1]))],
-                               options={"maxiter": 50})
-                fits.append({"estimate": float(np.exp(res.x[0])), "evaluations": int(res.nfev),
-                             "seconds": time.perf_counter() - t0, "status": int(res.status),
-                             "adjoint_last_rel_change": last["change"],
-                             "nonfinite_evaluations": last.get("nonfinite", 0)})
-            fg, _ = make(trajs[0])
-            fg([np.log(R11_START)])
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(2):
+                    def fg(phi):
+                        t4 = np.array([phi[0], th[1], th[2], th[0]])
+                        nll, g, ch, _, _ = B.sqsm_ipls_nll_grad(cq, t4, yq, [0, ns], m0q, N0q, M,
+                                                                ADJ, dt=dq["dt"],
+                                                                linearization=lin)
+                        last["change"] = ch.item()
+                        f, g0 = nll.item(), g[0].item()
+                        if not (np.isfinite(f) and np.isfinite(g0)):
+                            last["nonfinite"] = last.get("nonfinite", 0) + 1
+                        return f, np.array([g0])
+                    return fg, last
+                fits = []
+                for dq in trajs[:nfit]:
+                    fg, last = make(dq)
+                    fg([np.log(R11_START)])   # plan, workspace and graph
+                    t0 = time.perf_counter()
+                    res = minimize(fg, [np.log(R11_START)], jac=True, method="L-BFGS-B",
+                                   bounds=[(np.log(R11_BOUNDS[0]), np.log(R11_BOUNDS[1]))],
+                                   options={"maxiter": 50})
+                    fits.append({"estimate": float(np.exp(res.x[0])),
+                                 "evaluations": int(res.nfev),
+                                 "seconds": time.perf_counter() - t0, "status": int(res.status),
+                                 "adjoint_last_rel_change": last["change"],
+                                 "nonfinite_evaluations": last.get("nonfinite", 0)})
+                fg, _ = make(trajs[0])
                 fg([np.log(R11_START)])
-            per_eval = (time.perf_counter() - t0) / 2
-            ent = {"ms_per_evaluation": 1e3 * per_eval, "fits": len(fits)}
-            if fits:
-                est = np.array([f["estimate"] for f in fits])
-                ent.update({"estimate_mean": float(est.mean()), "estimate_std": float(est.std()),
-                            "seconds_per_fit_mean": float(np.mean([f["seconds"] for f in fits])),
-                            "evaluations_mean": float(np.mean([f["evaluations"] for f in fits])),
-                            "status": [f["status"] for f in fits],
-                            "max_adjoint_rel_change": max(f["adjoint_last_rel_change"]
-                                                          for f in fits),
-                            "nonfinite_evaluations": sum(f["nonfinite_evaluations"]
-                                                         for f in fits)})
-            row[mode] = ent
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(2):
+                    fg([np.log(R11_START)])
+                per_eval = (time.perf_counter() - t0) / 2
+                ent = {"ms_per_evaluation": 1e3 * per_eval, "fits": len(fits)}
+                if fits:
+                    est = np.array([f["estimate"] for f in fits])
+                    ent.update({"estimate_mean": float(est.mean()),
+                                "estimate_std": float(est.std()),
+                                "seconds_per_fit_mean": float(np.mean([f["seconds"]
+                                                                       for f in fits])),
+                                "evaluations_mean": float(np.mean([f["evaluations"]
+                                                                   for f in fits])),
+                                "status": [f["status"] for f in fits],
+                                "max_adjoint_rel_change": max(f["adjoint_last_rel_change"]
+                                                              for f in fits),
+                                "nonfinite_evaluations": sum(f["nonfinite_evaluations"]
+                                                             for f in fits)})
+                row[f"{rule}_{mode}"] = ent
         cseq.close()
         out["by_n"][str(ns)] = row
     return out

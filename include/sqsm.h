@@ -298,8 +298,10 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
  * and returns grad = d nll/d theta + (dKS/d theta)^T lambda.  The adjoint
  * pass is hand-written: reverse recurrences of the smoother and the filter
  * (as parallel scans), the Cholesky adjoint of the smoother factors and the
- * adjoint of the cubature regression.  Only SQSM_CUBATURE is supported
- * (SQSM_ERR_UNSUPPORTED otherwise).
+ * adjoint of the linearisation -- any sqsm_linearization: the sigma-point
+ * regressions (cubature, unscented, Gauss-Hermite) through every point,
+ * the Taylor linearisation through the second derivatives of the model
+ * functions (Sec. 4.2, 4.3).
  *
  *   adj_iters   adjoint iterations (>= 0); always all of them (a fixed
  *               amount of work per evaluation, replayable as one graph).

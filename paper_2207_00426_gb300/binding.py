@@ -394,8 +394,8 @@ def sqsm_ct_linearize(ctx, theta, y, offsets, ms, Ns, linearization=CUBATURE, dt
 
 def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, sensors=None,
                        init_ms=None, init_Ns=None, ms=None, Ns=None, nll=None, grad=None,
-                       change=None, tol=0.0, ipls_change=None):
-    """Call sqsm_ipls_nll_grad (cubature).  Returns (nll, grad, change, ms,
+                       change=None, tol=0.0, ipls_change=None, linearization=CUBATURE):
+    """Call sqsm_ipls_nll_grad (any SLR rule).  Returns (nll, grad, change, ms,
     Ns) as device tensors (nll [1], grad [len(theta)], change [1] float64).
     tol > 0 sets ERR_NOT_CONVERGED in the status word when a fixed point has
     not settled; ipls_change (float64 [1], optional) receives the relative
@@ -417,7 +417,8 @@ def sqsm_ipls_nll_grad(ctx, theta, y, offsets, m0, N0, M, adj_iters, dt=0.01, se
     change = torch.empty(1, dtype=f64, device=dev) if change is None else change
     mdl, th = _ct_model(theta, dt, sensors)
     grad = torch.empty(len(th), dtype=f64, device=dev) if grad is None else grad
-    rc = lib.sqsm_ipls_nll_grad(ctx.h, code, ctypes.byref(mdl), th, CUBATURE, int(M), int(adj_iters),
+    rc = lib.sqsm_ipls_nll_grad(ctx.h, code, ctypes.byref(mdl), th, int(linearization), int(M),
+                                int(adj_iters),
                                 float(tol), batch, off, _ptr(y, dtp, "y"), _ptr(m0, dtp, "m0"),
                                 _ptr(N0, dtp, "N0"), _ptr(init_ms, dtp, "init_ms"),
                                 _ptr(init_Ns, dtp, "init_Ns"), _ptr(ms, dtp, "ms"),

@@ -63,8 +63,9 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   cudaMemcpyAsync(g.nom_N, a.Ns, sizeof(T) * NX * NX * rows, cudaMemcpyDeviceToDevice, s);
   const RowsSplit<T, NX> nom{(T*)g.nom_m, (T*)g.nom_N}, fo{(T*)a.mf, (T*)a.Nf},
       so{(T*)g.ms2, (T*)g.Ns2};
-  launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, 0, Lf.lv[0], a.leaf, sq,
-                         (const CTParams<T>*)a.params, 0, nom, (const T*)a.y, (T*)a.F, (T*)nullptr,
+  launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), s, a.linearization, Lf.lv[0],
+                         a.leaf, sq, (const CTParams<T>*)a.params, 0, nom, (const T*)a.y, (T*)a.F,
+                         (T*)nullptr,
                          (T*)nullptr, (T*)nullptr, (T*)nullptr, (T*)nullptr);
   const GammaPacked<T> gv{(T*)a.F};
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.m0, (const T*)a.N0, fo,
@@ -84,7 +85,7 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
   AdjBufs ab{a.mf, a.Nf, g.ms2, g.Ns2, g.nom_m, g.nom_N, a.y, a.F,
              g.dir, g.dfilt, g.gbar, g.ktab, g.rtab, g.stab};
   adj_tables_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-      Lf.lv[0], a.leaf, (const CTParams<T>*)a.params, ab);
+      Lf.lv[0], a.leaf, (const CTParams<T>*)a.params, ab, a.linearization == 0);
   // 4. fixed-point iterations of the adjoint (NLL = -l, so lbar = -1)
   const T lbar = T(-1);
   T* lam_a = (T*)g.lam_a;
@@ -123,8 +124,26 @@ void adj_enqueue(const IplsArgs& a, const AdjArgs& g, const LevelSet& Lf, const 
         Lf.lv[0], a.leaf, per_step, sq, ab, lbar, (const T*)Wa.carry[1], Wa.flag[1]);
     // SLR adjoint -> next cotangent of the nominal trajectory (and its direct
     // cotangents for the next iteration), theta partials
-    adj_slr_kernel<T><<<slr_blocks, kBlock, 0, s>>>(
-        Ls.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, ab, lam_b, g.th_partial);
+    {
+      const CTParams<T>* Pp = (const CTParams<T>*)a.params;
+      switch (a.linearization) {
+        case 1:
+          adj_slr_kernel<T, 1><<<slr_blocks, kBlock, 0, s>>>(Ls.lv[0], a.leaf, sq, Pp, ab, lam_b,
+                                                              g.th_partial);
+          break;
+        case 2:
+          adj_slr_kernel<T, 2><<<slr_blocks, kBlock, 0, s>>>(Ls.lv[0], a.leaf, sq, Pp, ab, lam_b,
+                                                              g.th_partial);
+          break;
+        case 3:
+          adj_slr_kernel<T, 3><<<slr_blocks, kBlock, 0, s>>>(Ls.lv[0], a.leaf, sq, Pp, ab, lam_b,
+                                                              g.th_partial);
+          break;
+        default:
+          adj_slr_kernel<T, 0><<<slr_blocks, kBlock, 0, s>>>(Ls.lv[0], a.leaf, sq, Pp, ab, lam_b,
+                                                              g.th_partial);
+      }
+    }
     if (it + 1 == g.iters)   // the last iteration's change of lambda (words 0, 1)
       adj_change_partial<T><<<change_blocks, 256, 0, s>>>(X * rows, lam_b, lam_a, words);
     T* t = lam_a;

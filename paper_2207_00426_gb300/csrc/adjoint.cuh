@@ -614,6 +614,152 @@ SQSM_DEV void cubature_vjp(const T* m, const T* N, const T* G, const T* sres, co
   }
 }
 
+// VJP of a sigma-point regression with points X_p = m + N xi_p and weights
+// w_p (sum w = 1, sum w xi = 0, sum w xi xi^T = I): the unscented rule
+// (RULE 1: centre weight 1/6, pairs +-sqrt(6) e_i of weight 1/12) or the
+// tensor-product three-point Gauss-Hermite rule (RULE 2: 243 points).  With
+// the forward quantities D = sum w Dl_p xi_p^T (G = D N^{-1}, + I with
+// ADD_I), residuals r_p = Dl_p - Dl_bar - D xi_p (Dl_p the point differences
+// of DG, as in the forward kernel) and Lambda = Sc Sc^T + sum w r_p r_p^T,
+// the cotangent of Z_p = f(X_p) is
+//   Zb_p = w_p (Db xi_p + 2 Lb r_p + ob),  Db = (Gb - ob m^T) N^{-T},
+// (the G and z_bar dependence of Lambda has zero derivative: sum w r = 0
+// and sum w r xi^T = 0 at the regression), and it reaches (m, N) through
+// X_p (J = JAC at X_p) and through G = D N^{-1} (Nb -= G^T Db) and the
+// offset z_bar - G m (mb -= G^T ob).  Two passes over the points: the first
+// rebuilds D and Dl_bar, the second the residuals and cotangents.
+template <typename T, int NO, int RULE, bool ADD_I, typename DG, typename JAC>
+SQSM_DEV void sigma_vjp(const T* m, const T* N, DG dg, JAC jac, const T* Gb, const T* ob,
+                        const T* Lb, T* mb, T* Nb) {
+  constexpr int NX = 5;
+  constexpr int NP = RULE == 1 ? 2 * NX + 1 : 243;
+  // point p: unit point xi and weight
+  auto point = [&](int p, T* xi) -> T {
+    if constexpr (RULE == 1) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) xi[k] = T(0);
+      if (p == 0) return T(1.0 / 6.0);
+      const int i = (p - 1) % NX;
+      xi[i] = (p <= NX ? T(1) : T(-1)) * sq_sqrt(T(6));
+      return T(1.0 / 12.0);
+    } else {
+      const T r3 = sq_sqrt(T(3));
+      T w = T(1);
+      int q = p;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const int dgt = q % 3;
+        q /= 3;
+        xi[k] = dgt == 0 ? T(0) : (dgt == 1 ? r3 : -r3);
+        w *= dgt == 0 ? T(2.0 / 3.0) : T(1.0 / 6.0);
+      }
+      return w;
+    }
+  };
+  auto delta = [&](const T* xi, T* dl) {
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = T(0);
+#pragma unroll
+      for (int k = 0; k <= r; ++k) a += N[r * NX + k] * xi[k];
+      dl[r] = a;
+    }
+  };
+  T D[NO * NX], dbar[NO];
+#pragma unroll
+  for (int i = 0; i < NO * NX; ++i) D[i] = T(0);
+#pragma unroll
+  for (int r = 0; r < NO; ++r) dbar[r] = T(0);
+#pragma unroll 1
+  for (int p = 0; p < NP; ++p) {
+    T xi[NX], dl[NX], z[NO];
+    const T w = point(p, xi);
+    delta(xi, dl);
+    dg(m, dl, z);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      dbar[r] += w * z[r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) D[r * NX + k] += w * z[r] * xi[k];
+    }
+  }
+  T G[NO * NX];
+#pragma unroll
+  for (int i = 0; i < NO * NX; ++i) G[i] = D[i];
+  rsolve<T, NO, NX>(G, N);
+  if constexpr (ADD_I) {
+#pragma unroll
+    for (int r = 0; r < NO; ++r) G[r * NX + r] += T(1);
+  }
+  // offset and regression-matrix parts
+  T Db[NO * NX];
+#pragma unroll
+  for (int r = 0; r < NO; ++r)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Db[r * NX + j] = Gb[r * NX + j] - ob[r] * m[j];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T a = T(0);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) a += G[r * NX + j] * ob[r];
+    mb[j] -= a;
+  }
+  rsolve_t<T, NO, NX>(Db, N);
+  T GtDb[NX * NX];
+  mtm<T, NX, NO, NX>(G, Db, GtDb);
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) Nb[i] -= GtDb[i];
+#pragma unroll 1
+  for (int p = 0; p < NP; ++p) {
+    T xi[NX], dl[NX], z[NO], zb[NO], X[NX], J[NO * NX], xb[NX];
+    const T w = point(p, xi);
+    delta(xi, dl);
+    dg(m, dl, z);
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      T res = z[r] - dbar[r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) res -= D[r * NX + k] * xi[k];
+      z[r] = res;
+    }
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      T a = ob[r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) a += Db[r * NX + k] * xi[k];
+#pragma unroll
+      for (int k = 0; k < NO; ++k) a += T(2) * Lb[r * NO + k] * z[k];
+      zb[r] = w * a;
+    }
+#pragma unroll
+    for (int j = 0; j < NX; ++j) X[j] = m[j] + dl[j];
+    jac(X, J);
+    mtv<T, NO, NX>(J, zb, xb);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      mb[j] += xb[j];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) Nb[j * NX + k] += xb[j] * xi[k];
+    }
+  }
+}
+
+// VJP of the Taylor linearisation (Sec. 4.2) of one function about m:
+// G = J(m), offset z(m) - J(m) m (absolute form), noise factor independent
+// of m.  The offset's z(m) and -J m parts cancel in m, leaving
+//   mb += sum_ij (Gb - ob m^T)_ij dJ_ij/dm  (HJVP: the second derivatives
+// of the function contracted with a Jacobian cotangent).
+template <typename T, int NO, typename HJVP>
+SQSM_DEV void taylor_vjp(const T* m, const T* Gb, const T* ob, HJVP hjvp, T* mb) {
+  constexpr int NX = 5;
+  T Jb[NO * NX];
+#pragma unroll
+  for (int r = 0; r < NO; ++r)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) Jb[r * NX + j] = Gb[r * NX + j] - ob[r] * m[j];
+  hjvp(m, Jb, mb);
+}
+
 // Forward quantities of the cubature regression needed by its VJP: G and
 // the residual columns s_i, from the same difference formulas as the
 // forward kernel.

@@ -36,7 +36,8 @@ SQSM_DEV GammaPacked<T> gview(const AdjBufs& a) {
 // and smoother output, and the nominal trajectory.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-adj_tables_kernel(DevLevel lv, int leaf, const CTParams<T>* __restrict__ Pp, AdjBufs a) {
+adj_tables_kernel(DevLevel lv, int leaf, const CTParams<T>* __restrict__ Pp, AdjBufs a,
+                  bool slr_tab) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ch = tid / leaf;
   if (ch >= lv.n_chunks) return;
@@ -61,6 +62,7 @@ adj_tables_kernel(DevLevel lv, int leaf, const CTParams<T>* __restrict__ Pp, Adj
     vstore<T, KT::size>((T*)a.ktab + s * KT::size, kt);
     vstore<T, RT::size>((T*)a.rtab + s * RT::size, rt);
   }
+  if (!slr_tab) return;   // the other rules' VJPs recompute their regressions
   const CTParams<T> P = *Pp;
   T st[ST::size];
 #pragma unroll
@@ -429,7 +431,9 @@ adj_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items
 // step k - 1 (k >= 1), the row's theta partials added to th, and the direct
 // cotangents of the row that the next iteration starts from (step 1 applied
 // to lam); the regressions' forward quantities come from the SlrTab records.
-template <typename T>
+// LIN: 0 cubature (forward quantities from the SlrTab records), 1 Taylor,
+// 2 unscented, 3 Gauss-Hermite (recomputed from the nominal rows).
+template <typename T, int LIN = 0>
 SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>* __restrict__ Pp,
                           const AdjBufs& a, T* __restrict__ lam_out, double* th) {
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
@@ -448,15 +452,25 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
   if (k < nb) {
     const int64_t s = sq.offsets[b] + k;
     const T* gb = (const T*)a.gbar + s * GR::size;
-    T t[ST::obs];
-    vload<T, ST::obs>((const T*)a.stab + s * ST::size, t);
     T Lb[NX * NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i)
 #pragma unroll
       for (int q = 0; q < NX; ++q) Lb[i * NX + q] = T(0.5) * (gb[GR::L + i * NX + q] + gb[GR::L + q * NX + i]);
-    cubature_vjp<T, NX>(m, N, t + ST::Gf, t + ST::sf, gb + GR::F, gb + GR::c, Lb,
-                        [&](const T* xx, T* J) { ct_jac_f(P, xx, J); }, mb, Nb);
+    auto jf = [&](const T* xx, T* J) { ct_jac_f(P, xx, J); };
+    if constexpr (LIN == 0) {
+      T t[ST::obs];
+      vload<T, ST::obs>((const T*)a.stab + s * ST::size, t);
+      cubature_vjp<T, NX>(m, N, t + ST::Gf, t + ST::sf, gb + GR::F, gb + GR::c, Lb, jf, mb, Nb);
+    } else if constexpr (LIN == 1) {
+      taylor_vjp<T, NX>(m, gb + GR::F, gb + GR::c,
+                        [&](const T* xx, const T* Jb, T* o) { ct_jac_f_vjp(P, xx, Jb, o); }, mb);
+    } else {
+      const Turn<T> tm = turn(m[4], P.dt);
+      sigma_vjp<T, NX, LIN == 2 ? 1 : 2, true>(
+          m, N, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); }, jf,
+          gb + GR::F, gb + GR::c, Lb, mb, Nb);
+    }
     // Q = q_c Q_c + q_w Q_w (Q_w only at (4, 4)): d/d log q_c = Lambda-bar :
     // (Q - Q_44 e_4 e_4^T), d/d log q_w = Lambda-bar_44 Q_44
     T Q[NX * NX];
@@ -471,15 +485,25 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
   if (k >= 1) {
     const int64_t s = sq.offsets[b] + k - 1;
     const T* gb = (const T*)a.gbar + s * GR::size;
-    T t[ST::size - ST::obs];
-    vload<T, ST::size - ST::obs>((const T*)a.stab + s * ST::size + ST::obs, t);
     T Lb[NY * NY];
 #pragma unroll
     for (int i = 0; i < NY; ++i)
 #pragma unroll
       for (int q = 0; q < NY; ++q) Lb[i * NY + q] = T(0.5) * (gb[GR::O + i * NY + q] + gb[GR::O + q * NY + i]);
-    cubature_vjp<T, NY>(m, N, t + ST::Gh - ST::obs, t + ST::sh - ST::obs, gb + GR::H, gb + GR::d, Lb,
-                        [&](const T* xx, T* J) { ct_jac_h(P, xx, J); }, mb, Nb);
+    auto jh = [&](const T* xx, T* J) { ct_jac_h(P, xx, J); };
+    if constexpr (LIN == 0) {
+      T t[ST::size - ST::obs];
+      vload<T, ST::size - ST::obs>((const T*)a.stab + s * ST::size + ST::obs, t);
+      cubature_vjp<T, NY>(m, N, t + ST::Gh - ST::obs, t + ST::sh - ST::obs, gb + GR::H, gb + GR::d,
+                          Lb, jh, mb, Nb);
+    } else if constexpr (LIN == 1) {
+      taylor_vjp<T, NY>(m, gb + GR::H, gb + GR::d,
+                        [&](const T* xx, const T* Jb, T* o) { ct_jac_h_vjp(P, xx, Jb, o); }, mb);
+    } else {
+      sigma_vjp<T, NY, LIN == 2 ? 1 : 2, false>(
+          m, N, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); }, jh,
+          gb + GR::H, gb + GR::d, Lb, mb, Nb);
+    }
     // Omega = diag(sigma_1^2, sigma_2^2): d/d log sigma_i = 2 sigma_i^2 Omega-bar_ii
     th[0] += 2.0 * (double)P.sigma[0] * (double)P.sigma[0] * (double)Lb[0];
     th[3] += 2.0 * (double)P.sigma[1] * (double)P.sigma[1] * (double)Lb[3];
@@ -526,7 +550,7 @@ SQSM_DEV void block_sum4(double* v, double* __restrict__ out) {
 // thread of the block takes part in the block's theta sums (rows past the
 // end add zero), written to th_partial[4 * block]: log sigma_1, log q_c,
 // log q_w, log sigma_2.
-template <typename T>
+template <typename T, int LIN = 0>
 __global__ void __launch_bounds__(kBlock)
 adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
                T* __restrict__ lam_out, double* __restrict__ th_partial) {
@@ -535,7 +559,7 @@ adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
   const int jr = (int)(tid - ch * leaf);
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (ch < lv.n_chunks && jr < lv.count[ch])
-    adj_slr_row<T>(lv.first[ch] + jr, lv.seq[ch], sq, Pp, a, lam_out, th);
+    adj_slr_row<T, LIN>(lv.first[ch] + jr, lv.seq[ch], sq, Pp, a, lam_out, th);
   block_sum4(th, th_partial + 4 * blockIdx.x);
 }
 

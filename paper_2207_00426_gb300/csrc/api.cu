@@ -1134,8 +1134,8 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
     return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
   if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
   if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization != SQSM_CUBATURE)
-    return fail(ctx, SQSM_ERR_UNSUPPORTED, "the gradient is implemented for cubature SLR only");
+  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
   if (M < 0 || adj_iters < 0) return fail(ctx, SQSM_ERR_INVALID_ARG, "M, adj_iters must be >= 0");
   if (std::isnan(tol)) return fail(ctx, SQSM_ERR_INVALID_ARG, "tol is NaN");
   if (M == 0 && (!init_ms || !init_Ns))

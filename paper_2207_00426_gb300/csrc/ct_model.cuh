@@ -228,6 +228,71 @@ SQSM_DEV void ct_jac_f(const CTParams<T>& P, const T* x, T* J) {
   for (int i = 0; i < 25; ++i) J[i] = r[i];
 }
 
+// Second derivatives of the turn coefficients in w: d2S/dw2 = dt^3 u''(a)
+// with u(a) = sin(a)/a and d2C/dw2 = dt^3 v''(a) with v(a) = (1 - cos a)/a
+// (a = w dt): series for |a| < 0.1, closed forms otherwise.
+template <typename T>
+SQSM_DEV void turn_coeff_derivs2(T w, T dt, T& d2S, T& d2C) {
+  const T a = w * dt;
+  T u2, v2;
+  if (fabs(a) < T(0.1)) {
+    const T a2 = a * a;
+    u2 = T(-1) / T(3) + a2 * (T(1) / T(10) + a2 * (T(-1) / T(168) + a2 / T(6480)));
+    v2 = a * (T(-1) / T(4) + a2 * (T(1) / T(36) + a2 * (T(-1) / T(960) + a2 / T(50400))));
+  } else {
+    T sh, ch;
+    sq_sincos(T(0.5) * a, &sh, &ch);
+    const T sa = T(2) * sh * ch, omc = T(2) * sh * sh, ca = T(1) - omc;
+    const T a3 = a * a * a;
+    u2 = (-a * a * sa - T(2) * a * ca + T(2) * sa) / a3;
+    v2 = (a * a * ca - T(2) * a * sa + T(2) * omc) / a3;
+  }
+  d2S = dt * dt * dt * u2;
+  d2C = dt * dt * dt * v2;
+}
+
+// Contraction of the second derivatives of f with a cotangent of its
+// Jacobian: out_k += sum_ij Jb_ij d J_ij / d x_k, J = ct_jac_f (the
+// derivative of the Taylor linearisation F = J(m) in m, Sec. 4.2).
+template <typename T>
+SQSM_DEV void ct_jac_f_vjp(const CTParams<T>& P, const T* x, const T* Jb, T* out) {
+  T S, C, ca, sa, dS, dC, d2S, d2C;
+  const T dt = P.dt;
+  turn_coeffs(x[4], dt, S, C, ca, sa);
+  turn_coeff_derivs(x[4], dt, dS, dC);
+  turn_coeff_derivs2(x[4], dt, d2S, d2C);
+  const T vx = x[2], vy = x[3];
+  // d/dvx, d/dvy: only the omega column depends on v
+  out[2] += Jb[0 * 5 + 4] * dS + Jb[1 * 5 + 4] * dC + Jb[2 * 5 + 4] * (-dt * sa) +
+            Jb[3 * 5 + 4] * (dt * ca);
+  out[3] += Jb[0 * 5 + 4] * (-dC) + Jb[1 * 5 + 4] * dS + Jb[2 * 5 + 4] * (-dt * ca) +
+            Jb[3 * 5 + 4] * (-dt * sa);
+  // d/dw of every omega-dependent entry (d ca/dw = -dt sa, d sa/dw = dt ca)
+  const T dt2 = dt * dt;
+  out[4] += Jb[0 * 5 + 2] * dS + Jb[0 * 5 + 3] * (-dC) + Jb[0 * 5 + 4] * (vx * d2S - vy * d2C) +
+            Jb[1 * 5 + 2] * dC + Jb[1 * 5 + 3] * dS + Jb[1 * 5 + 4] * (vx * d2C + vy * d2S) +
+            Jb[2 * 5 + 2] * (-dt * sa) + Jb[2 * 5 + 3] * (-dt * ca) +
+            Jb[2 * 5 + 4] * (-dt2 * ca * vx + dt2 * sa * vy) +
+            Jb[3 * 5 + 2] * (dt * ca) + Jb[3 * 5 + 3] * (-dt * sa) +
+            Jb[3 * 5 + 4] * (-dt2 * sa * vx - dt2 * ca * vy);
+}
+
+// The same for the bearings: J_h row j = (-dy, dx, 0, 0, 0) / r^2 with
+// (dx, dy) = p - s_j, whose derivatives in (p_x, p_y) are
+// [[2 dx dy, dy^2 - dx^2], [dy^2 - dx^2, -2 dx dy]] / r^4.
+template <typename T>
+SQSM_DEV void ct_jac_h_vjp(const CTParams<T>& P, const T* x, const T* Jb, T* out) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T dx = x[0] - P.sx[j], dy = x[1] - P.sy[j];
+    const T r2 = dx * dx + dy * dy;
+    const T i4 = T(1) / (r2 * r2);
+    const T a = Jb[j * 5 + 0], b = Jb[j * 5 + 1];
+    out[0] += (a * T(2) * dx * dy + b * (dy * dy - dx * dx)) * i4;
+    out[1] += (a * (dy * dy - dx * dx) - b * T(2) * dx * dy) * i4;
+  }
+}
+
 template <typename T>
 SQSM_DEV void ct_h(const CTParams<T>& P, const T* x, T* o) {
 #pragma unroll

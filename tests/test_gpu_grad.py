@@ -104,7 +104,7 @@ def test_autograd_function(B, ctx):
     np.testing.assert_allclose(theta.grad.numpy(), 3.0 * rg, rtol=1e-6, atol=1e-9)
 
 
-def test_extended_is_rejected(B, ctx):
+def test_unknown_linearization_is_rejected(B, ctx):
     d = W.ct_sequence(n=10, seed=44)
     dt = torch.float64
     import ctypes
@@ -112,9 +112,57 @@ def test_extended_is_rejected(B, ctx):
     off, batch = B._offsets([0, 10])
     z = torch.zeros(64, dtype=dt, device="cuda:0")
     p = z.data_ptr()
-    rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, B.EXTENDED, 5, 5, 0.0, batch,
+    rc = B.lib.sqsm_ipls_nll_grad(ctx.h, 1, ctypes.byref(mdl), th, 7, 5, 5, 0.0, batch,
                                   off, p, p, p, None, None, p, p, p, p, None, None, None)
-    assert rc == B.ERR_UNSUPPORTED
+    assert rc == B.ERR_INVALID_ARG
+
+
+RULES = {"extended": 1, "unscented": 2, "gauss-hermite": 3}
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-6), ("f32", 1e-3)])
+@pytest.mark.parametrize("method", ["extended", "unscented", "gauss-hermite"])
+def test_gradient_other_rules_match_oracle_fd(B, ctx, prec, tol, method):
+    """The adjoint of the Taylor linearisation (second derivatives of the CT
+    transition and bearings contracted with the Jacobian cotangents) and of
+    the unscented and Gauss-Hermite regressions (every sigma point's
+    cotangent, two passes over the points) against the oracle's central
+    differences of the converged pseudo log-likelihood with the same rule
+    (Sec. 5.2 for the linearisations of Secs. 4.2, 4.3; the paper's
+    sqrt(R_11) study uses all four)."""
+    n = 40
+    d = W.ct_sequence(n=n, seed=61)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    theta = THETA + np.array([0.2, -0.3, 0.25])
+    nll, grad, change, _, _ = B.sqsm_ipls_nll_grad(
+        ctx, theta, _dev(d["y"], dt), [0, n], _dev(d["m0"][None], dt), _dev(d["N0"][None], dt),
+        M=40, adj_iters=40, dt=d["dt"], linearization=RULES[method])
+    torch.cuda.synchronize()
+    rnll = O.nll(OM.CTBearings, theta, d["y"], d["m0"], d["N0"], method, tol=1e-13, dt=d["dt"])
+    rg = O.nll_grad_fd(OM.CTBearings, theta, d["y"], d["m0"], d["N0"], method, h=1e-5, tol=1e-13,
+                       dt=d["dt"])
+    g = grad.cpu().numpy()
+    assert abs(nll.item() - rnll) <= (1e-9 if prec == "f64" else 1e-5) * abs(rnll)
+    assert np.linalg.norm(g - rg) <= tol * np.linalg.norm(rg), (g, rg)
+    assert change.item() < (1e-8 if prec == "f64" else 1e-3)
+
+
+def test_gradient_matches_oracle_forward_mode(B, ctx):
+    """Cubature gradient (FP64) against the oracle's second route, forward
+    mode through the fixed point (oracle/forward.py)."""
+    from oracle import forward as OF
+    n = 25
+    d = W.ct_sequence(n=n, seed=62)
+    theta = THETA + np.array([-0.1, 0.2, -0.15])
+    f64 = torch.float64
+    nll, grad, _, _, _ = B.sqsm_ipls_nll_grad(ctx, theta, _dev(d["y"], f64), [0, n],
+                                              _dev(d["m0"][None], f64), _dev(d["N0"][None], f64),
+                                              M=60, adj_iters=60, dt=d["dt"])
+    torch.cuda.synchronize()
+    rnll, rg, _ = OF.nll_grad_forward(OM.CTBearings(theta, dt=d["dt"]), d["y"], d["m0"], d["N0"])
+    g = grad.cpu().numpy()
+    assert abs(nll.item() - rnll) <= 1e-9 * abs(rnll)
+    assert np.linalg.norm(g - rg) <= 1e-8 * np.linalg.norm(rg), (g, rg)
 
 
 THETA_R = np.r_[np.log(0.03), THETA[1:], np.log(0.08)]
