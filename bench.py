@@ -513,8 +513,12 @@ def gpu_arm(args, rank, world, local):
     Ns64 = torch.empty((n + 1, 5, 5), dtype=f64, device=dev)
     ll64 = torch.empty(1, dtype=f64, device=dev)
 
+    # the unrefined mode: FP64 takes no refinement pass (its scans' error is
+    # already far below the targets), and the fast FP32 mode below
+    fctx = B.Context(local, use_graph=True, refine=0)
+
     def step64():
-        B.sqsm_ipls_smooth(ctx, d["theta"], y64, [0, n], m064, N064, M, B.CUBATURE, dt=d["dt"],
+        B.sqsm_ipls_smooth(fctx, d["theta"], y64, [0, n], m064, N064, M, B.CUBATURE, dt=d["dt"],
                            ms=ms64, Ns=Ns64, loglik=ll64)
     step64()
     torch.cuda.synchronize()
@@ -525,8 +529,6 @@ def gpu_arm(args, rank, world, local):
     ll_rel = abs(ll.item() - ll64.item()) / abs(ll64.item())
     ll_head = ll.item()
     # the unrefined FP32 mode: time and error against the same FP64 run
-    fctx = B.Context(local, use_graph=True, refine=0)
-
     def fstep():
         B.sqsm_ipls_smooth(fctx, d["theta"], y, [0, n], m0, N0, M, B.CUBATURE, dt=d["dt"],
                            ms=ms, Ns=Ns, loglik=ll)
@@ -537,14 +539,14 @@ def gpu_arm(args, rank, world, local):
             "f32_vs_f64_mean_rel_err": float((ms.double() - ms64).norm(dim=1).max()
                                              / ms64.norm(dim=1).max()),
             "f32_vs_f64_loglik_rel_err": abs(ll.item() - ll64.item()) / abs(ll64.item())}
-    fctx.close()
 
     studies = None
     if args.studies:
-        studies = run_studies(B, torch, ctx, local, dev, M, peak, timed)
+        studies = run_studies(B, torch, fctx, ctx, local, dev, M, peak, timed)
         os.makedirs(os.path.dirname(os.path.abspath(args.studies_out)), exist_ok=True)
         with open(args.studies_out, "w") as f:
             json.dump(studies, f, indent=1)
+    fctx.close()
 
     line = None
     if rank == 0:
@@ -593,26 +595,31 @@ def converged_nll_grad(B, torch, ctx, dev, timed):
     yk, m0k, N0k = T(yk, f32), T(dc["m0"][keep], f32), T(dc["N0"][keep], f32)
     offk = [L * i for i in range(51)]
     out = {}
+    ich = torch.zeros(1, dtype=f64, device=dev)
 
     def ev():
         out["r"] = B.sqsm_ipls_nll_grad(ctx, dc["theta"], yk, offk, m0k, N0k, 30, 40, dt=dc["dt"],
-                                        tol=1e-3)
+                                        tol=1e-3, ipls_change=ich)
+    ctx.status()  # clear what the context's earlier calls left in the word
     ev()
     torch.cuda.synchronize()
-    settled = ctx.status() == 0
+    st_first = ctx.status()
     t = timed(ev, 3)
     torch.cuda.synchronize()
-    settled = settled and ctx.status() == 0
+    st_timed = ctx.status()
     return {"evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t, "M": 30, "adjoint_iterations": 40,
-            "fixed_point_reached": bool(settled), "grad": out["r"][1].cpu().tolist(),
-            "adjoint_last_rel_change": out["r"][2].item()}
+            "fixed_point_reached": st_first == 0 and st_timed == 0,
+            "status": [st_first, st_timed], "grad": out["r"][1].cpu().tolist(),
+            "adjoint_last_rel_change": out["r"][2].item(), "ipls_last_rel_change": ich.item()}
 
 
-def run_studies(B, torch, ctx, local, dev, M, peak, timed):
+def run_studies(B, torch, ctx, rctx, local, dev, M, peak, timed):
     """The paper's further experiments on the GPU (returned as one dict):
     the SLR rules at n = 1e5, sequential against parallel, the population
     model, the sqrt(R_11) study, the length sweep and the FP32 robustness
-    experiment."""
+    experiment.  ctx is the unrefined context (the method as the paper
+    states it; every study runs on it), rctx the benchmark's refined one
+    (a column of the sweep)."""
     from paper_2207_00426_gb300 import costmodel as CM
     from paper_2207_00426_gb300 import workloads as W
     f32 = torch.float32
@@ -693,22 +700,24 @@ def run_studies(B, torch, ctx, local, dev, M, peak, timed):
         ns = 1 << lg
         ds = W.ct_sequence(n=ns, seed=2 + lg)
         row = {}
-        for name, dtp, lin in (("f32_cubature", torch.float32, B.CUBATURE),
-                               ("f32_extended", torch.float32, B.EXTENDED),
-                               ("f64_cubature", torch.float64, B.CUBATURE)):
+        for name, dtp, lin, cs, rf in (("f32_cubature", torch.float32, B.CUBATURE, ctx, 0),
+                                       ("f32_cubature_refined", torch.float32, B.CUBATURE, rctx, 1),
+                                       ("f32_extended", torch.float32, B.EXTENDED, ctx, 0),
+                                       ("f64_cubature", torch.float64, B.CUBATURE, ctx, 0)):
             ys = torch.tensor(ds["y"], dtype=dtp, device=dev)
             m0s = torch.tensor(ds["m0"][None], dtype=dtp, device=dev)
             N0s = torch.tensor(ds["N0"][None], dtype=dtp, device=dev)
 
-            def sstep():
-                B.sqsm_ipls_smooth(ctx, ds["theta"], ys, [0, ns], m0s, N0s, M, lin, dt=ds["dt"])
+            def sstep(cs=cs):
+                B.sqsm_ipls_smooth(cs, ds["theta"], ys, [0, ns], m0s, N0s, M, lin, dt=ds["dt"])
             sstep()
             torch.cuda.synchronize()
             ts = timed(sstep, 3 if dtp == torch.float32 else 1)
             row[name] = ns * M / ts
-            if name == "f32_cubature":
-                row["f32_cubature_frac_of_fp32_peak"] = (CM.ipls_iteration_flops([ns]) * M / ts
-                                                         / 1e12 / peak)
+            if name.startswith("f32_cubature"):
+                leaf = cs.scan_shape([0, ns])[0]
+                row[name + "_frac_of_fp32_peak"] = (
+                    CM.ipls_iteration_flops([ns], leaf=leaf, refine=rf) * M / ts / 1e12 / peak)
         sweep[str(ns)] = row
     out["sweep"] = {"unit": UNIT, "M": M, "by_n": sweep}
 
@@ -719,6 +728,9 @@ def run_studies(B, torch, ctx, local, dev, M, peak, timed):
     #      absolute coordinates and in the deviation coordinates used here,
     #      with the means' error against the FP64 square-root run (finite runs)
     cabs = B.Context(local, use_graph=True, absolute=True)
+    # the printed form: absolute coordinates and the SLR's sigma-point
+    # deviations formed by subtracting absolute function values
+    ctb = B.Context(local, use_graph=True, absolute=True, textbook_slr=True)
     stability = {}
     noise_sets = {"q_c=0.01,q_w=0.1": W.CT_THETA_TRUE,
                   "q_c=0.1,q_w=0.1": (W.CT_THETA_TRUE[0], float(np.log(0.1)), float(np.log(0.1)))}
@@ -734,7 +746,7 @@ def run_studies(B, torch, ctx, local, dev, M, peak, timed):
         for lin_name, lin in (("cubature", B.CUBATURE), ("extended", B.EXTENDED)):
             ms64, _, _ = B.sqsm_ipls_smooth(ctx, dsb["theta"], t64["y"], offs, t64["m0"],
                                             t64["N0"], 20, lin, dt=dsb["dt"])
-            for coords, c in (("absolute", cabs), ("deviation", ctx)):
+            for coords, c in (("absolute", cabs), ("deviation", ctx), ("textbook", ctb)):
                 for form in ("sqrt", "standard"):
                     if form == "sqrt":
                         msf, _, llf = B.sqsm_ipls_smooth(c, dsb["theta"], t32["y"], offs,
@@ -759,6 +771,7 @@ def run_studies(B, torch, ctx, local, dev, M, peak, timed):
                         "median_mean_rel_err_vs_f64": float(np.median(errs)) if errs else None}
         stability.setdefault(noise, {})[str(ns)] = res
     cabs.close()
+    ctb.close()
     out["stability_f32"] = {"sequences_per_n": 15, "M": 20, "by_noise_and_n": stability}
     return out
 

@@ -160,6 +160,16 @@ typedef struct {
                            from iteration to iteration.  Deviation
                            coordinates only (ignored with absolute).
                            Default 0.                                    */
+  int textbook_slr;     /* 1: the cubature SLR of sqsm_ipls_smooth,
+                           sqsm_ipls_smooth_tol and sqsm_ipls_smooth_std
+                           evaluates each sigma point's function value in
+                           absolute coordinates and subtracts the value at
+                           the mean, as the regression formulas are
+                           printed, instead of the cancellation-free
+                           differences (bearings from atan2 of absolute
+                           positions).  Less accurate in FP32 by design: a
+                           comparator for the robustness experiment of
+                           Sec. 6.  Default 0.                           */
 } sqsm_options;
 
 typedef struct sqsm_ctx sqsm_ctx;

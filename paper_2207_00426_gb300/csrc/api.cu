@@ -634,6 +634,7 @@ IplsArgs ctx_ipls_args(const sqsm_ctx* ctx, const Plan* p, const Workspace* w,
                               loglik);
   a.centered = ctx->opt.absolute ? 0 : 1;
   a.refine = ctx->opt.refine;
+  a.textbook = ctx->opt.textbook_slr ? 1 : 0;
   return a;
 }
 

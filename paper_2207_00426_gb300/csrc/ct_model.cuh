@@ -212,6 +212,22 @@ SQSM_DEV void ct_g_delta(const CTParams<T>& P, const Turn<T>& tm, const T* m, co
   o[4] = T(0);
 }
 
+// The same differences evaluated the way the SLR formulas are printed: the
+// function at the sigma point and at the mean in absolute coordinates, then
+// subtracted (g(m + dl) - g(m) with g(x) = f(x) - x).  Their FP32 rounding
+// is that of the absolute values (positions of size ~100), which the
+// textbook comparator of the robustness experiment keeps on purpose.
+template <typename T>
+SQSM_DEV void ct_g_delta_naive(const CTParams<T>& P, const T* m, const T* dl, T* o) {
+  T xa[5], fa[5], f0[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) xa[r] = m[r] + dl[r];
+  ct_f(P, xa, fa);
+  ct_f(P, m, f0);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) o[r] = (fa[r] - xa[r]) - (f0[r] - m[r]);
+}
+
 template <typename T>
 SQSM_DEV void ct_jac_f(const CTParams<T>& P, const T* x, T* J) {
   T S, C, ca, sa, dS, dC;
@@ -309,6 +325,20 @@ SQSM_DEV void ct_h_delta(const CTParams<T>& P, const T* m, const T* dl, T* o) {
     const T cross = ux * dl[1] - uy * dl[0];
     const T dot = ux * ux + uy * uy + ux * dl[0] + uy * dl[1];
     o[j] = sq_atan2(cross, dot);
+  }
+}
+
+// Bearing of m + dl minus the bearing of m, both from absolute positions
+// (atan2), wrapped into (-pi, pi] (textbook comparator, see above).
+template <typename T>
+SQSM_DEV void ct_h_delta_naive(const CTParams<T>& P, const T* m, const T* dl, T* o) {
+  const T twopi = T(6.283185307179586476925286766559);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T a = sq_atan2(m[1] + dl[1] - P.sy[j], m[0] + dl[0] - P.sx[j]);
+    const T a0 = sq_atan2(m[1] - P.sy[j], m[0] - P.sx[j]);
+    const T d = a - a0;
+    o[j] = d - twopi * sq_floor(d / twopi + T(0.5));
   }
 }
 
@@ -536,7 +566,7 @@ SQSM_DEV void gauss_hermite_regress(const T* m, const T* N, const T* gm, bool su
 // Steps are independent: one thread per step, addressed as (leaf chunk,
 // position in chunk) so that the chunk table gives the sequence; launch
 // n_chunks * leaf threads.
-template <typename T, bool PACKED, typename NO, int LIN>
+template <typename T, bool PACKED, typename NO, int LIN, bool TB = false>
 __global__ void __launch_bounds__(kBlock)
 ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
               int centered, NO nom, const T* __restrict__ y, T* __restrict__ F,
@@ -569,7 +599,10 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
       ct_f(P, m, fm);
     }
     const Turn<T> tm = turn(m[4], P.dt);
-    auto gd = [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); };
+    auto gd = [&](const T* mm_, const T* dl, T* o) {
+      if constexpr (TB) ct_g_delta_naive(P, mm_, dl, o);
+      else ct_g_delta(P, tm, mm_, dl, o);
+    };
     if constexpr (LIN == 0) {
       cubature_regress<T, NX, true>(m, N, fm, !centered, P.SQ, gd, Fm, cm, Sl);
     } else if constexpr (LIN == 2) {
@@ -608,7 +641,10 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
     load<T, NY>(y + s * NY, ys);
     ct_h(P, m, hm);
     const T Sr[NY * NY] = {P.sigma[0], T(0), T(0), P.sigma[1]};
-    auto hd = [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); };
+    auto hd = [&](const T* mm_, const T* dl, T* o) {
+      if constexpr (TB) ct_h_delta_naive(P, mm_, dl, o);
+      else ct_h_delta(P, mm_, dl, o);
+    };
     if constexpr (LIN == 0) {
       cubature_regress<T, NY, false>(m, N, hm, !centered, Sr, hd, Hm, dm, So);
     } else if constexpr (LIN == 2) {
@@ -648,10 +684,18 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
 // ct_slr_kernel_lin for a run-time linearisation (0 cubature, 1 Taylor,
 // 2 unscented, 3 Gauss-Hermite): one instantiation per rule, so that each
 // keeps its own register budget.
+// textbook: the cubature rule with the differences of the printed formulas
+// (ct_g_delta_naive, ct_h_delta_naive) instead of the cancellation-free ones.
 template <typename T, bool PACKED, typename NO>
 void launch_ct_slr(unsigned grid, cudaStream_t s, int linearization, DevLevel lv, int leaf,
                    DevSeqs sq, const CTParams<T>* Pp, int centered, NO nom, const T* y, T* F,
-                   T* c, T* SQo, T* H, T* d, T* SRo) {
+                   T* c, T* SQo, T* H, T* d, T* SRo, int textbook = 0) {
+  if (textbook && linearization == 0) {
+    ct_slr_kernel_lin<T, PACKED, NO, 0, true><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered,
+                                                                       nom, y, F, c, SQo, H, d,
+                                                                       SRo);
+    return;
+  }
   switch (linearization) {
     case 0:
       ct_slr_kernel_lin<T, PACKED, NO, 0><<<grid, kBlock, 0, s>>>(lv, leaf, sq, Pp, centered, nom,

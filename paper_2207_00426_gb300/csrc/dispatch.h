@@ -41,6 +41,7 @@ struct IplsArgs {
   void *frows, *nrows;   // packed filter output and nominal trajectory (RowsPacked)
   Prof* prof;   // optional per-kernel events
   int centered = 1;   // 1: deviation coordinates, 0: printed absolute coordinates
+  int textbook = 0;   // 1: cubature SLR with the printed (naive) differences
   // mixed-precision refinement of each iteration's linear smoother (deviation
   // coordinates only): passes, the nominal rows before the last smoother
   // pass (RowsPacked) and the refinement passes' log-likelihood partials

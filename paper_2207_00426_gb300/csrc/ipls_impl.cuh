@@ -121,7 +121,7 @@ void ipls_phase(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& Wf, co
     launch_ct_slr<T, true>(grid_for(Lf.lv[0].n_chunks * a.leaf), st, a.linearization, Lf.lv[0],
                            a.leaf, sq, (const CTParams<T>*)a.params, a.centered, nom,
                            (const T*)a.y, (T*)a.F, (T*)nullptr, (T*)nullptr, (T*)nullptr,
-                           (T*)nullptr, (T*)nullptr);
+                           (T*)nullptr, (T*)nullptr, a.textbook);
   };
   ipls_phase_model<T, 5, 2>(a, Lf, Wf, Ls, Ws, sq, partial, status, s, phase, dmax, slr);
 }

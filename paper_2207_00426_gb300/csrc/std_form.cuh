@@ -523,7 +523,7 @@ SQSM_DEV void cubature_regress_std(const T* m, const T* N, const T* P, const T* 
 // the nominal rows (m, P), cubature (linearization 0: Sec. 4.1 with sigma
 // points) or Taylor (1: Jacobians, Lambda = Q, Omega = R); centered as in
 // ct_slr_kernel (1: deviation form, 0: the printed absolute form).
-template <typename T, typename NO>
+template <typename T, typename NO, bool TB = false>
 __global__ void __launch_bounds__(kBlock)
 std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, NO nom,
                int linearization, int centered, const T* __restrict__ y, T* __restrict__ gam) {
@@ -557,7 +557,11 @@ std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
     if (linearization == 0) {
       const Turn<T> tm = turn(m[4], P.dt);
       cubature_regress_std<T, NX, true>(
-          m, N, Pc, fm, Qc, [&](const T* mm_, const T* dl, T* o) { ct_g_delta(P, tm, mm_, dl, o); },
+          m, N, Pc, fm, Qc,
+          [&](const T* mm_, const T* dl, T* o) {
+            if constexpr (TB) ct_g_delta_naive(P, mm_, dl, o);
+            else ct_g_delta(P, tm, mm_, dl, o);
+          },
           out.F, out.c, out.SQ);
     } else {
       ct_jac_f(P, m, out.F);
@@ -586,7 +590,11 @@ std_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict_
     const T Rc[NY * NY] = {P.sigma[0] * P.sigma[0], T(0), T(0), P.sigma[1] * P.sigma[1]};
     if (linearization == 0) {
       cubature_regress_std<T, NY, false>(
-          m, N, Pc, hm, Rc, [&](const T* mm_, const T* dl, T* o) { ct_h_delta(P, mm_, dl, o); },
+          m, N, Pc, hm, Rc,
+          [&](const T* mm_, const T* dl, T* o) {
+            if constexpr (TB) ct_h_delta_naive(P, mm_, dl, o);
+            else ct_h_delta(P, mm_, dl, o);
+          },
           out.H, out.d, out.SR);
     } else {
       ct_jac_h(P, m, out.H);
@@ -892,9 +900,14 @@ void std_ipls_enqueue(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   std_broadcast_prior<T, NX><<<grid_for(Ls.lv[0].n_chunks), kBlock, 0, s>>>(
       Ls.lv[0], (const T*)a.m0, P0, nom);
   for (int it = 0; it < a.M; ++it) {
-    std_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
-        Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, nom, a.linearization, a.centered,
-        (const T*)a.y, (T*)a.F);
+    if (a.textbook && a.linearization == 0)
+      std_slr_kernel<T, RowsSym<T, NX>, true><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+          Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, nom, a.linearization, a.centered,
+          (const T*)a.y, (T*)a.F);
+    else
+      std_slr_kernel<T><<<grid_for(Lf.lv[0].n_chunks * a.leaf), kBlock, 0, s>>>(
+          Lf.lv[0], a.leaf, sq, (const CTParams<T>*)a.params, nom, a.linearization, a.centered,
+          (const T*)a.y, (T*)a.F);
     if (a.centered)
       center_prior_kernel<T, NX><<<(sq.B + 127) / 128, 128, 0, s>>>(sq, (const T*)a.m0, nom,
                                                                      (T*)a.dm0);

@@ -122,3 +122,33 @@ def test_absolute_coordinates(B, method):
     cdev.close()
 
 
+def test_textbook_slr_is_the_same_regression(B):
+    """The textbook option (sigma-point deviations formed from absolute
+    function values, the printed formulas) computes the same cubature
+    regression: in FP64 both forms of both smoothers equal the oracle; in
+    FP32 on a short sequence it stays finite and near the FP64 run (its
+    larger error is what the robustness experiment measures)."""
+    d = W.ct_batch(lengths=[50, 23], seed=64)
+    f64, f32 = torch.float64, torch.float32
+    M = 5
+    ctb = B.Context(0, absolute=True, textbook_slr=True)
+    ct = OM.CTBearings(d["theta"], dt=d["dt"])
+    off = d["offsets"]
+    ms_q, _, ll_q = B.sqsm_ipls_smooth(ctb, d["theta"], _dev(d["y"], f64), off, _dev(d["m0"], f64),
+                                       _dev(d["N0"], f64), M, 0, dt=d["dt"])
+    ms_s, _, ll_s = B.sqsm_ipls_smooth_std(ctb, d["theta"], _dev(d["y"], f64), off,
+                                           _dev(d["m0"], f64), _dev(_P0(d), f64), M, 0, dt=d["dt"])
+    ms32, _, ll32 = B.sqsm_ipls_smooth(ctb, d["theta"], _dev(d["y"], f32), off, _dev(d["m0"], f32),
+                                       _dev(d["N0"], f32), M, 0, dt=d["dt"])
+    torch.cuda.synchronize()
+    for b in range(2):
+        yb = d["y"][off[b]:off[b + 1]]
+        rms, _, rll, _ = O.ipls(ct, yb, d["m0"][b], d["N0"][b], M, "cubature")
+        rows = slice(off[b] + b, off[b + 1] + b + 1)
+        for ms in (ms_q, ms_s):
+            assert rel_mean_err(ms[rows].cpu().numpy(), rms) < 1e-9
+        for ll in (ll_q, ll_s):
+            assert abs(ll[b].item() - rll) <= 1e-9 * abs(rll)
+        assert rel_mean_err(ms32[rows].double().cpu().numpy(), rms) < 1e-3
+    assert ctb.status() == 0
+    ctb.close()
