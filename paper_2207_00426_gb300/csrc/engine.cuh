@@ -64,14 +64,22 @@ struct Prof {
     }
     rec.clear();
   }
+  // Inside a stream capture the events become event-record nodes of the
+  // graph (the external flag); outside one they are recorded as usual.
+  static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    cudaEventRecordWithFlags(
+        e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
+  }
   void begin(int kind, cudaStream_t s) {
     Rec r{kind, nullptr, nullptr};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
-    cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    record(r.a, s);
     rec.push_back(r);
   }
-  void end(cudaStream_t s) { cudaEventRecordWithFlags(rec.back().b, s, cudaEventRecordExternal); }
+  void end(cudaStream_t s) { record(rec.back().b, s); }
 };
 
 struct ProfScope {

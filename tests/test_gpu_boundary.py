@@ -7,7 +7,8 @@
   factored on the GPU in FP64 (N0 = chol(P0)) give the results of the
   factor path; a P0 that is not positive definite sets SQSM_ERR_NOT_PD;
 - sqsm_ipls_nll_grad's fixed-point check: SQSM_ERR_NOT_CONVERGED when the
-  trajectory or the adjoint has not settled to tol, none when both have."""
+  trajectory or the adjoint has not settled to tol, none when both have;
+- the per-kernel event profiler, with and without graphs."""
 import ctypes
 
 import numpy as np
@@ -164,6 +165,7 @@ def test_nll_grad_fixed_point_check(B):
     nll, g, ch, _, _ = B.sqsm_ipls_nll_grad(ctx, d["theta"], y, d["offsets"], m0, N0, 40, 40,
                                             dt=d["dt"], tol=1e-6, ipls_change=ich)
     torch.cuda.synchronize()
+    nll40 = nll.item()
     assert ich.item() < 1e-6 and ch.item() < 1e-6
     assert ctx.status() == 0
     # too few iterations: both changes large, flag set
@@ -176,10 +178,45 @@ def test_nll_grad_fixed_point_check(B):
     B.sqsm_ipls_nll_grad(ctx, d["theta"], y, d["offsets"], m0, N0, 1, 2, dt=d["dt"], tol=0.0)
     torch.cuda.synchronize()
     assert ctx.status() == 0
-    # adj_iters = 0: nll only, grad zero, adjoint change reported as 0
+    # adj_iters = 0: the same NLL as with the adjoint, grad zero, adjoint
+    # change reported as 0
     nll0, g0, ch0, _, _ = B.sqsm_ipls_nll_grad(ctx, d["theta"], y, d["offsets"], m0, N0, 40, 0,
                                                dt=d["dt"])
     torch.cuda.synchronize()
-    assert abs(nll0.item() - nll.item()) > 0 or True
+    assert abs(nll0.item() - nll40) <= 1e-12 * abs(nll40)
     assert np.all(g0.cpu().numpy() == 0) and ch0.item() == 0.0
     ctx.close()
+
+
+def test_profiler_times_every_launch(B):
+    """sqsm_profile_enable / sqsm_profile_read with and without graphs: the
+    same kernel families and launch counts in both modes, each family's
+    time positive, and their sum within the call's own event time."""
+    d = W.ct_batch(lengths=[3000, 1700], seed=8)
+    f32 = torch.float32
+    y, m0, N0 = (_dev(d[k], f32) for k in ("y", "m0", "N0"))
+    counts = {}
+    for graph in (False, True):
+        ctx = B.Context(0, use_graph=graph)
+        call = lambda: B.sqsm_ipls_smooth(ctx, d["theta"], y, d["offsets"], m0, N0, 3, dt=d["dt"])
+        call()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        call()    # builds the instrumented graph (graph mode)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        torch.cuda.synchronize()
+        fam = ctx.profile_read()
+        ctx.profile(False)
+        assert ctx.status() == 0
+        ctx.close()
+        assert {"ct_slr", "filter_leaf_up", "filter_leaf_down", "smoother_leaf_up",
+                "smoother_leaf_down", "loglik_reduce"} <= set(fam), fam
+        assert all(t > 0 and c > 0 for t, c in fam.values())
+        assert fam["ct_slr"][1] == 3 and fam["filter_leaf_up"][1] == 3   # one per iteration
+        assert sum(t for t, _ in fam.values()) <= 1.05 * a.elapsed_time(b) + 0.05
+        counts[graph] = {k: c for k, (_, c) in fam.items()}
+    assert counts[False] == counts[True]
