@@ -170,6 +170,21 @@ typedef struct {
                            positions).  Less accurate in FP32 by design: a
                            comparator for the robustness experiment of
                            Sec. 6.  Default 0.                           */
+  int max_group_steps;  /* > 0: sqsm_ipls_nll_grad evaluates a batch whose
+                           total number of time steps exceeds this bound
+                           in groups of consecutive sequences of at most
+                           this many steps each, one group after another
+                           (the sequences are independent, so the NLL and
+                           the gradient are sums over the groups and the
+                           changes maxima), and frees each group's
+                           workspace before the next group's is made: the
+                           call's device memory is then that of one
+                           group, about 3.4 KB per time step in FP32 and
+                           6.6 KB in FP64.  A grouped call runs without
+                           graphs and synchronises the device between
+                           groups; a sequence longer than the bound
+                           returns SQSM_ERR_TOO_LARGE.  0 (default): the
+                           whole batch at once.                          */
 } sqsm_options;
 
 typedef struct sqsm_ctx sqsm_ctx;
@@ -336,6 +351,9 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
  *   ipls_change device double[1] or NULL: max-norm change of the smoothing
  *               means from n* to the smoother of its linearisation (one
  *               more iteration of Alg. 3), relative to their max-norm.
+ * With sqsm_options.max_group_steps a large batch is evaluated in groups of
+ * sequences with a bounded workspace (see there); adj_change and
+ * ipls_change are then the largest over the groups.
  * Other arguments as sqsm_ipls_smooth. */
 int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model,
                        const double* theta, int linearization, int M,

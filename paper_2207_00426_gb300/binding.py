@@ -42,7 +42,7 @@ _int = ctypes.c_int
 class Options(ctypes.Structure):
     _fields_ = [("leaf_chunk", _int), ("radix", _int), ("use_graph", _int), ("autotune", _int),
                 ("absolute", _int), ("prior_covariance", _int), ("refine", _int),
-                ("textbook_slr", _int)]
+                ("textbook_slr", _int), ("max_group_steps", _int)]
 
 
 class Model(ctypes.Structure):
@@ -142,14 +142,15 @@ class Context:
     """Owns an sqsm_ctx (workspaces, plans, graphs) on one device."""
 
     def __init__(self, device=None, leaf_chunk=0, radix=0, use_graph=True, autotune=False,
-                 absolute=False, prior_covariance=False, refine=0, textbook_slr=False):
+                 absolute=False, prior_covariance=False, refine=0, textbook_slr=False,
+                 max_group_steps=0):
         if device is None:
             device = torch.cuda.current_device()
         self.device = int(device)
         h = _p()
         opt = Options(leaf_chunk, radix, 1 if use_graph else 0, 1 if autotune else 0,
                       1 if absolute else 0, 1 if prior_covariance else 0, int(refine),
-                      1 if textbook_slr else 0)
+                      1 if textbook_slr else 0, int(max_group_steps))
         rc = lib.sqsm_create(ctypes.byref(h), self.device, ctypes.byref(opt))
         if rc != OK:
             raise SqsmError(rc, "sqsm_create failed")

@@ -111,6 +111,7 @@ struct sqsm_ctx {
   sqsm_options opt{};
   std::string err;
   int* d_status = nullptr;
+  double* d_group = nullptr;      // one group's nll, grad[4], changes (grouped nll_grad)
   cudaStream_t capture_stream = nullptr;   // graphs are recorded here
   cudaStream_t body_stream = nullptr;      // bodies of conditional graph nodes
   std::vector<std::unique_ptr<Plan>> plans;
@@ -443,7 +444,8 @@ extern "C" {
 int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
   if (!out) return SQSM_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt && (opt->refine < 0 || opt->refine > 2)) return SQSM_ERR_INVALID_ARG;
+  if (opt && (opt->refine < 0 || opt->refine > 2 || opt->max_group_steps < 0))
+    return SQSM_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return SQSM_ERR_CUDA;
@@ -455,12 +457,18 @@ int sqsm_create(sqsm_ctx** out, int device, const sqsm_options* opt) {
     delete ctx;
     return SQSM_ERR_CUDA;
   }
+  if (cudaMalloc(&ctx->d_group, 8 * sizeof(double)) != cudaSuccess) {
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return SQSM_ERR_CUDA;
+  }
   cudaMemset(ctx->d_status, 0, sizeof(int));
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_status);
+    cudaFree(ctx->d_group);
     delete ctx;
     return SQSM_ERR_CUDA;
   }
@@ -477,6 +485,7 @@ int sqsm_destroy(sqsm_ctx* ctx) {
     ctx->graphs.clear();
     ctx->plans.clear();
     cudaFree(ctx->d_status);
+    cudaFree(ctx->d_group);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   }
@@ -1121,39 +1130,13 @@ int sqsm_ipls_smooth_std(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   return SQSM_OK;
 }
 
-int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
-                       int linearization, int M, int adj_iters, double tol, int64_t batch,
-                       const int64_t* offsets, const void* y, const void* m0, const void* N0,
-                       const void* init_ms, const void* init_Ns, void* ms, void* Ns,
-                       double* nll, double* grad, double* adj_change, double* ipls_change,
-                       void* stream) {
-  if (!ctx) return SQSM_ERR_INVALID_ARG;
-  if (dtype != SQSM_F32 && dtype != SQSM_F64)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
-  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
-  if (!is_ct(model))
-    return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
-  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
-  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
-  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
-  if (M < 0 || adj_iters < 0) return fail(ctx, SQSM_ERR_INVALID_ARG, "M, adj_iters must be >= 0");
-  if (std::isnan(tol)) return fail(ctx, SQSM_ERR_INVALID_ARG, "tol is NaN");
-  if (M == 0 && (!init_ms || !init_Ns))
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "M = 0 needs an initial trajectory");
-  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
-  if (!valid_offsets(offsets, batch))
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
-  if (!y || !m0 || !N0 || !ms || !Ns || !nll || !grad)
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
-  if ((init_ms == nullptr) != (init_Ns == nullptr))
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
-  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
-  if (!aligned(elem_bytes(dtype), {y, m0, N0, init_ms, init_Ns, ms, Ns}) ||
-      !aligned(8, {nll, grad, adj_change, ipls_change}))
-    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
-  DeviceGuard g(ctx->device);
-  cudaStream_t s = (cudaStream_t)stream;
+// One NLL + gradient evaluation of a batch whose arguments were checked.
+static int nll_grad_run(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                        int linearization, int M, int adj_iters, double tol, int64_t batch,
+                        const int64_t* offsets, const void* y, const void* m0, const void* N0,
+                        const void* init_ms, const void* init_Ns, void* ms, void* Ns,
+                        double* nll, double* grad, double* adj_change, double* ipls_change,
+                        cudaStream_t s, bool use_graph) {
   cudaGetLastError();
   int L0 = 0, R = 0;
   const int trc = choose_ipls_shape(ctx, dtype, model, theta, linearization, batch, offsets, y,
@@ -1187,7 +1170,7 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
       adj_enqueue_f64(a, adj, p->filt, w->filt, p->smth, w->smth, w->adj_scan, sq, w->partial,
                       ctx->d_status, st);
   };
-  if (!ctx->opt.use_graph) {
+  if (!use_graph) {
     enqueue(s);
   } else {
     GraphKey key{p, dtype, linearization, M, 0, adj_iters + 1, y, m0, N0, init_ms, init_Ns,
@@ -1225,6 +1208,83 @@ int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_nll_grad launch");
+  return SQSM_OK;
+}
+
+int sqsm_ipls_nll_grad(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const double* theta,
+                       int linearization, int M, int adj_iters, double tol, int64_t batch,
+                       const int64_t* offsets, const void* y, const void* m0, const void* N0,
+                       const void* init_ms, const void* init_Ns, void* ms, void* Ns,
+                       double* nll, double* grad, double* adj_change, double* ipls_change,
+                       void* stream) {
+  if (!ctx) return SQSM_ERR_INVALID_ARG;
+  if (dtype != SQSM_F32 && dtype != SQSM_F64)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "dtype must be SQSM_F32 or SQSM_F64");
+  if (!known_model(model)) return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown model kind");
+  if (!is_ct(model))
+    return fail(ctx, SQSM_ERR_UNSUPPORTED, "implemented for the CT bearings model");
+  if (!(model->dt > 0)) return fail(ctx, SQSM_ERR_INVALID_ARG, "model dt must be > 0");
+  if (!theta) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta is null");
+  if (linearization < SQSM_CUBATURE || linearization > SQSM_GAUSS_HERMITE)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "unknown linearization");
+  if (M < 0 || adj_iters < 0) return fail(ctx, SQSM_ERR_INVALID_ARG, "M, adj_iters must be >= 0");
+  if (std::isnan(tol)) return fail(ctx, SQSM_ERR_INVALID_ARG, "tol is NaN");
+  if (M == 0 && (!init_ms || !init_Ns))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "M = 0 needs an initial trajectory");
+  if (batch < 1 || batch > (1 << 30)) return fail(ctx, SQSM_ERR_INVALID_ARG, "bad batch");
+  if (!valid_offsets(offsets, batch))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "offsets must start at 0 and increase strictly");
+  if (!y || !m0 || !N0 || !ms || !Ns || !nll || !grad)
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "null input or output pointer");
+  if ((init_ms == nullptr) != (init_Ns == nullptr))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "init_ms and init_Ns must both be set or both NULL");
+  if (!theta_finite(model, theta)) return fail(ctx, SQSM_ERR_INVALID_ARG, "theta not finite");
+  if (!aligned(elem_bytes(dtype), {y, m0, N0, init_ms, init_Ns, ms, Ns}) ||
+      !aligned(8, {nll, grad, adj_change, ipls_change}))
+    return fail(ctx, SQSM_ERR_INVALID_ARG, "pointer not a multiple of its element size");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t cap = ctx->opt.max_group_steps;
+  if (cap <= 0 || offsets[batch] <= cap)
+    return nll_grad_run(ctx, dtype, model, theta, linearization, M, adj_iters, tol, batch, offsets,
+                        y, m0, N0, init_ms, init_Ns, ms, Ns, nll, grad, adj_change, ipls_change,
+                        s, ctx->opt.use_graph != 0);
+  for (int64_t b = 0; b < batch; ++b)
+    if (offsets[b + 1] - offsets[b] > cap)
+      return fail(ctx, SQSM_ERR_TOO_LARGE, "a sequence is longer than max_group_steps");
+  // groups of consecutive sequences with at most cap steps each, evaluated
+  // one after another; each group's plan and workspace are freed before the
+  // next group's are made
+  const size_t es = elem_bytes(dtype);
+  constexpr int nx = 5, ny = 2;
+  auto at = [es](const void* p, int64_t elems) -> void* {
+    return p ? (void*)((const char*)p + elems * (int64_t)es) : nullptr;
+  };
+  std::vector<int64_t> sub;
+  for (int64_t g0 = 0; g0 < batch;) {
+    int64_t g1 = g0 + 1;
+    while (g1 < batch && offsets[g1 + 1] - offsets[g0] <= cap) ++g1;
+    sub.assign(offsets + g0, offsets + g1 + 1);
+    for (auto& v : sub) v -= offsets[g0];
+    const int64_t row0 = offsets[g0] + g0;   // the group's first state row
+    std::vector<const Plan*> before;
+    for (auto& q : ctx->plans) before.push_back(q.get());
+    const int rc = nll_grad_run(
+        ctx, dtype, model, theta, linearization, M, adj_iters, tol, g1 - g0, sub.data(),
+        at(y, offsets[g0] * ny), at(m0, g0 * nx), at(N0, g0 * nx * nx), at(init_ms, row0 * nx),
+        at(init_Ns, row0 * nx * nx), at(ms, row0 * nx), at(Ns, row0 * nx * nx), ctx->d_group,
+        ctx->d_group + 1, ctx->d_group + 5, ctx->d_group + 6, s, false);
+    if (rc != SQSM_OK) return rc;
+    enqueue_nll_grad_group_add(g0 == 0 ? 1 : 0, n_theta(model), ctx->d_group, nll, grad,
+                               adj_change, ipls_change, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sqsm_ipls_nll_grad group");
+    for (size_t k = ctx->plans.size(); k-- > 0;) {
+      const Plan* q = ctx->plans[k].get();
+      if (std::find(before.begin(), before.end(), q) == before.end()) drop_plan(ctx, q);
+    }
+    g0 = g1;
+  }
   return SQSM_OK;
 }
 

@@ -130,6 +130,11 @@ constexpr int kMaxPriorNx = 8;
 // N0[b] = chol(P0[b]) in FP64 for b < batch (nx x nx, row-major, element
 // type double if dtype_f64 else float); a P0 that is not positive definite
 // gives a NaN factor and sets SQSM_ERR_NOT_PD in *status.
+// Adds one group's {nll, grad[n_theta], adj_change, ipls_change} (device
+// doubles, grad at g + 1, the changes at g + 5 and g + 6) into the caller's
+// outputs (first group: copies).
+void enqueue_nll_grad_group_add(int first, int n_theta, const double* g, double* nll, double* grad,
+                                double* adj_change, double* ipls_change, cudaStream_t s);
 void enqueue_prior_cholesky(int dtype_f64, int64_t batch, int nx, const void* P0, void* N0,
                             int* status, cudaStream_t s);
 

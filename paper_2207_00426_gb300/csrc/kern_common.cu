@@ -74,7 +74,34 @@ __global__ void ipls_tol_check(unsigned* dmax, int* iters, int max_iters, float 
   if (go) *go = (int)more;
 }
 
+// One group of a grouped NLL + gradient evaluation: g = {nll, grad[n_theta],
+// adj_change, ipls_change} of the group; the first group is copied, later
+// ones are added (nll, grad) or maxed (changes; NaN, an unsettled change,
+// stays NaN).
+__global__ void nll_grad_group_add(int first, int n_theta, const double* __restrict__ g,
+                                   double* nll, double* grad, double* adj_change,
+                                   double* ipls_change) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  auto mx = [](double a, double b) { return (a != a || b != b) ? NAN : (a > b ? a : b); };
+  if (first) {
+    nll[0] = g[0];
+    for (int i = 0; i < n_theta; ++i) grad[i] = g[1 + i];
+    if (adj_change) adj_change[0] = g[5];
+    if (ipls_change) ipls_change[0] = g[6];
+  } else {
+    nll[0] += g[0];
+    for (int i = 0; i < n_theta; ++i) grad[i] += g[1 + i];
+    if (adj_change) adj_change[0] = mx(adj_change[0], g[5]);
+    if (ipls_change) ipls_change[0] = mx(ipls_change[0], g[6]);
+  }
+}
+
 }  // namespace
+
+void enqueue_nll_grad_group_add(int first, int n_theta, const double* g, double* nll, double* grad,
+                                double* adj_change, double* ipls_change, cudaStream_t s) {
+  nll_grad_group_add<<<1, 1, 0, s>>>(first, n_theta, g, nll, grad, adj_change, ipls_change);
+}
 
 void enqueue_prior_cholesky(int dtype_f64, int64_t batch, int nx, const void* P0, void* N0,
                             int* status, cudaStream_t s) {

@@ -281,21 +281,45 @@ filter_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   if (t == cnt - 1) vstore<T, REC>(out + c * REC, mine);
 }
 
-// One thread per item of the level.
+// The carries of one chunk (cnt consecutive items, CREC values each, lane j
+// holding item j's in b[NX], U[NX*NX]) written to their contiguous block of
+// g: staged in the warp's shared rows, then stored lane-strided so that every
+// store instruction covers consecutive words.
+template <typename T, int NX>
+SQSM_DEV void warp_store_carries(T* __restrict__ g, T* sh, const T* b, const T* U, int j, int cnt,
+                                 bool active) {
+  constexpr int CREC = NX + NX * NX;
+  const int lane = threadIdx.x % kWarp;
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < NX; ++k) sh[j * CREC + k] = b[k];
+#pragma unroll
+    for (int k = 0; k < NX * NX; ++k) sh[j * CREC + NX + k] = U[k];
+  }
+  __syncwarp();
+  for (int k = lane; k < cnt * CREC; k += kWarp) g[k] = sh[k];
+}
+
+// One thread per item of the level; each warp is one chunk.
 template <typename T, int NX>
 __global__ void __launch_bounds__(kBlock)
 filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
                const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
   constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX;
+  static_assert(kChunkScan == kWarp && kBlock % kWarp == 0, "one chunk per warp");
+  __shared__ T SO[kBlock / kWarp][kWarp * CREC];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = tid / kChunkScan;
-  if (c >= lv.n_chunks) return;
+  if (c >= lv.n_chunks) return;   // uniform per warp
   const int j = (int)(tid - c * kChunkScan);
-  if (j >= lv.count[c]) return;
-  const int64_t i = lv.first[c] + j;
+  const int cnt = lv.count[c];
+  const bool active = j < cnt;
+  const int64_t i0 = lv.first[c];
+  const int64_t i = i0 + j;
   const int flag = flag_in[c];
   T cb[NX], cU[NX * NX];
-  if (j == 0) {
+  if (!active) {
+  } else if (j == 0) {
     load<T, NX>(carry_in + c * CREC, cb);
     load<T, NX * NX>(carry_in + c * CREC + NX, cU);
   } else if (flag) {
@@ -308,9 +332,9 @@ filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ c
     load<T, NX>(items + (i - 1) * REC + FRec<NX>::b, cb);
     load<T, NX * NX>(items + (i - 1) * REC + FRec<NX>::U, cU);
   }
-  store<T, NX>(carry_out + i * CREC, cb);
-  store<T, NX * NX>(carry_out + i * CREC + NX, cU);
-  flag_out[i] = j == 0 ? flag : 1;
+  warp_store_carries<T, NX>(carry_out + i0 * CREC, SO[threadIdx.x / kWarp], cb, cU, j, cnt,
+                            active);
+  if (active) flag_out[i] = j == 0 ? flag : 1;
 }
 
 template <typename T, int NX>
@@ -342,16 +366,20 @@ __global__ void __launch_bounds__(kBlock)
 smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
                  const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
   constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
+  static_assert(kChunkScan == kWarp && kBlock % kWarp == 0, "one chunk per warp");
+  __shared__ T SO[kBlock / kWarp][kWarp * CREC];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = tid / kChunkScan;
-  if (c >= lv.n_chunks) return;
+  if (c >= lv.n_chunks) return;   // uniform per warp
   const int j = (int)(tid - c * kChunkScan);
   const int cnt = lv.count[c];
-  if (j >= cnt) return;
-  const int64_t i = lv.first[c] + j;
+  const bool active = j < cnt;
+  const int64_t i0 = lv.first[c];
+  const int64_t i = i0 + j;
   const int flag = flag_in[c];
   T cg[NX], cD[NX * NX];
-  if (j == cnt - 1) {
+  if (!active) {
+  } else if (j == cnt - 1) {
     load<T, NX>(carry_in + c * CREC, cg);
     load<T, NX * NX>(carry_in + c * CREC + NX, cD);
   } else if (flag) {
@@ -364,9 +392,9 @@ smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__
     load<T, NX>(items + (i + 1) * REC + SRec<NX>::g, cg);
     load<T, NX * NX>(items + (i + 1) * REC + SRec<NX>::D, cD);
   }
-  store<T, NX>(carry_out + i * CREC, cg);
-  store<T, NX * NX>(carry_out + i * CREC + NX, cD);
-  flag_out[i] = j == cnt - 1 ? flag : 1;
+  warp_store_carries<T, NX>(carry_out + i0 * CREC, SO[threadIdx.x / kWarp], cg, cD, j, cnt,
+                            active);
+  if (active) flag_out[i] = j == cnt - 1 ? flag : 1;
 }
 
 inline unsigned cs_down_grid(int64_t chunks) {
