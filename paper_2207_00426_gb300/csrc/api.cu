@@ -329,7 +329,10 @@ Workspace* get_ws(Plan* p, int dtype, int nx) {
   if (it != p->ws.end()) return it->second.get();
   auto w = std::make_unique<Workspace>();
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
-  const size_t frec = frec_size(nx), srec = srec_size(nx), crec = nx + nx * nx;
+  // carries: the square-root scans' packed records (XRow) and the standard
+  // form's vector + full covariance share the buffers
+  const size_t frec = frec_size(nx), srec = srec_size(nx),
+               crec = std::max(nx + nx * nx, xrow_size(nx));
   if (!alloc_scan(w->mem, p->filt, w->filt, es * frec, es * crec)) return nullptr;
   if (!alloc_scan(w->mem, p->smth, w->smth, es * srec, es * crec)) return nullptr;
   w->partial = (double*)w->mem.get(sizeof(double) * p->filt.lv[0].n_chunks);

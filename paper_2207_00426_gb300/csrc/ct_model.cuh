@@ -742,6 +742,39 @@ __global__ void __launch_bounds__(kBlock) rows_copy_kernel(int64_t rows, RI in, 
   out.store(e, m, N);
 }
 
+// Error-free transformations (Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005): TwoSum (Knuth) gives s + e = a + b
+// exactly with s = fl(a + b); TwoProduct with an FMA gives p + e = a b
+// exactly.  The explicit round-to-nearest intrinsics keep the compiler from
+// contracting or reordering them.
+SQSM_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+SQSM_DEV void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// r = x0 + sum_k A[k] (v_hi[k] + v_lo[k]) in the Dot2 scheme of the paper
+// above: the leading sum carried by TwoSum / TwoProduct, every rounding error
+// (and the products with v_lo) summed into a correction added once at the
+// end -- as accurate as the sum computed in twice the working precision and
+// then rounded.
+template <int N>
+SQSM_DEV float dot2(float s, float comp, const float* A, const float* vh, const float* vl) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float p, pe, e;
+    two_prod(A[k], vh[k], p, pe);
+    two_sum(s, p, s, e);
+    comp = __fadd_rn(comp, __fadd_rn(e, pe));
+    comp = __fmaf_rn(A[k], vl[k], comp);
+  }
+  return __fadd_rn(s, comp);
+}
+
 // Residual model of one refinement pass of the linear smoother (mixed
 // precision iterative refinement).  The smoother of the linearised model in
 // deviation coordinates about m (the iteration's nominal means, rows
@@ -749,10 +782,12 @@ __global__ void __launch_bounds__(kBlock) rows_copy_kernel(int64_t rows, RI in, 
 // linear-Gaussian model about n1, whose offsets are, with dx = n1 - m,
 //   c' = F dx_{k-1} + c~ - dx_k,   d' = d~ + H dx_k
 // (x_k = F x_{k-1} + c~ + q and y_k = H x_k + d~ + r written for x - dx);
-// the prior's is dm0 - dx_0 (center_prior_kernel on n1).  dx and the
-// offsets are formed in FP64 from the stored values -- dx exactly, the
-// products and sums with FP64 rounding -- and rounded once when written
-// back into the PRec records in place.  One thread per step.
+// the prior's is dm0 - dx_0 (center_prior_kernel on n1).  The offsets are
+// formed from the stored values beyond the working precision and rounded
+// once when written back into the PRec records in place: in FP32, dx exactly
+// as a TwoSum pair and the sums by Dot2 (FP64 arithmetic, far slower on this
+// GPU, is not needed for that accuracy); in FP64, in plain FP64.  One thread
+// per step.
 template <typename T, int NX, int NY, typename RI>
 __global__ void __launch_bounds__(kBlock)
 refine_residual_kernel(DevLevel lv, int leaf, RI prev, RI now, T* __restrict__ rec) {
@@ -770,27 +805,56 @@ refine_residual_kernel(DevLevel lv, int leaf, RI prev, RI now, T* __restrict__ r
   now.load_mean(rp, m1v);
   prev.load_mean(rk, k0v);
   now.load_mean(rk, k1v);
-  double dp[NX], dk[NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) {
-    dp[i] = (double)m1v[i] - (double)m0v[i];
-    dk[i] = (double)k1v[i] - (double)k0v[i];
-  }
+  // the record's 16-byte words that hold F, c (from word 0) and H, d (from
+  // P::H), read whole; only the words holding c and d are written back
+  static_assert(P::F == 0 && P::c == NX * NX && P::d == P::H + NY * NX && P::H % 4 == 0,
+                "PRec layout");
+  constexpr int LA = (P::c + NX + 3) / 4 * 4, LB = (NY * NX + NY + 3) / 4 * 4;
+  constexpr int C0 = P::c / 4 * 4, D0 = NY * NX / 4 * 4;
   T* r = rec + s * P::size;
+  T fa[LA], ha[LB];
+  vload<T, LA>(r, fa);
+  vload<T, LB>(r + P::H, ha);
+  if constexpr (sizeof(T) == 4) {
+    float dph[NX], dpl[NX], dkh[NX], dkl[NX];
 #pragma unroll
-  for (int i = 0; i < NX; ++i) {
-    double a = (double)r[P::c + i] - dk[i];
+    for (int i = 0; i < NX; ++i) {
+      two_sum(m1v[i], -m0v[i], dph[i], dpl[i]);
+      two_sum(k1v[i], -k0v[i], dkh[i], dkl[i]);
+    }
 #pragma unroll
-    for (int k = 0; k < NX; ++k) a += (double)r[P::F + i * NX + k] * dp[k];
-    r[P::c + i] = (T)a;
+    for (int i = 0; i < NX; ++i) {
+      float s0, e0;
+      two_sum(fa[P::c + i], -dkh[i], s0, e0);
+      fa[P::c + i] = dot2<NX>(s0, __fsub_rn(e0, dkl[i]), fa + i * NX, dph, dpl);
+    }
+#pragma unroll
+    for (int i = 0; i < NY; ++i)
+      ha[NY * NX + i] = dot2<NX>(ha[NY * NX + i], 0.f, ha + i * NX, dkh, dkl);
+  } else {
+    double dp[NX], dk[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      dp[i] = (double)m1v[i] - (double)m0v[i];
+      dk[i] = (double)k1v[i] - (double)k0v[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      double a = (double)fa[P::c + i] - dk[i];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) a += (double)fa[i * NX + k] * dp[k];
+      fa[P::c + i] = (T)a;
+    }
+#pragma unroll
+    for (int i = 0; i < NY; ++i) {
+      double a = (double)ha[NY * NX + i];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) a += (double)ha[i * NX + k] * dk[k];
+      ha[NY * NX + i] = (T)a;
+    }
   }
-#pragma unroll
-  for (int i = 0; i < NY; ++i) {
-    double a = (double)r[P::d + i];
-#pragma unroll
-    for (int k = 0; k < NX; ++k) a += (double)r[P::H + i * NX + k] * dk[k];
-    r[P::d + i] = (T)a;
-  }
+  vstore<T, LA - C0>(r + C0, fa + C0);
+  vstore<T, LB - D0>(r + P::H + D0, ha + D0);
 }
 
 // Prior of the deviation model: dm0[b] = m0[b] - m_0 (nominal row 0 of b).

@@ -85,7 +85,8 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   const RowsPacked<T, NX> prev{(T*)a.prevrows};
   auto keep_prev = [&]() {
     ProfScope ps(a.prof, K_INIT, s);
-    rows_copy_kernel<T, NX><<<grid_for(rows), kBlock, 0, s>>>(rows, nom, prev);
+    cudaMemcpyAsync(prev.rec, nom.rec, sizeof(T) * XRow<NX>::size * rows,
+                    cudaMemcpyDeviceToDevice, s);
   };
   if (passes > 0) keep_prev();
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y,

@@ -27,6 +27,7 @@
 // by the caller.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <initializer_list>
 #include <mutex>
@@ -234,7 +235,8 @@ extern "C" int sqsm_lgssm_smooth_noalloc(int dtype, int nx, int ny, int64_t n, c
   // leaf_chunk = 4, radix = 4
   const int L0 = 4, R = 4;
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
-  const size_t frec = frec_size(nx), srec = srec_size(nx), crec = nx + nx * nx;
+  const size_t frec = frec_size(nx), srec = srec_size(nx),
+               crec = std::max(nx + nx * nx, xrow_size(nx));   // carries: XRow records
 
   // measure first: reject problems that do not fit before touching the GPU
   for (int pass = 0; pass < 2; ++pass) {

@@ -114,17 +114,15 @@ filter_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carr
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = FRec<NX>::size;
-  constexpr int CREC = NX + NX * NX;
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   int flag = flag_in[c];
+  const RowsPacked<T, NX> cin{(T*)carry_in}, cout{carry_out};
   T cb[NX], cU[NX * NX];
-  load<T, NX>(carry_in + c * CREC, cb);
-  load<T, NX * NX>(carry_in + c * CREC + NX, cU);
+  cin.load(c, cb, cU);
   for (int j = 0; j < cnt; ++j) {
     const int64_t i = i0 + j;
-    store<T, NX>(carry_out + i * CREC, cb);
-    store<T, NX * NX>(carry_out + i * CREC + NX, cU);
+    cout.store(i, cb, cU);
     flag_out[i] = flag;
     if (j + 1 < cnt) {
       const T* it = items + i * REC;
@@ -154,14 +152,12 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
                  FO fo, double* __restrict__ partial, int* status) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
-  constexpr int CREC = NX + NX * NX;
   const int b = lv.seq[c];
   const int64_t s0 = lv.first[c];
   const int cnt = lv.count[c];
   T m[NX], N[NX * NX];
   if (flag[c]) {
-    load<T, NX>(carry + c * CREC, m);
-    load<T, NX * NX>(carry + c * CREC + NX, N);
+    RowsPacked<T, NX>{(T*)carry}.load(c, m, N);
   } else {
     load<T, NX>(m0 + (int64_t)b * NX, m);
     load_lower<T, NX>(N0 + (int64_t)b * NX * NX, N);
@@ -252,17 +248,15 @@ smoother_down(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
-  constexpr int CREC = NX + NX * NX;
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   int flag = flag_in[c];
+  const RowsPacked<T, NX> cin{(T*)carry_in}, cout{carry_out};
   T cg[NX], cD[NX * NX];
-  load<T, NX>(carry_in + c * CREC, cg);
-  load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+  cin.load(c, cg, cD);
   for (int j = cnt - 1; j >= 0; --j) {
     const int64_t i = i0 + j;
-    store<T, NX>(carry_out + i * CREC, cg);
-    store<T, NX * NX>(carry_out + i * CREC + NX, cD);
+    cout.store(i, cg, cD);
     flag_out[i] = flag;
     if (j > 0) {
       const T* it = items + i * REC;
@@ -294,7 +288,6 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
-  constexpr int CREC = NX + NX * NX;
   const int b = lv.seq[c];
   const int64_t e0 = lv.first[c];
   const int cnt = lv.count[c];
@@ -302,10 +295,7 @@ smoother_leaf_down(DevLevel lv, DevSeqs sq, GV gv, FO fo, const T* __restrict__ 
   const int64_t nb = sq.offsets[b + 1] - sq.offsets[b];
   float change = 0.f;
   T gm[NX], Dm[NX * NX];
-  if (flag[c]) {
-    load<T, NX>(carry + c * CREC, gm);
-    load<T, NX * NX>(carry + c * CREC + NX, Dm);
-  }
+  if (flag[c]) RowsPacked<T, NX>{(T*)carry}.load(c, gm, Dm);
   bool ok = true;
   // The inputs of a step (filter row, transition record, the mean held in
   // out_rows) do not depend on the steps after it, so each iteration issues

@@ -17,6 +17,26 @@ template <typename T, int NX> struct WFilterBuf {
   WFilterWs<T, NX> ws;
 };
 
+// Lane-parallel forms of RowsPacked::load / store for the warp kernels: a
+// scan carry (vector v, lower factor L) in the XRow layout at g.
+template <typename T, int NX>
+SQSM_DEV void wload_carry(const T* __restrict__ g, T* v, T* L, int lane) {
+  for (int i = lane; i < NX * NX; i += kWarp) {
+    const int r = i / NX, q = i % NX;
+    L[i] = q <= r ? g[NX + r * (r + 1) / 2 + q] : T(0);
+  }
+  for (int i = lane; i < NX; i += kWarp) v[i] = g[i];
+}
+
+template <typename T, int NX>
+SQSM_DEV void wstore_carry(T* __restrict__ g, const T* v, const T* L, int lane) {
+  for (int i = lane; i < NX * NX; i += kWarp) {
+    const int r = i / NX, q = i % NX;
+    if (q <= r) g[NX + r * (r + 1) / 2 + q] = L[i];
+  }
+  for (int i = lane; i < NX; i += kWarp) g[i] = v[i];
+}
+
 template <typename T, int NX>
 __global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
 filter_up_w(DevLevel lv, const T* __restrict__ in, T* __restrict__ out) {
@@ -48,7 +68,7 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
 filter_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
               const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX;
+  constexpr int REC = FRec<NX>::size, XS = XRow<NX>::size;
   __shared__ WFilterBuf<T, NX> sh[kWarpsPerBlock];
   const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
@@ -57,14 +77,11 @@ filter_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ ca
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   int flag = flag_in[c];
-  for (int i = lane; i < CREC; i += kWarp) {
-    const T v = carry_in[c * CREC + i];
-    if (i < NX) B.cb[i] = v; else B.cU[i - NX] = v;
-  }
+  wload_carry<T, NX>(carry_in + c * XS, B.cb, B.cU, lane);
   __syncwarp();
   for (int j = 0; j < cnt; ++j) {
     const int64_t it = i0 + j;
-    for (int i = lane; i < CREC; i += kWarp) carry_out[it * CREC + i] = i < NX ? B.cb[i] : B.cU[i - NX];
+    wstore_carry<T, NX>(carry_out + it * XS, B.cb, B.cU, lane);
     if (lane == 0) flag_out[it] = flag;
     __syncwarp();
     if (j + 1 < cnt) {
@@ -121,7 +138,7 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kWarp * kWarpsPerBlock)
 smoother_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
                 const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
+  constexpr int REC = SRec<NX>::size, XS = XRow<NX>::size;
   __shared__ WSmootherBuf<T, NX> sh[kWarpsPerBlock];
   const int wid = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
   const int64_t c = blockIdx.x * (int64_t)kWarpsPerBlock + wid;
@@ -130,14 +147,11 @@ smoother_down_w(DevLevel lv, const T* __restrict__ items, const T* __restrict__ 
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
   int flag = flag_in[c];
-  for (int i = lane; i < CREC; i += kWarp) {
-    const T v = carry_in[c * CREC + i];
-    if (i < NX) B.cg[i] = v; else B.cD[i - NX] = v;
-  }
+  wload_carry<T, NX>(carry_in + c * XS, B.cg, B.cD, lane);
   __syncwarp();
   for (int j = cnt - 1; j >= 0; --j) {
     const int64_t it = i0 + j;
-    for (int i = lane; i < CREC; i += kWarp) carry_out[it * CREC + i] = i < NX ? B.cg[i] : B.cD[i - NX];
+    wstore_carry<T, NX>(carry_out + it * XS, B.cg, B.cD, lane);
     if (lane == 0) flag_out[it] = flag;
     __syncwarp();
     if (j > 0) {
@@ -180,7 +194,7 @@ template <typename T, int NX>
 __global__ void __launch_bounds__((KsMax<T, FRec<NX>::size>::value))
 filter_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
               T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = FRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
+  constexpr int REC = FRec<NX>::size, KS = KsMax<T, REC>::value;
   __shared__ __align__(16) T S[KS * REC];
   const int b = blockIdx.x, t = threadIdx.x;
   const int64_t i0 = seq_item_off[b];
@@ -199,13 +213,9 @@ filter_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ it
   if (t < c) vstore<T, REC>(S + t * REC, mine);
   __syncthreads();
   if (t < c) {
-    T* co = carry_out + (i0 + t) * CREC;
     if (t > 0) {
       const T* p = S + (t - 1) * REC;
-#pragma unroll
-      for (int i = 0; i < NX; ++i) co[i] = p[FRec<NX>::b + i];
-#pragma unroll
-      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[FRec<NX>::U + i];
+      RowsPacked<T, NX>{carry_out}.store(i0 + t, p + FRec<NX>::b, p + FRec<NX>::U);
     }
     flag_out[i0 + t] = t > 0 ? 1 : 0;
   }
@@ -215,7 +225,7 @@ template <typename T, int NX>
 __global__ void __launch_bounds__((KsMax<T, SRec<NX>::size>::value))
 smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
                 T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = SRec<NX>::size, KS = KsMax<T, REC>::value, CREC = NX + NX * NX;
+  constexpr int REC = SRec<NX>::size, KS = KsMax<T, REC>::value;
   __shared__ __align__(16) T S[KS * REC];
   const int b = blockIdx.x, t = threadIdx.x;
   const int64_t i0 = seq_item_off[b];
@@ -234,13 +244,9 @@ smoother_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ 
   if (t < c) vstore<T, REC>(S + t * REC, mine);
   __syncthreads();
   if (t < c) {
-    T* co = carry_out + (i0 + t) * CREC;
     if (t + 1 < c) {
       const T* p = S + (t + 1) * REC;
-#pragma unroll
-      for (int i = 0; i < NX; ++i) co[i] = p[SRec<NX>::g + i];
-#pragma unroll
-      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[SRec<NX>::D + i];
+      RowsPacked<T, NX>{carry_out}.store(i0 + t, p + SRec<NX>::g, p + SRec<NX>::D);
     }
     flag_out[i0 + t] = t + 1 < c ? 1 : 0;
   }
@@ -281,23 +287,38 @@ filter_up_cs(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   if (t == cnt - 1) vstore<T, REC>(out + c * REC, mine);
 }
 
-// The carries of one chunk (cnt consecutive items, CREC values each, lane j
-// holding item j's in b[NX], U[NX*NX]) written to their contiguous block of
-// g: staged in the warp's shared rows, then stored lane-strided so that every
-// store instruction covers consecutive words.
+// The carries of one chunk (cnt consecutive items, lane j holding item j's
+// vector b[NX] and lower factor U[NX*NX]) written to their contiguous block
+// of XRow records at g: packed into the warp's shared rows, then copied in
+// 16-byte words, lane-strided, so that every store instruction covers
+// consecutive words.
 template <typename T, int NX>
 SQSM_DEV void warp_store_carries(T* __restrict__ g, T* sh, const T* b, const T* U, int j, int cnt,
                                  bool active) {
-  constexpr int CREC = NX + NX * NX;
+  constexpr int XS = XRow<NX>::size, WPR = XS * (int)sizeof(T) / 16;
+  static_assert(XS * sizeof(T) % 16 == 0, "whole 16-byte words per record");
   const int lane = threadIdx.x % kWarp;
   if (active) {
+    T* o = sh + j * XS;
 #pragma unroll
-    for (int k = 0; k < NX; ++k) sh[j * CREC + k] = b[k];
+    for (int k = 0; k < NX; ++k) o[k] = b[k];
 #pragma unroll
-    for (int k = 0; k < NX * NX; ++k) sh[j * CREC + NX + k] = U[k];
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = 0; q <= r; ++q) o[NX + r * (r + 1) / 2 + q] = U[r * NX + q];
+#pragma unroll
+    for (int k = NX + NX * (NX + 1) / 2; k < XS; ++k) o[k] = T(0);
   }
   __syncwarp();
-  for (int k = lane; k < cnt * CREC; k += kWarp) g[k] = sh[k];
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(sh);
+    float4* g4 = reinterpret_cast<float4*>(g);
+    for (int k = lane; k < cnt * WPR; k += kWarp) g4[k] = s4[k];
+  } else {
+    const double2* s4 = reinterpret_cast<const double2*>(sh);
+    double2* g4 = reinterpret_cast<double2*>(g);
+    for (int k = lane; k < cnt * WPR; k += kWarp) g4[k] = s4[k];
+  }
 }
 
 // One thread per item of the level; each warp is one chunk.
@@ -305,9 +326,9 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kBlock)
 filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
                const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX;
+  constexpr int REC = FRec<NX>::size, XS = XRow<NX>::size;
   static_assert(kChunkScan == kWarp && kBlock % kWarp == 0, "one chunk per warp");
-  __shared__ T SO[kBlock / kWarp][kWarp * CREC];
+  __shared__ __align__(16) T SO[kBlock / kWarp][kWarp * XS];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = tid / kChunkScan;
   if (c >= lv.n_chunks) return;   // uniform per warp
@@ -317,22 +338,21 @@ filter_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ c
   const int64_t i0 = lv.first[c];
   const int64_t i = i0 + j;
   const int flag = flag_in[c];
+  const RowsPacked<T, NX> cin{(T*)carry_in};
   T cb[NX], cU[NX * NX];
   if (!active) {
   } else if (j == 0) {
-    load<T, NX>(carry_in + c * CREC, cb);
-    load<T, NX * NX>(carry_in + c * CREC + NX, cU);
+    cin.load(c, cb, cU);
   } else if (flag) {
     T pb[NX], pU[NX * NX], el[REC];
-    load<T, NX>(carry_in + c * CREC, pb);
-    load<T, NX * NX>(carry_in + c * CREC + NX, pU);
+    cin.load(c, pb, pU);
     vload<T, REC>(items + (i - 1) * REC, el);
     filter_apply<T, NX>(pb, pU, el, cb, cU);
   } else {
     load<T, NX>(items + (i - 1) * REC + FRec<NX>::b, cb);
     load<T, NX * NX>(items + (i - 1) * REC + FRec<NX>::U, cU);
   }
-  warp_store_carries<T, NX>(carry_out + i0 * CREC, SO[threadIdx.x / kWarp], cb, cU, j, cnt,
+  warp_store_carries<T, NX>(carry_out + i0 * XS, SO[threadIdx.x / kWarp], cb, cU, j, cnt,
                             active);
   if (active) flag_out[i] = j == 0 ? flag : 1;
 }
@@ -365,9 +385,9 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(kBlock)
 smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ carry_in,
                  const int* __restrict__ flag_in, T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = SRec<NX>::size, CREC = NX + NX * NX;
+  constexpr int REC = SRec<NX>::size, XS = XRow<NX>::size;
   static_assert(kChunkScan == kWarp && kBlock % kWarp == 0, "one chunk per warp");
-  __shared__ T SO[kBlock / kWarp][kWarp * CREC];
+  __shared__ __align__(16) T SO[kBlock / kWarp][kWarp * XS];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = tid / kChunkScan;
   if (c >= lv.n_chunks) return;   // uniform per warp
@@ -377,22 +397,21 @@ smoother_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__
   const int64_t i0 = lv.first[c];
   const int64_t i = i0 + j;
   const int flag = flag_in[c];
+  const RowsPacked<T, NX> cin{(T*)carry_in};
   T cg[NX], cD[NX * NX];
   if (!active) {
   } else if (j == cnt - 1) {
-    load<T, NX>(carry_in + c * CREC, cg);
-    load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+    cin.load(c, cg, cD);
   } else if (flag) {
     T el[REC];
-    load<T, NX>(carry_in + c * CREC, cg);
-    load<T, NX * NX>(carry_in + c * CREC + NX, cD);
+    cin.load(c, cg, cD);
     vload<T, REC>(items + (i + 1) * REC, el);
     smoother_apply<T, NX>(el, cg, cD);
   } else {
     load<T, NX>(items + (i + 1) * REC + SRec<NX>::g, cg);
     load<T, NX * NX>(items + (i + 1) * REC + SRec<NX>::D, cD);
   }
-  warp_store_carries<T, NX>(carry_out + i0 * CREC, SO[threadIdx.x / kWarp], cg, cD, j, cnt,
+  warp_store_carries<T, NX>(carry_out + i0 * XS, SO[threadIdx.x / kWarp], cg, cD, j, cnt,
                             active);
   if (active) flag_out[i] = j == cnt - 1 ? flag : 1;
 }
@@ -475,7 +494,7 @@ template <typename T, int NX>
 __global__ void __launch_bounds__(3 * Ks3Max<T, FRec<NX>::size>::value)
 filter_top_ks3(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
                T* __restrict__ carry_out, int* __restrict__ flag_out) {
-  constexpr int REC = FRec<NX>::size, CREC = NX + NX * NX, W = REC * sizeof(T) / 16;
+  constexpr int REC = FRec<NX>::size, W = REC * sizeof(T) / 16;
   constexpr int KS = Ks3Max<T, REC>::value;
   __shared__ __align__(16) T S[KS * REC];
   const int b = blockIdx.x;
@@ -488,13 +507,9 @@ filter_top_ks3(const int64_t* __restrict__ seq_item_off, const T* __restrict__ i
   filter_ks3<T, NX, KS>(S, c);
   const int t = threadIdx.x;
   if (t < c) {
-    T* co = carry_out + (i0 + t) * CREC;
     if (t > 0) {
       const T* p = S + (t - 1) * REC;
-#pragma unroll
-      for (int i = 0; i < NX; ++i) co[i] = p[FRec<NX>::b + i];
-#pragma unroll
-      for (int i = 0; i < NX * NX; ++i) co[NX + i] = p[FRec<NX>::U + i];
+      RowsPacked<T, NX>{carry_out}.store(i0 + t, p + FRec<NX>::b, p + FRec<NX>::U);
     }
     flag_out[i0 + t] = t > 0 ? 1 : 0;
   }
