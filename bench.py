@@ -6,8 +6,9 @@ log-likelihood, parallel square-root smoother scan -- over one synthetic
 coordinated-turn sequence of n = 100000 observations (n_x = 5, n_y = 2),
 FP32 arithmetic with FP64 log-likelihood accumulation, each iteration's
 linear smoother refined once (one more filter and smoother pass on the
-residual model formed in FP64), the mode in which the FP32 means meet the
-1e-4 accuracy target at this non-converging configuration.  The unrefined
+residual model, its offsets formed in compensated FP32), the mode in which
+the FP32 means meet the 1e-4 accuracy target at this non-converging
+configuration.  The unrefined
 mode (half the work, 3.3e-4) is reported beside it as ``fast``.
 
 Metric: smoothed steps/s = (time steps x IPLS iterations) per second; the

@@ -150,9 +150,11 @@ typedef struct {
   int refine;           /* mixed-precision refinement passes (0..2) of
                            every IPLS iteration's linear smoother: after
                            the smoother, the residual model about its
-                           result is formed in FP64 (its offsets
-                           c' = F dx + c - dx_k, d' = d + H dx_k, rounded
-                           once) and smoothed again in the call's dtype,
+                           result is formed beyond the working precision
+                           (its offsets c' = F dx + c - dx_k,
+                           d' = d + H dx_k: in FP32 by compensated
+                           TwoSum / Dot2 arithmetic, in FP64 in FP64;
+                           rounded once) and smoothed again in the call's dtype,
                            the correction added to the trajectory.  Each
                            pass costs one more filter and smoother scan;
                            it removes most of the FP32 error of the linear
