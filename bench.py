@@ -64,7 +64,7 @@ GRAD_CPU_PREFIX = 100            # ... and of the 256 x 2000 batch (host baselin
 # (n = 1e5, FP32, default scan shape), from one ncu capture of the current
 # kernels: dram__bytes_read.sum + dram__bytes_write.sum.  A family whose
 # kernels changed since their capture has no entry (traffic null).
-NCU_TRAFFIC = {("filter_up", 100_000): 4.12e6}
+NCU_TRAFFIC = {("filter_up", 100_000): 4.10e6}
 
 
 def parse():

@@ -105,6 +105,29 @@ def test_invalid_arguments(B, ctx):
     assert "compiled" in B.lib.sqsm_last_error(ctx.h).decode()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("rank", [0, 1])
+def test_singular_process_noise(B, ctx, prec, rank):
+    """A noise factor S_Q of rank 1 or 0 (Q not positive definite): the
+    square-root form needs no positive-definite Q (Tria of a rank-deficient
+    block, reading 2), and the results equal the oracle's as long as the
+    predicted covariances stay positive definite -- here F is invertible and
+    P0 positive definite."""
+    m = W.random_lgssm(30, 4, 2, seed=77 + rank)
+    SQ = m["SQ"].copy()
+    SQ[:, :, rank:] = 0.0
+    # observations of this model (rank-deficient process noise)
+    rng = np.random.default_rng(5 + rank)
+    x = m["m0"] + m["N0"] @ rng.standard_normal(4)
+    y = np.zeros_like(m["y"])
+    for t in range(30):
+        x = m["F"][t] @ x + m["c"][t] + SQ[t] @ rng.standard_normal(4)
+        y[t] = m["H"][t] @ x + m["d"][t] + m["SR"][t] @ rng.standard_normal(2)
+    m = dict(m, SQ=SQ, y=y)
+    got = _run(B, ctx, m, torch.float64 if prec == "f64" else torch.float32)
+    _check(got, m, TOL[prec])
+
+
 def test_nonfinite_input_sets_status(B):
     c2 = B.Context(0)
     m = W.linear_cv(n=50, seed=1)
