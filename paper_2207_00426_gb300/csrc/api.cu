@@ -50,6 +50,7 @@ struct Workspace {
   void* n0fac = nullptr;     // prior factors chol(P0) when N0 arguments are covariances
   void* prevrows = nullptr;  // refinement: nominal rows before the last smoother pass
   double* partial2 = nullptr;   // refinement passes' log-likelihood partials
+  void* etab = nullptr;      // refinement: E_k of every state row (mean-only passes)
   bool ipls_ready = false;
   // NLL + gradient
   AdjArgs adj{};
@@ -365,6 +366,15 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype, int nx = 5, int ny = 2)
   return true;
 }
 
+// The per-row E_k table of the mean-only refinement passes, made when a
+// context with refinement first uses the workspace.
+bool ensure_etab(Workspace* w, const Plan* p, int dtype, int nx) {
+  if (w->etab) return true;
+  const size_t es = dtype == SQSM_F64 ? 8 : 4;
+  w->etab = w->mem.get(es * ((nx * nx + 3) / 4 * 4) * p->smth.n_items[0]);
+  return w->etab != nullptr;
+}
+
 bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
   if (w->adj_ready) return true;
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
@@ -635,6 +645,7 @@ IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* mod
   a.dm0 = w->dm0;
   a.prevrows = w->prevrows;
   a.partial2 = w->partial2;
+  a.etab = w->etab;
   return a;
 }
 
@@ -750,7 +761,10 @@ int choose_ipls_shape(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
     Plan* p = get_plan(ctx, offsets, batch, c[0], c[1]);
     if (!p) continue;
     Workspace* w = get_ws(p, dtype, 5);
-    const void* n0 = w && ensure_ipls(w, p, dtype) ? prior_input(ctx, w, p, dtype, 5, N0) : nullptr;
+    const void* n0 = w && ensure_ipls(w, p, dtype) &&
+                             (ctx->opt.refine == 0 || ensure_etab(w, p, dtype, 5))
+                         ? prior_input(ctx, w, p, dtype, 5, N0)
+                         : nullptr;
     if (!n0) {
       if (!existed) drop_plan(ctx, p);
       continue;
@@ -852,7 +866,8 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
   Workspace* w = get_ws(p, dtype, nx);
-  if (!w || !ensure_ipls(w, p, dtype, nx, ny))
+  if (!w || !ensure_ipls(w, p, dtype, nx, ny) ||
+      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, nx)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
@@ -966,7 +981,8 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
   Workspace* w = get_ws(p, dtype, nx);
-  if (!w || !ensure_ipls(w, p, dtype, nx, ny))
+  if (!w || !ensure_ipls(w, p, dtype, nx, ny) ||
+      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, nx)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
@@ -1148,7 +1164,8 @@ static int nll_grad_run(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const
   Plan* p = get_plan(ctx, offsets, batch, L0, R);
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
-  if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype))
+  if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype) ||
+      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, 5)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, 5, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");

@@ -48,6 +48,7 @@ struct IplsArgs {
   int refine = 0;
   void* prevrows = nullptr;
   double* partial2 = nullptr;
+  void* etab = nullptr;   // E_k per state row for the mean-only passes (null: full passes)
 };
 
 // Everything of Alg. 3 after the parameter kernel; capturable.

@@ -49,6 +49,12 @@ template <int NX> struct XRow {
   static constexpr int mvec = (NX + 3) / 4 * 4;   // leading words that hold m
 };
 
+// E_k of Table 4 for one state row, 16-byte aligned (the 25 values padded):
+// written by a full smoother pass, read by the mean-only refinement passes.
+template <int NX> struct ETab {
+  static constexpr int size = (NX * NX + 3) / 4 * 4;
+};
+
 template <typename T, int NX>
 struct RowsSplit {
   T* m;
@@ -630,6 +636,45 @@ SQSM_DEV void filter_apply(const T* bi, const T* Ui, const T* ej, T* bo, T* Uo) 
 // Smoother element of Lemma 3 / Table 4 (right column), 0 <= k < n, with Phi
 // of eq. smooth-init-2:  E = Phi_21 Phi_11^{-1}, g = m^f - E (F m^f + c),
 // D = Phi_22.  Uses only the transition part of g.
+// The mean parts of Table 4, Table 5 and the RTS step, shared by the full
+// kernels and by the mean-only kernels of the refinement passes (which must
+// repeat the full kernels' operations exactly):
+//   g_k = m^f_k - E_k (F m^f_k + c)                         (element),
+//   E_ij = E_i E_j, g_ij = E_i g_j + g_i                    (combine),
+//   g <- E_i g + g_i                                        (RTS step).
+template <typename T, int NX>
+SQSM_DEV void smoother_element_g(const T* E, const T* F, const T* c, const T* mf, T* g) {
+  T fm[NX];
+  mv<T, NX, NX>(F, mf, fm);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) fm[i] += c[i];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    T s = mf[i];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s -= E[i * NX + k] * fm[k];
+    g[i] = s;
+  }
+}
+
+template <typename T, int NX>
+SQSM_DEV void smoother_combine_g(const T* Ei, const T* gi, const T* Ej, const T* gj, T* Eo,
+                                 T* go) {
+  mm<T, NX, NX, NX>(Ei, Ej, Eo);
+  T t[NX];
+  mv<T, NX, NX>(Ei, gj, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) go[i] = t[i] + gi[i];
+}
+
+template <typename T, int NX>
+SQSM_DEV void smoother_apply_g(const T* Ei, const T* gi, T* gm) {
+  T t[NX];
+  mv<T, NX, NX>(Ei, gm, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) gm[i] = t[i] + gi[i];
+}
+
 template <typename T, int NX, int NY>
 SQSM_DEV void smoother_element(const Gamma<T, NX, NY>& g, const T* mf, const T* Nf, T* e) {
   using R = SRec<NX>;
@@ -655,20 +700,12 @@ SQSM_DEV void smoother_element(const Gamma<T, NX, NY>& g, const T* mf, const T* 
 #pragma unroll
     for (int j = 0; j < NX; ++j) e[R::E + i * NX + j] = Phi[(NX + i) * C2 + j];
   rsolve<T, NX, NX>(e + R::E, P11);
-  T fm[NX];
-  mv<T, NX, NX>(g.F, mf, fm);
+  smoother_element_g<T, NX>(e + R::E, g.F, g.c, mf, e + R::g);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) fm[i] += g.c[i];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) {
-    T s = mf[i];
-#pragma unroll
-    for (int k = 0; k < NX; ++k) s -= e[R::E + i * NX + k] * fm[k];
-    e[R::g + i] = s;
+  for (int i = 0; i < NX; ++i)
 #pragma unroll
     for (int j = 0; j < NX; ++j)
       e[R::D + i * NX + j] = j <= i ? Phi[(NX + i) * C2 + NX + j] : T(0);
-  }
   zero_pad<T, R::D + NX * NX, R::size>(e);
 }
 
@@ -692,11 +729,7 @@ template <typename T, int NX>
 SQSM_DEV void smoother_combine(const T* ei, const T* ej, T* out) {
   using R = SRec<NX>;
   constexpr int C2 = 2 * NX;
-  mm<T, NX, NX, NX>(ei + R::E, ej + R::E, out + R::E);
-  T t[NX];
-  mv<T, NX, NX>(ei + R::E, ej + R::g, t);
-#pragma unroll
-  for (int i = 0; i < NX; ++i) out[R::g + i] = t[i] + ei[R::g + i];
+  smoother_combine_g<T, NX>(ei + R::E, ei + R::g, ej + R::E, ej + R::g, out + R::E, out + R::g);
   T B[NX * C2];
 #pragma unroll
   for (int i = 0; i < NX; ++i)
@@ -720,8 +753,6 @@ template <typename T, int NX>
 SQSM_DEV void smoother_apply(const T* ei, T* gm, T* Dm) {
   using R = SRec<NX>;
   constexpr int C2 = 2 * NX;
-  T t[NX];
-  mv<T, NX, NX>(ei + R::E, gm, t);
   T B[NX * C2];
 #pragma unroll
   for (int i = 0; i < NX; ++i)
@@ -734,8 +765,7 @@ SQSM_DEV void smoother_apply(const T* ei, T* gm, T* Dm) {
       B[i * C2 + NX + j] = ei[R::D + i * NX + j];
     }
   tria<T, NX, C2>(B);
-#pragma unroll
-  for (int i = 0; i < NX; ++i) gm[i] = t[i] + ei[R::g + i];
+  smoother_apply_g<T, NX>(ei + R::E, ei + R::g, gm);
   take_lower<T, NX, C2>(B, Dm);
 }
 

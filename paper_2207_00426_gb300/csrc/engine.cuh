@@ -161,7 +161,7 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
 template <typename T, int NX, int NY, typename GV, typename FO, typename SO>
 void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv, FO fo, SO so,
                       int* status, cudaStream_t s, Prof* P = nullptr, bool add_nominal = false,
-                      unsigned* dmax = nullptr) {
+                      unsigned* dmax = nullptr, T* etab = nullptr) {
   const int Lc = (int)L.lv.size();
   constexpr int KS = KsMax<T, SRec<NX>::size>::value;
   const int Lk = L.ks_level(KS);
@@ -169,7 +169,7 @@ void enqueue_smoother(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv
     {
       ProfScope ps(P, K_SMOOTHER_LEAF_UP, s);
       smoother_leaf_up<T, NX, NY, GV, FO><<<grid_for(L.lv[0].n_chunks), kBlock, 0, s>>>(
-          L.lv[0], sq, gv, fo, (T*)W.items[1]);
+          L.lv[0], sq, gv, fo, (T*)W.items[1], etab);
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_SMOOTHER_UP, s);
@@ -216,3 +216,5 @@ template <int NX> constexpr int smoother_item_size() { return SRec<NX>::size; }
 template <int NX> constexpr int carry_size() { return NX + NX * NX; }
 
 }  // namespace sqsm
+
+#include "refine_scan.cuh"

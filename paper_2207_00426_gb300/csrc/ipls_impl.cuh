@@ -92,11 +92,16 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y,
                             (const T*)(a.centered ? a.dm0 : a.m0), (const T*)a.N0, fr, partial,
                             status, s, a.prof);
-  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax);
+  // with refinement passes to follow, the first pass keeps each row's E_k
+  T* etab = passes > 0 ? (T*)a.etab : nullptr;
+  enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax,
+                              etab);
   // Mixed-precision iterative refinement: the smoother's FP32 error is that
   // of a linear solve, so one more pass on the residual model about its own
-  // result (offsets formed in FP64) removes most of it; the factors do not
-  // change.  The change measure and the log-likelihood stay those of the
+  // result (offsets formed beyond FP32 precision) removes most of it; the
+  // factors do not change, so the pass's smoother recomputes only the means
+  // (refine_scan.cuh; the full scan where the level shape has no mean-only
+  // form).  The change measure and the log-likelihood stay those of the
   // first pass.
   for (int r = 0; r < passes; ++r) {
     {
@@ -109,7 +114,9 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
     if (r + 1 < passes) keep_prev();
     enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
                               a.partial2, status, s, a.prof);
-    enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, nullptr);
+    if (!etab || !enqueue_smoother_means<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, etab, status, s,
+                                                    a.prof))
+      enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, nullptr);
   }
 }
 

@@ -189,7 +189,8 @@ filter_leaf_down(DevLevel lv, DevSeqs sq, GV gv, const T* __restrict__ y,
 // rows) and fold them right to left with Table 5.
 template <typename T, int NX, int NY, typename GV, typename FO>
 __global__ void __launch_bounds__(kBlock)
-smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, FO fo, T* __restrict__ items) {
+smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, FO fo, T* __restrict__ items,
+                 T* __restrict__ etab) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n_chunks) return;
   constexpr int REC = SRec<NX>::size;
@@ -211,6 +212,9 @@ smoother_leaf_up(DevLevel lv, DevSeqs sq, GV gv, FO fo, T* __restrict__ items) {
       Gamma<T, NX, NY> g;
       g.load_transition(gv, sq.offsets[b] + k);
       smoother_element<T, NX, NY>(g, m, N, dst);
+      // E_k for the mean-only refinement passes (with the first words of g
+      // in the padding)
+      if (etab) vstore<T, ETab<NX>::size>(etab + e * ETab<NX>::size, dst + SRec<NX>::E);
     }
     if (j != cnt - 1) {
       smoother_combine<T, NX>(el, agg, tmp);
