@@ -148,34 +148,48 @@ adj_smoother_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
-  for (int j = 0; j < j1; ++j) {
+  // The RTS VJP of step j (the expensive part) and the map that carries the
+  // cotangent from step j to j + 1.  With one thread per step every lane of
+  // a warp first walks the maps before its own step, then all lanes take
+  // their VJP together (inside the walk each lane's VJP would come at a
+  // different trip and the warp would run it once per distinct step).
+  auto vjp = [&](int j) {
     const int64_t s = s0 + j, e = s + b;
     const T* rtg = (const T*)a.rtab + s * RT::size;
-    if (j >= jj) {
-      Gamma<T, NX, NY> g;
-      g.load_transition(gview<T>(a), s);
-      T mf[NX];
-      load<T, NX>((const T*)a.mf + e * NX, mf);
-      T df[X], gb[GR::size];
-      // FP32 holds the record in registers; FP64 reads it where it is used
-      // (twice the registers per value would spill).
-      T rtr[sizeof(T) == 4 ? RT::size : 4];
-      if constexpr (sizeof(T) == 4) vload<T, RT::size>(rtg, rtr);
-      const T* rt = sizeof(T) == 4 ? rtr : rtg;
-      rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
-      store<T, X>((T*)a.dfilt + e * X, df);
-      T* go = (T*)a.gbar + s * GR::size;
-      store<T, NX * NX>(go + GR::F, gb + GR::F);
-      store<T, NX>(go + GR::c, gb + GR::c);
-      store<T, NX * NX>(go + GR::L, gb + GR::L);
-    }
-    if (j + 1 < j1 || s == last) {
-      T G[RT::head], mp[REC], xn[X];
-      vload<T, RT::head>(rtg, G);
-      smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
-      map_apply<T, NX>(mp, x, xn);
-      copy<T, X>(xn, x);
-      if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
+    Gamma<T, NX, NY> g;
+    g.load_transition(gview<T>(a), s);
+    T mf[NX];
+    load<T, NX>((const T*)a.mf + e * NX, mf);
+    T df[X], gb[GR::size];
+    // FP32 holds the record in registers; FP64 reads it where it is used
+    // (twice the registers per value would spill).
+    T rtr[sizeof(T) == 4 ? RT::size : 4];
+    if constexpr (sizeof(T) == 4) vload<T, RT::size>(rtg, rtr);
+    const T* rt = sizeof(T) == 4 ? rtr : rtg;
+    rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
+    store<T, X>((T*)a.dfilt + e * X, df);
+    T* go = (T*)a.gbar + s * GR::size;
+    store<T, NX * NX>(go + GR::F, gb + GR::F);
+    store<T, NX>(go + GR::c, gb + GR::c);
+    store<T, NX * NX>(go + GR::L, gb + GR::L);
+  };
+  auto advance = [&](int j) {
+    const int64_t s = s0 + j, e = s + b;
+    T G[RT::head], mp[REC], xn[X];
+    vload<T, RT::head>((const T*)a.rtab + s * RT::size, G);
+    smoother_adj_map<T, NX>(G, (const T*)a.dir + (e + 1) * X, mp);
+    map_apply<T, NX>(mp, x, xn);
+    copy<T, X>(xn, x);
+    if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
+  };
+  if (per_step) {
+    for (int j = 0; j < jj; ++j) advance(j);
+    vjp(jj);
+    if (s0 + jj == last) advance(jj);
+  } else {
+    for (int j = 0; j < j1; ++j) {
+      vjp(j);
+      if (j + 1 < j1 || s0 + j == last) advance(j);
     }
   }
 }
@@ -242,28 +256,39 @@ adj_filter_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a
   T x[X];
   if (flag[c]) load<T, X>(carry + c * X, x);
   else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
-  for (int j = cnt - 1; j >= j1; --j) {
+  // The Kalman-step VJP of step j and the map that carries the cotangent
+  // from step j to j - 1; with one thread per step the lanes walk their maps
+  // first and take their VJPs together (as in adj_smoother_leaf_down).
+  auto vjp = [&](int j) {
     const int64_t s = s0 + j, e = s + b;
-    if (!per_step || j == jj) {
-      Gamma<T, NX, NY> g;
-      g.load_all(gview<T>(a), s);
-      T kt[KT::size], mprev[NX];
-      vload<T, KT::size>((const T*)a.ktab + s * KT::size, kt);
-      load<T, NX>((const T*)a.mf + e * NX, mprev);
-      KfQ<T, NX, NY> q;
-      q.load(kt);
-      T gb[GR::size];
-      T* go = (T*)a.gbar + s * GR::size;
-      load<T, GR::size>(go, gb);
-      kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
-      store<T, GR::size>(go, gb);
-    }
-    if (j > j1) {
-      T h[KT::head], mp[REC], xn[X];
-      vload<T, KT::head>((const T*)a.ktab + s * KT::size, h);
-      filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
-      map_apply<T, NX>(mp, x, xn);
-      copy<T, X>(xn, x);
+    Gamma<T, NX, NY> g;
+    g.load_all(gview<T>(a), s);
+    T kt[KT::size], mprev[NX];
+    vload<T, KT::size>((const T*)a.ktab + s * KT::size, kt);
+    load<T, NX>((const T*)a.mf + e * NX, mprev);
+    KfQ<T, NX, NY> q;
+    q.load(kt);
+    T gb[GR::size];
+    T* go = (T*)a.gbar + s * GR::size;
+    load<T, GR::size>(go, gb);
+    kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
+    store<T, GR::size>(go, gb);
+  };
+  auto advance = [&](int j) {
+    const int64_t s = s0 + j, e = s + b;
+    T h[KT::head], mp[REC], xn[X];
+    vload<T, KT::head>((const T*)a.ktab + s * KT::size, h);
+    filter_adj_map<T, NX, NY>(h, lbar, (const T*)a.dfilt + e * X, mp);
+    map_apply<T, NX>(mp, x, xn);
+    copy<T, X>(xn, x);
+  };
+  if (per_step) {
+    for (int j = cnt - 1; j > jj; --j) advance(j);
+    vjp(jj);
+  } else {
+    for (int j = cnt - 1; j >= j1; --j) {
+      vjp(j);
+      if (j > j1) advance(j);
     }
   }
 }
