@@ -381,13 +381,16 @@ __global__ void __launch_bounds__(kBlock)
 adj_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
             const int* __restrict__ fin, T* __restrict__ cout, int* __restrict__ fout) {
   constexpr int REC = MapRec<5>::size, X = XRec<5>::size;
+  static_assert(kChunkScan == kWarp && kBlock % kWarp == 0, "one chunk per warp");
+  __shared__ T SO[kBlock / kWarp][kWarp * X];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = tid / kChunkScan;
-  if (c >= lv.n_chunks) return;
+  if (c >= lv.n_chunks) return;   // uniform per warp
   const int j = (int)(tid - c * kChunkScan);
   const int cnt = lv.count[c];
-  if (j >= cnt) return;
-  const int64_t i = lv.first[c] + j;
+  const bool active = j < cnt;
+  const int64_t i0 = lv.first[c];
+  const int64_t i = i0 + j;
   const bool head = FWD ? j == 0 : j == cnt - 1;
   const int flag = fin[c];
   T x[X];
@@ -396,14 +399,15 @@ adj_down_cs(DevLevel lv, const T* __restrict__ items, const T* __restrict__ cin,
 #pragma unroll
     for (int k = 0; k < X; ++k) x[k] = T(0);
   }
-  if (!head) {
+  if (active && !head) {
     T mp[REC], xn[X];
     vload<T, REC>(items + (FWD ? i - 1 : i + 1) * REC, mp);
     map_apply<T, 5>(mp, x, xn);
     copy<T, X>(xn, x);
   }
-  store<T, X>(cout + i * X, x);
-  fout[i] = head ? flag : 1;
+  // the chunk's items are consecutive: their rows go out as one block
+  warp_store_rows<T, X>(cout + i0 * X, SO[threadIdx.x / kWarp], x, j, cnt, active);
+  if (active) fout[i] = head ? flag : 1;
 }
 
 // Top of an adjoint scan: one block per sequence scans the sequence's items

@@ -321,6 +321,21 @@ SQSM_DEV void warp_store_carries(T* __restrict__ g, T* sh, const T* b, const T* 
   }
 }
 
+// The W-value rows of one chunk's cnt consecutive items (lane j holding item
+// j's row v) written to their contiguous block g: staged in the warp's
+// shared rows sh, then stored lane-strided, each store instruction covering
+// consecutive words.
+template <typename T, int W>
+SQSM_DEV void warp_store_rows(T* __restrict__ g, T* sh, const T* v, int j, int cnt, bool active) {
+  const int lane = threadIdx.x % kWarp;
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) sh[j * W + k] = v[k];
+  }
+  __syncwarp();
+  for (int k = lane; k < cnt * W; k += kWarp) g[k] = sh[k];
+}
+
 // One thread per item of the level; each warp is one chunk.
 template <typename T, int NX>
 __global__ void __launch_bounds__(kBlock)
