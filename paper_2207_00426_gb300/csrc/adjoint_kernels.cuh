@@ -464,7 +464,7 @@ adj_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items
 // 2 unscented, 3 Gauss-Hermite (recomputed from the nominal rows).
 template <typename T, int LIN = 0>
 SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>* __restrict__ Pp,
-                          const AdjBufs& a, T* __restrict__ lam_out, double* th) {
+                          const AdjBufs& a, T* o, T* d, double* th) {
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
   using GR = GRec<NX, NY>;
   using ST = SlrTab<NX, NY>;
@@ -537,19 +537,16 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
     th[0] += 2.0 * (double)P.sigma[0] * (double)P.sigma[0] * (double)Lb[0];
     th[3] += 2.0 * (double)P.sigma[1] * (double)P.sigma[1] * (double)Lb[3];
   }
-  T o[X];
 #pragma unroll
   for (int i = 0; i < NX; ++i) o[i] = mb[i];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int q = 0; q < NX; ++q) o[NX + r * NX + q] = q <= r ? Nb[r * NX + q] : T(0);
-  store<T, X>(lam_out + e * X, o);
   // the next iteration's direct cotangents of this row (step 1)
-  T L[NX * NX], d[X];
+  T L[NX * NX];
   load_lower<T, NX>((const T*)a.Ns + e * NX * NX, L);
   direct_row<T, NX>(L, o, d);
-  store<T, X>((T*)a.dir + e * X, d);
 }
 
 // Sum of four values over the block (kBlock threads) in a fixed order,
@@ -583,12 +580,29 @@ template <typename T, int LIN = 0>
 __global__ void __launch_bounds__(kBlock)
 adj_slr_kernel(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp, AdjBufs a,
                T* __restrict__ lam_out, double* __restrict__ th_partial) {
+  constexpr int X = XRec<5>::size;
+  __shared__ T SO[kBlock / kWarp][kWarp * X];
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ch = tid / leaf;
   const int jr = (int)(tid - ch * leaf);
   double th[4] = {0.0, 0.0, 0.0, 0.0};
-  if (ch < lv.n_chunks && jr < lv.count[ch])
-    adj_slr_row<T, LIN>(lv.first[ch] + jr, lv.seq[ch], sq, Pp, a, lam_out, th);
+  const bool active = ch < lv.n_chunks && jr < lv.count[ch];
+  const int64_t e = active ? lv.first[ch] + jr : 0;
+  T o[X], d[X];
+  if (active) adj_slr_row<T, LIN>(e, lv.seq[ch], sq, Pp, a, o, d, th);
+  // The rows of a warp's active lanes are consecutive and increase with the
+  // lane (chunks of consecutive rows; only a sequence's last chunk is
+  // short): the two rows of each lane go out as two blocks through shared
+  // memory, every store instruction covering consecutive words.
+  const unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (mask) {
+    const int64_t e_lo = __shfl_sync(0xffffffffu, e, __ffs(mask) - 1);
+    const int na = __popc(mask), r = active ? (int)(e - e_lo) : 0;
+    T* sh = SO[threadIdx.x / kWarp];
+    warp_store_rows<T, X>(lam_out + e_lo * X, sh, o, r, na, active);
+    __syncwarp();
+    warp_store_rows<T, X>((T*)a.dir + e_lo * X, sh, d, r, na, active);
+  }
   block_sum4(th, th_partial + 4 * blockIdx.x);
 }
 
