@@ -241,25 +241,29 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 adj_filter_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a, T lbar,
                      const T* __restrict__ carry, const int* __restrict__ flag) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t c = per_step ? tid / leaf : tid;
-  if (c >= lv.n_chunks) return;
-  const int cnt = lv.count[c];
-  const int jj = per_step ? (int)(tid - c * leaf) : 0;
-  if (jj >= cnt) return;
-  const int j1 = per_step ? jj : 0;   // steps cnt-1 .. j1 are walked
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
   using KT = KfTab<NX, NY>;
-  const int b = lv.seq[c];
-  const int64_t s0 = lv.first[c];
+  // FP32 moves the gbar records of a warp's steps through shared memory
+  // (FP64 records would not fit beside the block's other data)
+  constexpr bool STAGE = sizeof(T) == 4;
+  __shared__ T SG[STAGE ? kBlock * GR::size : 1];
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = per_step ? tid / leaf : tid;
+  const bool in = c < lv.n_chunks;
+  const int cnt = in ? lv.count[c] : 0;
+  const int jj = per_step ? (int)(tid - c * leaf) : 0;
+  const bool active = in && jj < cnt;
+  const int b = active ? lv.seq[c] : 0;
+  const int64_t s0 = active ? lv.first[c] : 0;
   T x[X];
-  if (flag[c]) load<T, X>(carry + c * X, x);
-  else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
-  // The Kalman-step VJP of step j and the map that carries the cotangent
-  // from step j to j - 1; with one thread per step the lanes walk their maps
-  // first and take their VJPs together (as in adj_smoother_leaf_down).
-  auto vjp = [&](int j) {
+  if (active) {
+    if (flag[c]) load<T, X>(carry + c * X, x);
+    else load<T, X>((const T*)a.dfilt + (s0 + cnt - 1 + b + 1) * X, x);
+  }
+  // The Kalman-step VJP of step j on the record at go and the map that
+  // carries the cotangent from step j to j - 1.
+  auto vjp = [&](int j, T* go) {
     const int64_t s = s0 + j, e = s + b;
     Gamma<T, NX, NY> g;
     g.load_all(gview<T>(a), s);
@@ -269,7 +273,6 @@ adj_filter_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a
     KfQ<T, NX, NY> q;
     q.load(kt);
     T gb[GR::size];
-    T* go = (T*)a.gbar + s * GR::size;
     load<T, GR::size>(go, gb);
     kf_vjp<T, NX, NY>(q, g, mprev, lbar, x, gb);
     store<T, GR::size>(go, gb);
@@ -282,14 +285,38 @@ adj_filter_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a
     map_apply<T, NX>(mp, x, xn);
     copy<T, X>(xn, x);
   };
-  if (per_step) {
-    for (int j = cnt - 1; j > jj; --j) advance(j);
-    vjp(jj);
-  } else {
-    for (int j = cnt - 1; j >= j1; --j) {
-      vjp(j);
-      if (j > j1) advance(j);
+  T* gbar = (T*)a.gbar;
+  if (!per_step) {   // one thread walks its whole chunk
+    if (!active) return;
+    for (int j = cnt - 1; j >= 0; --j) {
+      vjp(j, gbar + (s0 + j) * GR::size);
+      if (j > 0) advance(j);
     }
+    return;
+  }
+  // One thread per step: the lanes walk their maps first and take their VJPs
+  // together (as in adj_smoother_leaf_down).
+  if (active)
+    for (int j = cnt - 1; j > jj; --j) advance(j);
+  const int64_t s = s0 + jj;
+  if constexpr (STAGE) {
+    // The steps of a warp's active lanes are consecutive and increase with
+    // the lane (chunks of consecutive steps; only a sequence's last chunk is
+    // short): their records are read and written as one block.
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (mask == 0) return;   // uniform per warp
+    const int lane = threadIdx.x % kWarp;
+    const int64_t s_lo = __shfl_sync(0xffffffffu, s, __ffs(mask) - 1);
+    const int na = __popc(mask);
+    T* sh = SG + (threadIdx.x / kWarp) * kWarp * GR::size;
+    T* gw = gbar + s_lo * GR::size;
+    for (int k = lane; k < na * GR::size; k += kWarp) sh[k] = gw[k];
+    __syncwarp();
+    if (active) vjp(jj, sh + (int)(s - s_lo) * GR::size);
+    __syncwarp();
+    for (int k = lane; k < na * GR::size; k += kWarp) gw[k] = sh[k];
+  } else {
+    if (active) vjp(jj, gbar + s * GR::size);
   }
 }
 
