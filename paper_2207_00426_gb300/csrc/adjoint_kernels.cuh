@@ -132,28 +132,30 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 adj_smoother_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs a,
                        const T* __restrict__ carry, const int* __restrict__ flag) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t c = per_step ? tid / leaf : tid;
-  if (c >= lv.n_chunks) return;
-  const int cnt = lv.count[c];
-  const int jj = per_step ? (int)(tid - c * leaf) : 0;
-  if (jj >= cnt) return;
-  const int j1 = per_step ? jj + 1 : cnt;   // steps [jj0, j1) take their VJP
   constexpr int NX = 5, NY = 2, X = XRec<NX>::size, REC = MapRec<NX>::size;
   using GR = GRec<NX, NY>;
   using RT = RtsTab<NX>;
-  const int b = lv.seq[c];
-  const int64_t s0 = lv.first[c];
-  const int64_t last = sq.offsets[b + 1] - 1;
+  // FP32 writes the gbar records of a warp's steps through shared memory
+  constexpr bool STAGE = sizeof(T) == 4;
+  __shared__ T SG[STAGE ? kBlock * GR::size : 1];
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = per_step ? tid / leaf : tid;
+  const bool in = c < lv.n_chunks;
+  const int cnt = in ? lv.count[c] : 0;
+  const int jj = per_step ? (int)(tid - c * leaf) : 0;
+  const bool active = in && jj < cnt;
+  const int b = active ? lv.seq[c] : 0;
+  const int64_t s0 = active ? lv.first[c] : 0;
+  const int64_t last = active ? sq.offsets[b + 1] - 1 : -1;
   T x[X];
-  if (flag[c]) load<T, X>(carry + c * X, x);
-  else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
-  // The RTS VJP of step j (the expensive part) and the map that carries the
-  // cotangent from step j to j + 1.  With one thread per step every lane of
-  // a warp first walks the maps before its own step, then all lanes take
-  // their VJP together (inside the walk each lane's VJP would come at a
-  // different trip and the warp would run it once per distinct step).
-  auto vjp = [&](int j) {
+  if (active) {
+    if (flag[c]) load<T, X>(carry + c * X, x);
+    else load<T, X>((const T*)a.dir + (s0 + b) * X, x);
+  }
+  // The RTS VJP of step j (the expensive part), writing its record part
+  // F | c | Lambda at go, and the map that carries the cotangent from step j
+  // to j + 1.
+  auto vjp = [&](int j, T* go) {
     const int64_t s = s0 + j, e = s + b;
     const T* rtg = (const T*)a.rtab + s * RT::size;
     Gamma<T, NX, NY> g;
@@ -168,7 +170,6 @@ adj_smoother_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs
     const T* rt = sizeof(T) == 4 ? rtr : rtg;
     rts_vjp<T, NX, NY>(rt, g.F, mf, x, df, gb);
     store<T, X>((T*)a.dfilt + e * X, df);
-    T* go = (T*)a.gbar + s * GR::size;
     store<T, NX * NX>(go + GR::F, gb + GR::F);
     store<T, NX>(go + GR::c, gb + GR::c);
     store<T, NX * NX>(go + GR::L, gb + GR::L);
@@ -182,14 +183,47 @@ adj_smoother_leaf_down(DevLevel lv, int leaf, bool per_step, DevSeqs sq, AdjBufs
     copy<T, X>(xn, x);
     if (s == last) store<T, X>((T*)a.dfilt + (e + 1) * X, x);   // k = n: dmf_n = x_n
   };
-  if (per_step) {
+  T* gbar = (T*)a.gbar;
+  if (!per_step) {   // one thread walks its whole chunk
+    if (!active) return;
+    for (int j = 0; j < cnt; ++j) {
+      vjp(j, gbar + (s0 + j) * GR::size);
+      if (j + 1 < cnt || s0 + j == last) advance(j);
+    }
+    return;
+  }
+  // One thread per step: every lane first walks the maps before its own
+  // step, then all lanes take their VJP together (inside the walk each
+  // lane's VJP would come at a different trip and the warp would run it once
+  // per distinct step).
+  if (active)
     for (int j = 0; j < jj; ++j) advance(j);
-    vjp(jj);
-    if (s0 + jj == last) advance(jj);
+  const int64_t s = s0 + jj;
+  if constexpr (STAGE) {
+    // The steps of a warp's active lanes are consecutive and increase with
+    // the lane: their records go out as one block.  The observation part
+    // H | d | Omega is written as zeros here; the filter adjoint, which runs
+    // next, assigns it.
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (mask == 0) return;   // uniform per warp
+    const int lane = threadIdx.x % kWarp;
+    const int64_t s_lo = __shfl_sync(0xffffffffu, s, __ffs(mask) - 1);
+    const int na = __popc(mask);
+    T* sh = SG + (threadIdx.x / kWarp) * kWarp * GR::size;
+    if (active) {
+      T* rec = sh + (int)(s - s_lo) * GR::size;
+      vjp(jj, rec);
+#pragma unroll
+      for (int k = GR::H; k < GR::size; ++k) rec[k] = T(0);
+      if (s == last) advance(jj);
+    }
+    __syncwarp();
+    T* gw = gbar + s_lo * GR::size;
+    for (int k = lane; k < na * GR::size; k += kWarp) gw[k] = sh[k];
   } else {
-    for (int j = 0; j < j1; ++j) {
-      vjp(j);
-      if (j + 1 < j1 || s0 + j == last) advance(j);
+    if (active) {
+      vjp(jj, gbar + s * GR::size);
+      if (s == last) advance(jj);
     }
   }
 }
