@@ -196,3 +196,36 @@ def test_full_size_fp32_accuracy_against_fp64(B):
         assert abs(out[0][1] - out[1][1]) < 1e-5 * abs(out[1][1])
     c32.close()
     c64.close()
+
+
+@pytest.mark.parametrize("model", ["ct", "population"])
+def test_refinement_passes_leave_fp64_unchanged(B, model):
+    """In FP64 the linear smoother's error is already at rounding level, so
+    one or two refinement passes (a residual filter pass and the mean-only
+    smoother scan that reuses the first pass's E_k) must leave the means, the
+    factors and the log-likelihood as the unrefined solve has them, to
+    rounding -- on a ragged batch of the CT model (n_x = 5) and of the
+    population model (n_x = 1)."""
+    f64 = torch.float64
+    if model == "ct":
+        d = W.ct_batch(lengths=[700, 45, 1300], seed=19)
+        call = lambda c: B.sqsm_ipls_smooth(c, d["theta"], _dev(d["y"], f64), d["offsets"],
+                                            _dev(d["m0"], f64), _dev(d["N0"], f64), 6, 0,
+                                            dt=d["dt"])
+    else:
+        d = W.ricker_batch([400, 33, 900], seed=29)
+        call = lambda c: B.sqsm_ipls_smooth_population(c, d["theta"], _dev(d["y"], f64),
+                                                       d["offsets"], _dev(d["m0"], f64),
+                                                       _dev(d["N0"], f64), 6, 0)
+    out = {}
+    for refine in (0, 1, 2):
+        c = B.Context(0, refine=refine)
+        ms, Ns, ll = call(c)
+        torch.cuda.synchronize()
+        assert c.status() == 0
+        out[refine] = (ms.cpu().numpy(), Ns.cpu().numpy(), ll.cpu().numpy())
+        c.close()
+    for refine in (1, 2):
+        assert rel_mean_err(out[refine][0], out[0][0]) < 1e-10
+        assert rel_cov_err(out[refine][1], out[0][1]) < 1e-10
+        assert np.allclose(out[refine][2], out[0][2], rtol=1e-11, atol=0)
