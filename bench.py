@@ -41,6 +41,7 @@ import json
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -78,7 +79,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--studies", action="store_true",
                     help="also run the paper's further experiments (minutes)")
-    ap.add_argument("--studies-out", default=os.path.join("gpurun_out", "bench_studies.json"))
+    ap.add_argument("--studies-out",
+                    default=os.path.join(tempfile.gettempdir(), "bench_studies.json"))
     return ap.parse_args()
 
 

@@ -11,7 +11,9 @@
 // table the full pass's leaf up-sweep wrote), so the means equal those of a
 // full pass bit for bit while no Tria runs.  The factors already held in the
 // rows are left as the full pass wrote them; the D fields of the scan
-// records and carries are not written (nothing reads them in this pass).
+// records and carries are not recomputed (the words these kernels store
+// whole are zeroed or left stale there, and nothing reads them in this
+// pass).
 #pragma once
 
 #include "wscan.cuh"
