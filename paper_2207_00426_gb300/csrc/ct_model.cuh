@@ -566,8 +566,18 @@ SQSM_DEV void gauss_hermite_regress(const T* m, const T* N, const T* gm, bool su
 // Steps are independent: one thread per step, addressed as (leaf chunk,
 // position in chunk) so that the chunk table gives the sequence; launch
 // n_chunks * leaf threads.
+//
+// Resident blocks per SM the kernel is compiled for: in FP32 the cubature,
+// Taylor and unscented rules take five (96 registers, a spill of a few
+// words), whose extra warps hide more of the latency of the
+// transcendental-heavy model code (5-8% faster than at 120 registers);
+// FP64 and the 243-point Gauss-Hermite rule keep their registers.
+template <typename T, int LIN> constexpr int slr_min_blocks() {
+  return sizeof(T) == 4 && LIN != 3 ? 5 : 1;
+}
+
 template <typename T, bool PACKED, typename NO, int LIN, bool TB = false>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, (slr_min_blocks<T, LIN>()))
 ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restrict__ Pp,
               int centered, NO nom, const T* __restrict__ y, T* __restrict__ F,
               T* __restrict__ c, T* __restrict__ SQo, T* __restrict__ H, T* __restrict__ d,
