@@ -73,6 +73,20 @@ def smoother_apply(nx):
     return 2 * nx * nx + nx + tri_mm(nx, nx) + tria(nx, 2 * nx)
 
 
+# The mean-only smoother of the refinement passes (E_k read back, no Tria):
+# g = m^f - E (F m^f + c); E_ij = E_i E_j, g_ij = E_i g_j + g_i; g <- E g + g_i.
+def smoother_element_g(nx):
+    return 4 * nx * nx + 2 * nx
+
+
+def smoother_combine_g(nx):
+    return 2 * nx ** 3 + 2 * nx * nx + nx
+
+
+def smoother_apply_g(nx):
+    return 2 * nx * nx + nx
+
+
 # CT cubature SLR: per sigma point the transition difference costs two turn
 # coefficient evaluations (sincos x2, series or divide) and ~24 flops; a
 # bearing difference costs ~8 flops + atan2 per sensor.
@@ -133,8 +147,10 @@ def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cu
                       refine=0):
     """Algorithmic flops per launch of each kernel family for one IPLS
     iteration over sequences of the given lengths; with `refine` passes the
-    filter and smoother scans run 1 + refine times per iteration.  Returns
-    {family: (flops per launch, launches per iteration)}."""
+    filter scan runs 1 + refine times per iteration in full and the smoother
+    scan once in full and `refine` times mean-only (flops per launch then
+    the average over its passes).  Returns {family: (flops per launch,
+    launches per iteration)}."""
     out = {}
     nsteps = sum(lengths)
     leaf = default_leaf(nsteps) if leaf is None else leaf
@@ -151,19 +167,31 @@ def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cu
         out["filter_up"] = (sum(ups) / len(ups), len(ups))
         out["filter_down"] = (sum(downs) / len(downs), len(downs))
     out["filter_leaf_down"] = (nsteps * kf_step(nx, ny), 1)
-    se, sc, sa = smoother_element(nx), smoother_combine(nx), smoother_apply(nx)
     nel = nsteps + len(lengths)
-    if len(sl) > 1:
-        out["smoother_leaf_up"] = (sum(c * se + (c - 1) * sc for c in sl[0])
-                                   - len(lengths) * se, 1)
-    ups = [sum((c - 1) * sc for c in lv) for lv in sl[1:]]
-    downs = [sum((c - 1) * sa for c in lv) for lv in sl[1:]]
-    if ups:
-        out["smoother_up"] = (sum(ups) / len(ups), len(ups))
-        out["smoother_down"] = (sum(downs) / len(downs), len(downs))
-    out["smoother_leaf_down"] = ((nel - len(lengths)) * (se + sa), 1)
+
+    def smoother(se, sc, sa):
+        sm = {}
+        if len(sl) > 1:
+            sm["smoother_leaf_up"] = (sum(c * se + (c - 1) * sc for c in sl[0])
+                                      - len(lengths) * se, 1)
+        ups = [sum((c - 1) * sc for c in lv) for lv in sl[1:]]
+        downs = [sum((c - 1) * sa for c in lv) for lv in sl[1:]]
+        if ups:
+            sm["smoother_up"] = (sum(ups) / len(ups), len(ups))
+            sm["smoother_down"] = (sum(downs) / len(downs), len(downs))
+        sm["smoother_leaf_down"] = ((nel - len(lengths)) * (se + sa), 1)
+        return sm
+    full = smoother(smoother_element(nx), smoother_combine(nx), smoother_apply(nx))
+    out.update(full)
     if refine:
-        out = {k: (f, n * (1 + refine) if k != "ct_slr" else n) for k, (f, n) in out.items()}
+        # each refinement pass: the filter scan again in full, the smoother
+        # scan mean-only (chunk-scan level shapes, the default ones)
+        out = {k: (f, n * (1 + refine)) if k.startswith("filter") else (f, n)
+               for k, (f, n) in out.items()}
+        mean = smoother(smoother_element_g(nx), smoother_combine_g(nx), smoother_apply_g(nx))
+        for k, (f, n) in full.items():
+            fg, _ = mean[k]
+            out[k] = ((f + refine * fg) / (1 + refine), n * (1 + refine))
     return out
 
 
