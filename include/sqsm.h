@@ -156,8 +156,13 @@ typedef struct {
                            TwoSum / Dot2 arithmetic, in FP64 in FP64;
                            rounded once) and smoothed again in the call's dtype,
                            the correction added to the trajectory.  Each
-                           pass costs one more filter and smoother scan;
-                           it removes most of the FP32 error of the linear
+                           pass costs one more filter scan and a smoother
+                           scan of the means alone (the factors do not
+                           change; in FP32 with at most 64 sequences and
+                           n_x >= 3 the filter scan's top levels too,
+                           replayed from what
+                           the first pass stores: about 3.4 MB at
+                           n = 1e5); it removes most of the FP32 error of the linear
                            solve, which a non-converging Alg. 3 amplifies
                            from iteration to iteration.  Deviation
                            coordinates only (ignored with absolute).

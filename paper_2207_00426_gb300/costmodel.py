@@ -87,6 +87,22 @@ def smoother_apply_g(nx):
     return 2 * nx * nx + nx
 
 
+# The mean-only upper filter levels of the refinement passes: b_ij, eta_ij of
+# Table 3 from the factors the full pass stored -- three triangular products
+# with U_i, two with Z_j, three full ones (A_j (I - U_i G^T), G, A_i^T) and
+# five vector sums.  The library takes that form, in FP32, for levels of at
+# most CS3_MAX_CHUNKS chunks (the three-role chunk levels and the top) when a
+# batch has at most FMEANS_MAX_SEQS sequences and the state at least
+# FMEANS_MIN_NX entries.
+CS3_MAX_CHUNKS = 512
+FMEANS_MAX_SEQS = 64
+FMEANS_MIN_NX = 3
+
+
+def filter_combine_means(nx):
+    return 5 * nx * (nx + 1) + 6 * nx * nx + 5 * nx
+
+
 # CT cubature SLR: per sigma point the transition difference costs two turn
 # coefficient evaluations (sincos x2, series or divide) and ~24 flops; a
 # bearing difference costs ~8 flops + atan2 per sensor.
@@ -147,10 +163,11 @@ def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cu
                       refine=0):
     """Algorithmic flops per launch of each kernel family for one IPLS
     iteration over sequences of the given lengths; with `refine` passes the
-    filter scan runs 1 + refine times per iteration in full and the smoother
-    scan once in full and `refine` times mean-only (flops per launch then
-    the average over its passes).  Returns {family: (flops per launch,
-    launches per iteration)}."""
+    filter scan runs 1 + refine times per iteration (its latency-bound upper
+    levels mean-only in the refinement passes of a batch of at most
+    FMEANS_MAX_SEQS sequences; FP32) and the smoother scan once in full and
+    `refine` times mean-only (flops per launch then the average over its
+    passes).  Returns {family: (flops per launch, launches per iteration)}."""
     out = {}
     nsteps = sum(lengths)
     leaf = default_leaf(nsteps) if leaf is None else leaf
@@ -184,10 +201,17 @@ def ipls_kernel_flops(lengths, nx=5, ny=2, leaf=None, radix=0, linearization="cu
     full = smoother(smoother_element(nx), smoother_combine(nx), smoother_apply(nx))
     out.update(full)
     if refine:
-        # each refinement pass: the filter scan again in full, the smoother
-        # scan mean-only (chunk-scan level shapes, the default ones)
+        # each refinement pass: the filter scan again (its small upper levels
+        # mean-only for few sequences), the smoother scan mean-only
+        # (chunk-scan level shapes, the default ones)
         out = {k: (f, n * (1 + refine)) if k.startswith("filter") else (f, n)
                for k, (f, n) in out.items()}
+        if ups and len(lengths) <= FMEANS_MAX_SEQS and nx >= FMEANS_MIN_NX:
+            fm = filter_combine_means(nx)
+            ups_r = [sum((c - 1) * (fm if len(lv) <= CS3_MAX_CHUNKS else fc) for c in lv)
+                     for lv in fl[1:]]
+            out["filter_up"] = ((sum(ups) + refine * sum(ups_r)) / (len(ups) * (1 + refine)),
+                                len(ups) * (1 + refine))
         mean = smoother(smoother_element_g(nx), smoother_combine_g(nx), smoother_apply_g(nx))
         for k, (f, n) in full.items():
             fg, _ = mean[k]

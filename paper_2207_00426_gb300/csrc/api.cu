@@ -51,6 +51,8 @@ struct Workspace {
   void* prevrows = nullptr;  // refinement: nominal rows before the last smoother pass
   double* partial2 = nullptr;   // refinement passes' log-likelihood partials
   void* etab = nullptr;      // refinement: E_k of every state row (mean-only passes)
+  void* ftab = nullptr;      // refinement: the filter's stored combine factors (mean-only
+                             // upper levels; null where the plan has none)
   bool ipls_ready = false;
   // NLL + gradient
   AdjArgs adj{};
@@ -366,13 +368,19 @@ bool ensure_ipls(Workspace* w, const Plan* p, int dtype, int nx = 5, int ny = 2)
   return true;
 }
 
-// The per-row E_k table of the mean-only refinement passes, made when a
-// context with refinement first uses the workspace.
-bool ensure_etab(Workspace* w, const Plan* p, int dtype, int nx) {
-  if (w->etab) return true;
+// The tables of the mean-only refinement passes, made when a context with
+// refinement first uses the workspace: the smoother's per-row E_k and, where
+// the plan's filter levels take the mean-only form (fmeans_layout), the
+// filter's stored combine factors.
+bool ensure_refine_tabs(Workspace* w, const Plan* p, int dtype, int nx) {
   const size_t es = dtype == SQSM_F64 ? 8 : 4;
-  w->etab = w->mem.get(es * ((nx * nx + 3) / 4 * 4) * p->smth.n_items[0]);
-  return w->etab != nullptr;
+  if (!w->etab) w->etab = w->mem.get(es * ((nx * nx + 3) / 4 * 4) * p->smth.n_items[0]);
+  if (!w->etab) return false;
+  if (w->ftab) return true;
+  const FMeansLayout f = fmeans_layout(p->filt, es, nx);
+  if (!f.on) return true;
+  w->ftab = w->mem.get(es * f.size);
+  return w->ftab != nullptr;
 }
 
 bool ensure_adj(Workspace* w, const Plan* p, int dtype) {
@@ -646,6 +654,7 @@ IplsArgs make_ipls_args(const Plan* p, const Workspace* w, const sqsm_model* mod
   a.prevrows = w->prevrows;
   a.partial2 = w->partial2;
   a.etab = w->etab;
+  a.ftab = w->ftab;
   return a;
 }
 
@@ -762,7 +771,7 @@ int choose_ipls_shape(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const d
     if (!p) continue;
     Workspace* w = get_ws(p, dtype, 5);
     const void* n0 = w && ensure_ipls(w, p, dtype) &&
-                             (ctx->opt.refine == 0 || ensure_etab(w, p, dtype, 5))
+                             (ctx->opt.refine == 0 || ensure_refine_tabs(w, p, dtype, 5))
                          ? prior_input(ctx, w, p, dtype, 5, N0)
                          : nullptr;
     if (!n0) {
@@ -867,7 +876,7 @@ int sqsm_ipls_smooth(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const do
   const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
   Workspace* w = get_ws(p, dtype, nx);
   if (!w || !ensure_ipls(w, p, dtype, nx, ny) ||
-      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, nx)))
+      (ctx->opt.refine > 0 && !ensure_refine_tabs(w, p, dtype, nx)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
@@ -982,7 +991,7 @@ int sqsm_ipls_smooth_tol(sqsm_ctx* ctx, int dtype, const sqsm_model* model, cons
   const int nx = pop ? 1 : 5, ny = pop ? 1 : 2;
   Workspace* w = get_ws(p, dtype, nx);
   if (!w || !ensure_ipls(w, p, dtype, nx, ny) ||
-      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, nx)))
+      (ctx->opt.refine > 0 && !ensure_refine_tabs(w, p, dtype, nx)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, nx, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
@@ -1165,7 +1174,7 @@ static int nll_grad_run(sqsm_ctx* ctx, int dtype, const sqsm_model* model, const
   if (!p) return fail(ctx, SQSM_ERR_NO_MEMORY, "plan allocation failed");
   Workspace* w = get_ws(p, dtype, 5);
   if (!w || !ensure_ipls(w, p, dtype) || !ensure_adj(w, p, dtype) ||
-      (ctx->opt.refine > 0 && !ensure_etab(w, p, dtype, 5)))
+      (ctx->opt.refine > 0 && !ensure_refine_tabs(w, p, dtype, 5)))
     return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");
   const void* n0 = prior_input(ctx, w, p, dtype, 5, N0);
   if (!n0) return fail(ctx, SQSM_ERR_NO_MEMORY, "workspace");

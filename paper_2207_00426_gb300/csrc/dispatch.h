@@ -49,6 +49,8 @@ struct IplsArgs {
   void* prevrows = nullptr;
   double* partial2 = nullptr;
   void* etab = nullptr;   // E_k per state row for the mean-only passes (null: full passes)
+  void* ftab = nullptr;   // factors of the filter's latency-bound combines (FMeansTab;
+                          // null: full filter passes)
 };
 
 // Everything of Alg. 3 after the parameter kernel; capturable.

@@ -198,8 +198,14 @@ template <int NX> struct SRec {
   static constexpr int E = 0, g = NX * NX, D = NX * NX + NX,
                        size = (2 * NX * NX + NX + 3) / 4 * 4;
 };
+// A Table 3 combine's gain G and A_j (I - U_i G^T), as the full filter pass
+// stores them for the mean-only refinement passes (padded to 16 bytes).
+template <int NX> struct FGm {
+  static constexpr int G = 0, M = NX * NX, size = (2 * NX * NX + 3) / 4 * 4;
+};
 inline int frec_size(int nx) { return (3 * nx * nx + 2 * nx + 3) / 4 * 4; }
 inline int srec_size(int nx) { return (2 * nx * nx + nx + 3) / 4 * 4; }
+inline int fgm_size(int nx) { return (2 * nx * nx + 3) / 4 * 4; }
 // Run-time sizes of PRec<nx, ny> and XRow<nx> (same formulas).
 inline int prec_size(int nx, int ny) {
   const int h = (nx * nx + nx + nx * (nx + 1) / 2 + 3) / 4 * 4;
@@ -484,6 +490,38 @@ SQSM_DEV void xi_gain(const T* Zj, const T* Mx, const T* X11, T* G) {
   rsolve<T, NX, NX>(G, X11);
 }
 
+// b_ij and eta_ij of Table 3 from the combine's factors: A_i, U_i, Z_j, the
+// gain G and A_j (I - U_i G^T) (see filter_combine).  The full operator and
+// the mean-only refinement passes (which read the factors back from a
+// table) both take this path, so the two give the same values bit for bit.
+template <typename T, int NX>
+SQSM_DEV void filter_combine_means(const T* Ai, const T* Ui, const T* Zj, const T* G,
+                                   const T* AjM, const T* bi, const T* etai, const T* bj,
+                                   const T* etaj, T* bo, T* etao) {
+  // b_ij
+  T t[NX], u[NX];
+  mtv<T, NX, NX>(Ui, etaj, t);
+  mv<T, NX, NX>(Ui, t, u);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) u[i] += bi[i];
+  mv<T, NX, NX>(AjM, u, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) bo[i] = t[i] + bj[i];
+  // eta_ij
+  T sv[NX], r[NX];
+  mtv<T, NX, NX>(Zj, bi, sv);
+  mv<T, NX, NX>(Zj, sv, r);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) r[i] = etaj[i] - r[i];
+  mtv<T, NX, NX>(Ui, r, t);
+  mv<T, NX, NX>(G, t, sv);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) r[i] -= sv[i];
+  mtv<T, NX, NX>(Ai, r, t);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) etao[i] = t[i] + etai[i];
+}
+
 // Filter operator of Lemma 2 / Table 3 (right column) on full elements:
 // out = e_i (x) e_j.  out must not alias the inputs.
 //   G = Xi_21 Xi_11^{-1} (so that Xi_11^{-T} Xi_21^T = G^T),
@@ -495,9 +533,11 @@ SQSM_DEV void xi_gain(const T* Zj, const T* Mx, const T* X11, T* G) {
 //   Z_ij = Tria([A_i^T Xi_22, Z_i])  (with Xi_22 -> W, see above).
 // PARTS selects the fields computed (bit 0: A, b, eta; bit 1: U; bit 2: Z),
 // so that three threads can each take one part of a combine, each forming
-// only the factors its part needs.
+// only the factors its part needs.  With gm (part 0) the combine's G and
+// A_j (I - U_i G^T) are also stored there (FGm layout), for the mean-only
+// passes that replay b_ij and eta_ij.
 template <typename T, int NX, int PARTS = 7>
-SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
+SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out, T* gm = nullptr) {
   using R = FRec<NX>;
   constexpr int C2 = 2 * NX;
   constexpr bool ABE = PARTS & 1, UU = PARTS & 2, ZZ = PARTS & 4;
@@ -524,28 +564,19 @@ SQSM_DEV void filter_combine(const T* ei, const T* ej, T* out) {
     T AjM[NX * NX];
     mm<T, NX, NX, NX>(ej + R::A, Mi, AjM);
     mm<T, NX, NX, NX>(AjM, ei + R::A, out + R::A);
-    // b_ij
-    T t[NX], u[NX];
-    mtv<T, NX, NX>(Ui, ej + R::eta, t);
-    mv<T, NX, NX>(Ui, t, u);
+    filter_combine_means<T, NX>(ei + R::A, Ui, Zj, G, AjM, ei + R::b, ei + R::eta, ej + R::b,
+                                ej + R::eta, out + R::b, out + R::eta);
+    if (gm) {
+      T v[FGm<NX>::size];
 #pragma unroll
-    for (int i = 0; i < NX; ++i) u[i] += ei[R::b + i];
-    mv<T, NX, NX>(AjM, u, t);
+      for (int i = 0; i < NX * NX; ++i) {
+        v[FGm<NX>::G + i] = G[i];
+        v[FGm<NX>::M + i] = AjM[i];
+      }
 #pragma unroll
-    for (int i = 0; i < NX; ++i) out[R::b + i] = t[i] + ej[R::b + i];
-    // eta_ij
-    T sv[NX], r[NX];
-    mtv<T, NX, NX>(Zj, ei + R::b, sv);
-    mv<T, NX, NX>(Zj, sv, r);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) r[i] = ej[R::eta + i] - r[i];
-    mtv<T, NX, NX>(Ui, r, t);
-    mv<T, NX, NX>(G, t, sv);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) r[i] -= sv[i];
-    mtv<T, NX, NX>(ei + R::A, r, t);
-#pragma unroll
-    for (int i = 0; i < NX; ++i) out[R::eta + i] = t[i] + ei[R::eta + i];
+      for (int i = 2 * NX * NX; i < FGm<NX>::size; ++i) v[i] = T(0);
+      vstore<T, FGm<NX>::size>(gm, v);
+    }
   }
   if constexpr (UU) {
     // U_ij = Tria([A_j U_i Xi11^{-T}, U_j])

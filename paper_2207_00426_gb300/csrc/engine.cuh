@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "wscan.cuh"
+#include "refine_filter.cuh"
 
 namespace sqsm {
 
@@ -97,16 +98,89 @@ struct ProfScope {
 // per combine (latency-bound); larger ones one (throughput-bound).
 constexpr int64_t kCs3MaxChunks = 512;
 
+inline bool cs3_level(const LevelSet& L, int l, bool r3) {
+  return r3 && L.chunk_scan(l) && L.lv[l].n_chunks <= kCs3MaxChunks;
+}
+
+// Mean-only filter passes (FP32 refinement, refine_filter.cuh): for at most
+// this many sequences the three-role levels and the top are latency-bound,
+// and their combines are replayed from the table the full pass stores; for
+// states smaller than kFMeansMinNx the full combine is cheaper than reading
+// its factors back (measured on the population model, n_x = 1).
+constexpr int kFMeansMaxSeqs = 64;
+constexpr int kFMeansMinNx = 3;
+
+// Where each level's part of that table starts (elements; -1: the level
+// stores nothing) and its size, for elements of es bytes and state size nx:
+// per three-role chunk level 5 Kogge-Stone rounds, at the top as many as its
+// largest sequence needs; on = false (FP64, n_x < kFMeansMinNx, one leaf
+// chunk per sequence, more sequences than kFMeansMaxSeqs): no table, full
+// refinement passes.
+struct FMeansLayout {
+  std::vector<int64_t> rec, gm, fin;
+  int64_t size = 0;
+  bool on = false;
+};
+
+inline FMeansLayout fmeans_layout(const LevelSet& L, size_t es, int nx) {
+  FMeansLayout f;
+  const int Lc = (int)L.lv.size();
+  if (es != 4 || nx < kFMeansMinNx || Lc <= 1 || L.B > kFMeansMaxSeqs) return f;
+  const int rec = frec_size(nx), gm = fgm_size(nx);
+  const int Lk = L.ks_level(ks3_max_items(rec * (int)es));
+  f.rec.assign(Lc + 1, -1);
+  f.gm = f.rec;
+  f.fin = f.rec;
+  auto rounds = [](int64_t m) {
+    int r = 0;
+    while ((int64_t(1) << r) < m) ++r;
+    return r;
+  };
+  auto add = [&](int l, int nr, bool fin) {
+    const int64_t n = L.n_items[l];
+    f.rec[l] = f.size;
+    f.size += nr * n * rec;
+    f.gm[l] = f.size;
+    f.size += nr * n * gm;
+    if (fin) {
+      f.fin[l] = f.size;
+      f.size += n * rec;
+    }
+  };
+  for (int l = 1; l < Lk; ++l)
+    if (cs3_level(L, l, true)) add(l, rounds(kChunkScan), true);
+  add(Lk, rounds(L.max_seq_items[Lk]), false);
+  f.on = true;
+  return f;
+}
+
+// ftab (FP32, a table laid out by fmeans_layout): a full pass stores the
+// factors of its three-role levels' and top's combines there, a means_only
+// pass (the residual model of the pass that stored them) replays those
+// levels on b and eta alone.
 template <typename T, int NX, int NY, typename GV, typename FO>
 void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
                     const T* y, const T* m0, const T* N0, FO fo, double* partial,
-                    int* status, cudaStream_t s, Prof* P = nullptr) {
+                    int* status, cudaStream_t s, Prof* P = nullptr, T* ftab = nullptr,
+                    bool means_only = false) {
   const int Lc = (int)L.lv.size();
   // FP32 takes three threads per combine at the top of the tree; FP64 records
   // and factors do not fit three such threads' registers.
   constexpr bool R3 = sizeof(T) == 4;
   constexpr int KS = R3 ? Ks3Max<T, FRec<NX>::size>::value : KsMax<T, FRec<NX>::size>::value;
   const int Lk = L.ks_level(KS);
+  const FMeansLayout fm = ftab ? fmeans_layout(L, sizeof(T), NX) : FMeansLayout{};
+  const bool mo = means_only && fm.on;
+  auto tab = [&](int l) {
+    FMeansTab<T> tb{nullptr, nullptr, nullptr, 0};
+    if (fm.on && fm.rec[l] >= 0) {
+      tb.rec = ftab + fm.rec[l];
+      tb.gm = ftab + fm.gm[l];
+      tb.fin = fm.fin[l] >= 0 ? ftab + fm.fin[l] : nullptr;
+      tb.n = L.n_items[l];
+    }
+    return tb;
+  };
   if (Lc > 1) {  // with one leaf chunk per sequence every carry is the prior
     {
       ProfScope ps(P, K_FILTER_LEAF_UP, s);
@@ -115,10 +189,22 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
     }
     for (int l = 1; l < Lk; ++l) {
       ProfScope ps(P, K_FILTER_UP, s);
-      if (R3 && L.chunk_scan(l) && L.lv[l].n_chunks <= kCs3MaxChunks)
-        filter_up_cs3<T, NX><<<(unsigned)L.lv[l].n_chunks, 3 * kChunkScan, 0, s>>>(
-            L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
-      else if (L.chunk_scan(l))
+      if constexpr (R3) {
+        if (cs3_level(L, l, R3)) {
+          const unsigned g = (unsigned)L.lv[l].n_chunks;
+          if (mo)
+            filter_up_cs_be<T, NX><<<g, kChunkScan, 0, s>>>(L.lv[l], tab(l), (T*)W.items[l],
+                                                             (T*)W.items[l + 1]);
+          else if (tab(l).rec)
+            filter_up_cs3<T, NX, true><<<g, 3 * kChunkScan, 0, s>>>(
+                L.lv[l], (T*)W.items[l], (T*)W.items[l + 1], tab(l));
+          else
+            filter_up_cs3<T, NX, false><<<g, 3 * kChunkScan, 0, s>>>(
+                L.lv[l], (T*)W.items[l], (T*)W.items[l + 1], tab(l));
+          continue;
+        }
+      }
+      if (L.chunk_scan(l))
         filter_up_cs<T, NX><<<(unsigned)L.lv[l].n_chunks, kChunkScan, 0, s>>>(
             L.lv[l], (T*)W.items[l], (T*)W.items[l + 1]);
       else if (L.lv[l].n_chunks <= kWarpLevelMaxChunks)
@@ -129,10 +215,18 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
             L.lv[l], (const T*)W.items[l], (T*)W.items[l + 1]);
     }
     ProfScope ps(P, K_FILTER_UP, s);
-    if constexpr (R3)
-      filter_top_ks3<T, NX><<<L.B, 3 * KS, 0, s>>>(L.seq_item_off[Lk], (const T*)W.items[Lk],
-                                                  (T*)W.carry[Lk], W.flag[Lk]);
-    else
+    if constexpr (R3) {
+      if (mo)
+        filter_top_ks_be<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk], tab(Lk),
+                                                   (const T*)W.items[Lk], (T*)W.carry[Lk],
+                                                   W.flag[Lk]);
+      else if (tab(Lk).rec)
+        filter_top_ks3<T, NX, true><<<L.B, 3 * KS, 0, s>>>(
+            L.seq_item_off[Lk], (const T*)W.items[Lk], (T*)W.carry[Lk], W.flag[Lk], tab(Lk));
+      else
+        filter_top_ks3<T, NX, false><<<L.B, 3 * KS, 0, s>>>(
+            L.seq_item_off[Lk], (const T*)W.items[Lk], (T*)W.carry[Lk], W.flag[Lk], tab(Lk));
+    } else
       filter_top_ks<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk], (const T*)W.items[Lk],
                                               (T*)W.carry[Lk], W.flag[Lk]);
   } else {

@@ -89,9 +89,12 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
                     cudaMemcpyDeviceToDevice, s);
   };
   if (passes > 0) keep_prev();
+  // with refinement passes to follow, the first filter pass stores the
+  // factors of its latency-bound levels' combines (refine_filter.cuh)
+  T* ftab = passes > 0 ? (T*)a.ftab : nullptr;
   enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y,
                             (const T*)(a.centered ? a.dm0 : a.m0), (const T*)a.N0, fr, partial,
-                            status, s, a.prof);
+                            status, s, a.prof, ftab);
   // with refinement passes to follow, the first pass keeps each row's E_k
   T* etab = passes > 0 ? (T*)a.etab : nullptr;
   enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, a.centered != 0, dmax,
@@ -101,8 +104,9 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
   // result (offsets formed beyond FP32 precision) removes most of it; the
   // factors do not change, so the pass's smoother recomputes only the means
   // (refine_scan.cuh; the full scan where the level shape has no mean-only
-  // form).  The change measure and the log-likelihood stay those of the
-  // first pass.
+  // form), and so do its filter scan's latency-bound upper levels
+  // (refine_filter.cuh).  The change measure and the log-likelihood stay
+  // those of the first pass.
   for (int r = 0; r < passes; ++r) {
     {
       ProfScope ps(a.prof, K_INIT, s);
@@ -113,7 +117,7 @@ void ipls_phase_model(const IplsArgs& a, const LevelSet& Lf, const ScanBuffers& 
     }
     if (r + 1 < passes) keep_prev();
     enqueue_filter<T, NX, NY>(Lf, Wf, sq, gv, (const T*)a.y, (const T*)a.dm0, (const T*)a.N0, fr,
-                              a.partial2, status, s, a.prof);
+                              a.partial2, status, s, a.prof, ftab, true);
     if (!etab || !enqueue_smoother_means<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, etab, status, s,
                                                     a.prof))
       enqueue_smoother<T, NX, NY>(Ls, Ws, sq, gv, fr, nom, status, s, a.prof, true, nullptr);

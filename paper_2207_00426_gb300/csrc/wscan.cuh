@@ -435,26 +435,52 @@ inline unsigned cs_down_grid(int64_t chunks) {
   return (unsigned)((chunks * kChunkScan + kBlock - 1) / kBlock);
 }
 
+// Where a full filter pass stores, for one level, what the mean-only
+// refinement passes replay (refine_scan.cuh); rec null: nothing is stored.
+// For Kogge-Stone round r and item i of the level (n items): the record at
+// the round's start at rec[(r * n + i) * FRec] and the combine's G and
+// A_j (I - U_i G^T) at gm[(r * n + i) * FGm]; for chunk levels also the
+// records the scan leaves at fin[i * FRec] (fin null at the top).
+template <typename T> struct FMeansTab {
+  T* rec;
+  T* gm;
+  T* fin;
+  int64_t n;
+};
+
 // Filter scans with three threads per combine.  In the latency-bound top
 // levels (few chunks, one warp per SM or less) a combine's chain of dependent
 // instructions sets the time per Kogge-Stone round.  Thread (role r, item t)
 // computes only part r of S[t - d] (x) S[t] (r = 0: A, b, eta; 1: U; 2: Z;
 // each forms the factors it needs itself), which shortens that chain; role
 // r runs in warps of its own, so no warp diverges.
-template <typename T, int NX, int CAP>
-SQSM_DEV void filter_ks3(T* S, int c) {
+//
+// With STORE, the rounds also store what the mean-only refinement passes
+// replay (FMeansTab, here offset to the first item): the records at the
+// start of round r at trec[(r * n + t) * REC] and each combine's G and
+// A_j (I - U_i G^T) at tgm[(r * n + t) * FGm].
+template <typename T, int NX, int CAP, bool STORE = false>
+SQSM_DEV void filter_ks3(T* S, int c, T* trec = nullptr, T* tgm = nullptr, int64_t n = 0) {
   using R = FRec<NX>;
-  constexpr int REC = R::size;
+  constexpr int REC = R::size, W = REC * sizeof(T) / 16, GMS = FGm<NX>::size;
   static_assert(CAP % 32 == 0, "roles in whole warps");
   const int role = threadIdx.x / CAP, t = threadIdx.x - role * CAP;
-  for (int d = 1; d < c; d <<= 1) {
+  int r = 0;
+  for (int d = 1; d < c; d <<= 1, ++r) {
+    if constexpr (STORE) {   // S is read-only until the barrier below
+      const float4* S4 = reinterpret_cast<const float4*>(S);
+      float4* D4 = reinterpret_cast<float4*>(trec + r * n * REC);
+      for (int w = threadIdx.x; w < c * W; w += blockDim.x) D4[w] = S4[w];
+    }
     T part[REC];
     const bool act = t < c && t >= d;
     if (act) {
       const T* ei = S + (t - d) * REC;
       const T* ej = S + t * REC;
-      if (role == 0) filter_combine<T, NX, 1>(ei, ej, part);
-      else if (role == 1) filter_combine<T, NX, 2>(ei, ej, part);
+      if (role == 0) {
+        if constexpr (STORE) filter_combine<T, NX, 1>(ei, ej, part, tgm + (r * n + t) * GMS);
+        else filter_combine<T, NX, 1>(ei, ej, part);
+      } else if (role == 1) filter_combine<T, NX, 2>(ei, ej, part);
       else filter_combine<T, NX, 4>(ei, ej, part);
     }
     __syncthreads();
@@ -478,10 +504,11 @@ SQSM_DEV void filter_ks3(T* S, int c) {
 }
 
 // Chunk-scan up level (see filter_up_cs) with three threads per combine: one
-// block of 3 x 32 threads per chunk.
-template <typename T, int NX>
+// block of 3 x 32 threads per chunk.  STORE: also fill tb (a full pass
+// followed by mean-only ones).
+template <typename T, int NX, bool STORE>
 __global__ void __launch_bounds__(3 * kChunkScan)
-filter_up_cs3(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
+filter_up_cs3(DevLevel lv, T* __restrict__ items, T* __restrict__ out, FMeansTab<T> tb) {
   constexpr int REC = FRec<NX>::size, W = REC * sizeof(T) / 16;   // 16-byte words
   __shared__ __align__(16) T S[kChunkScan * REC];
   const int64_t c = blockIdx.x;
@@ -491,8 +518,16 @@ filter_up_cs3(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
   float4* I4 = reinterpret_cast<float4*>(items + i0 * REC);
   for (int w = threadIdx.x; w < cnt * W; w += blockDim.x) S4[w] = I4[w];
   __syncthreads();
-  filter_ks3<T, NX, kChunkScan>(S, cnt);
+  if constexpr (STORE)
+    filter_ks3<T, NX, kChunkScan, true>(S, cnt, tb.rec + i0 * REC, tb.gm + i0 * FGm<NX>::size,
+                                        tb.n);
+  else
+    filter_ks3<T, NX, kChunkScan>(S, cnt);
   for (int w = threadIdx.x; w < cnt * W; w += blockDim.x) I4[w] = S4[w];
+  if constexpr (STORE) {
+    float4* F4 = reinterpret_cast<float4*>(tb.fin + i0 * REC);
+    for (int w = threadIdx.x; w < cnt * W; w += blockDim.x) F4[w] = S4[w];
+  }
   float4* O4 = reinterpret_cast<float4*>(out + c * REC);
   for (int w = threadIdx.x; w < W; w += blockDim.x) O4[w] = S4[(cnt - 1) * W + w];
 }
@@ -500,15 +535,17 @@ filter_up_cs3(DevLevel lv, T* __restrict__ items, T* __restrict__ out) {
 // Top of the tree (see filter_top_ks) with three threads per combine, for
 // sequences of at most Ks3Max items at that level (64, fewer where the
 // records would not fit 48 KB of static shared memory).
+constexpr int ks3_max_items(int rec_bytes) {
+  return (48 * 1024) / rec_bytes / 32 * 32 < 64 ? (48 * 1024) / rec_bytes / 32 * 32 : 64;
+}
 template <typename T, int REC> struct Ks3Max {
-  static constexpr int fit = (int)((48 * 1024) / (REC * sizeof(T)) / 32 * 32);
-  static constexpr int value = 64 < fit ? 64 : fit;
+  static constexpr int value = ks3_max_items(REC * (int)sizeof(T));
 };
 
-template <typename T, int NX>
+template <typename T, int NX, bool STORE>
 __global__ void __launch_bounds__(3 * Ks3Max<T, FRec<NX>::size>::value)
 filter_top_ks3(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items,
-               T* __restrict__ carry_out, int* __restrict__ flag_out) {
+               T* __restrict__ carry_out, int* __restrict__ flag_out, FMeansTab<T> tb) {
   constexpr int REC = FRec<NX>::size, W = REC * sizeof(T) / 16;
   constexpr int KS = Ks3Max<T, REC>::value;
   __shared__ __align__(16) T S[KS * REC];
@@ -519,7 +556,10 @@ filter_top_ks3(const int64_t* __restrict__ seq_item_off, const T* __restrict__ i
   const float4* I4 = reinterpret_cast<const float4*>(items + i0 * REC);
   for (int w = threadIdx.x; w < c * W; w += blockDim.x) S4[w] = I4[w];
   __syncthreads();
-  filter_ks3<T, NX, KS>(S, c);
+  if constexpr (STORE)
+    filter_ks3<T, NX, KS, true>(S, c, tb.rec + i0 * REC, tb.gm + i0 * FGm<NX>::size, tb.n);
+  else
+    filter_ks3<T, NX, KS>(S, c);
   const int t = threadIdx.x;
   if (t < c) {
     if (t > 0) {

@@ -229,3 +229,38 @@ def test_refinement_passes_leave_fp64_unchanged(B, model):
         assert rel_mean_err(out[refine][0], out[0][0]) < 1e-10
         assert rel_cov_err(out[refine][1], out[0][1]) < 1e-10
         assert np.allclose(out[refine][2], out[0][2], rtol=1e-11, atol=0)
+
+
+def test_mean_only_filter_levels_equal_full_pass(B):
+    """FP32 refinement (CT model, n_x = 5): for a batch of at most 64
+    sequences the refinement pass's filter scan replays its latency-bound
+    upper levels (here a three-role chunk level and the top) on b and eta
+    alone, from the factors of each Table 3 combine the first pass stored;
+    for 65 it runs them in full.  A 64-sequence batch (two sequences long
+    enough for a three-role level below the top, the rest short and ragged)
+    and the same batch with a 65th one-step sequence appended give every
+    shared sequence the same scan bracketing, so their means, factors and
+    log-likelihoods agree bit for bit -- with one and with two refinement
+    passes."""
+    f32 = torch.float32
+    rng = np.random.default_rng(5)
+    lengths = [20000, 18000] + [int(v) for v in rng.integers(100, 900, size=62)]
+    d = W.ct_batch(lengths=lengths, seed=37)
+    call = lambda c, y, off, m0, N0: B.sqsm_ipls_smooth(c, d["theta"], y, off, m0, N0, 3, 0,
+                                                       dt=d["dt"])
+    off64 = [int(v) for v in d["offsets"]]
+    off65 = off64 + [off64[-1] + 1]
+    y64, m064, N064 = (np.asarray(d[k]) for k in ("y", "m0", "N0"))
+    y65 = np.concatenate([y64, y64[:1]])
+    m065, N065 = np.concatenate([m064, m064[:1]]), np.concatenate([N064, N064[:1]])
+    rows = off64[-1] + 64
+    for refine in (1, 2):
+        c = B.Context(0, refine=refine)
+        ms_a, Ns_a, ll_a = call(c, _dev(y64, f32), off64, _dev(m064, f32), _dev(N064, f32))
+        ms_b, Ns_b, ll_b = call(c, _dev(y65, f32), off65, _dev(m065, f32), _dev(N065, f32))
+        torch.cuda.synchronize()
+        assert c.status() == 0
+        assert torch.equal(ms_a, ms_b[:rows]) and torch.equal(Ns_a, Ns_b[:rows])
+        assert torch.equal(ll_a, ll_b[:64])
+        assert torch.isfinite(ms_a).all()
+        c.close()
