@@ -116,6 +116,13 @@ constexpr int kFMeansMinNx = 3;
 // largest sequence needs; on = false (FP64, n_x < kFMeansMinNx, one leaf
 // chunk per sequence, more sequences than kFMeansMaxSeqs): no table, full
 // refinement passes.
+// Kogge-Stone rounds over m items: d = 1, 2, 4, ... < m.
+inline int ks_rounds(int64_t m) {
+  int r = 0;
+  while ((int64_t(1) << r) < m) ++r;
+  return r;
+}
+
 struct FMeansLayout {
   std::vector<int64_t> rec, gm, fin;
   int64_t size = 0;
@@ -131,11 +138,6 @@ inline FMeansLayout fmeans_layout(const LevelSet& L, size_t es, int nx) {
   f.rec.assign(Lc + 1, -1);
   f.gm = f.rec;
   f.fin = f.rec;
-  auto rounds = [](int64_t m) {
-    int r = 0;
-    while ((int64_t(1) << r) < m) ++r;
-    return r;
-  };
   auto add = [&](int l, int nr, bool fin) {
     const int64_t n = L.n_items[l];
     f.rec[l] = f.size;
@@ -148,10 +150,19 @@ inline FMeansLayout fmeans_layout(const LevelSet& L, size_t es, int nx) {
     }
   };
   for (int l = 1; l < Lk; ++l)
-    if (cs3_level(L, l, true)) add(l, rounds(kChunkScan), true);
-  add(Lk, rounds(L.max_seq_items[Lk]), false);
+    if (cs3_level(L, l, true)) add(l, ks_rounds(kChunkScan), true);
+  add(Lk, ks_rounds(L.max_seq_items[Lk]), false);
   f.on = true;
   return f;
+}
+
+// Allow a kernel the dynamic shared memory of its next launch where that
+// exceeds the 48 KB default (a function attribute, not a stream operation,
+// so it may be set while the stream is being captured).
+template <typename K>
+void dyn_smem(K* kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ftab (FP32, a table laid out by fmeans_layout): a full pass stores the
@@ -192,9 +203,13 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
       if constexpr (R3) {
         if (cs3_level(L, l, R3)) {
           const unsigned g = (unsigned)L.lv[l].n_chunks;
-          if (mo)
-            filter_up_cs_be<T, NX><<<g, kChunkScan, 0, s>>>(L.lv[l], tab(l), (T*)W.items[l],
-                                                             (T*)W.items[l + 1]);
+          if (mo) {
+            const int nr = ks_rounds(kChunkScan);
+            const size_t sm = fmeans_smem_bytes<T, NX>(kChunkScan, nr, true);
+            dyn_smem(filter_up_cs_be<T, NX>, sm);
+            filter_up_cs_be<T, NX><<<g, kFMeansThreads, sm, s>>>(L.lv[l], tab(l), (T*)W.items[l],
+                                                                  (T*)W.items[l + 1], nr);
+          }
           else if (tab(l).rec)
             filter_up_cs3<T, NX, true><<<g, 3 * kChunkScan, 0, s>>>(
                 L.lv[l], (T*)W.items[l], (T*)W.items[l + 1], tab(l));
@@ -216,11 +231,14 @@ void enqueue_filter(const LevelSet& L, const ScanBuffers& W, DevSeqs sq, GV gv,
     }
     ProfScope ps(P, K_FILTER_UP, s);
     if constexpr (R3) {
-      if (mo)
-        filter_top_ks_be<T, NX><<<L.B, KS, 0, s>>>(L.seq_item_off[Lk], tab(Lk),
-                                                   (const T*)W.items[Lk], (T*)W.carry[Lk],
-                                                   W.flag[Lk]);
-      else if (tab(Lk).rec)
+      if (mo) {
+        const int cap = (int)L.max_seq_items[Lk], nr = ks_rounds(cap);
+        const size_t sm = fmeans_smem_bytes<T, NX>(cap, nr, false);
+        dyn_smem(filter_top_ks_be<T, NX>, sm);
+        filter_top_ks_be<T, NX><<<L.B, kFMeansThreads, sm, s>>>(
+            L.seq_item_off[Lk], tab(Lk), (const T*)W.items[Lk], (T*)W.carry[Lk], W.flag[Lk], cap,
+            nr);
+      } else if (tab(Lk).rec)
         filter_top_ks3<T, NX, true><<<L.B, 3 * KS, 0, s>>>(
             L.seq_item_off[Lk], (const T*)W.items[Lk], (T*)W.carry[Lk], W.flag[Lk], tab(Lk));
       else

@@ -21,56 +21,73 @@
 
 namespace sqsm {
 
-// Hint the cache lines of n elements at p into L1, the block's threads
-// taking one line each in turn (the whole table of a block's rounds fits
-// L1, so only the first round waits on memory).
-template <typename T>
-SQSM_DEV void prefetch_l1(const T* p, int64_t n) {
-  constexpr int64_t LINE = 128 / sizeof(T);
-  if (n <= 0) return;
-  for (int64_t k = threadIdx.x * LINE; k < n + LINE - 1; k += blockDim.x * LINE) {
-    const T* a = p + (k < n ? k : n - 1);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-  }
+// Threads of the mean-only launches: more than the at most 64 items of a
+// top block, so that the staging copies below issue from four warps.
+constexpr int kFMeansThreads = 128;
+
+// A level's table for one block in shared memory: per round r < nr the
+// records at the round's start ([r][cap] x FRec, cap items per round slab)
+// and the combines' gain blocks ([r][cap] x FGm), then (chunk levels) the
+// final records ([cap] x FRec).  Bytes of that layout:
+template <typename T, int NX>
+constexpr size_t fmeans_smem_bytes(int cap, int nr, bool fin) {
+  return sizeof(T) * ((size_t)nr * cap * (FRec<NX>::size + FGm<NX>::size) +
+                      (fin ? (size_t)cap * FRec<NX>::size : 0));
 }
 
-// The table of the rounds of c items starting at item i0 of a level (and,
-// for chunk levels, their final records) into L1.
+// n16 16-byte words from global src to shared dst, copied asynchronously by
+// the block's threads (cp.async; one hardware wait in stage_wait, no spin).
+SQSM_DEV void stage_async(void* dst, const void* src, int64_t n16) {
+  const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+  const char* g = static_cast<const char*>(src);
+  for (int64_t w = threadIdx.x; w < n16; w += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * (unsigned)w),
+                 "l"(g + 16 * w)
+                 : "memory");
+}
+
+SQSM_DEV void stage_wait() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+}
+
+// Stage the table of c items starting at item i0 of a level (tb, n items
+// per round) into the layout of fmeans_smem_bytes.
 template <typename T, int NX>
-SQSM_DEV void prefetch_rounds(const FMeansTab<T>& tb, int64_t i0, int c) {
+SQSM_DEV void stage_rounds(const FMeansTab<T>& tb, int64_t i0, int c, int cap, T* SR, T* SG,
+                           T* SF) {
   constexpr int REC = FRec<NX>::size, GMS = FGm<NX>::size;
+  constexpr int W = REC * sizeof(T) / 16, WG = GMS * sizeof(T) / 16;
   for (int r = 0; (1 << r) < c; ++r) {
-    prefetch_l1(tb.rec + (r * tb.n + i0) * REC, (int64_t)c * REC);
-    prefetch_l1(tb.gm + (r * tb.n + i0) * GMS, (int64_t)c * GMS);
+    stage_async(SR + (int64_t)r * cap * REC, tb.rec + (r * tb.n + i0) * REC, (int64_t)c * W);
+    stage_async(SG + (int64_t)r * cap * GMS, tb.gm + (r * tb.n + i0) * GMS, (int64_t)c * WG);
   }
-  if (tb.fin) prefetch_l1(tb.fin + i0 * REC, (int64_t)c * REC);
+  if (SF) stage_async(SF, tb.fin + i0 * REC, (int64_t)c * W);
 }
 
 // Kogge-Stone rounds over c items held as (b | eta) rows of SB, one thread
 // per item: in round r item t combines with item t - d using the factors
-// stored for that round (trec, tgm offset to the first item, n items per
-// round, as in filter_ks3).
+// the full pass stored for that round, staged in SR / SG (cap items per
+// round slab).
 template <typename T, int NX>
-SQSM_DEV void filter_ks_be(T* SB, int c, const T* __restrict__ trec, const T* __restrict__ tgm,
-                           int64_t n) {
+SQSM_DEV void filter_ks_be(T* SB, int c, const T* SR, const T* SG, int cap) {
   using R = FRec<NX>;
   using GM = FGm<NX>;
-  constexpr int REC = R::size, BE = 2 * NX, ZW = REC - R::Z;
-  static_assert(R::Z % 4 == 0 && ZW % 4 == 0, "Z starts a 16-byte word");
+  constexpr int REC = R::size, BE = 2 * NX;
   const int t = threadIdx.x;
   int r = 0;
   for (int d = 1; d < c; d <<= 1, ++r) {
     const bool act = t < c && t >= d;
     T nb[NX], ne[NX];
     if (act) {
-      T ri[REC], zj[ZW], gm[GM::size];
-      vload<T, REC>(trec + (r * n + t - d) * REC, ri);
-      vload<T, ZW>(trec + (r * n + t) * REC + R::Z, zj);
-      vload<T, GM::size>(tgm + (r * n + t) * GM::size, gm);
+      const T* ri = SR + (r * cap + t - d) * REC;
+      const T* rj = SR + (r * cap + t) * REC;
+      const T* gm = SG + (r * cap + t) * GM::size;
       const T* si = SB + (t - d) * BE;
       const T* sj = SB + t * BE;
-      filter_combine_means<T, NX>(ri + R::A, ri + R::U, zj, gm + GM::G, gm + GM::M, si, si + NX,
-                                  sj, sj + NX, nb, ne);
+      filter_combine_means<T, NX>(ri + R::A, ri + R::U, rj + R::Z, gm + GM::G, gm + GM::M, si,
+                                  si + NX, sj, sj + NX, nb, ne);
     }
     __syncthreads();
     if (act) {
@@ -95,24 +112,30 @@ SQSM_DEV void load_be(const T* __restrict__ rec, T* sb) {
   }
 }
 
-// Chunk-scan up level (see filter_up_cs3), mean-only: one warp per chunk.
+// Chunk-scan up level (see filter_up_cs3), mean-only: one block per chunk,
+// dynamic shared memory fmeans_smem_bytes(kChunkScan, nr, true).
 template <typename T, int NX>
-__global__ void __launch_bounds__(kChunkScan)
-filter_up_cs_be(DevLevel lv, FMeansTab<T> tb, T* __restrict__ items, T* __restrict__ out) {
+__global__ void __launch_bounds__(kFMeansThreads)
+filter_up_cs_be(DevLevel lv, FMeansTab<T> tb, T* __restrict__ items, T* __restrict__ out, int nr) {
   using R = FRec<NX>;
-  constexpr int REC = R::size, BE = 2 * NX;
-  __shared__ T SB[kChunkScan * BE];
+  constexpr int REC = R::size, BE = 2 * NX, CAP = kChunkScan;
+  extern __shared__ float4 fm_smem[];
+  T* SR = reinterpret_cast<T*>(fm_smem);
+  T* SG = SR + (int64_t)nr * CAP * REC;
+  T* SF = SG + (int64_t)nr * CAP * FGm<NX>::size;
+  __shared__ T SB[CAP * BE];
   const int64_t c = blockIdx.x;
   const int t = threadIdx.x;
   const int64_t i0 = lv.first[c];
   const int cnt = lv.count[c];
-  prefetch_rounds<T, NX>(tb, i0, cnt);
+  stage_rounds<T, NX>(tb, i0, cnt, CAP, SR, SG, SF);
   if (t < cnt) load_be<T, NX>(items + (i0 + t) * REC, SB + t * BE);
-  __syncthreads();
-  filter_ks_be<T, NX>(SB, cnt, tb.rec + i0 * REC, tb.gm + i0 * FGm<NX>::size, tb.n);
+  stage_wait();
+  filter_ks_be<T, NX>(SB, cnt, SR, SG, CAP);
   if (t < cnt) {
     T v[REC];
-    vload<T, REC>(tb.fin + (i0 + t) * REC, v);
+#pragma unroll
+    for (int i = 0; i < REC; ++i) v[i] = SF[t * REC + i];
 #pragma unroll
     for (int i = 0; i < NX; ++i) {
       v[R::b + i] = SB[t * BE + i];
@@ -124,23 +147,30 @@ filter_up_cs_be(DevLevel lv, FMeansTab<T> tb, T* __restrict__ items, T* __restri
 }
 
 // Top of the tree (see filter_top_ks3), mean-only: one block per sequence,
-// one thread per item; only the means of the carries are written.
+// one thread per item, dynamic shared memory fmeans_smem_bytes(cap, nr,
+// false) for at most cap items per sequence; only the means of the carries
+// are written.
 template <typename T, int NX>
-__global__ void __launch_bounds__(Ks3Max<T, FRec<NX>::size>::value)
+__global__ void __launch_bounds__(kFMeansThreads)
 filter_top_ks_be(const int64_t* __restrict__ seq_item_off, FMeansTab<T> tb,
-                 const T* __restrict__ items, T* __restrict__ carry_out, int* __restrict__ flag_out) {
+                 const T* __restrict__ items, T* __restrict__ carry_out, int* __restrict__ flag_out,
+                 int cap, int nr) {
   using R = FRec<NX>;
   constexpr int REC = R::size, BE = 2 * NX, XS = XRow<NX>::size;
   constexpr int KS = Ks3Max<T, REC>::value;
+  static_assert(KS <= kFMeansThreads, "one thread per item");
+  extern __shared__ float4 fm_smem[];
+  T* SR = reinterpret_cast<T*>(fm_smem);
+  T* SG = SR + (int64_t)nr * cap * REC;
   __shared__ T SB[KS * BE];
   const int b = blockIdx.x;
   const int64_t i0 = seq_item_off[b];
   const int c = (int)(seq_item_off[b + 1] - i0);
   const int t = threadIdx.x;
-  prefetch_rounds<T, NX>(tb, i0, c);
+  stage_rounds<T, NX>(tb, i0, c, cap, SR, SG, nullptr);
   if (t < c) load_be<T, NX>(items + (i0 + t) * REC, SB + t * BE);
-  __syncthreads();
-  filter_ks_be<T, NX>(SB, c, tb.rec + i0 * REC, tb.gm + i0 * FGm<NX>::size, tb.n);
+  stage_wait();
+  filter_ks_be<T, NX>(SB, c, SR, SG, cap);
   if (t < c) {
     if (t > 0) {
 #pragma unroll
