@@ -92,3 +92,27 @@ def test_invalid_tolerance_arguments(B):
                                    dt=d["dt"])
         assert e.value.code == B.ERR_INVALID_ARG
     c.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_refined_tolerance_mode_equals_fixed_m(B, use_graph):
+    """FP32 with one refinement pass per iteration (whose filter scan
+    replays its top levels mean-only, from shared-memory staged factors; in
+    the graph form inside the conditional WHILE node): the tolerance run
+    stops where the fixed-M smoother with the same M gives the same means,
+    factors and log-likelihood bit for bit.  The 6000-step sequence has a
+    three-role chunk level and a top of 63 items (the largest staging)."""
+    d = W.ct_batch(lengths=[6000, 300, 45], seed=12)
+    f32 = torch.float32
+    y, m0, N0 = _inputs(d, f32)
+    c = B.Context(0, use_graph=use_graph, refine=1)
+    ms, Ns, ll, it = B.sqsm_ipls_smooth_tol(c, d["theta"], y, d["offsets"], m0, N0, 30, 1e-3,
+                                            dt=d["dt"])
+    torch.cuda.synchronize()
+    M = it.item()
+    assert 1 < M <= 30 and c.status() == 0
+    msM, NsM, llM = B.sqsm_ipls_smooth(c, d["theta"], y, d["offsets"], m0, N0, M, 0, dt=d["dt"])
+    torch.cuda.synchronize()
+    assert torch.equal(ms, msM) and torch.equal(Ns, NsM) and torch.equal(ll, llM)
+    assert torch.isfinite(ms).all()
+    c.close()
