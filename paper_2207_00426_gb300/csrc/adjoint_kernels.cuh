@@ -526,7 +526,7 @@ adj_top_ks(const int64_t* __restrict__ seq_item_off, const T* __restrict__ items
 template <typename T, int LIN = 0>
 SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>* __restrict__ Pp,
                           const AdjBufs& a, T* o, T* d, double* th) {
-  constexpr int NX = 5, NY = 2, X = XRec<NX>::size;
+  constexpr int NX = 5, NY = 2;
   using GR = GRec<NX, NY>;
   using ST = SlrTab<NX, NY>;
   const CTParams<T> P = *Pp;
@@ -584,8 +584,8 @@ SQSM_DEV void adj_slr_row(int64_t e, int b, const DevSeqs& sq, const CTParams<T>
     if constexpr (LIN == 0) {
       T t[ST::size - ST::obs];
       vload<T, ST::size - ST::obs>((const T*)a.stab + s * ST::size + ST::obs, t);
-      cubature_vjp<T, NY>(m, N, t + ST::Gh - ST::obs, t + ST::sh - ST::obs, gb + GR::H, gb + GR::d,
-                          Lb, jh, mb, Nb);
+      cubature_vjp<T, NY>(m, N, t + (ST::Gh - ST::obs), t + (ST::sh - ST::obs), gb + GR::H,
+                          gb + GR::d, Lb, jh, mb, Nb);
     } else if constexpr (LIN == 1) {
       taylor_vjp<T, NY>(m, gb + GR::H, gb + GR::d,
                         [&](const T* xx, const T* Jb, T* o) { ct_jac_h_vjp(P, xx, Jb, o); }, mb);

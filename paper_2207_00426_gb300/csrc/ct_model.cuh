@@ -590,7 +590,6 @@ ct_slr_kernel_lin(DevLevel lv, int leaf, DevSeqs sq, const CTParams<T>* __restri
   constexpr int NX = 5, NY = 2;
   const CTParams<T> P = *Pp;
   const int b = lv.seq[ch];
-  constexpr int linearization = LIN;
   {
     const int64_t s = lv.first[ch] + j;
     const int64_t rp = s + b, rk = s + b + 1;
