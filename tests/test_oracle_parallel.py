@@ -157,3 +157,53 @@ def test_smoother_operator_associative():
     np.testing.assert_allclose(l[0], r[0], atol=1e-12)
     np.testing.assert_allclose(l[1], r[1], atol=1e-12)
     np.testing.assert_allclose(l[2] @ l[2].T, r[2] @ r[2].T, atol=1e-12)
+
+
+def test_offsets_change_only_the_mean_parts():
+    """The principle the refinement passes' mean-only scans rest on: with F,
+    S_Q, H, S_R and N_0 fixed, the offsets c, d, the data y and the prior
+    mean enter the filtering elements (Lemma 1, Tables 1-2) and the
+    smoothing elements (Lemma 3, Table 4) only through b, eta resp. g, so a
+    second pass on another set of offsets has the same A, U, Z, E, D in
+    every element and every combine of every scan order (here exactly:
+    the same arithmetic on the same factors), and Table 3's b_ij, eta_ij
+    are affine in the operands' (b, eta) with coefficients fixed by the
+    factors."""
+    m = _model(12, 5, 2, seed=21)
+    rng = np.random.default_rng(22)
+    m2 = dict(m)
+    m2["c"] = m["c"] + rng.standard_normal(m["c"].shape)
+    m2["d"] = m["d"] + rng.standard_normal(m["d"].shape)
+    m2["y"] = m["y"] + rng.standard_normal(m["y"].shape)
+    m2["m0"] = m["m0"] + rng.standard_normal(m["m0"].shape)
+    e1, _ = _elements(m)
+    e2, _ = _elements(m2)
+    for a, b in zip(e1, e2):
+        for k in (0, 2, 4):                      # A, U, Z
+            assert np.array_equal(a[k], b[k])
+        assert not np.allclose(a[1], b[1])       # b moves
+    for scan in (P.scan_sequential, P.scan_tree):
+        p1, p2 = scan(P.sqrt_filter_combine, e1), scan(P.sqrt_filter_combine, e2)
+        for a, b in zip(p1, p2):
+            for k in (0, 2, 4):
+                assert np.array_equal(a[k], b[k])
+    # b_ij, eta_ij affine in the operands' (b, eta): second differences vanish
+    ei, ej = e1[3], e1[4]
+    def mean_part(db_i, de_i, db_j, de_j):
+        out = P.sqrt_filter_combine((ei[0], ei[1] + db_i, ei[2], ei[3] + de_i, ei[4]),
+                                    (ej[0], ej[1] + db_j, ej[2], ej[3] + de_j, ej[4]))
+        return np.concatenate([out[1], out[3]])
+    u = [rng.standard_normal(5) for _ in range(4)]
+    v = [rng.standard_normal(5) for _ in range(4)]
+    f0 = mean_part(*[np.zeros(5)] * 4)
+    fu, fv = mean_part(*u), mean_part(*v)
+    fuv = mean_part(*[a + b for a, b in zip(u, v)])
+    np.testing.assert_allclose(fuv - f0, (fu - f0) + (fv - f0), atol=1e-10)
+    f2u = mean_part(*[2 * a for a in u])
+    np.testing.assert_allclose(f2u - f0, 2 * (fu - f0), atol=1e-10)
+    # smoothing elements: E, D fixed by F, S_Q and the filter factor
+    Nf = np.tril(rng.standard_normal((5, 5))) + 3 * np.eye(5)
+    s1 = P.sqrt_smoother_element(m["F"][2], m["c"][2], m["SQ"][2], rng.standard_normal(5), Nf)
+    s2 = P.sqrt_smoother_element(m["F"][2], m2["c"][2], m["SQ"][2], rng.standard_normal(5), Nf)
+    assert np.array_equal(s1[0], s2[0]) and np.array_equal(s1[2], s2[2])
+    assert not np.allclose(s1[1], s2[1])
